@@ -1,0 +1,101 @@
+"""Pins of the oracle against closed-form flows: shear-wave viscosity
+(Sec. III.A), Poiseuille flow with the no-slip rule (Sec. III.B) and the
+square duct (Sec. III.C).
+
+Paper: Fei, Luo & Li, arXiv:1801.04586.
+"""
+import numpy as np
+import pytest
+
+import analytic as an
+import oracle as o
+
+
+def _shear_wave_nu(L, nu, s2b=None, t1=200, t2=2200):
+    s2 = an.s2_from_nu(nu)
+    lat = o.Lattice(1, L, 1, s2=s2, s2b=s2b if s2b is not None else 1.0)
+    y = np.arange(L)
+    u = np.zeros((3, 1, L, 1))
+    u[0, 0, :, 0] = 1e-4 * np.sin(2 * np.pi * y / L)
+    f = o.step(lat, o.init(lat, None, u), None, t1)
+    a1 = an.shear_wave_amplitude(o.macros(lat, f)[1][0, 0, :, 0])
+    f = o.step(lat, f, None, t2 - t1)
+    a2 = an.shear_wave_amplitude(o.macros(lat, f)[1][0, 0, :, 0])
+    return np.log(a1 / a2) / ((2 * np.pi / L) ** 2 * (t2 - t1))
+
+
+@pytest.mark.parametrize("nu,s2b", [(0.05, None), (0.1, 0.5)])
+def test_shear_wave_viscosity(nu, s2b):
+    """Decay of a shear wave measures nu = (1/s2 - 1/2) cs^2 (Sec. II.B) within
+    0.1% on L = 101 (the paper reports 0.08% on 5 x 101 x 5); the bulk rate s2b
+    does not enter a shear wave."""
+    assert _shear_wave_nu(101, nu, s2b) == pytest.approx(nu, rel=1e-3)
+
+
+def _poiseuille(n, nu, steps, s3=None, s2b=None, F=1e-6):
+    s2 = an.s2_from_nu(nu)
+    lat = o.Lattice(1, 1, n, walls=4, s2=s2, s2b=s2b if s2b is not None else 1.0,
+                    s3=s3 if s3 is not None else 1.0)
+    Ff = np.zeros((3, n, 1, 1))
+    Ff[0] = F
+    f = o.step(lat, o.init(lat, None, None, Ff), Ff, steps)
+    return o.macros(lat, f, Ff)[1][0, :, 0, 0]
+
+
+def _e2(u, ua):
+    """Global relative error of Sec. III.B."""
+    return float(np.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum()))
+
+
+@pytest.mark.parametrize("nu", [0.1, 0.2])
+def test_poiseuille_noslip_rule_is_exact(nu):
+    """Sec. III.B: with s3 = (16 - 8 s2)/(8 - s2) and s2b = s2 the steady
+    Poiseuille profile of the consistent forcing scheme carries no numerical slip
+    (E2 'negligible'); with s3 = 1 it does."""
+    n, F = 20, 1e-6
+    s2 = an.s2_from_nu(nu)
+    ua = an.poiseuille_steady(n, F, nu)
+    steps = int(30 * 4 * (n / 2) ** 2 / (np.pi ** 2 * nu))
+    exact = _poiseuille(n, nu, steps, s3=an.noslip_s3(s2), s2b=s2, F=F)
+    assert _e2(exact, ua) < 1e-8
+    slip = _poiseuille(n, nu, steps, s3=1.0, s2b=s2, F=F)
+    assert _e2(slip, ua) > 1e-5
+
+
+def test_poiseuille_startup_series():
+    """Force-driven start-up from rest in a 32-node channel at nu = 0.1,
+    F = 1e-6 (the shape of the 16 x 32 x 32 channel along z), 2000 steps,
+    against the eigen-expansion of the Sec. III.B parabola."""
+    n, nu, F, t = 32, 0.1, 1e-6, 2000
+    ua = an.poiseuille_startup(n, F, nu, t)
+    assert _e2(_poiseuille(n, nu, t, F=F), ua) < 5e-4
+    s2 = an.s2_from_nu(nu)
+    assert _e2(_poiseuille(n, nu, t, s3=an.noslip_s3(s2), s2b=s2, F=F), ua) < 1e-4
+
+
+def test_square_duct_series():
+    """Sec. III.C duct at nu = 0.2, Fx = 2e-4 on a 16 x 16 cross-section: the
+    steady series is met within 0.15% with the no-slip s3 (16/13 at nu = 0.2),
+    and less well with s3 = 1 (the rule is only approximate in 2D)."""
+    n, nu, F = 16, 0.2, 2e-4
+    s2 = an.s2_from_nu(nu)
+    ua = an.duct_steady(n, F, nu)
+    errs = []
+    for s3 in (an.noslip_s3(s2), 1.0):
+        lat = o.Lattice(1, n, n, walls=6, s2=s2, s2b=s2, s3=s3)
+        Ff = np.zeros((3, n, n, 1))
+        Ff[0] = F
+        f = o.step(lat, o.init(lat, None, None, Ff), Ff, 5500)
+        errs.append(_e2(o.macros(lat, f, Ff)[1][0, :, :, 0], ua))
+    assert errs[0] < 1.5e-3
+    assert errs[1] > 2 * errs[0]
+
+
+def test_noslip_rule_constants():
+    """The two cases of Sec. III.B: nu = 0.1 gives s2 = 5/4 and s3 = 8/9;
+    nu = 0.2 gives s2 = 10/11 (printed as 20/11) and s3 = 16/13 = 1.23077
+    (printed as 1.33077 in Sec. III.C)."""
+    assert an.s2_from_nu(0.1) == pytest.approx(5 / 4)
+    assert an.noslip_s3(5 / 4) == pytest.approx(8 / 9)
+    assert an.s2_from_nu(0.2) == pytest.approx(10 / 11)
+    assert an.noslip_s3(10 / 11) == pytest.approx(16 / 13)
