@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the D3Q19 cascaded-LBM step on GB300.
+
+Workload: the periodic 256^3 Kolmogorov box (F_x = 1e-5 sin(2 pi z / 256),
+nu = 0.01, rho = 1, seeded divergence-free u0 with max |u| = 0.02 on
+wavenumbers 1..4), FP32 populations, A/B pull scheme. One bench step is one
+lattice time step: one launch of the fused stream-and-collide kernel over all
+16,777,216 nodes. The two population buffers (1.27 GB each) are ten times the
+129 MB L2, so every step streams from HBM.
+
+Prints one JSON line (rank 0). Under torchrun (N > 1) every rank runs its own
+independent 256^3 box (weak scaling, no collective on the data path); the
+timed region is bracketed by barriers and the slowest rank's time is used.
+
+--impl reference times the FP64 CPU oracle, as it stands, on the host cores on
+a bounded slab of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 CLBM MLUPS at 256³ and % HBM roofline; adjoint/forward time ratio"
+N_SIDE = 256
+NU = 0.01
+F0 = 1e-5
+UMAX = 0.02
+BYTES_PER_NODE = 152  # 19 x 4 B read + 19 x 4 B written (FP32 A/B)
+WORKLOAD = "periodic 256^3 Kolmogorov box, F_x = 1e-5 sin(2 pi z/256), nu = 0.01, FP32 populations"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--block", default="0,0", help="step kernel block shape bx,by (0,0 = default)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    for rel in ("paper_1801_04586_gb300/csrc/step.cu", "paper_1801_04586_gb300/csrc/d3q19.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if the kernel sources still match the digest recorded there."""
+    path = os.path.join(ROOT, "profiles", "k_step_f32_kolmogorov256.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    d = re.search(r"source_digest:\s*([0-9a-f]+)", text)
+    if not m or not d or d.group(1) != kernel_source_digest():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the run."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[4:]))
+            except Exception:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        inside = [r for r in rows if t0 - 1.0 <= r[0] <= t1 + 1.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in inside for k, v in enumerate(r[3][1:5]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(seconds: float = 10.0, max_steps: int = 20):
+    """FP64 oracle on a 256 x 256 x 16 periodic slab of the workload with all
+    host cores: MLUPS over whole steps until `seconds` have elapsed."""
+    import numpy as np
+
+    import oracle
+    from paper_1801_04586_gb300 import synthetic
+
+    nz = 16
+    shape = (nz, N_SIDE, N_SIDE)
+    lat = oracle.Lattice.from_nu(N_SIDE, N_SIDE, nz, NU)
+    F = synthetic.profile_to_field(synthetic.kolmogorov_profile(N_SIDE, F0)[:, :nz], shape)
+    u0 = synthetic.divfree_velocity((N_SIDE, N_SIDE, N_SIDE), seed=1, umax=UMAX)[:, :nz]
+    f = oracle.init(lat, None, np.ascontiguousarray(u0), F)
+    f = oracle.step(lat, f, F, 1)  # warm
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        f = oracle.step(lat, f, F, 1)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": lat.n * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} steps of a 256x256x16 periodic slab of the workload ({lat.n} nodes), "
+                      f"FP64, OpenMP over rows, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1801_04586_gb300 import synthetic
+
+    oracle.build()
+    nz = 4
+    shape = (nz, N_SIDE, N_SIDE)
+    lat = oracle.Lattice.from_nu(N_SIDE, N_SIDE, nz, NU)
+    F = synthetic.profile_to_field(synthetic.kolmogorov_profile(N_SIDE, F0)[:, :nz], shape)
+    u0 = synthetic.divfree_velocity((N_SIDE, N_SIDE, N_SIDE), seed=1, umax=UMAX)[:, :nz]
+    f = oracle.init(lat, None, np.ascontiguousarray(u0), F)
+    for _ in range(args.warmup):
+        f = oracle.step(lat, f, F, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.step(lat, f, F, 1)
+    dt = time.perf_counter() - t0
+    value = lat.n * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": "256x256x4 periodic slab per step"},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} steps of a 256x256x4 periodic slab ({lat.n} nodes)"},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    from paper_1801_04586_gb300 import Lattice, synthetic
+    from paper_1801_04586_gb300.builder import build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build()
+    if dist is not None:
+        dist.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    bx, by = (int(v) for v in args.block.split(","))
+    shape = (N_SIDE, N_SIDE, N_SIDE)
+    lat = Lattice(N_SIDE, N_SIDE, N_SIDE, NU, walls=0, storage="f32", block=(bx, by), device=dev)
+    prof = torch.from_numpy(synthetic.kolmogorov_profile(N_SIDE, F0)).to(dev)
+    u0_np = synthetic.divfree_velocity(shape, seed=1, umax=UMAX)
+    u0 = torch.from_numpy(u0_np).to(dev)
+    lat.set_force_profile_z(prof)
+    lat.init_equilibrium(None, u0)
+    stream = lat.stream
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+
+    # warm-up
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    lat.check()
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_host0 = time.time()
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            starts[k].record(stream)
+            lat.step(1)
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t_host1 = time.time()
+    elapsed_ms = starts[0].elapsed_time(ends[-1])
+    per_launch = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    lat.check()
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    clocks = sampler.stop(t_host0, t_host1) if sampler else None
+
+    nodes = lat.n
+    value = ws * nodes * K / (elapsed_ms * 1e-3) / 1e6
+    mean_launch_s = statistics.mean(per_launch) * 1e-3
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_NODE * nodes / mean_launch_s / 1e9
+    traffic = profiled_traffic()
+
+    e2e = None
+    if not args.no_e2e:
+        lat_e = Lattice(N_SIDE, N_SIDE, N_SIDE, NU, walls=0, storage="f32", block=(bx, by), device=dev)
+        lat_e.set_force_profile_z(prof)
+        rho_h = torch.ones(shape, dtype=torch.float32).pin_memory()
+        u_h = torch.from_numpy(u0_np).pin_memory()
+        rho_o = torch.empty(shape, dtype=torch.float32).pin_memory()
+        u_o = torch.empty((3,) + shape, dtype=torch.float32).pin_memory()
+        mom = torch.empty(4 * K, dtype=torch.float64).pin_memory()
+        lat_e.run_host(rho_h, u_h, max(1, min(args.warmup, 3)), rho_o, u_o, mom[: 4 * max(1, min(args.warmup, 3))])
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat_e.run_host(rho_h, u_h, K, rho_o, u_o, mom)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = (rho_h.numel() + u_h.numel()) * 4
+        d2h = (rho_o.numel() + u_o.numel()) * 4 + mom.numel() * 8
+        e2e = {"value": ws * nodes * K / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / K,
+               "d2h_bytes_per_step": d2h / K,
+               "what": "clbm_run_host: pinned host rho,u -> init -> K steps, FP64 mass/momentum read back "
+                       "after every step, final rho,u read back"}
+        lat_e.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_oracle_rate()
+        except Exception as exc:  # reported, never fatal for the GPU number
+            cpu = {"error": str(exc)[:200]}
+
+    if rank == 0:
+        info = lat.info()
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": N_SIDE, "ny": N_SIDE, "nz": N_SIDE, "nu": NU, "F0": F0,
+                       "storage": "f32 A/B pull", "block": [info["block_x"], info["block_y"]],
+                       "l2": "inputs larger than L2: two 1.27 GB population buffers vs 129 MB L2, no flush",
+                       "parallelism": f"{ws} independent replica(s), one per GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": BYTES_PER_NODE * nodes, "kernel": "k_step<float,1,false>"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": K,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

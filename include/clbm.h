@@ -1,0 +1,192 @@
+/*
+ * clbm.h -- C ABI of the GB300 (sm_103a) D3Q19 cascaded lattice Boltzmann
+ * library: the fused stream-and-collide step of Fei, Luo & Li,
+ * "Three-dimensional cascaded lattice Boltzmann method: improved
+ * implementation and consistent forcing scheme" (arXiv:1801.04586),
+ * Appendix A (D3Q19) with the collision of Sec. II.A-B.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: CLBM_OK (0) or a negative CLBM_ERR_* code. No C++ exception
+ *   crosses this boundary. clbm_last_error() gives a message for the calling
+ *   thread's most recent failure.
+ * - Lattice: nx x ny x nz nodes, node index s = (z*ny + y)*nx + x (x fastest),
+ *   N = nx*ny*nz. Node spacing and time step are 1 (lattice units, c_s^2 = 1/3).
+ * - Population arrays exchanged with the caller are float32, structure of
+ *   arrays, f[i*N + s] for the 19 velocities in the order of Eq. A1. Vector
+ *   fields are 3 x N (component-major: F[a*N + s]); scalar fields are N.
+ * - Every pointer marked _dev is a CUDA device pointer owned by the caller; it
+ *   must stay valid until the work that uses it has finished on the context's
+ *   stream. Pointers marked _host are ordinary host memory.
+ * - All GPU work is enqueued on the stream given to clbm_create; entry points
+ *   return without synchronising unless they say otherwise.
+ * - "State at step n" is the post-streaming distribution f(x, n) of Eq. 8;
+ *   rho and u are always Eq. 9 on that state (with the +F/2 term).
+ * - The library stores populations internally as deviations h = f - w_i from
+ *   the rest weights w = {1/3, 1/18, 1/36} in the chosen storage format; this
+ *   changes rounding only, not the method.
+ */
+#ifndef CLBM_H
+#define CLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define CLBM_OK            0
+#define CLBM_ERR_ARG      -1  /* invalid argument (null pointer, bad size, bad rate) */
+#define CLBM_ERR_OOM      -2  /* device allocation failed */
+#define CLBM_ERR_CUDA     -3  /* a CUDA runtime call or kernel launch failed */
+#define CLBM_ERR_UNSTABLE -4  /* a node's density left (0.1, 1.9) or became non-finite */
+#define CLBM_ERR_STATE    -5  /* call not valid in the context's current state */
+
+/* ---- storage formats of the populations (deviations f - w_i) ---- */
+#define CLBM_STORAGE_F32   0
+#define CLBM_STORAGE_F16   1  /* IEEE binary16, round to nearest even */
+#define CLBM_STORAGE_BF16  2  /* bfloat16, round to nearest even */
+
+/* ---- wall axes: both faces of the axis are halfway bounce-back walls ---- */
+#define CLBM_WALL_X 1u
+#define CLBM_WALL_Y 2u
+#define CLBM_WALL_Z 4u
+
+/* Lattice and relaxation parameters.
+ * nu:  kinematic viscosity, s2 = 1/(3 nu + 1/2) (Sec. II.B after Eq. 13); it
+ *      relaxes k~110, k~101, k~011 and the normal-stress differences.
+ * s2b: rate of the trace k~200 + k~020 + k~002 (bulk viscosity
+ *      xi = 2/3 (1/s2b - 1/2) c_s^2); s3: third-order moments (Eq. A3);
+ *      s4: fourth-order moments. Each must lie in (0, 2).
+ * s0 = s1 = 1 (Sec. III); the method's result does not depend on them.
+ * walls: CLBM_WALL_* bits; an axis without a bit is periodic.
+ * block_x, block_y: CUDA block shape of the step kernel (block_x a multiple
+ *      of 32, block_x*block_y <= 1024); 0 selects the built-in default. */
+typedef struct clbm_params {
+    int32_t nx, ny, nz;
+    uint32_t walls;
+    double nu;
+    double s2b, s3, s4;
+    int32_t storage;
+    int32_t block_x, block_y;
+    int32_t reserved;
+} clbm_params;
+
+typedef struct clbm_info {
+    int64_t n_nodes;          /* N */
+    int64_t pop_stride;       /* elements between consecutive population arrays */
+    int64_t state_bytes;      /* bytes of one population buffer (19 * pop_stride * elem) */
+    int64_t steps_done;       /* time steps since init */
+    int32_t storage;
+    int32_t block_x, block_y; /* block shape in use */
+    double s2;                /* 1/(3 nu + 1/2) */
+} clbm_info;
+
+typedef struct clbm_ctx clbm_ctx;
+
+/* Create a lattice context: validates p, allocates two population buffers
+ * (A/B) of 19 * N elements each on the current CUDA device, and binds the
+ * context to `stream` (a cudaStream_t; NULL = legacy default stream).
+ * The populations are zero deviations (f = w, rest at rho = 1) until an init
+ * call. *out receives the context (owned by the caller; free with
+ * clbm_destroy). Errors: CLBM_ERR_ARG, CLBM_ERR_OOM, CLBM_ERR_CUDA. */
+int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out);
+
+/* Release all device memory of the context (synchronises its stream). NULL is
+ * accepted. */
+int clbm_destroy(clbm_ctx *ctx);
+
+/* Fill *info. */
+int clbm_get_info(const clbm_ctx *ctx, clbm_info *info);
+
+/* Body force (Sec. II.A, Eqs. 5-6 and 9; a force density). Exactly one force
+ * source is active; the latest call wins. Uniform: F is the same at every node
+ * (F = 0 after create). Profile along z: F_dev holds 3 x nz floats,
+ * F_a(z) at F_dev[a*nz + z]. Field: F_dev holds 3 x N floats. Profile and
+ * field pointers are borrowed, not copied: they must stay valid and unchanged
+ * while steps run. */
+int clbm_set_force_uniform(clbm_ctx *ctx, double fx, double fy, double fz);
+int clbm_set_force_profile_z(clbm_ctx *ctx, const float *F_dev);
+int clbm_set_force_field(clbm_ctx *ctx, const float *F_dev);
+
+/* Initial state: at every node the generalized local equilibrium (Sec. II.B
+ * after Eq. 15, central moments of Eq. A5) at density rho and velocity
+ * u' = u - F/(2 rho), so that Eq. 9 returns exactly the given rho and u.
+ * rho_dev (N floats) may be NULL for rho = 1; u_dev (3 x N) may be NULL for
+ * u = 0. Uses the force set at the time of the call. Resets steps_done. */
+int clbm_init_equilibrium(clbm_ctx *ctx, const float *rho_dev, const float *u_dev);
+
+/* Advance nsteps >= 0 time steps. Each step is one launch of the fused pull
+ * kernel: for every node it gathers the post-collision populations of the
+ * neighbours (Eq. 8, periodic wrap, or halfway bounce-back f_i <- f*_ibar at
+ * a wall face), forms rho and u (Eq. 9), raw moments T = M f (Eq. A4),
+ * central moments N(u) T (Eq. 4), relaxes them with S, T~eq and C
+ * (Eqs. 5, A3, A5, A6), maps back with N(u)^-1 = N(-u) and M^-1 (Eq. 7) and
+ * stores f*. Asynchronous. */
+int clbm_step(clbm_ctx *ctx, int64_t nsteps);
+
+/* Eq. 9 on the current state: rho_dev (N floats) and u_dev (3 x N floats);
+ * either may be NULL. */
+int clbm_get_macros(clbm_ctx *ctx, float *rho_dev, float *u_dev);
+
+/* Copy the current post-streaming populations out (19 x N floats). With
+ * deviation != 0 the values are f - w_i, else f. */
+int clbm_get_populations(clbm_ctx *ctx, float *f_dev, int deviation);
+
+/* Replace the current state by the given post-streaming populations
+ * (19 x N floats, f - w_i if deviation != 0, else f). Values are rounded to
+ * the storage format. Resets steps_done. */
+int clbm_set_populations(clbm_ctx *ctx, const float *f_dev, int deviation);
+
+/* FP64 conservation sums over the current state (Eq. 9): out_dev[0] = sum rho,
+ * out_dev[1..3] = sum rho*u (including the F/2 term). out_dev: 4 doubles on
+ * the device. Deterministic (fixed reduction order). */
+int clbm_reduce_moments(clbm_ctx *ctx, double *out_dev);
+
+/* FP64 reductions of two float arrays of n elements, for error norms and
+ * finite-difference dot products: out_dev[0] = sum (a-b)^2, out_dev[1] =
+ * sum b^2, out_dev[2] = sum a*b. b_dev may be NULL (treated as zeros).
+ * Deterministic. Runs on the context's stream. */
+int clbm_reduce_pair(clbm_ctx *ctx, const float *a_dev, const float *b_dev, int64_t n, double *out_dev);
+
+/* Read the instability flag (synchronises the stream): CLBM_OK, or
+ * CLBM_ERR_UNSTABLE if any step since the last clear saw a density outside
+ * (0.1, 1.9) or a non-finite one. clear != 0 resets the flag. */
+int clbm_check(clbm_ctx *ctx, int clear);
+
+/* Raw state: the internal population buffer (clbm_info.state_bytes bytes).
+ * Device-to-device copies on the context's stream, for checkpoints. Importing
+ * does not change steps_done unless set_steps >= 0, which sets it. */
+int clbm_export_state(clbm_ctx *ctx, void *dst_dev);
+int clbm_import_state(clbm_ctx *ctx, const void *src_dev, int64_t set_steps);
+
+/* Checkpoint to / restore from host memory: a small header (geometry,
+ * storage, steps_done) plus the raw buffer. clbm_save_state with
+ * host_buf == NULL writes the required size to *bytes. Both synchronise. A
+ * restored context continues bit-identically. */
+int clbm_save_state(clbm_ctx *ctx, void *host_buf, size_t *bytes);
+int clbm_load_state(clbm_ctx *ctx, const void *host_buf, size_t bytes);
+
+/* One user job with host buffers: copy rho_host (N floats, may be NULL) and
+ * u_host (3 x N, may be NULL) to the device, initialise as
+ * clbm_init_equilibrium, run nsteps steps, then copy Eq. 9 rho and u of the
+ * final state back to rho_out_host / u_out_host (either may be NULL). If
+ * moments_host is not NULL, after every step the FP64 sums of
+ * clbm_reduce_moments are copied back into moments_host[4*k .. 4*k+3]
+ * (4 * nsteps doubles), which also checks the instability flag. Host buffers
+ * should be pinned for full copy speed. Synchronous. */
+int clbm_run_host(clbm_ctx *ctx, const float *rho_host, const float *u_host, int64_t nsteps,
+                  float *rho_out_host, float *u_out_host, double *moments_host);
+
+/* Text for a status code; clbm_last_error(): message of this thread's last
+ * failure ("" if none). Both strings are owned by the library. */
+const char *clbm_status_string(int status);
+const char *clbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLBM_H */

@@ -305,9 +305,9 @@ int ora_step(const ora_lattice *L, const double *F, double *f, int nsteps, int n
     if (!tmp) return -1;
     set_threads(nthreads);
     for (int t = 0; t < nsteps; ++t) {
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
         for (int z = 0; z < L->nz; ++z) {
-            for (int y = 0; y < L->ny; ++y)
+            for (int y = 0; y < L->ny; ++y) {
                 for (int x = 0; x < L->nx; ++x) {
                     long s = ((long)z * L->ny + y) * L->nx + x;
                     double fl[Q], Fl[3], fs[Q];
@@ -320,6 +320,7 @@ int ora_step(const ora_lattice *L, const double *F, double *f, int nsteps, int n
                         tmp[d * N + t2] = fs[i];
                     }
                 }
+            }
         }
         memcpy(f, tmp, sizeof(double) * Q * N);
     }

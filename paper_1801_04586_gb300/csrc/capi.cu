@@ -1,0 +1,393 @@
+// capi.cu -- the extern "C" boundary declared in include/clbm.h: context
+// lifetime, argument validation, A/B buffer bookkeeping and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/clbm.h"
+#include "kernels.cuh"
+
+using namespace clbm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    return fail(CLBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t elem_size(int storage) { return storage == CLBM_STORAGE_F32 ? 4 : 2; }
+
+constexpr int kReduceBlocks = 4 * 152;  // fixed reduction grid: deterministic sums
+
+struct StateHeader {
+    char magic[8];
+    int32_t version, nx, ny, nz, walls, storage;
+    int64_t stride, steps_done, bytes;
+};
+
+}  // namespace
+
+struct clbm_ctx {
+    clbm_params p;
+    Geom g;
+    int64_t n;
+    size_t elem;
+    void *buf[2];
+    int cur;
+    cudaStream_t stream;
+    Rates rates;
+    double s2;
+    ForceArgs force;
+    int *d_flag;
+    double *d_partials;
+    float *d_io;          // 4 x N floats for clbm_run_host (allocated on first use)
+    double *d_mom;        // 4 doubles for clbm_run_host
+    int64_t steps_done;
+    dim3 block;
+};
+
+namespace {
+
+Launch launch_of(const clbm_ctx *c) {
+    Launch L;
+    L.g = c->g;
+    L.block = c->block;
+    L.grid = dim3((c->g.nx + c->block.x - 1) / c->block.x, (c->g.ny + c->block.y - 1) / c->block.y, c->g.nz);
+    L.stream = c->stream;
+    return L;
+}
+
+bool rate_ok(double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *clbm_status_string(int status) {
+    switch (status) {
+        case CLBM_OK: return "ok";
+        case CLBM_ERR_ARG: return "invalid argument";
+        case CLBM_ERR_OOM: return "device out of memory";
+        case CLBM_ERR_CUDA: return "CUDA error";
+        case CLBM_ERR_UNSTABLE: return "unstable: density out of range or non-finite";
+        case CLBM_ERR_STATE: return "invalid state";
+        default: return "unknown status";
+    }
+}
+
+const char *clbm_last_error(void) { return g_last_error.c_str(); }
+
+int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
+    if (!p || !out) return fail(CLBM_ERR_ARG, "clbm_create: null pointer");
+    *out = nullptr;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nx > 65535 || p->ny > 65535 || p->nz > 65535)
+        return fail(CLBM_ERR_ARG, "clbm_create: each extent must be in [1, 65535]");
+    const int64_t n = (int64_t)p->nx * p->ny * p->nz;
+    if (n > ((int64_t)1 << 31) - 1) return fail(CLBM_ERR_ARG, "clbm_create: more than 2^31-1 nodes");
+    if (p->walls & ~7u) return fail(CLBM_ERR_ARG, "clbm_create: unknown wall bits");
+    if (!(std::isfinite(p->nu) && p->nu > 0.0)) return fail(CLBM_ERR_ARG, "clbm_create: nu must be > 0");
+    const double s2 = 1.0 / (3.0 * p->nu + 0.5);
+    if (!rate_ok(s2) || !rate_ok(p->s2b) || !rate_ok(p->s3) || !rate_ok(p->s4))
+        return fail(CLBM_ERR_ARG, "clbm_create: relaxation rates must lie in (0, 2)");
+    if (p->storage < CLBM_STORAGE_F32 || p->storage > CLBM_STORAGE_BF16)
+        return fail(CLBM_ERR_ARG, "clbm_create: unknown storage format");
+    int bx = p->block_x, by = p->block_y;
+    if (bx == 0) bx = p->nx >= 128 ? 128 : ((p->nx + 31) / 32) * 32;
+    if (by == 0) by = std::max(1, std::min(p->ny, 256 / bx));
+    if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 512)
+        return fail(CLBM_ERR_ARG, "clbm_create: block_x must be a multiple of 32 and block_x*block_y <= 512");
+    if ((p->ny + by - 1) / by > 65535) return fail(CLBM_ERR_ARG, "clbm_create: ny / block_y exceeds grid limit");
+
+    clbm_ctx *c = new (std::nothrow) clbm_ctx();
+    if (!c) return fail(CLBM_ERR_OOM, "clbm_create: host allocation failed");
+    c->p = *p;
+    c->n = n;
+    c->elem = elem_size(p->storage);
+    c->g.nx = p->nx; c->g.ny = p->ny; c->g.nz = p->nz;
+    c->g.walls = p->walls;
+    c->g.stride = (n + 63) / 64 * 64;  // every population array starts 256-byte aligned (f32)
+    c->stream = (cudaStream_t)stream;
+    c->s2 = s2;
+    c->rates.om2 = (float)(1.0 - s2);
+    c->rates.cb = (float)((p->s2b - s2) / 3.0);
+    c->rates.om3 = (float)(1.0 - p->s3);
+    c->rates.c3 = (float)((1.0 - 0.5 * p->s3) / 3.0);
+    c->rates.om4 = (float)(1.0 - p->s4);
+    c->force.mode = kForceUniform;
+    c->force.fx = c->force.fy = c->force.fz = 0.0f;
+    c->force.profile = nullptr;
+    c->force.field = nullptr;
+    c->force.n = n;
+    c->block = dim3(bx, by, 1);
+    c->cur = 0;
+    c->steps_done = 0;
+    const size_t bytes = (size_t)kQ * c->g.stride * c->elem;
+    cudaError_t e = cudaMalloc(&c->buf[0], 2 * bytes);
+    if (e != cudaSuccess) {
+        delete c;
+        cudaGetLastError();
+        return fail(CLBM_ERR_OOM, std::string("clbm_create: cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->buf[1] = (char *)c->buf[0] + bytes;
+    e = cudaMalloc(&c->d_flag, 256 + sizeof(double) * 4 * kReduceBlocks);
+    if (e != cudaSuccess) {
+        cudaFree(c->buf[0]);
+        delete c;
+        cudaGetLastError();
+        return fail(CLBM_ERR_OOM, std::string("clbm_create: cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->d_partials = (double *)((char *)c->d_flag + 256);
+    // rest state: zero deviations in both buffers (zero bits are zero in all formats)
+    if ((e = cudaMemsetAsync(c->buf[0], 0, 2 * bytes, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream)) != cudaSuccess) {
+        cudaFree(c->d_flag);
+        cudaFree(c->buf[0]);
+        delete c;
+        return cuda_fail(e, "clbm_create");
+    }
+    *out = c;
+    return CLBM_OK;
+}
+
+int clbm_destroy(clbm_ctx *c) {
+    if (!c) return CLBM_OK;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->buf[0]);
+    cudaFree(c->d_flag);
+    if (c->d_io) cudaFree(c->d_io);
+    if (c->d_mom) cudaFree(c->d_mom);
+    delete c;
+    return CLBM_OK;
+}
+
+int clbm_get_info(const clbm_ctx *c, clbm_info *info) {
+    if (!c || !info) return fail(CLBM_ERR_ARG, "clbm_get_info: null pointer");
+    info->n_nodes = c->n;
+    info->pop_stride = c->g.stride;
+    info->state_bytes = (int64_t)kQ * c->g.stride * (int64_t)c->elem;
+    info->steps_done = c->steps_done;
+    info->storage = c->p.storage;
+    info->block_x = (int32_t)c->block.x;
+    info->block_y = (int32_t)c->block.y;
+    info->s2 = c->s2;
+    return CLBM_OK;
+}
+
+int clbm_set_force_uniform(clbm_ctx *c, double fx, double fy, double fz) {
+    if (!c) return fail(CLBM_ERR_ARG, "clbm_set_force_uniform: null context");
+    if (!(std::isfinite(fx) && std::isfinite(fy) && std::isfinite(fz)))
+        return fail(CLBM_ERR_ARG, "clbm_set_force_uniform: non-finite force");
+    c->force.mode = kForceUniform;
+    c->force.fx = (float)fx; c->force.fy = (float)fy; c->force.fz = (float)fz;
+    return CLBM_OK;
+}
+
+int clbm_set_force_profile_z(clbm_ctx *c, const float *F) {
+    if (!c || !F) return fail(CLBM_ERR_ARG, "clbm_set_force_profile_z: null pointer");
+    c->force.mode = kForceProfileZ;
+    c->force.profile = F;
+    return CLBM_OK;
+}
+
+int clbm_set_force_field(clbm_ctx *c, const float *F) {
+    if (!c || !F) return fail(CLBM_ERR_ARG, "clbm_set_force_field: null pointer");
+    c->force.mode = kForceField;
+    c->force.field = F;
+    return CLBM_OK;
+}
+
+int clbm_init_equilibrium(clbm_ctx *c, const float *rho, const float *u) {
+    if (!c) return fail(CLBM_ERR_ARG, "clbm_init_equilibrium: null context");
+    cudaError_t e = launch_init_eq(c->p.storage, launch_of(c), c->buf[c->cur], rho, u, c->n, c->force);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_init_equilibrium");
+    c->steps_done = 0;
+    return CLBM_OK;
+}
+
+int clbm_step(clbm_ctx *c, int64_t nsteps) {
+    if (!c) return fail(CLBM_ERR_ARG, "clbm_step: null context");
+    if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_step: nsteps < 0");
+    const Launch L = launch_of(c);
+    for (int64_t t = 0; t < nsteps; ++t) {
+        cudaError_t e = launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force, c->d_flag);
+        if (e != cudaSuccess) return cuda_fail(e, "clbm_step");
+        c->cur ^= 1;
+        ++c->steps_done;
+    }
+    return CLBM_OK;
+}
+
+int clbm_get_macros(clbm_ctx *c, float *rho, float *u) {
+    if (!c) return fail(CLBM_ERR_ARG, "clbm_get_macros: null context");
+    if (!rho && !u) return CLBM_OK;
+    cudaError_t e = launch_macros(c->p.storage, launch_of(c), c->buf[c->cur], c->force, rho, u, c->n);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_get_macros");
+    return CLBM_OK;
+}
+
+int clbm_get_populations(clbm_ctx *c, float *f, int deviation) {
+    if (!c || !f) return fail(CLBM_ERR_ARG, "clbm_get_populations: null pointer");
+    cudaError_t e = launch_gather(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_get_populations");
+    return CLBM_OK;
+}
+
+int clbm_set_populations(clbm_ctx *c, const float *f, int deviation) {
+    if (!c || !f) return fail(CLBM_ERR_ARG, "clbm_set_populations: null pointer");
+    cudaError_t e = launch_scatter(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_set_populations");
+    c->steps_done = 0;
+    return CLBM_OK;
+}
+
+int clbm_reduce_moments(clbm_ctx *c, double *out) {
+    if (!c || !out) return fail(CLBM_ERR_ARG, "clbm_reduce_moments: null pointer");
+    cudaError_t e = launch_reduce_moments(c->p.storage, launch_of(c), c->buf[c->cur], c->force, c->d_partials,
+                                          kReduceBlocks, out);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_reduce_moments");
+    return CLBM_OK;
+}
+
+int clbm_reduce_pair(clbm_ctx *c, const float *a, const float *b, int64_t n, double *out) {
+    if (!c || !out || n < 0 || (!a && n > 0)) return fail(CLBM_ERR_ARG, "clbm_reduce_pair: bad argument");
+    cudaError_t e = launch_reduce_pair(a, b, n, c->d_partials, kReduceBlocks, out, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_reduce_pair");
+    return CLBM_OK;
+}
+
+int clbm_check(clbm_ctx *c, int clear) {
+    if (!c) return fail(CLBM_ERR_ARG, "clbm_check: null context");
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_check");
+    if (clear) {
+        e = cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "clbm_check");
+    }
+    if (h) return fail(CLBM_ERR_UNSTABLE, "clbm_check: a node's density left (0.1, 1.9) or became non-finite");
+    return CLBM_OK;
+}
+
+int clbm_export_state(clbm_ctx *c, void *dst) {
+    if (!c || !dst) return fail(CLBM_ERR_ARG, "clbm_export_state: null pointer");
+    const size_t bytes = (size_t)kQ * c->g.stride * c->elem;
+    cudaError_t e = cudaMemcpyAsync(dst, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_export_state");
+    return CLBM_OK;
+}
+
+int clbm_import_state(clbm_ctx *c, const void *src, int64_t set_steps) {
+    if (!c || !src) return fail(CLBM_ERR_ARG, "clbm_import_state: null pointer");
+    const size_t bytes = (size_t)kQ * c->g.stride * c->elem;
+    cudaError_t e = cudaMemcpyAsync(c->buf[c->cur], src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_import_state");
+    if (set_steps >= 0) c->steps_done = set_steps;
+    return CLBM_OK;
+}
+
+int clbm_save_state(clbm_ctx *c, void *host, size_t *bytes) {
+    if (!c || !bytes) return fail(CLBM_ERR_ARG, "clbm_save_state: null pointer");
+    const size_t raw = (size_t)kQ * c->g.stride * c->elem;
+    const size_t need = sizeof(StateHeader) + raw;
+    if (!host) {
+        *bytes = need;
+        return CLBM_OK;
+    }
+    if (*bytes < need) return fail(CLBM_ERR_ARG, "clbm_save_state: buffer too small");
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "CLBMQ19", 8);
+    h.version = 1;
+    h.nx = c->g.nx; h.ny = c->g.ny; h.nz = c->g.nz;
+    h.walls = (int32_t)c->g.walls;
+    h.storage = c->p.storage;
+    h.stride = c->g.stride;
+    h.steps_done = c->steps_done;
+    h.bytes = (int64_t)raw;
+    std::memcpy(host, &h, sizeof(h));
+    cudaError_t e = cudaMemcpyAsync((char *)host + sizeof(h), c->buf[c->cur], raw, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_save_state");
+    *bytes = need;
+    return CLBM_OK;
+}
+
+int clbm_load_state(clbm_ctx *c, const void *host, size_t bytes) {
+    if (!c || !host) return fail(CLBM_ERR_ARG, "clbm_load_state: null pointer");
+    if (bytes < sizeof(StateHeader)) return fail(CLBM_ERR_ARG, "clbm_load_state: buffer too small");
+    StateHeader h;
+    std::memcpy(&h, host, sizeof(h));
+    const size_t raw = (size_t)kQ * c->g.stride * c->elem;
+    if (std::memcmp(h.magic, "CLBMQ19", 8) != 0 || h.version != 1)
+        return fail(CLBM_ERR_ARG, "clbm_load_state: not a state buffer");
+    if (h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz || h.walls != (int32_t)c->g.walls ||
+        h.storage != c->p.storage || h.stride != c->g.stride || h.bytes != (int64_t)raw ||
+        bytes < sizeof(h) + raw)
+        return fail(CLBM_ERR_ARG, "clbm_load_state: geometry, storage or size mismatch");
+    cudaError_t e =
+        cudaMemcpyAsync(c->buf[c->cur], (const char *)host + sizeof(h), raw, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_load_state");
+    c->steps_done = h.steps_done;
+    return CLBM_OK;
+}
+
+int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nsteps, float *rho_out,
+                  float *u_out, double *moments_h) {
+    if (!c) return fail(CLBM_ERR_ARG, "clbm_run_host: null context");
+    if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_run_host: nsteps < 0");
+    cudaError_t e;
+    if (!c->d_io) {
+        if ((e = cudaMalloc(&c->d_io, sizeof(float) * 4 * (size_t)c->n)) != cudaSuccess) {
+            c->d_io = nullptr;
+            cudaGetLastError();
+            return fail(CLBM_ERR_OOM, "clbm_run_host: cudaMalloc failed");
+        }
+        if ((e = cudaMalloc(&c->d_mom, sizeof(double) * 4)) != cudaSuccess) {
+            c->d_mom = nullptr;
+            cudaGetLastError();
+            return fail(CLBM_ERR_OOM, "clbm_run_host: cudaMalloc failed");
+        }
+    }
+    float *d_rho = c->d_io, *d_u = c->d_io + c->n;
+    const size_t nb = sizeof(float) * (size_t)c->n;
+    if (rho_h && (e = cudaMemcpyAsync(d_rho, rho_h, nb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return cuda_fail(e, "clbm_run_host: copy rho");
+    if (u_h && (e = cudaMemcpyAsync(d_u, u_h, 3 * nb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return cuda_fail(e, "clbm_run_host: copy u");
+    int rc = clbm_init_equilibrium(c, rho_h ? d_rho : nullptr, u_h ? d_u : nullptr);
+    if (rc != CLBM_OK) return rc;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        if ((rc = clbm_step(c, 1)) != CLBM_OK) return rc;
+        if (moments_h) {
+            if ((rc = clbm_reduce_moments(c, c->d_mom)) != CLBM_OK) return rc;
+            e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: moments");
+            if (!std::isfinite(moments_h[4 * t])) return fail(CLBM_ERR_UNSTABLE, "clbm_run_host: non-finite mass");
+        }
+    }
+    if ((rho_out || u_out) && (rc = clbm_get_macros(c, rho_out ? d_rho : nullptr, u_out ? d_u : nullptr)) != CLBM_OK)
+        return rc;
+    if (rho_out && (e = cudaMemcpyAsync(rho_out, d_rho, nb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return cuda_fail(e, "clbm_run_host: copy rho back");
+    if (u_out && (e = cudaMemcpyAsync(u_out, d_u, 3 * nb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return cuda_fail(e, "clbm_run_host: copy u back");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e, "clbm_run_host");
+    return clbm_check(c, 0);
+}
+
+}  // extern "C"

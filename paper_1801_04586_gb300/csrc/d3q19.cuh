@@ -1,0 +1,337 @@
+// d3q19.cuh -- device-side D3Q19 cascaded-LBM node arithmetic for sm_103a.
+//
+// Method: Fei, Luo & Li, arXiv:1801.04586, Appendix A (D3Q19) with the GMRT
+// collision of Sec. II.A (Eq. 5), the simplified central-moment set (Eq. A2),
+// the block-diagonal S (Eq. A3), the continuous-Maxwellian equilibria (Eq. A5)
+// and the consistent forcing terms (Eq. A6).
+//
+// Velocity order (Eq. A1): 0 rest; 1,2 = +-x; 3,4 = +-y; 5,6 = +-z;
+// 7..10 = (+1,+1,0) (-1,+1,0) (+1,-1,0) (-1,-1,0); 11..14 = the same pattern
+// in (x,z); 15..18 = the same pattern in (y,z).
+//
+// Arithmetic is done on deviations so that FP32 keeps its relative precision
+// on the small quantities that carry the physics:
+//   h_i = f_i - w_i                       (w = rest weights 1/3, 1/18, 1/36)
+//   dT  = M h                             (raw-moment deviations, Eq. 4)
+//   R   = M f - rho G(u)                  (non-equilibrium raw moments; rho G(u)
+//                                          are the raw moments of the generalized
+//                                          equilibrium, a product of the 1D moments
+//                                          1, u, u^2 + c_s^2 per axis)
+//   D   = N(u) R = T~ - T~eq              (non-equilibrium central moments)
+//   D*  = (I - S) D + (I - S/2) C         (Eq. 5 minus T~eq on both sides)
+//   h*  = M^-1 (N(-u) D* + rho G(u) - M w)
+// which is Eq. 5 and Eq. 7 rearranged exactly. N(u) is applied as three
+// per-axis binomial shifts (x, then y, then z), each acting on triplets
+// (k0, k1, k2) of moments that differ only in that axis' exponent; N(-u)
+// undoes them. M and M^-1 are written out from the plane structure of the
+// velocity set (91 non-zeros of M^-1, Eq. 7).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace clbm {
+
+constexpr int kQ = 19;
+constexpr float kC = 1.0f / 3.0f;   // c_s^2
+constexpr float kC2 = 1.0f / 9.0f;  // c_s^4
+
+// Rest weights w_i (the u = 0 equilibrium at rho = 1).
+__host__ __device__ constexpr float rest_weight(int i) {
+    return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+
+// Opposite direction (bounce-back partner): pairs (1,2) (3,4) (5,6), and in
+// each diagonal plane group of four starting at b = 7, 11, 15: b+k <-> b+3-k.
+__host__ __device__ constexpr int opposite(int i) {
+    return i == 0 ? 0 : (i <= 6 ? ((i & 1) ? i + 1 : i - 1) : (2 * (7 + 4 * ((i - 7) / 4)) + 3 - i));
+}
+
+// ---------------------------------------------------------------- storage
+template <typename T> struct Codec;
+template <> struct Codec<float> {
+    static __device__ __forceinline__ float load(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float load_plain(const float *p) { return *p; }
+    static __device__ __forceinline__ float to_f(float v) { return v; }
+    static __device__ __forceinline__ float from_f(float v) { return v; }
+};
+template <> struct Codec<__half> {
+    static __device__ __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float load_plain(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half from_f(float v) { return __float2half_rn(v); }
+};
+template <> struct Codec<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float load_plain(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 from_f(float v) { return __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+    int nx, ny, nz;
+    uint32_t walls;     // bit 0: x walls, bit 1: y walls, bit 2: z walls
+    int64_t stride;     // elements between population arrays
+};
+
+// Pull sources of the 19 populations arriving at node (x, y, z) (Eq. 8 read
+// backwards): population i comes from (i, x - e_i) with periodic wrap, or,
+// when x - e_i lies beyond a wall face, from (ibar, x) -- halfway bounce-back.
+// pop[i] is the population array index and off[i] the node offset to read.
+// The same map, used to write instead of read, turns a post-streaming state
+// into the post-collision buffer a later pull reproduces it from.
+template <bool WALLS>
+__device__ __forceinline__ void pull_sources(const Geom &g, int x, int y, int z,
+                                             uint32_t (&off)[kQ], int (&pop)[kQ]) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    const uint32_t unx = (uint32_t)nx, uny = (uint32_t)ny;
+    const uint32_t rc = ((uint32_t)z * uny + y) * unx;
+    const uint32_t rym = ((uint32_t)z * uny + ym) * unx, ryp = ((uint32_t)z * uny + yp) * unx;
+    const uint32_t rzm = ((uint32_t)zm * uny + y) * unx, rzp = ((uint32_t)zp * uny + y) * unx;
+    const uint32_t rmm = ((uint32_t)zm * uny + ym) * unx, rpm = ((uint32_t)zm * uny + yp) * unx;
+    const uint32_t rmp = ((uint32_t)zp * uny + ym) * unx, rpp = ((uint32_t)zp * uny + yp) * unx;
+    const uint32_t self = rc + x;
+    off[0] = self;
+    off[1] = rc + xm;   off[2] = rc + xp;
+    off[3] = rym + x;   off[4] = ryp + x;
+    off[5] = rzm + x;   off[6] = rzp + x;
+    off[7] = rym + xm;  off[8] = rym + xp;  off[9] = ryp + xm;  off[10] = ryp + xp;
+    off[11] = rzm + xm; off[12] = rzm + xp; off[13] = rzp + xm; off[14] = rzp + xp;
+    off[15] = rmm + x;  off[16] = rpm + x;  off[17] = rmp + x;  off[18] = rpp + x;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) pop[i] = i;
+    if (WALLS) {
+        const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
+        const bool xl = wx && x == 0, xh = wx && x == nx - 1;  // ex = +1 / -1 bounce
+        const bool yl = wy && y == 0, yh = wy && y == ny - 1;
+        const bool zl = wz && z == 0, zh = wz && z == nz - 1;
+        // ex, ey, ez of each direction decide which faces it can cross.
+        const bool bb[kQ] = {false,
+                             xl, xh, yl, yh, zl, zh,
+                             xl || yl, xh || yl, xl || yh, xh || yh,
+                             xl || zl, xh || zl, xl || zh, xh || zh,
+                             yl || zl, yh || zl, yl || zh, yh || zh};
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) {
+            if (bb[i]) { pop[i] = opposite(i); off[i] = self; }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- collision
+struct Rates {
+    float om2;  // 1 - s2
+    float cb;   // (s2b - s2)/3: trace coupling of the 3x3 block of Eq. A3
+    float om3;  // 1 - s3
+    float c3;   // (1 - s3/2) c_s^2: coefficient of F in the third-order terms (Eq. A6)
+    float om4;  // 1 - s4
+};
+
+// Central shift of one triplet along an axis with velocity v (one factor of
+// N(u)): (k0, k1, k2) -> (k0, k1 - v k0, k2 - 2 v k1 + v^2 k0).
+__device__ __forceinline__ void shift3(float k0, float &k1, float &k2, float v) {
+    const float c1 = fmaf(-v, k0, k1);
+    k2 = fmaf(-v, k1 + c1, k2);
+    k1 = c1;
+}
+// Its inverse (one factor of N(-u)): (c0, c1, c2) -> (c0, c1 + v c0, c2 + 2 v c1 + v^2 c0).
+__device__ __forceinline__ void unshift3(float c0, float &c1, float &c2, float v) {
+    const float k1 = fmaf(v, c0, c1);
+    c2 = fmaf(v, c1 + k1, c2);
+    c1 = k1;
+}
+
+// Raw-moment deviations dT = M h, named by exponents (Eq. A2 with k~002 as the
+// tenth moment).
+struct Moments {
+    float m000, m100, m010, m001, m110, m101, m011, m200, m020, m002;
+    float m120, m102, m210, m201, m012, m021, m220, m202, m022;
+};
+
+__device__ __forceinline__ void raw_moments(const float (&h)[kQ], Moments &k) {
+    // xy plane (7..10): four moments ex^a ey^b with a, b in {1, 2}
+    const float a = h[7] + h[8], b = h[9] + h[10], c = h[7] + h[9], d = h[8] + h[10];
+    const float e = h[7] + h[10], f = h[8] + h[9];
+    k.m220 = a + b; k.m210 = a - b; k.m120 = c - d; k.m110 = e - f;
+    // xz plane (11..14)
+    const float a2 = h[11] + h[12], b2 = h[13] + h[14], c2 = h[11] + h[13], d2 = h[12] + h[14];
+    const float e2 = h[11] + h[14], f2 = h[12] + h[13];
+    k.m202 = a2 + b2; k.m201 = a2 - b2; k.m102 = c2 - d2; k.m101 = e2 - f2;
+    // yz plane (15..18)
+    const float a3 = h[15] + h[16], b3 = h[17] + h[18], c3 = h[15] + h[17], d3 = h[16] + h[18];
+    const float e3 = h[15] + h[18], f3 = h[16] + h[17];
+    k.m022 = a3 + b3; k.m021 = a3 - b3; k.m012 = c3 - d3; k.m011 = e3 - f3;
+    // axes
+    const float s12 = h[1] + h[2], s34 = h[3] + h[4], s56 = h[5] + h[6];
+    k.m200 = s12 + k.m220 + k.m202;
+    k.m020 = s34 + k.m220 + k.m022;
+    k.m002 = s56 + k.m202 + k.m022;
+    k.m100 = (h[1] - h[2]) + k.m120 + k.m102;
+    k.m010 = (h[3] - h[4]) + k.m210 + k.m012;
+    k.m001 = (h[5] - h[6]) + k.m201 + k.m021;
+    k.m000 = h[0] + s12 + s34 + s56 + k.m220 + k.m202 + k.m022;
+}
+
+// Deviations of the generalized-equilibrium raw moments, rho G(u) - M w,
+// for the 15 moments other than the ones with a zero/first-order closed form.
+struct EqDev {
+    float d110, d101, d011, d200, d020, d002, d120, d102, d210, d201, d012, d021, d220, d202, d022;
+};
+
+__device__ __forceinline__ void eq_dev(float drho, float rho, float jx, float jy, float jz,
+                                       float ux, float uy, float uz, EqDev &q) {
+    const float X = ux * ux, Y = uy * uy, Z = uz * uz;
+    q.d110 = jx * uy; q.d101 = jx * uz; q.d011 = jy * uz;
+    q.d200 = fmaf(jx, ux, drho * kC); q.d020 = fmaf(jy, uy, drho * kC); q.d002 = fmaf(jz, uz, drho * kC);
+    q.d120 = jx * (Y + kC); q.d102 = jx * (Z + kC);
+    q.d210 = jy * (X + kC); q.d201 = jz * (X + kC);
+    q.d012 = jy * (Z + kC); q.d021 = jz * (Y + kC);
+    q.d220 = fmaf(rho, fmaf(X, Y, kC * (X + Y)), drho * kC2);
+    q.d202 = fmaf(rho, fmaf(X, Z, kC * (X + Z)), drho * kC2);
+    q.d022 = fmaf(rho, fmaf(Y, Z, kC * (Y + Z)), drho * kC2);
+}
+
+// h = M^-1 Q for raw-moment deviations Q (Eq. 7, M^-1 of Eq. A4).
+__device__ __forceinline__ void inverse_moments(const Moments &q, float (&h)[kQ]) {
+    h[7] = 0.25f * ((q.m220 + q.m210) + (q.m120 + q.m110));
+    h[8] = 0.25f * ((q.m220 + q.m210) - (q.m120 + q.m110));
+    h[9] = 0.25f * ((q.m220 - q.m210) + (q.m120 - q.m110));
+    h[10] = 0.25f * ((q.m220 - q.m210) - (q.m120 - q.m110));
+    h[11] = 0.25f * ((q.m202 + q.m201) + (q.m102 + q.m101));
+    h[12] = 0.25f * ((q.m202 + q.m201) - (q.m102 + q.m101));
+    h[13] = 0.25f * ((q.m202 - q.m201) + (q.m102 - q.m101));
+    h[14] = 0.25f * ((q.m202 - q.m201) - (q.m102 - q.m101));
+    h[15] = 0.25f * ((q.m022 + q.m021) + (q.m012 + q.m011));
+    h[16] = 0.25f * ((q.m022 + q.m021) - (q.m012 + q.m011));
+    h[17] = 0.25f * ((q.m022 - q.m021) + (q.m012 - q.m011));
+    h[18] = 0.25f * ((q.m022 - q.m021) - (q.m012 - q.m011));
+    const float px = q.m200 - q.m220 - q.m202, vx = q.m100 - q.m120 - q.m102;
+    const float py = q.m020 - q.m220 - q.m022, vy = q.m010 - q.m210 - q.m012;
+    const float pz = q.m002 - q.m202 - q.m022, vz = q.m001 - q.m201 - q.m021;
+    h[1] = 0.5f * (px + vx); h[2] = 0.5f * (px - vx);
+    h[3] = 0.5f * (py + vy); h[4] = 0.5f * (py - vy);
+    h[5] = 0.5f * (pz + vz); h[6] = 0.5f * (pz - vz);
+    h[0] = q.m000 - (q.m200 + q.m020 + q.m002) + (q.m220 + q.m202 + q.m022);
+}
+
+// One collision (Steps 1-3 of Sec. II.B) on deviations h, in place.
+// Returns drho = rho - 1 of the pre-collision state (Eq. 9).
+__device__ __forceinline__ float collide(float (&h)[kQ], float Fx, float Fy, float Fz, const Rates &r) {
+    Moments k;
+    raw_moments(h, k);
+    const float drho = k.m000;
+    const float rho = 1.0f + drho;
+    const float inv = 1.0f / rho;
+    const float jx = fmaf(0.5f, Fx, k.m100), jy = fmaf(0.5f, Fy, k.m010), jz = fmaf(0.5f, Fz, k.m001);
+    const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    EqDev e;
+    eq_dev(drho, rho, jx, jy, jz, ux, uy, uz, e);
+
+    // non-equilibrium raw moments R = dT - (rho G - M w); R000 = 0, R100 = -Fx/2, ...
+    const float hFx = 0.5f * Fx, hFy = 0.5f * Fy, hFz = 0.5f * Fz;
+    float r110 = k.m110 - e.d110, r101 = k.m101 - e.d101, r011 = k.m011 - e.d011;
+    float r200 = k.m200 - e.d200, r020 = k.m020 - e.d020, r002 = k.m002 - e.d002;
+    float r120 = k.m120 - e.d120, r102 = k.m102 - e.d102, r210 = k.m210 - e.d210;
+    float r201 = k.m201 - e.d201, r012 = k.m012 - e.d012, r021 = k.m021 - e.d021;
+    float r220 = k.m220 - e.d220, r202 = k.m202 - e.d202, r022 = k.m022 - e.d022;
+
+    // D = N(u) R: x shift on (000,100,200) (010,110,210) (001,101,201) (020,120,220) (002,102,202)
+    r200 = fmaf(ux, Fx, r200);                 // R000 = 0, R100 = -Fx/2
+    shift3(-hFy, r110, r210, ux);
+    shift3(-hFz, r101, r201, ux);
+    shift3(r020, r120, r220, ux);
+    shift3(r002, r102, r202, ux);
+    // y shift on (000,010,020) (100,110,120) (001,011,021) (200,210,220) (002,012,022)
+    r020 = fmaf(uy, Fy, r020);
+    shift3(-hFx, r110, r120, uy);
+    shift3(-hFz, r011, r021, uy);
+    shift3(r200, r210, r220, uy);
+    shift3(r002, r012, r022, uy);
+    // z shift on (000,001,002) (100,101,102) (010,011,012) (200,201,202) (020,021,022)
+    r002 = fmaf(uz, Fz, r002);
+    shift3(-hFx, r101, r102, uz);
+    shift3(-hFy, r011, r012, uz);
+    shift3(r200, r201, r202, uz);
+    shift3(r020, r021, r022, uz);
+
+    // Eq. 5 on non-equilibrium central moments: D* = (I - S) D + (I - S/2) C.
+    // s0 = s1 = 1: D*000 = 0, D*100 = Fx/2, ...
+    r110 *= r.om2; r101 *= r.om2; r011 *= r.om2;
+    {
+        const float tr = r.cb * (r200 + r020 + r002);
+        r200 = fmaf(r.om2, r200, -tr);
+        r020 = fmaf(r.om2, r020, -tr);
+        r002 = fmaf(r.om2, r002, -tr);
+    }
+    r120 = fmaf(r.om3, r120, r.c3 * Fx);
+    r102 = fmaf(r.om3, r102, r.c3 * Fx);
+    r210 = fmaf(r.om3, r210, r.c3 * Fy);
+    r201 = fmaf(r.om3, r201, r.c3 * Fz);
+    r012 = fmaf(r.om3, r012, r.c3 * Fy);
+    r021 = fmaf(r.om3, r021, r.c3 * Fz);
+    r220 *= r.om4; r202 *= r.om4; r022 *= r.om4;
+
+    // R* = N(-u) D*: undo z, then y, then x (D*000 = 0, D*100 = Fx/2, ...)
+    r002 = fmaf(uz, Fz, r002);
+    unshift3(hFx, r101, r102, uz);
+    unshift3(hFy, r011, r012, uz);
+    unshift3(r200, r201, r202, uz);
+    unshift3(r020, r021, r022, uz);
+    r020 = fmaf(uy, Fy, r020);
+    unshift3(hFx, r110, r120, uy);
+    unshift3(hFz, r011, r021, uy);
+    unshift3(r200, r210, r220, uy);
+    unshift3(r002, r012, r022, uy);
+    r200 = fmaf(ux, Fx, r200);
+    unshift3(hFy, r110, r210, ux);
+    unshift3(hFz, r101, r201, ux);
+    unshift3(r020, r120, r220, ux);
+    unshift3(r002, r102, r202, ux);
+
+    // Q = R* + (rho G(u) - M w); first order: R*100 = Fx/2, so Q100 = jx + Fx/2.
+    Moments q;
+    q.m000 = drho;
+    q.m100 = jx + hFx; q.m010 = jy + hFy; q.m001 = jz + hFz;
+    q.m110 = r110 + e.d110; q.m101 = r101 + e.d101; q.m011 = r011 + e.d011;
+    q.m200 = r200 + e.d200; q.m020 = r020 + e.d020; q.m002 = r002 + e.d002;
+    q.m120 = r120 + e.d120; q.m102 = r102 + e.d102; q.m210 = r210 + e.d210;
+    q.m201 = r201 + e.d201; q.m012 = r012 + e.d012; q.m021 = r021 + e.d021;
+    q.m220 = r220 + e.d220; q.m202 = r202 + e.d202; q.m022 = r022 + e.d022;
+    inverse_moments(q, h);
+    return drho;
+}
+
+// Deviations of the generalized local equilibrium at (rho, u):
+// h = M^-1 (rho G(u) - M w).
+__device__ __forceinline__ void equilibrium_dev(float rho, float ux, float uy, float uz, float (&h)[kQ]) {
+    const float drho = rho - 1.0f;
+    const float jx = rho * ux, jy = rho * uy, jz = rho * uz;
+    EqDev e;
+    eq_dev(drho, rho, jx, jy, jz, ux, uy, uz, e);
+    Moments q;
+    q.m000 = drho; q.m100 = jx; q.m010 = jy; q.m001 = jz;
+    q.m110 = e.d110; q.m101 = e.d101; q.m011 = e.d011;
+    q.m200 = e.d200; q.m020 = e.d020; q.m002 = e.d002;
+    q.m120 = e.d120; q.m102 = e.d102; q.m210 = e.d210; q.m201 = e.d201;
+    q.m012 = e.d012; q.m021 = e.d021;
+    q.m220 = e.d220; q.m202 = e.d202; q.m022 = e.d022;
+    inverse_moments(q, h);
+}
+
+// Eq. 9 on deviations: returns drho and writes rho*u (momentum incl. F/2).
+__device__ __forceinline__ float macros_dev(const float (&h)[kQ], float Fx, float Fy, float Fz,
+                                            float &jx, float &jy, float &jz) {
+    Moments k;
+    raw_moments(h, k);
+    jx = fmaf(0.5f, Fx, k.m100);
+    jy = fmaf(0.5f, Fy, k.m010);
+    jz = fmaf(0.5f, Fz, k.m001);
+    return k.m000;
+}
+
+}  // namespace clbm

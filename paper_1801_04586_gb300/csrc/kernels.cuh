@@ -1,0 +1,42 @@
+// kernels.cuh -- launch interface between the C ABI (capi.cu) and the kernel
+// translation units. Plain structs only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "d3q19.cuh"
+
+namespace clbm {
+
+enum ForceMode : int { kForceUniform = 0, kForceProfileZ = 1, kForceField = 2 };
+
+struct ForceArgs {
+    int mode;
+    float fx, fy, fz;        // uniform
+    const float *profile;    // 3 x nz
+    const float *field;      // 3 x N
+    int64_t n;               // N, component stride of `field`
+};
+
+struct Launch {
+    Geom g;
+    dim3 block, grid;
+    cudaStream_t stream;
+};
+
+// storage: 0 = f32, 1 = f16, 2 = bf16 (CLBM_STORAGE_*)
+cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
+                        const ForceArgs &F, int *flag);
+cudaError_t launch_scatter(int storage, const Launch &L, void *dst, const float *f, int64_t n, int deviation);
+cudaError_t launch_init_eq(int storage, const Launch &L, void *dst, const float *rho, const float *u, int64_t n,
+                           const ForceArgs &F);
+cudaError_t launch_gather(int storage, const Launch &L, const void *src, float *f, int64_t n, int deviation);
+cudaError_t launch_macros(int storage, const Launch &L, const void *src, const ForceArgs &F, float *rho, float *u,
+                          int64_t n);
+cudaError_t launch_reduce_moments(int storage, const Launch &L, const void *src, const ForceArgs &F,
+                                  double *partials, int nblocks, double *out);
+cudaError_t launch_reduce_pair(const float *a, const float *b, int64_t n, double *partials, int nblocks,
+                               double *out, cudaStream_t stream);
+
+}  // namespace clbm

@@ -1,0 +1,81 @@
+// step.cu -- the fused pull stream-and-collide kernel (one launch per time step).
+//
+// Per node (x, y, z): gather the 19 post-collision populations of the previous
+// step from the neighbours x - e_i (Eq. 8; periodic wrap or halfway
+// bounce-back), collide them (Eqs. 5, 7, 9 with A3, A5, A6; see d3q19.cuh)
+// and store the 19 post-collision values at the node itself. Loads use the
+// read-only path so that the +-1 x-shifted reads of neighbouring threads share
+// L1 sectors; stores are coalesced and aligned. One thread per node, x
+// fastest, so each warp touches 19 contiguous 128-byte segments per direction.
+#include "kernels.cuh"
+
+namespace clbm {
+
+template <int FM>
+__device__ __forceinline__ void force_at(const ForceArgs &F, const Geom &g, int z, uint32_t self, float &fx,
+                                         float &fy, float &fz) {
+    if (FM == kForceUniform) {
+        fx = F.fx; fy = F.fy; fz = F.fz;
+    } else if (FM == kForceProfileZ) {
+        fx = __ldg(F.profile + z);
+        fy = __ldg(F.profile + g.nz + z);
+        fz = __ldg(F.profile + 2 * g.nz + z);
+    } else {
+        fx = __ldg(F.field + self);
+        fy = __ldg(F.field + F.n + self);
+        fz = __ldg(F.field + 2 * F.n + self);
+    }
+}
+
+template <typename S, int FM, bool WALLS>
+__global__ void __launch_bounds__(512) k_step(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r,
+                                              ForceArgs F, int *__restrict__ flag) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    uint32_t off[kQ];
+    int pop[kQ];
+    pull_sources<WALLS>(g, x, y, z, off, pop);
+    float h[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
+    float fx, fy, fz;
+    force_at<FM>(F, g, z, off[0], fx, fy, fz);
+    const float drho = collide(h, fx, fy, fz, r);
+    if (!(fabsf(drho) < 0.9f)) *flag = 1;
+    S *d = dst + off[0];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) d[(size_t)i * g.stride] = Codec<S>::from_f(h[i]);
+}
+
+template <typename S, int FM>
+static cudaError_t step_walls(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
+                              int *flag) {
+    if (L.g.walls)
+        k_step<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag);
+    else
+        k_step<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag);
+    return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t step_force(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
+                              int *flag) {
+    switch (F.mode) {
+        case kForceUniform: return step_walls<S, kForceUniform>(L, src, dst, r, F, flag);
+        case kForceProfileZ: return step_walls<S, kForceProfileZ>(L, src, dst, r, F, flag);
+        default: return step_walls<S, kForceField>(L, src, dst, r, F, flag);
+    }
+}
+
+cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
+                        const ForceArgs &F, int *flag) {
+    switch (storage) {
+        case 0: return step_force<float>(L, src, dst, r, F, flag);
+        case 1: return step_force<__half>(L, src, dst, r, F, flag);
+        default: return step_force<__nv_bfloat16>(L, src, dst, r, F, flag);
+    }
+}
+
+}  // namespace clbm

@@ -1,0 +1,121 @@
+"""GPU checks of the rest of the C ABI: reductions, state round trips,
+checkpoint/resume, the host-buffer job and the instability flag."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import dev, make_pair, t
+from paper_1801_04586_gb300 import UnstableError, synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+def test_reduce_pair_matches_numpy():
+    g, _ = make_pair(8, 8, 8, 0.1)
+    rng = np.random.default_rng(3)
+    for n in (1, 257, 100_003, 3 * 64 ** 3):
+        a = rng.normal(size=n).astype(np.float32)
+        b = rng.normal(size=n).astype(np.float32)
+        out = g.reduce_pair(t(a), t(b)).cpu().numpy()
+        a64, b64 = a.astype(np.float64), b.astype(np.float64)
+        np.testing.assert_allclose(out, [((a64 - b64) ** 2).sum(), (b64 ** 2).sum(), (a64 * b64).sum()],
+                                   rtol=1e-12)
+        out0 = g.reduce_pair(t(a)).cpu().numpy()
+        np.testing.assert_allclose(out0[0], (a64 ** 2).sum(), rtol=1e-12)
+    empty = torch.empty(0, device=dev())
+    np.testing.assert_array_equal(g.reduce_pair(empty).cpu().numpy(), [0.0, 0.0, 0.0])
+
+
+def test_reduce_moments_matches_macros():
+    nx, ny, nz = 33, 17, 9
+    shape = (nz, ny, nx)
+    g, _ = make_pair(nx, ny, nz, 0.05, walls=2)
+    F = synthetic.gaussian_force(shape, 1e-4, seed=5)
+    g.set_force_field(t(F))
+    g.init_equilibrium(t(synthetic.density_perturbation(shape, 0.01, 6)),
+                       t(synthetic.divfree_velocity(shape, seed=7, umax=0.03)))
+    g.step(7)
+    rho, u = g.macros()
+    m = g.reduce_moments().cpu().numpy()
+    r64, u64 = rho.double().cpu().numpy(), u.double().cpu().numpy()
+    assert m[0] == pytest.approx(r64.sum(), rel=1e-7)
+    np.testing.assert_allclose(m[1:], (r64[None] * u64).sum(axis=(1, 2, 3)), rtol=1e-4, atol=1e-8)
+
+
+@pytest.mark.parametrize("walls", [0, 5])
+def test_set_get_populations_roundtrip(walls):
+    nx, ny, nz = 21, 10, 7
+    g, _ = make_pair(nx, ny, nz, 0.05, walls=walls)
+    h = synthetic.random_deviations((nz, ny, nx), 1e-2, seed=9)
+    g.set_populations(t(h), deviation=True)
+    np.testing.assert_array_equal(g.populations(deviation=True).cpu().numpy(), h)
+    f = h.astype(np.float32) + np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12, np.float32).reshape(19, 1, 1, 1)
+    g.set_populations(t(f), deviation=False)
+    np.testing.assert_allclose(g.populations(deviation=False).cpu().numpy(), f, rtol=0, atol=1e-7)
+
+
+def test_checkpoint_resume_bit_exact():
+    nx, ny, nz = 40, 30, 20
+    shape = (nz, ny, nx)
+    g, _ = make_pair(nx, ny, nz, 0.02, walls=4, s3=1.2)
+    g.set_force_uniform(1e-5, 2e-6)
+    g.init_equilibrium(None, t(synthetic.divfree_velocity(shape, seed=3, umax=0.02)))
+    g.step(60)
+    blob = g.save_state()
+    g.step(40)
+    a = g.populations(deviation=True).cpu()
+    assert g.steps_done == 100
+    g2, _ = make_pair(nx, ny, nz, 0.02, walls=4, s3=1.2)
+    g2.set_force_uniform(1e-5, 2e-6)
+    g2.load_state(blob)
+    assert g2.steps_done == 60
+    g2.step(40)
+    assert torch.equal(a, g2.populations(deviation=True).cpu())
+    # device-side export/import
+    snap = g.export_state()
+    g.step(5)
+    g.import_state(snap, set_steps=100)
+    assert torch.equal(a, g.populations(deviation=True).cpu())
+    with pytest.raises(Exception):
+        g3, _ = make_pair(nx, ny, nz + 1, 0.02, walls=4)
+        g3.load_state(blob)
+
+
+def test_run_host_job_matches_device_path():
+    nx, ny, nz, steps = 48, 32, 24, 25
+    shape = (nz, ny, nx)
+    rho = synthetic.density_perturbation(shape, 1e-3, 1)
+    u = synthetic.divfree_velocity(shape, seed=2, umax=0.02)
+    g, _ = make_pair(nx, ny, nz, 0.05, walls=4)
+    g.set_force_uniform(1e-5)
+    g.init_equilibrium(t(rho), t(u))
+    g.step(steps)
+    r_ref, u_ref = g.macros()
+    m_ref = g.reduce_moments().cpu()
+    g2, _ = make_pair(nx, ny, nz, 0.05, walls=4)
+    g2.set_force_uniform(1e-5)
+    rho_h = torch.from_numpy(rho).pin_memory()
+    u_h = torch.from_numpy(u).pin_memory()
+    r_out = torch.empty(shape).pin_memory()
+    u_out = torch.empty((3,) + shape).pin_memory()
+    mom = torch.empty(4 * steps, dtype=torch.float64).pin_memory()
+    g2.run_host(rho_h, u_h, steps, r_out, u_out, mom)
+    assert torch.equal(r_out, r_ref.cpu())
+    assert torch.equal(u_out, u_ref.cpu())
+    assert torch.equal(mom[-4:], m_ref)
+
+
+def test_instability_flag():
+    g, _ = make_pair(16, 8, 8, 0.05)
+    g.init_equilibrium()
+    g.step(3)
+    g.check()
+    h = torch.zeros(19, 8, 8, 16, device=dev())
+    h[0, 3, 4, 5] = float("nan")
+    g.set_populations(h, deviation=True)
+    g.step(2)
+    with pytest.raises(UnstableError):
+        g.check(clear=True)
+    g.init_equilibrium()
+    g.step(2)
+    g.check()
