@@ -4,6 +4,9 @@ Inputs come from paper_1801_04586_gb300.synthetic as float32; the oracle gets
 the same values widened to float64. Nothing the GPU computes is fed to the
 oracle.
 """
+import json
+import os
+
 import numpy as np
 import torch
 
@@ -46,3 +49,11 @@ def rel_err(f_gpu, f_ora):
 def dev_err(f_gpu, f_ora):
     """Error relative to the size of the deviations from the rest weights."""
     return float(np.max(np.abs(f_gpu - f_ora)) / max(np.max(np.abs(f_ora - W)), 1e-300))
+
+
+def report(name, **values):
+    """Append measured figures to the file named by CLBM_REPORT (if set)."""
+    path = os.environ.get("CLBM_REPORT")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps({"test": name, **values}) + "\n")

@@ -11,7 +11,7 @@ import torch
 
 import analytic as an
 import oracle
-from gpu_common import F32_REL_TOL, W, dev, dev_err, gpu_f, make_pair, rel_err, t
+from gpu_common import F32_REL_TOL, W, dev, dev_err, gpu_f, make_pair, rel_err, report, t
 from paper_1801_04586_gb300 import synthetic
 
 pytestmark = pytest.mark.gpu
@@ -64,6 +64,7 @@ def test_100_steps_parity(case):
     g.step(100)
     fo = oracle.step(o, oracle.init(o, None, u0, F), F, 100)
     fg = gpu_f(g)
+    report("parity_100_steps", case=str(case[:5]), rel=rel_err(fg, fo), dev=dev_err(fg, fo))
     assert rel_err(fg, fo) < F32_REL_TOL
     assert dev_err(fg, fo) < 1e-4
     g.check()
@@ -85,6 +86,7 @@ def test_random_state_parity():
     np.testing.assert_array_equal(g.populations(deviation=True).cpu().numpy(), h0)
     g.step(100)
     fo = oracle.step(o, h0.astype(np.float64) + W, F, 100)
+    report("parity_random_state", rel=rel_err(gpu_f(g), fo), dev=dev_err(gpu_f(g), fo))
     assert rel_err(gpu_f(g), fo) < F32_REL_TOL
 
 
@@ -132,12 +134,14 @@ def test_poiseuille_channel_2000_steps():
     g.init_equilibrium(None, t(u0))
     g.step(steps)
     fo = oracle.step(o, oracle.init(o, None, u0, Ff), Ff, steps, nthreads=0)
+    report("parity_poiseuille_2000", rel=rel_err(gpu_f(g), fo), dev=dev_err(gpu_f(g), fo))
     assert rel_err(gpu_f(g), fo) < F32_REL_TOL
     ux = g.macros()[1][0].double().cpu().numpy()
     uo = oracle.macros(o, fo, Ff)[1][0]
     assert np.max(np.abs(ux - uo)) < 1e-4 * np.max(np.abs(uo))
     ua = an.poiseuille_startup(nz, F, nu, steps)[:, None, None] * np.ones(shape)
     e2 = np.sqrt(((ux - ua) ** 2).sum() / (ua ** 2).sum())
+    report("poiseuille_vs_series", e2=e2)
     assert e2 < 5e-4
 
 
@@ -171,6 +175,7 @@ def test_full_size_kolmogorov_sampled_first_step():
     F = synthetic.profile_to_field(prof, shape)
     fo = oracle.first_step_nodes(o, nodes, None, u0, F)
     err = np.max(np.abs(hg + W.reshape(1, 19) - fo) / np.abs(fo))
+    report("full_size_sampled_first_step", rel=float(err))
     assert err < 1e-6
     g.close()
 
@@ -212,4 +217,6 @@ def test_momentum_grows_by_total_force():
     m1 = g.reduce_moments().cpu().numpy()
     gain = 50 * F.astype(np.float64).sum(axis=(1, 2, 3))
     np.testing.assert_allclose(m1[1:] - m0[1:], gain, rtol=1e-5, atol=1e-9)
-    assert abs(m1[0] - m0[0]) < 1e-9
+    # FP32 rounding of the stored deviations is not exactly mass-conserving: a
+    # random walk of ~1e-10 per node and step (15360 nodes x 50 steps here)
+    assert abs(m1[0] - m0[0]) < 1e-6
