@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--block", default="0,0", help="step kernel block shape bx,by (0,0 = default)")
+    ap.add_argument("--size", type=int, default=N_SIDE,
+                    help="box side (the benchmark workload is 256; smaller sides are for profiling captures)")
     return ap.parse_args()
 
 
@@ -224,9 +226,10 @@ def run_gb300(args):
         dist.barrier()
     dev = torch.device("cuda", torch.cuda.current_device())
     bx, by = (int(v) for v in args.block.split(","))
-    shape = (N_SIDE, N_SIDE, N_SIDE)
-    lat = Lattice(N_SIDE, N_SIDE, N_SIDE, NU, walls=0, storage="f32", block=(bx, by), device=dev)
-    prof = torch.from_numpy(synthetic.kolmogorov_profile(N_SIDE, F0)).to(dev)
+    side = args.size
+    shape = (side, side, side)
+    lat = Lattice(side, side, side, NU, walls=0, storage="f32", block=(bx, by), device=dev)
+    prof = torch.from_numpy(synthetic.kolmogorov_profile(side, F0)).to(dev)
     u0_np = synthetic.divfree_velocity(shape, seed=1, umax=UMAX)
     u0 = torch.from_numpy(u0_np).to(dev)
     lat.set_force_profile_z(prof)
@@ -273,7 +276,7 @@ def run_gb300(args):
 
     e2e = None
     if not args.no_e2e:
-        lat_e = Lattice(N_SIDE, N_SIDE, N_SIDE, NU, walls=0, storage="f32", block=(bx, by), device=dev)
+        lat_e = Lattice(side, side, side, NU, walls=0, storage="f32", block=(bx, by), device=dev)
         lat_e.set_force_profile_z(prof)
         rho_h = torch.ones(shape, dtype=torch.float32).pin_memory()
         u_h = torch.from_numpy(u0_np).pin_memory()
@@ -313,7 +316,8 @@ def run_gb300(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": N_SIDE, "ny": N_SIDE, "nz": N_SIDE, "nu": NU, "F0": F0,
+            "config": {"workload": WORKLOAD if side == N_SIDE else WORKLOAD.replace("256", str(side)),
+                       "nx": side, "ny": side, "nz": side, "nu": NU, "F0": F0,
                        "storage": "f32 A/B pull", "block": [info["block_x"], info["block_y"]],
                        "l2": "inputs larger than L2: two 1.27 GB population buffers vs 129 MB L2, no flush",
                        "parallelism": f"{ws} independent replica(s), one per GPU"},

@@ -63,7 +63,7 @@ extern "C" {
  * s0 = s1 = 1 (Sec. III); the method's result does not depend on them.
  * walls: CLBM_WALL_* bits; an axis without a bit is periodic.
  * block_x, block_y: CUDA block shape of the step kernel (block_x a multiple
- *      of 32, block_x*block_y <= 1024); 0 selects the built-in default. */
+ *      of 32, block_x*block_y <= 512); 0 selects the built-in default. */
 typedef struct clbm_params {
     int32_t nx, ny, nz;
     uint32_t walls;
@@ -179,6 +179,34 @@ int clbm_load_state(clbm_ctx *ctx, const void *host_buf, size_t bytes);
  * should be pinned for full copy speed. Synchronous. */
 int clbm_run_host(clbm_ctx *ctx, const float *rho_host, const float *u_host, int64_t nsteps,
                   float *rho_out_host, float *u_out_host, double *moments_host);
+
+/* ---- recomputation and adjoint (FP32 storage only; CLBM_ERR_ARG otherwise) ----
+ *
+ * A "raw state" is a device buffer of clbm_info.state_bytes bytes in the
+ * context's internal layout (clbm_export_state); pulling it gives the
+ * post-streaming state f^t. Adjoint arrays (lam, 19 x N floats) are in the
+ * post-streaming layout f[i*N + s]: lam^t = dL/df^t.
+ *
+ * clbm_step_raw: one time step (as clbm_step) from src_dev into dst_dev with
+ * the context's parameters and force; the context's own state and step count
+ * are untouched. src_dev and dst_dev must not overlap.
+ *
+ * clbm_adjoint_seed: start the adjoint from a cotangent gu_dev (3 x N floats)
+ * on the Eq. 9 velocity of the state in state_dev (NULL: the context's current
+ * state): lam_i = sum_a gu_a (e_ia - u_a)/rho is written to lam_dev, and
+ * gF_dev (3 x N) is SET to the direct term gu/(2 rho) of Eq. 9.
+ *
+ * clbm_adjoint_step: adjoint of the step f^{t+1} = P C(f^t, F) (Eqs. 5, 7, 8,
+ * 9), with f^t the pull of state_dev: lam_dev = J_f^T lam*, where lam* is
+ * lam_next_dev read at the slot each population streams into (periodic wrap,
+ * or its opposite at its own node across a wall face), and gF_dev +=
+ * J_F^T lam* (dL/dF of a force field, accumulated). lam_dev must not alias
+ * lam_next_dev. The force in use is the context's (any mode; for a uniform or
+ * profile force gF is still per node). */
+int clbm_step_raw(clbm_ctx *ctx, const void *src_dev, void *dst_dev);
+int clbm_adjoint_seed(clbm_ctx *ctx, const void *state_dev, const float *gu_dev, float *lam_dev, float *gF_dev);
+int clbm_adjoint_step(clbm_ctx *ctx, const void *state_dev, const float *lam_next_dev, float *lam_dev,
+                      float *gF_dev);
 
 /* Text for a status code; clbm_last_error(): message of this thread's last
  * failure ("" if none). Both strings are owned by the library. */

@@ -61,6 +61,9 @@ SIGNATURES = {
     "clbm_save_state": [P, P, ctypes.POINTER(ctypes.c_size_t)],
     "clbm_load_state": [P, P, ctypes.c_size_t],
     "clbm_run_host": [P, P, P, I64, P, P, P],
+    "clbm_step_raw": [P, P, P],
+    "clbm_adjoint_seed": [P, P, P, P, P],
+    "clbm_adjoint_step": [P, P, P, P, P],
     "clbm_status_string": [I32],
     "clbm_last_error": [],
 }

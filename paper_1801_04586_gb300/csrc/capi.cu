@@ -345,6 +345,35 @@ int clbm_load_state(clbm_ctx *c, const void *host, size_t bytes) {
     return CLBM_OK;
 }
 
+int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
+    if (!c || !src || !dst) return fail(CLBM_ERR_ARG, "clbm_step_raw: null pointer");
+    const size_t bytes = (size_t)kQ * c->g.stride * c->elem;
+    if ((const char *)src < (const char *)dst + bytes && (const char *)dst < (const char *)src + bytes)
+        return fail(CLBM_ERR_ARG, "clbm_step_raw: src and dst overlap");
+    cudaError_t e = launch_step(c->p.storage, launch_of(c), src, dst, c->rates, c->force, c->d_flag);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_step_raw");
+    return CLBM_OK;
+}
+
+int clbm_adjoint_seed(clbm_ctx *c, const void *state, const float *gu, float *lam, float *gF) {
+    if (!c || !gu || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: null pointer");
+    if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: FP32 storage only");
+    cudaError_t e = launch_adjoint_seed(c->p.storage, launch_of(c), state ? state : c->buf[c->cur], gu, lam, gF,
+                                        c->force, c->n);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_adjoint_seed");
+    return CLBM_OK;
+}
+
+int clbm_adjoint_step(clbm_ctx *c, const void *state, const float *lam_next, float *lam, float *gF) {
+    if (!c || !state || !lam_next || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: null pointer");
+    if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: FP32 storage only");
+    if (lam == lam_next) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: lam aliases lam_next");
+    cudaError_t e =
+        launch_adjoint_step(c->p.storage, launch_of(c), state, lam_next, lam, gF, c->rates, c->force, c->n);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_adjoint_step");
+    return CLBM_OK;
+}
+
 int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nsteps, float *rho_out,
                   float *u_out, double *moments_h) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_run_host: null context");

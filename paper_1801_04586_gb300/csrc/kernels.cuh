@@ -36,6 +36,10 @@ cudaError_t launch_macros(int storage, const Launch &L, const void *src, const F
                           int64_t n);
 cudaError_t launch_reduce_moments(int storage, const Launch &L, const void *src, const ForceArgs &F,
                                   double *partials, int nblocks, double *out);
+cudaError_t launch_adjoint_step(int storage, const Launch &L, const void *state, const float *lam_next, float *lam,
+                                float *gF, const Rates &r, const ForceArgs &F, int64_t n);
+cudaError_t launch_adjoint_seed(int storage, const Launch &L, const void *state, const float *gu, float *lam,
+                                float *gF, const ForceArgs &F, int64_t n);
 cudaError_t launch_reduce_pair(const float *a, const float *b, int64_t n, double *partials, int nblocks,
                                double *out, cudaStream_t stream);
 

@@ -183,3 +183,28 @@ class Lattice:
     @property
     def steps_done(self) -> int:
         return int(self.info()["steps_done"])
+
+    # ---- recomputation and adjoint (FP32 storage)
+    def step_raw(self, src: torch.Tensor, dst: torch.Tensor):
+        """One step from raw state buffer src into dst (context state untouched)."""
+        nb = self.state_bytes()
+        for name, b in (("src", src), ("dst", dst)):
+            if b.device != self.device or b.numel() * b.element_size() < nb or not b.is_contiguous():
+                raise ValueError(f"{name}: expected a contiguous device buffer of >= {nb} bytes")
+        check(self.lib.clbm_step_raw(self.h, _ptr(src), _ptr(dst)), "clbm_step_raw")
+
+    def adjoint_seed(self, gu: torch.Tensor, lam: torch.Tensor, gF: torch.Tensor,
+                     state: Optional[torch.Tensor] = None):
+        self._dev(gu, (3,) + self.shape, "gu")
+        self._dev(lam, (19,) + self.shape, "lam")
+        self._dev(gF, (3,) + self.shape, "gF")
+        check(self.lib.clbm_adjoint_seed(self.h, _ptr(state), _ptr(gu), _ptr(lam), _ptr(gF)), "clbm_adjoint_seed")
+
+    def adjoint_step(self, state: torch.Tensor, lam_next: torch.Tensor, lam: torch.Tensor, gF: torch.Tensor):
+        self._dev(lam_next, (19,) + self.shape, "lam_next")
+        self._dev(lam, (19,) + self.shape, "lam")
+        self._dev(gF, (3,) + self.shape, "gF")
+        if state.numel() * state.element_size() < self.state_bytes():
+            raise ValueError("state: buffer too small")
+        check(self.lib.clbm_adjoint_step(self.h, _ptr(state), _ptr(lam_next), _ptr(lam), _ptr(gF)),
+              "clbm_adjoint_step")

@@ -1,0 +1,138 @@
+"""The hand-written adjoint kernel against the FP64 oracle adjoint
+(complex-step Jacobians) and against central finite differences of the FP32
+forward, for L = 1/2 sum |u(T) - u*|^2 as a function of a body-force field."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_common import W, dev, make_pair, report, t
+from paper_1801_04586_gb300 import synthetic
+from paper_1801_04586_gb300.autograd import final_velocity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("walls", [0, 4, 7])
+def test_single_adjoint_step_matches_oracle(walls):
+    nx, ny, nz = 13, 9, 7
+    shape = (nz, ny, nx)
+    g, o = make_pair(nx, ny, nz, 0.03, walls=walls, s2b=1.2, s3=0.9, s4=1.3)
+    h0 = synthetic.random_deviations(shape, 5e-3, seed=71)
+    F = synthetic.gaussian_force(shape, 1e-3, seed=72)
+    lam_next = synthetic.rng(73).normal(size=(19,) + shape).astype(np.float32)
+    g.set_force_field(t(F))
+    g.set_populations(t(h0), deviation=True)
+    state = g.export_state()
+    lam = g.empty(19, *shape)
+    gF = torch.zeros(3, *shape, device=dev())
+    g.adjoint_step(state, t(lam_next), lam, gF)
+    gFo = np.zeros((3,) + shape)
+    lam_o = oracle.adjoint_step(o, h0.astype(np.float64) + W, lam_next, F, gFo)
+    lam_g = lam.double().cpu().numpy()
+    err_l = np.max(np.abs(lam_g - lam_o)) / np.max(np.abs(lam_o))
+    err_f = np.max(np.abs(gF.double().cpu().numpy() - gFo)) / np.max(np.abs(gFo))
+    report("adjoint_step_vs_oracle", walls=walls, lam=float(err_l), gF=float(err_f))
+    assert err_l < 1e-5
+    assert err_f < 1e-5
+
+
+def test_adjoint_seed_matches_oracle():
+    nx, ny, nz = 11, 8, 6
+    shape = (nz, ny, nx)
+    g, o = make_pair(nx, ny, nz, 0.03, walls=2)
+    h0 = synthetic.random_deviations(shape, 5e-3, seed=74)
+    F = synthetic.gaussian_force(shape, 1e-3, seed=75)
+    gu = synthetic.rng(76).normal(size=(3,) + shape).astype(np.float32)
+    g.set_force_field(t(F))
+    g.set_populations(t(h0), deviation=True)
+    lam = g.empty(19, *shape)
+    gF = g.empty(3, *shape)
+    g.adjoint_seed(t(gu), lam, gF)
+    gFo = np.zeros((3,) + shape)
+    lam_o = oracle.adjoint_seed(o, h0.astype(np.float64) + W, gu, F, gFo)
+    np.testing.assert_allclose(lam.double().cpu().numpy(), lam_o, rtol=0, atol=1e-6 * np.abs(lam_o).max())
+    np.testing.assert_allclose(gF.double().cpu().numpy(), gFo, rtol=0, atol=1e-6 * np.abs(gFo).max())
+
+
+def _oracle_gradient(o, F, u_target, T):
+    shape = o.shape
+    states = [oracle.equilibrium(1.0, np.zeros(3)).reshape(19, 1, 1, 1) * np.ones((19,) + shape)]
+    for _ in range(T):
+        states.append(oracle.step(o, states[-1], F, 1))
+    u = oracle.macros(o, states[-1], F)[1]
+    gF = np.zeros((3,) + shape)
+    lam = oracle.adjoint_seed(o, states[-1], u - u_target, F, gF)
+    for k in range(T - 1, -1, -1):
+        lam = oracle.adjoint_step(o, states[k], lam, F, gF)
+    return gF, u
+
+
+@pytest.mark.parametrize("walls,every", [(0, 4), (4, 5), (6, 7)])
+def test_unrolled_gradient_matches_oracle(walls, every):
+    """The autograd Function (forward with checkpoints, backward recomputation
+    plus adjoint kernel) against the chained FP64 oracle adjoint."""
+    nx, ny, nz, T = 10, 8, 6, 20
+    shape = (nz, ny, nx)
+    g, o = make_pair(nx, ny, nz, 0.02, walls=walls, s2b=1.1, s3=1.2)
+    F = synthetic.gaussian_force(shape, 1e-4, seed=81)
+    ut = synthetic.gaussian_force(shape, 1e-3, seed=82)
+    g.init_equilibrium()  # rest state, independent of F
+    init = g.export_state().clone()
+    Ft = t(F).requires_grad_(True)
+    u = final_velocity(Ft, g, init, T, every)
+    loss = 0.5 * ((u.double() - t(ut).double()) ** 2).sum()
+    loss.backward()
+    gFo, uo = _oracle_gradient(o, F, ut, T)
+    np.testing.assert_allclose(u.detach().double().cpu().numpy(), uo, rtol=0, atol=1e-8)
+    err = np.max(np.abs(Ft.grad.double().cpu().numpy() - gFo)) / np.max(np.abs(gFo))
+    report("unrolled_gradient_vs_oracle", walls=walls, every=every, rel=float(err))
+    assert err < 1e-4
+
+
+def test_gradient_against_finite_differences_64cube():
+    """64^3 periodic box, F ~ N(0, (1e-5)^2) per component (seed 3), nu = 0.02,
+    200 steps with checkpoints every 20, target a divergence-free field with
+    max |u*| = 1e-3 (seed 4): dL/dF against central differences (FP64 loss by
+    the library's reduction) at 32 seeded nodes, all three components."""
+    n, nu, T, every = 64, 0.02, 200, 20
+    shape = (n, n, n)
+    g, _ = make_pair(n, n, n, nu)
+    F = t(synthetic.gaussian_force(shape, 1e-5, seed=3))
+    ut = t(synthetic.divfree_velocity(shape, seed=4, umax=1e-3))
+    g.init_equilibrium()
+    init = g.export_state().clone()
+    Ft = F.clone().requires_grad_(True)
+    u = final_velocity(Ft, g, init, T, every)
+    (0.5 * ((u.double() - ut.double()) ** 2).sum()).backward()
+    grad = Ft.grad.detach()
+
+    def loss(Fv):
+        g.set_force_field(Fv)
+        g.import_state(init, set_steps=0)
+        g.step(T)
+        _, uu = g.macros()
+        return 0.5 * float(g.reduce_pair(uu, ut)[0].item())
+
+    rng = np.random.default_rng(5)
+    nodes = rng.choice(n ** 3, 32, replace=False)
+    h = 1e-6
+    errs = []
+    for s in nodes:
+        for a in range(3):
+            Fp = F.clone()
+            Fm = F.clone()
+            Fp.view(3, -1)[a, s] += h
+            Fm.view(3, -1)[a, s] -= h
+            fd = (loss(Fp) - loss(Fm)) / (2 * h)
+            ad = float(grad.view(3, -1)[a, s].item())
+            errs.append(abs(fd - ad) / max(abs(fd), 1e-30))
+    # a random direction: dot product form
+    v = torch.from_numpy(rng.normal(size=(3,) + shape).astype(np.float32)).to(dev())
+    hv = 1e-7
+    fd = (loss(F + hv * v) - loss(F - hv * v)) / (2 * hv)
+    ad = float((grad.double() * v.double()).sum().item())
+    report("adjoint_vs_fd_64cube", max_rel=max(errs), median_rel=float(np.median(errs)),
+           dir_rel=abs(fd - ad) / abs(fd))
+    assert max(errs) < 1e-3
+    assert abs(fd - ad) < 1e-3 * abs(fd)
