@@ -173,10 +173,16 @@ int clbm_load_state(clbm_ctx *ctx, const void *host_buf, size_t bytes);
  * u_host (3 x N, may be NULL) to the device, initialise as
  * clbm_init_equilibrium, run nsteps steps, then copy Eq. 9 rho and u of the
  * final state back to rho_out_host / u_out_host (either may be NULL). If
- * moments_host is not NULL, after every step the FP64 sums of
- * clbm_reduce_moments are copied back into moments_host[4*k .. 4*k+3]
- * (4 * nsteps doubles), which also checks the instability flag. Host buffers
- * should be pinned for full copy speed. Synchronous. */
+ * moments_host is not NULL it receives 4 * (nsteps + 1) doubles: entry k
+ * (k = 0..nsteps) holds the FP64 sums of clbm_reduce_moments for the state at
+ * step k. For k < nsteps they are formed inside step k+1's kernel from the
+ * state it pulls (block sums, no extra pass over the populations) and copied
+ * back asynchronously after every step; the last comes from one reduction
+ * after the final step. The call synchronises once, at the end, then returns
+ * CLBM_ERR_UNSTABLE if any mass sum is non-finite or the instability flag is
+ * set. Device scratch for the staging fields and block sums is allocated on
+ * first use and kept by the context. Host buffers should be pinned for full
+ * copy speed and for the copies to overlap the steps. */
 int clbm_run_host(clbm_ctx *ctx, const float *rho_host, const float *u_host, int64_t nsteps,
                   float *rho_out_host, float *u_out_host, double *moments_host);
 

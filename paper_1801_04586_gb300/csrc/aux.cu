@@ -1,5 +1,6 @@
 // aux.cu -- kernels around the step: initial equilibrium, state import/export
 // in post-streaming form, Eq. 9 read-out and deterministic FP64 reductions.
+#include "block_reduce.cuh"
 #include "kernels.cuh"
 
 namespace clbm {
@@ -105,30 +106,8 @@ __global__ void k_macros(const S *src, Geom g, ForceArgs F, float *__restrict__ 
     }
 }
 
-// ---- deterministic FP64 reductions: fixed grid, grid-stride loop, shuffle +
-// shared-memory block sum, per-block partials, one final block.
-template <int K>
-__device__ __forceinline__ void block_sum_store(double (&v)[K], double *partials) {
-    __shared__ double sm[32][K];
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) sm[warp][k] = v[k];
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double t = lane < nw ? sm[lane][k] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-            if (lane == 0) partials[(size_t)blockIdx.x * K + k] = t;
-        }
-    }
-}
-
+// ---- deterministic FP64 reductions: fixed grid, grid-stride loop, block
+// sums (block_reduce.cuh) into per-block partials, one final block.
 template <int K>
 __global__ void k_reduce_final(const double *partials, int nblocks, double *out, double add0) {
     double v[K];
@@ -138,9 +117,7 @@ __global__ void k_reduce_final(const double *partials, int nblocks, double *out,
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] += partials[(size_t)b * K + k];
     __shared__ double tmp[K];
-    double *dst = tmp;
-    // reuse the block reduction, writing to shared memory through a 1-block "partials"
-    block_sum_store<K>(v, dst);
+    block_sum_store<K>(v, tmp);
     __syncthreads();
     if (threadIdx.x == 0)
 #pragma unroll
@@ -162,7 +139,7 @@ __global__ void k_reduce_moments(const S *src, Geom g, ForceArgs F, double *part
         const float drho = macros_dev(h, fx, fy, fz, jx, jy, jz);
         v[0] += drho; v[1] += jx; v[2] += jy; v[3] += jz;
     }
-    block_sum_store<4>(v, partials);
+    block_sum_store<4>(v, partials + (size_t)blockIdx.x * 4);
 }
 
 __global__ void k_reduce_pair(const float *__restrict__ a, const float *__restrict__ b, int64_t n,
@@ -173,7 +150,7 @@ __global__ void k_reduce_pair(const float *__restrict__ a, const float *__restri
         const double d = av - bv;
         v[0] += d * d; v[1] += bv * bv; v[2] += av * bv;
     }
-    block_sum_store<3>(v, partials);
+    block_sum_store<3>(v, partials + (size_t)blockIdx.x * 3);
 }
 
 // ---- dispatch helpers
@@ -260,6 +237,12 @@ cudaError_t launch_reduce_moments(int storage, const Launch &L, const void *src,
     if (e != cudaSuccess) return e;
     const double n = (double)L.g.nx * L.g.ny * L.g.nz;
     k_reduce_final<4><<<1, 256, 0, L.stream>>>(partials, nblocks, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_final4(const double *partials, int nblocks, double *out, double add0,
+                                 cudaStream_t stream) {
+    k_reduce_final<4><<<1, 256, 0, stream>>>(partials, nblocks, out, add0);
     return cudaGetLastError();
 }
 

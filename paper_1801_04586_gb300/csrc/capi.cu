@@ -39,6 +39,8 @@ struct StateHeader {
 
 }  // namespace
 
+int clbm::set_error(int code, const char *msg) { return fail(code, msg); }
+
 struct clbm_ctx {
     clbm_params p;
     Geom g;
@@ -52,8 +54,10 @@ struct clbm_ctx {
     ForceArgs force;
     int *d_flag;
     double *d_partials;
-    float *d_io;          // 4 x N floats for clbm_run_host (allocated on first use)
-    double *d_mom;        // 4 doubles for clbm_run_host
+    float *d_io;          // clbm_run_host scratch (first use): 4 x N floats, then
+    double *d_mom;        //   4 doubles of sums and
+    double *d_diag;       //   4 doubles per step-kernel block
+    int64_t diag_blocks;
     int64_t steps_done;
     dim3 block;
 };
@@ -167,7 +171,6 @@ int clbm_destroy(clbm_ctx *c) {
     cudaFree(c->buf[0]);
     cudaFree(c->d_flag);
     if (c->d_io) cudaFree(c->d_io);
-    if (c->d_mom) cudaFree(c->d_mom);
     delete c;
     return CLBM_OK;
 }
@@ -378,18 +381,24 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
                   float *u_out, double *moments_h) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_run_host: null context");
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_run_host: nsteps < 0");
+    const Launch L = launch_of(c);
+    const int64_t nblocks = (int64_t)L.grid.x * L.grid.y * L.grid.z;
     cudaError_t e;
-    if (!c->d_io) {
-        if ((e = cudaMalloc(&c->d_io, sizeof(float) * 4 * (size_t)c->n)) != cudaSuccess) {
+    if (!c->d_io || c->diag_blocks < nblocks) {
+        if (c->d_io) cudaFree(c->d_io);
+        const size_t bytes = sizeof(float) * 4 * (size_t)c->n + 256 + sizeof(double) * (4 * (size_t)nblocks + 4);
+        void *p = nullptr;
+        if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) {
             c->d_io = nullptr;
+            c->diag_blocks = 0;
             cudaGetLastError();
             return fail(CLBM_ERR_OOM, "clbm_run_host: cudaMalloc failed");
         }
-        if ((e = cudaMalloc(&c->d_mom, sizeof(double) * 4)) != cudaSuccess) {
-            c->d_mom = nullptr;
-            cudaGetLastError();
-            return fail(CLBM_ERR_OOM, "clbm_run_host: cudaMalloc failed");
-        }
+        c->d_io = (float *)p;
+        const size_t io = (sizeof(float) * 4 * (size_t)c->n + 255) / 256 * 256;
+        c->d_mom = (double *)((char *)p + io);
+        c->d_diag = c->d_mom + 4;
+        c->diag_blocks = nblocks;
     }
     float *d_rho = c->d_io, *d_u = c->d_io + c->n;
     const size_t nb = sizeof(float) * (size_t)c->n;
@@ -400,14 +409,25 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     int rc = clbm_init_equilibrium(c, rho_h ? d_rho : nullptr, u_h ? d_u : nullptr);
     if (rc != CLBM_OK) return rc;
     for (int64_t t = 0; t < nsteps; ++t) {
-        if ((rc = clbm_step(c, 1)) != CLBM_OK) return rc;
         if (moments_h) {
-            if ((rc = clbm_reduce_moments(c, c->d_mom)) != CLBM_OK) return rc;
-            e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: moments");
-            if (!std::isfinite(moments_h[4 * t])) return fail(CLBM_ERR_UNSTABLE, "clbm_run_host: non-finite mass");
+            // fused step: FP64 sums of the state it pulls (state t) into per-block partials
+            e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force, c->d_flag,
+                                 c->d_diag);
+            if (e == cudaSuccess) e = launch_reduce_final4(c->d_diag, (int)nblocks, c->d_mom, (double)c->n, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                                    c->stream);
+        } else {
+            e = launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force, c->d_flag);
         }
+        if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: step");
+        c->cur ^= 1;
+        ++c->steps_done;
+    }
+    if (moments_h) {
+        if ((rc = clbm_reduce_moments(c, c->d_mom)) != CLBM_OK) return rc;
+        e = cudaMemcpyAsync(moments_h + 4 * nsteps, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: moments");
     }
     if ((rho_out || u_out) && (rc = clbm_get_macros(c, rho_out ? d_rho : nullptr, u_out ? d_u : nullptr)) != CLBM_OK)
         return rc;
@@ -416,6 +436,9 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     if (u_out && (e = cudaMemcpyAsync(u_out, d_u, 3 * nb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
         return cuda_fail(e, "clbm_run_host: copy u back");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e, "clbm_run_host");
+    if (moments_h)
+        for (int64_t t = 0; t <= nsteps; ++t)
+            if (!std::isfinite(moments_h[4 * t])) return fail(CLBM_ERR_UNSTABLE, "clbm_run_host: non-finite mass");
     return clbm_check(c, 0);
 }
 

@@ -220,8 +220,10 @@ __device__ __forceinline__ void inverse_moments(const Moments &q, float (&h)[kQ]
 }
 
 // One collision (Steps 1-3 of Sec. II.B) on deviations h, in place.
-// Returns drho = rho - 1 of the pre-collision state (Eq. 9).
-__device__ __forceinline__ float collide(float (&h)[kQ], float Fx, float Fy, float Fz, const Rates &r) {
+// Returns drho = rho - 1 of the pre-collision state (Eq. 9); if j_out is not
+// null it receives rho*u of Eq. 9 (momentum including F/2).
+__device__ __forceinline__ float collide(float (&h)[kQ], float Fx, float Fy, float Fz, const Rates &r,
+                                         float3 *j_out = nullptr) {
     Moments k;
     raw_moments(h, k);
     const float drho = k.m000;
@@ -229,6 +231,7 @@ __device__ __forceinline__ float collide(float (&h)[kQ], float Fx, float Fy, flo
     const float inv = 1.0f / rho;
     const float jx = fmaf(0.5f, Fx, k.m100), jy = fmaf(0.5f, Fy, k.m010), jz = fmaf(0.5f, Fz, k.m001);
     const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    if (j_out) *j_out = make_float3(jx, jy, jz);
     EqDev e;
     eq_dev(drho, rho, jx, jy, jz, ux, uy, uz, e);
 

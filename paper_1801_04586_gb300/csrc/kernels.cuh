@@ -28,6 +28,10 @@ struct Launch {
 // storage: 0 = f32, 1 = f16, 2 = bf16 (CLBM_STORAGE_*)
 cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
                         const ForceArgs &F, int *flag);
+cudaError_t launch_step_diag(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
+                             const ForceArgs &F, int *flag, double *partials);
+cudaError_t launch_reduce_final4(const double *partials, int nblocks, double *out, double add0,
+                                 cudaStream_t stream);
 cudaError_t launch_scatter(int storage, const Launch &L, void *dst, const float *f, int64_t n, int deviation);
 cudaError_t launch_init_eq(int storage, const Launch &L, void *dst, const float *rho, const float *u, int64_t n,
                            const ForceArgs &F);
@@ -42,5 +46,8 @@ cudaError_t launch_adjoint_seed(int storage, const Launch &L, const void *state,
                                 float *gF, const ForceArgs &F, int64_t n);
 cudaError_t launch_reduce_pair(const float *a, const float *b, int64_t n, double *partials, int nblocks,
                                double *out, cudaStream_t stream);
+
+// Record `msg` as the calling thread's last error (clbm_last_error) and return code.
+int set_error(int code, const char *msg);
 
 }  // namespace clbm
