@@ -214,6 +214,24 @@ int clbm_adjoint_seed(clbm_ctx *ctx, const void *state_dev, const float *gu_dev,
 int clbm_adjoint_step(clbm_ctx *ctx, const void *state_dev, const float *lam_next_dev, float *lam_dev,
                       float *gF_dev);
 
+/* ---- FP64 pair reduction without a context or allocation ----
+ *
+ * Same sums as clbm_reduce_pair (out_dev[0] = sum (a-b)^2, out_dev[1] =
+ * sum b^2, out_dev[2] = sum a*b over n floats; b_dev may be NULL), enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default) of the current device. The
+ * paper has no counterpart: this exists for callers that cannot allocate
+ * device memory, because cudaMalloc/cudaFree can synchronise the device and
+ * can fail with out-of-memory (for example a hook inside a running simulation,
+ * or code beside a caching allocator that holds nearly all device memory).
+ * It allocates nothing and needs no context: the per-block partial sums live
+ * in a fixed 384 KiB __device__ array that every GPU loading the library holds
+ * until exit. n may not exceed 134,217,728 (CLBM_ERR_ARG, with a message).
+ * The first call on each device looks up that array's device address; make it
+ * before any stream capture. All calls on a device share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller. The sums may
+ * differ from clbm_reduce_pair's in the last bits (different block count). */
+int clbm_reduce_pair_noalloc(const float *a_dev, const float *b_dev, int64_t n, double *out_dev, void *stream);
+
 /* Text for a status code; clbm_last_error(): message of this thread's last
  * failure ("" if none). Both strings are owned by the library. */
 const char *clbm_status_string(int status);
