@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16, adjoint and batched lines")
     ap.add_argument("--block", default="0,0", help="step kernel block shape bx,by (0,0 = default)")
     ap.add_argument("--size", type=int, default=N_SIDE,
                     help="box side (the benchmark workload is 256; smaller sides are for profiling captures)")
@@ -205,6 +206,116 @@ def run_reference(args):
     return 0
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def bench_storage(storage, K, warmup, dev, side, prof, u0, peak):
+    """The same workload with populations stored as FP16/BF16 deviations."""
+    import torch
+
+    from paper_1801_04586_gb300 import Lattice
+    lat = Lattice(side, side, side, NU, storage=storage, device=dev)
+    lat.set_force_profile_z(prof)
+    lat.init_equilibrium(None, u0)
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record(lat.stream)
+    lat.step(K)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    lat.check()
+    ms = e0.elapsed_time(e1)
+    n = lat.n
+    lat.close()
+    achieved = 76 * n / (ms / K * 1e-3) / 1e9
+    return {"value": n * K / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / K, "bytes_per_node": 76,
+            "achieved_gbs": achieved, "frac": achieved / peak}
+
+
+def bench_adjoint(dev, side, K, peak):
+    """Adjoint step kernel versus forward step kernel on the same lattice with a
+    force field (F ~ N(0, 1e-5^2), seed 3): per-launch times."""
+    import numpy as np
+    import torch
+
+    from paper_1801_04586_gb300 import Lattice, synthetic
+    shape = (side, side, side)
+    lat = Lattice(side, side, side, 0.02, device=dev)
+    F = torch.from_numpy(synthetic.gaussian_force(shape, 1e-5, seed=3)).to(dev)
+    lat.set_force_field(F)
+    lat.init_equilibrium()
+    lat.step(5)
+    state = lat.export_state()
+    lam = torch.from_numpy(synthetic.rng(4).normal(size=(19,) + shape).astype(np.float32)).to(dev) \
+        if side <= 64 else torch.full((19,) + shape, 1e-3, device=dev)
+    lam2 = torch.empty_like(lam)
+    gF = torch.zeros((3,) + shape, device=dev)
+    for _ in range(3):
+        lat.adjoint_step(state, lam, lam2, gF)
+    lat.step(3)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record(lat.stream)
+    lat.step(K)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    ms_f = e0.elapsed_time(e1) / K
+    e0.record(lat.stream)
+    a, b = lam, lam2
+    for _ in range(K):
+        lat.adjoint_step(state, a, b, gF)
+        a, b = b, a
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    ms_a = e0.elapsed_time(e1) / K
+    n = lat.n
+    lat.close()
+    return {"forward_ms": ms_f, "adjoint_ms": ms_a, "ratio": ms_a / ms_f,
+            "forward_gbs": 164 * n / (ms_f * 1e-3) / 1e9, "adjoint_gbs": 264 * n / (ms_a * 1e-3) / 1e9,
+            "adjoint_frac": 264 * n / (ms_a * 1e-3) / 1e9 / peak}
+
+
+def bench_unroll(dev, reps=3):
+    """The differentiable 64^3 box: 200-step unroll with checkpoints every 20,
+    full backward (recompute + adjoint) over full forward (steps + checkpoints)."""
+    import torch
+
+    from paper_1801_04586_gb300 import Lattice, synthetic
+    from paper_1801_04586_gb300.autograd import final_velocity
+    n = 64
+    shape = (n, n, n)
+    lat = Lattice(n, n, n, 0.02, device=dev)
+    F = torch.from_numpy(synthetic.gaussian_force(shape, 1e-5, seed=3)).to(dev)
+    ut = torch.from_numpy(synthetic.divfree_velocity(shape, seed=4, umax=1e-3)).to(dev)
+    lat.init_equilibrium()
+    init = lat.export_state().clone()
+    fw, bw = [], []
+    for _ in range(reps + 1):
+        Ft = F.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        u = final_velocity(Ft, lat, init, 200, 20)
+        e1.record()
+        loss = 0.5 * ((u - ut) ** 2).sum()
+        g = torch.autograd.grad(loss, [u])[0]
+        e1b = torch.cuda.Event(enable_timing=True)
+        e1b.record()
+        u.backward(g)
+        e2.record()
+        torch.cuda.synchronize()
+        fw.append(e0.elapsed_time(e1))
+        bw.append(e1b.elapsed_time(e2))
+    lat.close()
+    fwm, bwm = statistics.median(fw[1:]), statistics.median(bw[1:])
+    return {"forward_ms": fwm, "backward_ms": bwm, "ratio": bwm / fwm, "steps": 200, "checkpoint_every": 20,
+            "note": "64^3 is L2-resident: time ratio, not a roofline figure"}
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -304,6 +415,16 @@ def run_gb300(args):
                        "sums (formed in the step kernel) copied back, final rho,u read back"}
         lat_e.close()
 
+    variants = None
+    if not args.no_variants:
+        import numpy as np  # noqa: F401
+        variants = {
+            "f16_storage": bench_storage("f16", K, args.warmup, dev, side, prof, u0, peak),
+            "bf16_storage": bench_storage("bf16", K, args.warmup, dev, side, prof, u0, peak),
+            "adjoint_kernel_256": bench_adjoint(dev, side, max(10, min(K, 100)), peak),
+            "adjoint_unroll_64": bench_unroll(dev),
+        }
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
@@ -327,6 +448,7 @@ def run_gb300(args):
                          "algorithmic_bytes_per_launch": BYTES_PER_NODE * nodes, "kernel": "k_step<float,1,false>"},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "variants": variants,
             "gpu_launches": K,
             "clocks": clocks,
         }

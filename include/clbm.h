@@ -210,6 +210,17 @@ int clbm_run_host(clbm_ctx *ctx, const float *rho_host, const float *u_host, int
  * lam_next_dev. The force in use is the context's (any mode; for a uniform or
  * profile force gF is still per node). */
 int clbm_step_raw(clbm_ctx *ctx, const void *src_dev, void *dst_dev);
+
+/* Backward pass over one checkpointed segment of k >= 1 steps (Eqs. 5, 7, 8,
+ * 9 reversed): recompute the segment's states 1..k-1 from its checkpoint
+ * ckpt_dev (state 0, a raw state) into tape_dev ((k-1) * state_bytes bytes,
+ * may be NULL when k == 1), then apply clbm_adjoint_step k times back to
+ * front. On entry lam_dev holds the adjoint at the end of the segment; on
+ * return it holds the adjoint at its start. lam_tmp_dev (19 x N floats) is
+ * scratch; gF_dev accumulates dL/dF. One call replaces 2k - 1 launches issued
+ * from the caller. */
+int clbm_adjoint_segment(clbm_ctx *ctx, const void *ckpt_dev, void *tape_dev, int64_t k, float *lam_dev,
+                         float *lam_tmp_dev, float *gF_dev);
 int clbm_adjoint_seed(clbm_ctx *ctx, const void *state_dev, const float *gu_dev, float *lam_dev, float *gF_dev);
 int clbm_adjoint_step(clbm_ctx *ctx, const void *state_dev, const float *lam_next_dev, float *lam_dev,
                       float *gF_dev);

@@ -64,6 +64,7 @@ SIGNATURES = {
     "clbm_step_raw": [P, P, P],
     "clbm_adjoint_seed": [P, P, P, P, P],
     "clbm_adjoint_step": [P, P, P, P, P],
+    "clbm_adjoint_segment": [P, P, P, I64, P, P, P],
     "clbm_reduce_pair_noalloc": [P, P, I64, P, P],
     "clbm_status_string": [I32],
     "clbm_last_error": [],

@@ -3,9 +3,9 @@ field, with gradients from the hand-written adjoint kernel.
 
 Forward runs `nsteps` lattice steps from a fixed initial raw state, keeping a
 checkpoint of the raw state every `every` steps. Backward walks the segments
-from last to first: it recomputes the segment's states from its checkpoint
-straight into a tape (clbm_step_raw, no extra copies), then runs the adjoint
-step kernel back to front, accumulating dL/dF. Memory: one checkpoint per
+from last to first with one clbm_adjoint_segment call each: the segment's
+states are recomputed from its checkpoint straight into a tape (no extra
+copies), then the adjoint step kernel runs back to front, accumulating dL/dF. Memory: one checkpoint per
 segment plus one tape of `every` states.
 """
 from __future__ import annotations
@@ -48,14 +48,9 @@ class ForceToVelocity(torch.autograd.Function):
         gF = lat.empty(3, *lat.shape)
         lat.adjoint_seed(gu, lam, gF, state=ctx.final)
         nb = lat.state_bytes()
-        tape = [None] + [torch.empty(nb, dtype=torch.uint8, device=lat.device) for _ in range(ctx.every - 1)]
+        tape = torch.empty(max(ctx.every - 1, 1) * nb, dtype=torch.uint8, device=lat.device)
         for k, ck in reversed(ctx.ckpts):
-            tape[0] = ck
-            for j in range(1, k):
-                lat.step_raw(tape[j - 1], tape[j])
-            for j in range(k - 1, -1, -1):
-                lat.adjoint_step(tape[j], lam, lam2, gF)
-                lam, lam2 = lam2, lam
+            lat.adjoint_segment(ck, tape, k, lam, lam2, gF)
         ctx.ckpts = None
         return gF, None, None, None, None
 

@@ -30,6 +30,7 @@ int cuda_fail(cudaError_t e, const char *where) {
 size_t elem_size(int storage) { return storage == CLBM_STORAGE_F32 ? 4 : 2; }
 
 constexpr int kReduceBlocks = 4 * 152;  // fixed reduction grid: deterministic sums
+constexpr int kMidBlocks = 152;         // first pass over the step kernel's block sums
 
 struct StateHeader {
     char magic[8];
@@ -56,6 +57,7 @@ struct clbm_ctx {
     double *d_partials;
     float *d_io;          // clbm_run_host scratch (first use): 4 x N floats, then
     double *d_mom;        //   4 doubles of sums and
+    double *d_mid;        //   4 doubles per first-pass block of the partial sums and
     double *d_diag;       //   4 doubles per step-kernel block
     int64_t diag_blocks;
     int64_t steps_done;
@@ -377,6 +379,28 @@ int clbm_adjoint_step(clbm_ctx *c, const void *state, const float *lam_next, flo
     return CLBM_OK;
 }
 
+int clbm_adjoint_segment(clbm_ctx *c, const void *ckpt, void *tape, int64_t k, float *lam, float *lam_tmp,
+                         float *gF) {
+    if (!c || !ckpt || !lam || !lam_tmp || !gF || k < 1 || (k > 1 && !tape) || lam == lam_tmp)
+        return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: bad argument");
+    if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: FP32 storage only");
+    const Launch L = launch_of(c);
+    const size_t sb = (size_t)kQ * c->g.stride * c->elem;
+    auto state = [&](int64_t j) -> const void * { return j == 0 ? ckpt : (const char *)tape + (j - 1) * sb; };
+    cudaError_t e = cudaSuccess;
+    for (int64_t j = 1; j < k && e == cudaSuccess; ++j)
+        e = launch_step(c->p.storage, L, state(j - 1), (char *)tape + (j - 1) * sb, c->rates, c->force, c->d_flag);
+    float *in = lam, *out = lam_tmp;
+    for (int64_t j = k - 1; j >= 0 && e == cudaSuccess; --j) {
+        e = launch_adjoint_step(c->p.storage, L, state(j), in, out, gF, c->rates, c->force, c->n);
+        float *t = in; in = out; out = t;
+    }
+    if (e == cudaSuccess && in != lam)
+        e = cudaMemcpyAsync(lam, in, sizeof(float) * kQ * (size_t)c->n, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_adjoint_segment");
+    return CLBM_OK;
+}
+
 int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nsteps, float *rho_out,
                   float *u_out, double *moments_h) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_run_host: null context");
@@ -386,7 +410,8 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     cudaError_t e;
     if (!c->d_io || c->diag_blocks < nblocks) {
         if (c->d_io) cudaFree(c->d_io);
-        const size_t bytes = sizeof(float) * 4 * (size_t)c->n + 256 + sizeof(double) * (4 * (size_t)nblocks + 4);
+        const size_t bytes =
+            sizeof(float) * 4 * (size_t)c->n + 256 + sizeof(double) * (4 * (size_t)nblocks + 4 + 4 * kMidBlocks);
         void *p = nullptr;
         if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) {
             c->d_io = nullptr;
@@ -397,7 +422,8 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         c->d_io = (float *)p;
         const size_t io = (sizeof(float) * 4 * (size_t)c->n + 255) / 256 * 256;
         c->d_mom = (double *)((char *)p + io);
-        c->d_diag = c->d_mom + 4;
+        c->d_mid = c->d_mom + 4;
+        c->d_diag = c->d_mid + 4 * kMidBlocks;
         c->diag_blocks = nblocks;
     }
     float *d_rho = c->d_io, *d_u = c->d_io + c->n;
@@ -413,7 +439,8 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
             // fused step: FP64 sums of the state it pulls (state t) into per-block partials
             e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force, c->d_flag,
                                  c->d_diag);
-            if (e == cudaSuccess) e = launch_reduce_final4(c->d_diag, (int)nblocks, c->d_mom, (double)c->n, c->stream);
+            if (e == cudaSuccess)
+                e = launch_sum_partials4(c->d_diag, nblocks, c->d_mid, kMidBlocks, c->d_mom, (double)c->n, c->stream);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                                     c->stream);

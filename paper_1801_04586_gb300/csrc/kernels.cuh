@@ -32,6 +32,8 @@ cudaError_t launch_step_diag(int storage, const Launch &L, const void *src, void
                              const ForceArgs &F, int *flag, double *partials);
 cudaError_t launch_reduce_final4(const double *partials, int nblocks, double *out, double add0,
                                  cudaStream_t stream);
+cudaError_t launch_sum_partials4(const double *partials, int64_t nblocks, double *mid, int mid_blocks, double *out,
+                                 double add0, cudaStream_t stream);
 cudaError_t launch_scatter(int storage, const Launch &L, void *dst, const float *f, int64_t n, int deviation);
 cudaError_t launch_init_eq(int storage, const Launch &L, void *dst, const float *rho, const float *u, int64_t n,
                            const ForceArgs &F);

@@ -7,7 +7,6 @@
 // read-only path so that the +-1 x-shifted reads of neighbouring threads share
 // L1 sectors; stores are coalesced and aligned. One thread per node, x
 // fastest, so each warp touches 19 contiguous 128-byte segments per direction.
-#include "block_reduce.cuh"
 #include "kernels.cuh"
 
 namespace clbm {
@@ -28,78 +27,54 @@ __device__ __forceinline__ void force_at(const ForceArgs &F, const Geom &g, int 
     }
 }
 
-// DIAG: also sum, in FP64 over the block, the Eq. 9 density deviation and
-// momentum of the state this step pulls (the state before the step) and write
-// the four totals to partials[block]; a final pass adds the blocks.
-template <typename S, int FM, bool WALLS, bool DIAG>
+template <typename S, int FM, bool WALLS>
 __global__ void __launch_bounds__(512) k_step(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r,
-                                              ForceArgs F, int *__restrict__ flag, double *__restrict__ partials) {
+                                              ForceArgs F, int *__restrict__ flag) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    const bool active = x < g.nx && y < g.ny;
-    if (!DIAG && !active) return;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (active) {
-        uint32_t off[kQ];
-        int pop[kQ];
-        pull_sources<WALLS>(g, x, y, z, off, pop);
-        float h[kQ];
+    if (x >= g.nx || y >= g.ny) return;
+    uint32_t off[kQ];
+    int pop[kQ];
+    pull_sources<WALLS>(g, x, y, z, off, pop);
+    float h[kQ];
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
-        float fx, fy, fz;
-        force_at<FM>(F, g, z, off[0], fx, fy, fz);
-        float3 j;
-        const float drho = collide(h, fx, fy, fz, r, DIAG ? &j : nullptr);
-        if (!(fabsf(drho) < 0.9f)) *flag = 1;
-        S *d = dst + off[0];
+    for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
+    float fx, fy, fz;
+    force_at<FM>(F, g, z, off[0], fx, fy, fz);
+    const float drho = collide(h, fx, fy, fz, r);
+    if (!(fabsf(drho) < 0.9f)) *flag = 1;
+    S *d = dst + off[0];
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) d[(size_t)i * g.stride] = Codec<S>::from_f(h[i]);
-        if (DIAG) { v[0] = drho; v[1] = j.x; v[2] = j.y; v[3] = j.z; }
-    }
-    if (DIAG) {
-        const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        block_sum_store<4>(v, partials + 4 * b);
-    }
+    for (int i = 0; i < kQ; ++i) d[(size_t)i * g.stride] = Codec<S>::from_f(h[i]);
 }
 
-template <typename S, int FM, bool DIAG>
+template <typename S, int FM>
 static cudaError_t step_walls(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
-                              int *flag, double *partials) {
+                              int *flag) {
     if (L.g.walls)
-        k_step<S, FM, true, DIAG><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag,
-                                                                    partials);
+        k_step<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag);
     else
-        k_step<S, FM, false, DIAG><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag,
-                                                                     partials);
+        k_step<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag);
     return cudaGetLastError();
 }
 
-template <typename S, bool DIAG>
+template <typename S>
 static cudaError_t step_force(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
-                              int *flag, double *partials) {
+                              int *flag) {
     switch (F.mode) {
-        case kForceUniform: return step_walls<S, kForceUniform, DIAG>(L, src, dst, r, F, flag, partials);
-        case kForceProfileZ: return step_walls<S, kForceProfileZ, DIAG>(L, src, dst, r, F, flag, partials);
-        default: return step_walls<S, kForceField, DIAG>(L, src, dst, r, F, flag, partials);
+        case kForceUniform: return step_walls<S, kForceUniform>(L, src, dst, r, F, flag);
+        case kForceProfileZ: return step_walls<S, kForceProfileZ>(L, src, dst, r, F, flag);
+        default: return step_walls<S, kForceField>(L, src, dst, r, F, flag);
     }
 }
 
 cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
                         const ForceArgs &F, int *flag) {
     switch (storage) {
-        case 0: return step_force<float, false>(L, src, dst, r, F, flag, nullptr);
-        case 1: return step_force<__half, false>(L, src, dst, r, F, flag, nullptr);
-        default: return step_force<__nv_bfloat16, false>(L, src, dst, r, F, flag, nullptr);
-    }
-}
-
-cudaError_t launch_step_diag(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
-                             const ForceArgs &F, int *flag, double *partials) {
-    switch (storage) {
-        case 0: return step_force<float, true>(L, src, dst, r, F, flag, partials);
-        case 1: return step_force<__half, true>(L, src, dst, r, F, flag, partials);
-        default: return step_force<__nv_bfloat16, true>(L, src, dst, r, F, flag, partials);
+        case 0: return step_force<float>(L, src, dst, r, F, flag);
+        case 1: return step_force<__half>(L, src, dst, r, F, flag);
+        default: return step_force<__nv_bfloat16>(L, src, dst, r, F, flag);
     }
 }
 

@@ -208,3 +208,17 @@ class Lattice:
             raise ValueError("state: buffer too small")
         check(self.lib.clbm_adjoint_step(self.h, _ptr(state), _ptr(lam_next), _ptr(lam), _ptr(gF)),
               "clbm_adjoint_step")
+
+    def adjoint_segment(self, ckpt: torch.Tensor, tape: Optional[torch.Tensor], k: int, lam: torch.Tensor,
+                        lam_tmp: torch.Tensor, gF: torch.Tensor):
+        """Backward over one checkpointed segment of k steps (recompute into tape,
+        then k adjoint steps); lam holds the adjoint at the segment end on entry
+        and at its start on return."""
+        nb = self.state_bytes()
+        if k > 1 and (tape is None or tape.numel() * tape.element_size() < (k - 1) * nb):
+            raise ValueError("tape too small")
+        for name, a in (("lam", lam), ("lam_tmp", lam_tmp)):
+            self._dev(a, (19,) + self.shape, name)
+        self._dev(gF, (3,) + self.shape, "gF")
+        check(self.lib.clbm_adjoint_segment(self.h, _ptr(ckpt), _ptr(tape), int(k), _ptr(lam), _ptr(lam_tmp),
+                                            _ptr(gF)), "clbm_adjoint_segment")
