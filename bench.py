@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16, adjoint and batched lines")
+    ap.add_argument("--batch-steps", type=int, default=5000, help="steps per mode of the 64-domain batch")
     ap.add_argument("--block", default="0,0", help="step kernel block shape bx,by (0,0 = default)")
     ap.add_argument("--size", type=int, default=N_SIDE,
                     help="box side (the benchmark workload is 256; smaller sides are for profiling captures)")
@@ -316,6 +317,38 @@ def bench_unroll(dev, reps=3):
             "note": "64^3 is L2-resident: time ratio, not a roofline figure"}
 
 
+def bench_batch(dev, steps, peak):
+    """64 independent channels/ducts (sides U{32..128}, nu U[0.005, 0.1],
+    F_x U[1e-7, 1e-5], seed 6): autotuned block, then the whole batch stepped
+    with one launch per step replayed from a CUDA graph, one launch per step
+    issued directly, and one launch per domain per step."""
+    import torch
+
+    from paper_1801_04586_gb300 import Batch, synthetic
+    doms = synthetic.batch_domains(64, seed=6)
+    b = Batch(doms, device=dev)
+    b.init_equilibrium()
+    bx, by = b.autotune(trial_steps=10)
+    b.step(32, Batch.GRAPH)
+    nodes = b.total_nodes
+    out = {"domains": len(doms), "total_nodes": nodes, "steps": steps, "block": [bx, by]}
+    for name, mode in (("graph", Batch.GRAPH), ("direct", Batch.DIRECT), ("per_domain", Batch.PER_DOMAIN)):
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record(b.stream)
+        b.step(steps, mode)
+        e1.record(b.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name + "_mlups"] = nodes * steps / (ms * 1e-3) / 1e6
+    b.check()
+    b.close()
+    out["graph_vs_per_domain"] = out["graph_mlups"] / out["per_domain_mlups"]
+    out["graph_gbs"] = BYTES_PER_NODE * out["graph_mlups"] * 1e6 / 1e9
+    out["graph_frac"] = out["graph_gbs"] / peak
+    return out
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -423,6 +456,7 @@ def run_gb300(args):
             "bf16_storage": bench_storage("bf16", K, args.warmup, dev, side, prof, u0, peak),
             "adjoint_kernel_256": bench_adjoint(dev, side, max(10, min(K, 100)), peak),
             "adjoint_unroll_64": bench_unroll(dev),
+            "batched_64_domains": bench_batch(dev, args.batch_steps, peak),
         }
 
     cpu = None

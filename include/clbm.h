@@ -45,9 +45,17 @@ extern "C" {
 #define CLBM_ERR_STATE    -5  /* call not valid in the context's current state */
 
 /* ---- storage formats of the populations (deviations f - w_i) ---- */
-#define CLBM_STORAGE_F32   0
-#define CLBM_STORAGE_F16   1  /* IEEE binary16, round to nearest even */
-#define CLBM_STORAGE_BF16  2  /* bfloat16, round to nearest even */
+#define CLBM_STORAGE_F32     0
+#define CLBM_STORAGE_F16     1  /* IEEE binary16, round to nearest even */
+#define CLBM_STORAGE_BF16    2  /* bfloat16, round to nearest even */
+/* Stochastic rounding of the step's stores: the value rounds up with
+ * probability equal to the dropped fraction of a unit in the last place, so
+ * stored deviations are unbiased and per-step increments far below the
+ * format's resolution are not lost. The dither comes from a counter-based hash
+ * of (step, node, direction): runs are reproducible. Initialisation and
+ * clbm_set_populations round to nearest. Not available in batches. */
+#define CLBM_STORAGE_F16_SR  3
+#define CLBM_STORAGE_BF16_SR 4
 
 /* ---- wall axes: both faces of the axis are halfway bounce-back walls ---- */
 #define CLBM_WALL_X 1u
@@ -242,6 +250,65 @@ int clbm_adjoint_step(clbm_ctx *ctx, const void *state_dev, const float *lam_nex
  * overlap on the GPU race and must be serialised by the caller. The sums may
  * differ from clbm_reduce_pair's in the last bits (different block count). */
 int clbm_reduce_pair_noalloc(const float *a_dev, const float *b_dev, int64_t n, double *out_dev, void *stream);
+
+/* ---- many independent lattices in one launch per step ----
+ *
+ * A batch holds ndomains complete lattices, each with its own extents, walls,
+ * rates (as clbm_params) and uniform body force, all in one storage format.
+ * Each domain follows exactly the per-node update of clbm_step. The batch
+ * steps all domains with one launch per time step: a grid of (SMs x resident
+ * blocks) walks a work list of tiles (block_x x block_y nodes of one z plane of
+ * one domain). The batch owns its population buffers. */
+typedef struct clbm_domain {
+    int32_t nx, ny, nz;
+    uint32_t walls;
+    double nu, s2b, s3, s4;
+    double fx, fy, fz;
+} clbm_domain;
+
+typedef struct clbm_batch_info {
+    int32_t ndomains;
+    int32_t ntiles, grid, block_x, block_y, graph_steps;
+    int64_t total_nodes;
+    int64_t state_bytes;   /* both buffers: 2 x state_bytes are allocated */
+    int64_t steps_done;
+} clbm_batch_info;
+
+/* Step modes of clbm_batch_step. */
+#define CLBM_BATCH_GRAPH       0  /* one launch per step, replayed from a captured CUDA graph */
+#define CLBM_BATCH_DIRECT      1  /* one launch per step, issued directly */
+#define CLBM_BATCH_PER_DOMAIN  2  /* one clbm_step-style launch per domain per step (reference schedule) */
+
+typedef struct clbm_batch clbm_batch;
+
+/* Create: validates every domain as clbm_create does, allocates the A/B
+ * population buffers of all domains and a work list for block 128 x 2, binds
+ * to `stream`. Populations start at rest (f = w). Errors: CLBM_ERR_ARG,
+ * CLBM_ERR_OOM, CLBM_ERR_CUDA. */
+int clbm_batch_create(const clbm_domain *domains, int32_t ndomains, int32_t storage, void *stream,
+                      clbm_batch **out);
+int clbm_batch_destroy(clbm_batch *b);
+int clbm_batch_get_info(const clbm_batch *b, clbm_batch_info *info);
+/* Rebuild the work list for another block shape (block_x a multiple of 32,
+ * block_x * block_y <= 512). Synchronises the stream. */
+int clbm_batch_set_block(clbm_batch *b, int32_t block_x, int32_t block_y);
+/* Time trial_steps launches for each of a fixed set of block shapes (trials
+ * read the current state and write the other buffer, so the state is not
+ * changed), keep the fastest and report it. Synchronises. */
+int clbm_batch_autotune(clbm_batch *b, int32_t trial_steps, int32_t *block_x_out, int32_t *block_y_out);
+/* Every domain to the generalized equilibrium at rho = 1, u = 0 (u' = -F/2). */
+int clbm_batch_init_equilibrium(clbm_batch *b);
+/* Advance every domain by nsteps steps with the given CLBM_BATCH_* mode. The
+ * graph mode captures graph_steps steps once (on a private stream) and replays
+ * them; remaining steps are launched directly. */
+int clbm_batch_step(clbm_batch *b, int64_t nsteps, int32_t mode);
+/* Per-domain read-out and state, as clbm_get_macros / clbm_get_populations /
+ * clbm_set_populations with the domain's N. */
+int clbm_batch_get_macros(clbm_batch *b, int32_t domain, float *rho_dev, float *u_dev);
+int clbm_batch_get_populations(clbm_batch *b, int32_t domain, float *f_dev, int deviation);
+int clbm_batch_set_populations(clbm_batch *b, int32_t domain, const float *f_dev, int deviation);
+/* Instability flag of the batch, as clbm_check. */
+int clbm_batch_check(clbm_batch *b, int clear);
 
 /* Text for a status code; clbm_last_error(): message of this thread's last
  * failure ("" if none). Both strings are owned by the library. */

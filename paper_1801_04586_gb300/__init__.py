@@ -4,4 +4,5 @@ declared in include/clbm.h) and a thin PyTorch-facing binding.
 """
 from .builder import build  # noqa: F401
 from .lattice import Lattice  # noqa: F401
+from .batch import Batch  # noqa: F401
 from ._capi import CLBMError, UnstableError, WALL_X, WALL_Y, WALL_Z  # noqa: F401

@@ -18,7 +18,7 @@ CLBM_ERR_CUDA = -3
 CLBM_ERR_UNSTABLE = -4
 CLBM_ERR_STATE = -5
 
-STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "f16sr": 3, "bf16sr": 4}
 WALL_X, WALL_Y, WALL_Z = 1, 2, 4
 
 
@@ -27,6 +27,22 @@ class Params(ctypes.Structure):
                 ("walls", ctypes.c_uint32), ("nu", ctypes.c_double), ("s2b", ctypes.c_double),
                 ("s3", ctypes.c_double), ("s4", ctypes.c_double), ("storage", ctypes.c_int32),
                 ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Domain(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("walls", ctypes.c_uint32), ("nu", ctypes.c_double), ("s2b", ctypes.c_double),
+                ("s3", ctypes.c_double), ("s4", ctypes.c_double), ("fx", ctypes.c_double),
+                ("fy", ctypes.c_double), ("fz", ctypes.c_double)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("ndomains", ctypes.c_int32), ("ntiles", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
+                ("total_nodes", ctypes.c_int64), ("state_bytes", ctypes.c_int64), ("steps_done", ctypes.c_int64)]
+
+
+BATCH_GRAPH, BATCH_DIRECT, BATCH_PER_DOMAIN = 0, 1, 2
 
 
 class Info(ctypes.Structure):
@@ -66,6 +82,17 @@ SIGNATURES = {
     "clbm_adjoint_step": [P, P, P, P, P],
     "clbm_adjoint_segment": [P, P, P, I64, P, P, P],
     "clbm_reduce_pair_noalloc": [P, P, I64, P, P],
+    "clbm_batch_create": [P, I32, I32, P, ctypes.POINTER(P)],
+    "clbm_batch_destroy": [P],
+    "clbm_batch_get_info": [P, P],
+    "clbm_batch_set_block": [P, I32, I32],
+    "clbm_batch_autotune": [P, I32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+    "clbm_batch_init_equilibrium": [P],
+    "clbm_batch_step": [P, I64, I32],
+    "clbm_batch_get_macros": [P, I32, P, P],
+    "clbm_batch_get_populations": [P, I32, P, I32],
+    "clbm_batch_set_populations": [P, I32, P, I32],
+    "clbm_batch_check": [P, I32],
     "clbm_status_string": [I32],
     "clbm_last_error": [],
 }

@@ -124,9 +124,23 @@ __global__ void k_reduce_final(const double *partials, int nblocks, double *out,
         for (int k = 0; k < K; ++k) out[k] = tmp[k] + (k == 0 ? add0 : 0.0);
 }
 
+// Fixed-point totals of nblocks partials (one block), as FP64 (+ add0 on the first).
+__global__ void k_fixed_final4(const long long *partials, int nblocks, double *out, double add0) {
+    long long q[4] = {0ll, 0ll, 0ll, 0ll};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] += partials[(size_t)b * 4 + k];
+    __shared__ long long tmp[4];
+    block_sum_fixed<4>(q, tmp);
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = (double)tmp[k] * kFixUnit + (k == 0 ? add0 : 0.0);
+}
+
 template <typename S, int FM, bool WALLS>
-__global__ void k_reduce_moments(const S *src, Geom g, ForceArgs F, double *partials) {
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+__global__ void k_reduce_moments(const S *src, Geom g, ForceArgs F, long long *partials) {
+    long long q[4] = {0ll, 0ll, 0ll, 0ll};
     const int64_t n = (int64_t)g.nx * g.ny * g.nz;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(s % g.nx);
@@ -137,9 +151,9 @@ __global__ void k_reduce_moments(const S *src, Geom g, ForceArgs F, double *part
         float fx, fy, fz, jx, jy, jz;
         force_node<FM>(F, g, z, self, fx, fy, fz);
         const float drho = macros_dev(h, fx, fy, fz, jx, jy, jz);
-        v[0] += drho; v[1] += jx; v[2] += jy; v[3] += jz;
+        q[0] += to_fixed(drho); q[1] += to_fixed(jx); q[2] += to_fixed(jy); q[3] += to_fixed(jz);
     }
-    block_sum_store<4>(v, partials + (size_t)blockIdx.x * 4);
+    block_sum_fixed<4>(q, partials + (size_t)blockIdx.x * 4);
 }
 
 __global__ void k_reduce_pair(const float *__restrict__ a, const float *__restrict__ b, int64_t n,
@@ -154,10 +168,12 @@ __global__ void k_reduce_pair(const float *__restrict__ a, const float *__restri
 }
 
 // ---- dispatch helpers
+// Stochastic formats share the bits of FP16 / BF16; state import and
+// initialisation round them to nearest.
 #define CLBM_DISPATCH_STORAGE(storage, ...)                                 \
     switch (storage) {                                                      \
         case 0: { using S = float; __VA_ARGS__; } break;                    \
-        case 1: { using S = __half; __VA_ARGS__; } break;                   \
+        case 1: case 3: { using S = __half; __VA_ARGS__; } break;           \
         default: { using S = __nv_bfloat16; __VA_ARGS__; } break;           \
     }
 
@@ -219,13 +235,13 @@ cudaError_t launch_macros(int storage, const Launch &L, const void *src, const F
 }
 
 template <typename S, int FM>
-static void moments_t(const Launch &L, const void *src, const ForceArgs &F, double *partials, int nb) {
+static void moments_t(const Launch &L, const void *src, const ForceArgs &F, long long *partials, int nb) {
     if (L.g.walls) k_reduce_moments<S, FM, true><<<nb, 256, 0, L.stream>>>((const S *)src, L.g, F, partials);
     else k_reduce_moments<S, FM, false><<<nb, 256, 0, L.stream>>>((const S *)src, L.g, F, partials);
 }
 
 cudaError_t launch_reduce_moments(int storage, const Launch &L, const void *src, const ForceArgs &F,
-                                  double *partials, int nblocks, double *out) {
+                                  long long *partials, int nblocks, double *out) {
     CLBM_DISPATCH_STORAGE(storage, {
         switch (F.mode) {
             case kForceUniform: moments_t<S, kForceUniform>(L, src, F, partials, nblocks); break;
@@ -236,13 +252,13 @@ cudaError_t launch_reduce_moments(int storage, const Launch &L, const void *src,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const double n = (double)L.g.nx * L.g.ny * L.g.nz;
-    k_reduce_final<4><<<1, 256, 0, L.stream>>>(partials, nblocks, out, n);
+    k_fixed_final4<<<1, 256, 0, L.stream>>>(partials, nblocks, out, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_final4(const double *partials, int nblocks, double *out, double add0,
-                                 cudaStream_t stream) {
-    k_reduce_final<4><<<1, 256, 0, stream>>>(partials, nblocks, out, add0);
+cudaError_t launch_fixed_final4(const long long *partials, int nblocks, double *out, double add0,
+                                cudaStream_t stream) {
+    k_fixed_final4<<<1, 256, 0, stream>>>(partials, nblocks, out, add0);
     return cudaGetLastError();
 }
 

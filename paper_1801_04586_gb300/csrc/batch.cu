@@ -1,0 +1,440 @@
+// batch.cu -- many independent lattices of uneven sizes and parameters stepped
+// by one launch per time step.
+//
+// Every domain is a complete D3Q19 lattice (its own extents, walls, relaxation
+// rates and uniform body force) with the per-node update of the single-lattice
+// kernel (pull, Eqs. 5, 7, 8, 9 in deviation form; see d3q19.cuh). The
+// domains' populations share two A/B allocations, domain after domain, each in
+// the single-lattice layout. A host-built work list cuts every domain into
+// tiles of one block (block_x nodes along x, block_y rows along y, one z
+// plane); a grid of (SMs x resident blocks) walks the list with a stride, so
+// one launch covers all domains with no tail per domain, and consecutive tiles
+// are consecutive in memory. Steps are replayed from a captured CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/clbm.h"
+#include "kernels.cuh"
+
+using namespace clbm;
+
+namespace clbm {
+
+struct DomainDesc {
+    Geom g;
+    Rates r;
+    float fx, fy, fz;
+    int64_t offset;  // element offset of the domain's 19 x stride block in A and in B
+};
+
+template <typename S>
+__global__ void __launch_bounds__(512) k_batch_step(const S *__restrict__ A, S *__restrict__ B,
+                                                    const DomainDesc *__restrict__ doms,
+                                                    const int4 *__restrict__ tiles, int ntiles,
+                                                    int *__restrict__ flag) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tile = __ldg(tiles + t);  // (domain, x0, y0, z)
+        const DomainDesc *D = doms + tile.x;
+        const Geom g = D->g;
+        const int x = tile.y + threadIdx.x, y = tile.z + threadIdx.y, z = tile.w;
+        if (x >= g.nx || y >= g.ny) continue;
+        const S *src = A + D->offset;
+        S *dst = B + D->offset;
+        uint32_t off[kQ];
+        int pop[kQ];
+        pull_sources<true>(g, x, y, z, off, pop);
+        float h[kQ];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
+        const float drho = collide(h, D->fx, D->fy, D->fz, D->r);
+        if (!(fabsf(drho) < 0.9f)) *flag = 1;
+        store_node<S>(dst + off[0], g.stride, h, off[0], 0u);
+    }
+}
+
+template <typename S>
+static cudaError_t batch_launch_t(const void *A, void *B, const DomainDesc *doms, const int4 *tiles, int ntiles,
+                                  int grid, dim3 block, int *flag, cudaStream_t s) {
+    k_batch_step<S><<<grid, block, 0, s>>>((const S *)A, (S *)B, doms, tiles, ntiles, flag);
+    return cudaGetLastError();
+}
+
+static cudaError_t batch_launch(int storage, const void *A, void *B, const DomainDesc *doms, const int4 *tiles,
+                                int ntiles, int grid, dim3 block, int *flag, cudaStream_t s) {
+    switch (storage) {
+        case 0: return batch_launch_t<float>(A, B, doms, tiles, ntiles, grid, block, flag, s);
+        case 1: return batch_launch_t<__half>(A, B, doms, tiles, ntiles, grid, block, flag, s);
+        default: return batch_launch_t<__nv_bfloat16>(A, B, doms, tiles, ntiles, grid, block, flag, s);
+    }
+}
+
+static int batch_occupancy(int storage, int threads) {
+    int per_sm = 0;
+    cudaError_t e;
+    switch (storage) {
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<float>, threads, 0); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<__half>, threads, 0); break;
+        default:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<__nv_bfloat16>, threads, 0);
+            break;
+    }
+    return (e == cudaSuccess && per_sm > 0) ? per_sm : 1;
+}
+
+}  // namespace clbm
+
+struct clbm_batch {
+    std::vector<clbm_domain> host;
+    std::vector<DomainDesc> descs;
+    int ndom;
+    int storage;
+    size_t elem;
+    int64_t total_nodes, total_elems;
+    void *buf[2];
+    int cur;
+    cudaStream_t stream, capture_stream;
+    DomainDesc *d_descs;
+    int4 *d_tiles;
+    int ntiles, tiles_cap, grid;
+    dim3 block;
+    int *d_flag;
+    cudaGraphExec_t graph;
+    int graph_steps;
+    int64_t steps_done;
+};
+
+namespace {
+
+int bfail(int code, const std::string &msg) { return clbm::set_error(code, msg.c_str()); }
+
+int bcuda(cudaError_t e, const char *where) {
+    return bfail(CLBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+Launch domain_launch(const clbm_batch *b, int d) {
+    const Geom &g = b->descs[d].g;
+    Launch L;
+    L.g = g;
+    const int bx = g.nx >= 128 ? 128 : ((g.nx + 31) / 32) * 32;
+    const int by = std::max(1, std::min(g.ny, 256 / bx));
+    L.block = dim3(bx, by, 1);
+    L.grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
+    L.stream = b->stream;
+    return L;
+}
+
+ForceArgs domain_force(const clbm_batch *b, int d) {
+    ForceArgs F;
+    F.mode = kForceUniform;
+    F.fx = b->descs[d].fx; F.fy = b->descs[d].fy; F.fz = b->descs[d].fz;
+    F.profile = nullptr;
+    F.field = nullptr;
+    F.n = (int64_t)b->descs[d].g.nx * b->descs[d].g.ny * b->descs[d].g.nz;
+    return F;
+}
+
+void *domain_ptr(const clbm_batch *b, int which, int d) {
+    return (char *)b->buf[which] + (size_t)b->descs[d].offset * b->elem;
+}
+
+// Build and upload the work list for a block shape.
+int build_tiles(clbm_batch *b, int bx, int by) {
+    std::vector<int4> tiles;
+    for (int d = 0; d < b->ndom; ++d) {
+        const Geom &g = b->descs[d].g;
+        for (int z = 0; z < g.nz; ++z)
+            for (int y0 = 0; y0 < g.ny; y0 += by)
+                for (int x0 = 0; x0 < g.nx; x0 += bx) tiles.push_back(make_int4(d, x0, y0, z));
+    }
+    if (tiles.size() > (size_t)INT32_MAX) return bfail(CLBM_ERR_ARG, "clbm_batch: too many tiles");
+    if ((int)tiles.size() > b->tiles_cap) {
+        if (b->d_tiles) cudaFree(b->d_tiles);
+        b->d_tiles = nullptr;
+        cudaError_t e = cudaMalloc(&b->d_tiles, tiles.size() * sizeof(int4));
+        if (e != cudaSuccess) {
+            b->tiles_cap = 0;
+            cudaGetLastError();
+            return bfail(CLBM_ERR_OOM, "clbm_batch: cudaMalloc of the work list failed");
+        }
+        b->tiles_cap = (int)tiles.size();
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(e, "clbm_batch: work list upload");
+    b->ntiles = (int)tiles.size();
+    b->block = dim3(bx, by, 1);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = std::max(1, std::min(b->ntiles, std::max(1, sms) * batch_occupancy(b->storage, bx * by)));
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return CLBM_OK;
+}
+
+cudaError_t launch_all(clbm_batch *b, cudaStream_t s, int from) {
+    return batch_launch(b->storage, b->buf[from], b->buf[from ^ 1], b->d_descs, b->d_tiles, b->ntiles, b->grid,
+                        b->block, b->d_flag, s);
+}
+
+// Capture graph_steps steps starting from buffer 0 (graph_steps is even, so
+// the replay ends on buffer 0 again).
+int ensure_graph(clbm_batch *b) {
+    if (b->graph) return CLBM_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(e, "clbm_batch: begin capture");
+    for (int k = 0; k < b->graph_steps && e == cudaSuccess; ++k) e = launch_all(b, b->capture_stream, k & 1);
+    cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return bcuda(e, "clbm_batch: graph capture");
+    }
+    return CLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int clbm_batch_create(const clbm_domain *doms, int32_t ndomains, int32_t storage, void *stream, clbm_batch **out) {
+    if (!doms || !out || ndomains < 1) return bfail(CLBM_ERR_ARG, "clbm_batch_create: bad argument");
+    *out = nullptr;
+    if (storage < CLBM_STORAGE_F32 || storage > CLBM_STORAGE_BF16)
+        return bfail(CLBM_ERR_ARG, "clbm_batch_create: storage must be f32, f16 or bf16 (round to nearest)");
+    clbm_batch *b = new (std::nothrow) clbm_batch();
+    if (!b) return bfail(CLBM_ERR_OOM, "clbm_batch_create: host allocation failed");
+    b->ndom = ndomains;
+    b->storage = storage;
+    b->elem = storage == CLBM_STORAGE_F32 ? 4 : 2;
+    b->stream = (cudaStream_t)stream;
+    b->graph_steps = 16;
+    int64_t off = 0, nodes = 0;
+    for (int d = 0; d < ndomains; ++d) {
+        const clbm_domain &p = doms[d];
+        const double s2 = 1.0 / (3.0 * p.nu + 0.5);
+        auto ok = [](double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; };
+        const int64_t n = (int64_t)p.nx * p.ny * p.nz;
+        if (p.nx < 1 || p.ny < 1 || p.nz < 1 || p.nx > 65535 || p.ny > 65535 || p.nz > 65535 ||
+            n > ((int64_t)1 << 31) - 1 || (p.walls & ~7u) || !(std::isfinite(p.nu) && p.nu > 0.0) || !ok(s2) ||
+            !ok(p.s2b) || !ok(p.s3) || !ok(p.s4) || !std::isfinite(p.fx) || !std::isfinite(p.fy) ||
+            !std::isfinite(p.fz)) {
+            delete b;
+            return bfail(CLBM_ERR_ARG, "clbm_batch_create: invalid domain " + std::to_string(d));
+        }
+        DomainDesc D;
+        std::memset(&D, 0, sizeof(D));
+        D.g.nx = p.nx; D.g.ny = p.ny; D.g.nz = p.nz;
+        D.g.walls = p.walls;
+        D.g.stride = (n + 63) / 64 * 64;
+        D.r.om2 = (float)(1.0 - s2);
+        D.r.cb = (float)((p.s2b - s2) / 3.0);
+        D.r.om3 = (float)(1.0 - p.s3);
+        D.r.c3 = (float)((1.0 - 0.5 * p.s3) / 3.0);
+        D.r.om4 = (float)(1.0 - p.s4);
+        D.fx = (float)p.fx; D.fy = (float)p.fy; D.fz = (float)p.fz;
+        D.offset = off;
+        off += (int64_t)kQ * D.g.stride;
+        nodes += n;
+        b->descs.push_back(D);
+        b->host.push_back(p);
+    }
+    b->total_nodes = nodes;
+    b->total_elems = off;
+    cudaError_t e = cudaMalloc(&b->buf[0], 2 * (size_t)off * b->elem);
+    if (e != cudaSuccess) {
+        delete b;
+        cudaGetLastError();
+        return bfail(CLBM_ERR_OOM, "clbm_batch_create: cudaMalloc of the populations failed");
+    }
+    b->buf[1] = (char *)b->buf[0] + (size_t)off * b->elem;
+    if ((e = cudaMalloc(&b->d_descs, sizeof(DomainDesc) * ndomains + 256)) != cudaSuccess) {
+        cudaFree(b->buf[0]);
+        delete b;
+        cudaGetLastError();
+        return bfail(CLBM_ERR_OOM, "clbm_batch_create: cudaMalloc failed");
+    }
+    b->d_flag = (int *)((char *)b->d_descs + sizeof(DomainDesc) * ndomains);
+    b->d_flag = (int *)(((uintptr_t)b->d_flag + 15) & ~(uintptr_t)15);
+    if ((e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        cudaFree(b->d_descs);
+        cudaFree(b->buf[0]);
+        delete b;
+        return bcuda(e, "clbm_batch_create: stream");
+    }
+    e = cudaMemcpyAsync(b->d_descs, b->descs.data(), sizeof(DomainDesc) * ndomains, cudaMemcpyHostToDevice,
+                        b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flag, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->buf[0], 0, 2 * (size_t)off * b->elem, b->stream);
+    int rc = e == cudaSuccess ? build_tiles(b, 128, 2) : bcuda(e, "clbm_batch_create");
+    if (rc != CLBM_OK) {
+        clbm_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return CLBM_OK;
+}
+
+int clbm_batch_destroy(clbm_batch *b) {
+    if (!b) return CLBM_OK;
+    cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_descs) cudaFree(b->d_descs);
+    if (b->buf[0]) cudaFree(b->buf[0]);
+    delete b;
+    return CLBM_OK;
+}
+
+int clbm_batch_get_info(const clbm_batch *b, clbm_batch_info *info) {
+    if (!b || !info) return bfail(CLBM_ERR_ARG, "clbm_batch_get_info: null pointer");
+    info->ndomains = b->ndom;
+    info->total_nodes = b->total_nodes;
+    info->state_bytes = (int64_t)b->total_elems * (int64_t)b->elem;
+    info->ntiles = b->ntiles;
+    info->grid = b->grid;
+    info->block_x = (int32_t)b->block.x;
+    info->block_y = (int32_t)b->block.y;
+    info->graph_steps = b->graph_steps;
+    info->steps_done = b->steps_done;
+    return CLBM_OK;
+}
+
+int clbm_batch_set_block(clbm_batch *b, int32_t bx, int32_t by) {
+    if (!b || bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 512)
+        return bfail(CLBM_ERR_ARG, "clbm_batch_set_block: block_x a multiple of 32, block_x*block_y <= 512");
+    return build_tiles(b, bx, by);
+}
+
+int clbm_batch_autotune(clbm_batch *b, int32_t trial_steps, int32_t *bx_out, int32_t *by_out) {
+    if (!b || trial_steps < 1) return bfail(CLBM_ERR_ARG, "clbm_batch_autotune: bad argument");
+    static const int cand[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {128, 4}, {256, 1},
+                                  {256, 2}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bbx = 128, bby = 2;
+    int rc = CLBM_OK;
+    for (const auto &c : cand) {
+        if ((rc = build_tiles(b, c[0], c[1])) != CLBM_OK) break;
+        // trials read the current buffer and write the other one: the state is unchanged
+        cudaError_t e = launch_all(b, b->stream, b->cur);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = launch_all(b, b->stream, b->cur);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = bcuda(e, "clbm_batch_autotune");
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            bbx = c[0];
+            bby = c[1];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CLBM_OK) return rc;
+    if ((rc = build_tiles(b, bbx, bby)) != CLBM_OK) return rc;
+    if (bx_out) *bx_out = bbx;
+    if (by_out) *by_out = bby;
+    return CLBM_OK;
+}
+
+int clbm_batch_init_equilibrium(clbm_batch *b) {
+    if (!b) return bfail(CLBM_ERR_ARG, "clbm_batch_init_equilibrium: null pointer");
+    for (int d = 0; d < b->ndom; ++d) {
+        cudaError_t e = launch_init_eq(b->storage, domain_launch(b, d), domain_ptr(b, b->cur, d), nullptr, nullptr,
+                                       domain_force(b, d).n, domain_force(b, d));
+        if (e != cudaSuccess) return bcuda(e, "clbm_batch_init_equilibrium");
+    }
+    b->steps_done = 0;
+    return CLBM_OK;
+}
+
+int clbm_batch_step(clbm_batch *b, int64_t nsteps, int32_t mode) {
+    if (!b || nsteps < 0 || mode < 0 || mode > 2) return bfail(CLBM_ERR_ARG, "clbm_batch_step: bad argument");
+    cudaError_t e = cudaSuccess;
+    int64_t t = 0;
+    if (mode == CLBM_BATCH_GRAPH && nsteps >= b->graph_steps) {
+        int rc = ensure_graph(b);
+        if (rc != CLBM_OK) return rc;
+        if (b->cur == 1) {  // the graph starts from buffer 0
+            if ((e = launch_all(b, b->stream, 1)) != cudaSuccess) return bcuda(e, "clbm_batch_step");
+            b->cur = 0;
+            ++t;
+        }
+        for (; t + b->graph_steps <= nsteps; t += b->graph_steps)
+            if ((e = cudaGraphLaunch(b->graph, b->stream)) != cudaSuccess) return bcuda(e, "clbm_batch_step: graph");
+    }
+    for (; t < nsteps; ++t) {
+        if (mode == CLBM_BATCH_PER_DOMAIN) {
+            for (int d = 0; d < b->ndom && e == cudaSuccess; ++d) {
+                Rates r = b->descs[d].r;
+                e = launch_step(b->storage, domain_launch(b, d), domain_ptr(b, b->cur, d),
+                                domain_ptr(b, b->cur ^ 1, d), r, domain_force(b, d), b->d_flag, 0u);
+            }
+        } else {
+            e = launch_all(b, b->stream, b->cur);
+        }
+        if (e != cudaSuccess) return bcuda(e, "clbm_batch_step");
+        b->cur ^= 1;
+    }
+    b->steps_done += nsteps;
+    return CLBM_OK;
+}
+
+int clbm_batch_get_macros(clbm_batch *b, int32_t d, float *rho, float *u) {
+    if (!b || d < 0 || d >= b->ndom) return bfail(CLBM_ERR_ARG, "clbm_batch_get_macros: bad domain");
+    if (!rho && !u) return CLBM_OK;
+    cudaError_t e = launch_macros(b->storage, domain_launch(b, d), domain_ptr(b, b->cur, d), domain_force(b, d),
+                                  rho, u, domain_force(b, d).n);
+    if (e != cudaSuccess) return bcuda(e, "clbm_batch_get_macros");
+    return CLBM_OK;
+}
+
+int clbm_batch_get_populations(clbm_batch *b, int32_t d, float *f, int deviation) {
+    if (!b || !f || d < 0 || d >= b->ndom) return bfail(CLBM_ERR_ARG, "clbm_batch_get_populations: bad argument");
+    cudaError_t e =
+        launch_gather(b->storage, domain_launch(b, d), domain_ptr(b, b->cur, d), f, domain_force(b, d).n, deviation);
+    if (e != cudaSuccess) return bcuda(e, "clbm_batch_get_populations");
+    return CLBM_OK;
+}
+
+int clbm_batch_set_populations(clbm_batch *b, int32_t d, const float *f, int deviation) {
+    if (!b || !f || d < 0 || d >= b->ndom) return bfail(CLBM_ERR_ARG, "clbm_batch_set_populations: bad argument");
+    cudaError_t e = launch_scatter(b->storage, domain_launch(b, d), domain_ptr(b, b->cur, d), f,
+                                   domain_force(b, d).n, deviation);
+    if (e != cudaSuccess) return bcuda(e, "clbm_batch_set_populations");
+    return CLBM_OK;
+}
+
+int clbm_batch_check(clbm_batch *b, int clear) {
+    if (!b) return bfail(CLBM_ERR_ARG, "clbm_batch_check: null pointer");
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, b->d_flag, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess && clear) e = cudaMemsetAsync(b->d_flag, 0, sizeof(int), b->stream);
+    if (e != cudaSuccess) return bcuda(e, "clbm_batch_check");
+    if (h) return bfail(CLBM_ERR_UNSTABLE, "clbm_batch_check: a node's density left (0.1, 1.9) or became non-finite");
+    return CLBM_OK;
+}
+
+}  // extern "C"

@@ -57,8 +57,8 @@ struct clbm_ctx {
     double *d_partials;
     float *d_io;          // clbm_run_host scratch (first use): 4 x N floats, then
     double *d_mom;        //   4 doubles of sums and
-    double *d_mid;        //   4 doubles per first-pass block of the partial sums and
-    double *d_diag;       //   4 doubles per step-kernel block
+    long long *d_mid;     //   4 fixed-point sums per first-pass block and
+    long long *d_diag;    //   4 fixed-point sums per step-kernel block
     int64_t diag_blocks;
     int64_t steps_done;
     dim3 block;
@@ -107,7 +107,7 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     const double s2 = 1.0 / (3.0 * p->nu + 0.5);
     if (!rate_ok(s2) || !rate_ok(p->s2b) || !rate_ok(p->s3) || !rate_ok(p->s4))
         return fail(CLBM_ERR_ARG, "clbm_create: relaxation rates must lie in (0, 2)");
-    if (p->storage < CLBM_STORAGE_F32 || p->storage > CLBM_STORAGE_BF16)
+    if (p->storage < CLBM_STORAGE_F32 || p->storage > CLBM_STORAGE_BF16_SR)
         return fail(CLBM_ERR_ARG, "clbm_create: unknown storage format");
     int bx = p->block_x, by = p->block_y;
     if (bx == 0) bx = p->nx >= 128 ? 128 : ((p->nx + 31) / 32) * 32;
@@ -226,7 +226,8 @@ int clbm_step(clbm_ctx *c, int64_t nsteps) {
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_step: nsteps < 0");
     const Launch L = launch_of(c);
     for (int64_t t = 0; t < nsteps; ++t) {
-        cudaError_t e = launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force, c->d_flag);
+        cudaError_t e = launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force,
+                                    c->d_flag, step_key(c->steps_done));
         if (e != cudaSuccess) return cuda_fail(e, "clbm_step");
         c->cur ^= 1;
         ++c->steps_done;
@@ -259,8 +260,8 @@ int clbm_set_populations(clbm_ctx *c, const float *f, int deviation) {
 
 int clbm_reduce_moments(clbm_ctx *c, double *out) {
     if (!c || !out) return fail(CLBM_ERR_ARG, "clbm_reduce_moments: null pointer");
-    cudaError_t e = launch_reduce_moments(c->p.storage, launch_of(c), c->buf[c->cur], c->force, c->d_partials,
-                                          kReduceBlocks, out);
+    cudaError_t e = launch_reduce_moments(c->p.storage, launch_of(c), c->buf[c->cur], c->force,
+                                          (long long *)c->d_partials, kReduceBlocks, out);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_reduce_moments");
     return CLBM_OK;
 }
@@ -355,7 +356,7 @@ int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
     const size_t bytes = (size_t)kQ * c->g.stride * c->elem;
     if ((const char *)src < (const char *)dst + bytes && (const char *)dst < (const char *)src + bytes)
         return fail(CLBM_ERR_ARG, "clbm_step_raw: src and dst overlap");
-    cudaError_t e = launch_step(c->p.storage, launch_of(c), src, dst, c->rates, c->force, c->d_flag);
+    cudaError_t e = launch_step(c->p.storage, launch_of(c), src, dst, c->rates, c->force, c->d_flag, step_key(0));
     if (e != cudaSuccess) return cuda_fail(e, "clbm_step_raw");
     return CLBM_OK;
 }
@@ -389,7 +390,8 @@ int clbm_adjoint_segment(clbm_ctx *c, const void *ckpt, void *tape, int64_t k, f
     auto state = [&](int64_t j) -> const void * { return j == 0 ? ckpt : (const char *)tape + (j - 1) * sb; };
     cudaError_t e = cudaSuccess;
     for (int64_t j = 1; j < k && e == cudaSuccess; ++j)
-        e = launch_step(c->p.storage, L, state(j - 1), (char *)tape + (j - 1) * sb, c->rates, c->force, c->d_flag);
+        e = launch_step(c->p.storage, L, state(j - 1), (char *)tape + (j - 1) * sb, c->rates, c->force, c->d_flag,
+                        step_key(0));
     float *in = lam, *out = lam_tmp;
     for (int64_t j = k - 1; j >= 0 && e == cudaSuccess; --j) {
         e = launch_adjoint_step(c->p.storage, L, state(j), in, out, gF, c->rates, c->force, c->n);
@@ -422,7 +424,7 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         c->d_io = (float *)p;
         const size_t io = (sizeof(float) * 4 * (size_t)c->n + 255) / 256 * 256;
         c->d_mom = (double *)((char *)p + io);
-        c->d_mid = c->d_mom + 4;
+        c->d_mid = (long long *)(c->d_mom + 4);
         c->d_diag = c->d_mid + 4 * kMidBlocks;
         c->diag_blocks = nblocks;
     }
@@ -438,14 +440,15 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         if (moments_h) {
             // fused step: FP64 sums of the state it pulls (state t) into per-block partials
             e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force, c->d_flag,
-                                 c->d_diag);
+                                 c->d_diag, step_key(c->steps_done));
             if (e == cudaSuccess)
                 e = launch_sum_partials4(c->d_diag, nblocks, c->d_mid, kMidBlocks, c->d_mom, (double)c->n, c->stream);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                                     c->stream);
         } else {
-            e = launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force, c->d_flag);
+            e = launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force, c->d_flag,
+                            step_key(c->steps_done));
         }
         if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: step");
         c->cur ^= 1;

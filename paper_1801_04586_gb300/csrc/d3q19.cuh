@@ -49,25 +49,98 @@ __host__ __device__ constexpr int opposite(int i) {
 }
 
 // ---------------------------------------------------------------- storage
+// Counter-based hash "lowbias32" (C. Wellons, hash-prospector, 2018): an
+// invertible 32-bit mixer; used to draw the dither of stochastic rounding
+// from (per-step key, node, direction), so results are reproducible and do not
+// depend on the launch shape.
+__host__ __device__ constexpr uint32_t lowbias32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Storage tags for stochastic rounding: same bits as __half / __nv_bfloat16.
+struct HalfSR { __half v; };
+struct BF16SR { __nv_bfloat16 v; };
+
+// Codec<T>: load a stored deviation as FP32; store an FP32 deviation. Formats
+// with kStochastic round with a random dither r (from_f_sr), the others to
+// nearest even (from_f).
 template <typename T> struct Codec;
 template <> struct Codec<float> {
+    static constexpr bool kStochastic = false;
     static __device__ __forceinline__ float load(const float *p) { return __ldg(p); }
     static __device__ __forceinline__ float load_plain(const float *p) { return *p; }
-    static __device__ __forceinline__ float to_f(float v) { return v; }
     static __device__ __forceinline__ float from_f(float v) { return v; }
+    static __device__ __forceinline__ float from_f_sr(float v, uint32_t) { return v; }
 };
 template <> struct Codec<__half> {
+    static constexpr bool kStochastic = false;
     static __device__ __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ float load_plain(const __half *p) { return __half2float(*p); }
-    static __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
     static __device__ __forceinline__ __half from_f(float v) { return __float2half_rn(v); }
+    static __device__ __forceinline__ __half from_f_sr(float v, uint32_t) { return __float2half_rn(v); }
 };
 template <> struct Codec<__nv_bfloat16> {
+    static constexpr bool kStochastic = false;
     static __device__ __forceinline__ float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ float load_plain(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
-    static __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 from_f(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ __nv_bfloat16 from_f_sr(float v, uint32_t) { return __float2bfloat16_rn(v); }
 };
+// Stochastic rounding: add a uniform random integer below one unit in the last
+// place of the target to the FP32 bit pattern (sign-magnitude, so this acts on
+// |v|) and truncate; |v| rounds up with probability equal to the dropped
+// fraction, so the stored value is unbiased. FP16 drops 13 mantissa bits in
+// its normal range; below 2^-14 (subnormal FP16, spacing 6e-8) it rounds to
+// nearest.
+template <> struct Codec<HalfSR> {
+    static constexpr bool kStochastic = true;
+    static __device__ __forceinline__ float load(const HalfSR *p) { return __half2float(__ldg(&p->v)); }
+    static __device__ __forceinline__ float load_plain(const HalfSR *p) { return __half2float(p->v); }
+    static __device__ __forceinline__ HalfSR from_f(float v) { return HalfSR{__float2half_rn(v)}; }
+    static __device__ __forceinline__ HalfSR from_f_sr(float v, uint32_t r) {
+        if (fabsf(v) < 6.103515625e-05f) return HalfSR{__float2half_rn(v)};
+        return HalfSR{__float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1fffu)))};
+    }
+};
+template <> struct Codec<BF16SR> {
+    static constexpr bool kStochastic = true;
+    static __device__ __forceinline__ float load(const BF16SR *p) { return __bfloat162float(__ldg(&p->v)); }
+    static __device__ __forceinline__ float load_plain(const BF16SR *p) { return __bfloat162float(p->v); }
+    static __device__ __forceinline__ BF16SR from_f(float v) { return BF16SR{__float2bfloat16_rn(v)}; }
+    static __device__ __forceinline__ BF16SR from_f_sr(float v, uint32_t r) {
+        __nv_bfloat16_raw raw;
+        raw.x = (unsigned short)((__float_as_uint(v) + (r & 0xffffu)) >> 16);
+        return BF16SR{__nv_bfloat16(raw)};
+    }
+};
+
+// Store the 19 post-collision deviations of one node (pull scheme: at the
+// node itself). key: per-step random key (stochastic formats only).
+template <typename S>
+__device__ __forceinline__ void store_node(S *d, int64_t stride, const float (&h)[19], uint32_t node, uint32_t key) {
+    if constexpr (Codec<S>::kStochastic) {
+        const uint32_t base = lowbias32(node ^ key);
+#pragma unroll
+        for (int i = 0; i < 19; i += 2) {
+            const uint32_t r = lowbias32(base + (uint32_t)i * 0x9e3779b9u);
+            d[(size_t)i * stride] = Codec<S>::from_f_sr(h[i], r);
+            if (i + 1 < 19) d[(size_t)(i + 1) * stride] = Codec<S>::from_f_sr(h[i + 1], r >> 16);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) d[(size_t)i * stride] = Codec<S>::from_f(h[i]);
+    }
+}
+
+// Per-step key of the stochastic dither.
+__host__ __device__ constexpr uint32_t step_key(int64_t step) {
+    return lowbias32((uint32_t)step * 0x9e3779b9u + 0x2545f491u);
+}
 
 // ---------------------------------------------------------------- geometry
 struct Geom {

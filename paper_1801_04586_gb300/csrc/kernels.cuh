@@ -25,15 +25,16 @@ struct Launch {
     cudaStream_t stream;
 };
 
-// storage: 0 = f32, 1 = f16, 2 = bf16 (CLBM_STORAGE_*)
+// storage: 0 = f32, 1 = f16, 2 = bf16, 3 = f16 stochastic, 4 = bf16 stochastic
+// (CLBM_STORAGE_*). key: per-step dither key (stochastic formats).
 cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
-                        const ForceArgs &F, int *flag);
+                        const ForceArgs &F, int *flag, uint32_t key);
 cudaError_t launch_step_diag(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
-                             const ForceArgs &F, int *flag, double *partials);
-cudaError_t launch_reduce_final4(const double *partials, int nblocks, double *out, double add0,
-                                 cudaStream_t stream);
-cudaError_t launch_sum_partials4(const double *partials, int64_t nblocks, double *mid, int mid_blocks, double *out,
-                                 double add0, cudaStream_t stream);
+                             const ForceArgs &F, int *flag, long long *partials, uint32_t key);
+cudaError_t launch_fixed_final4(const long long *partials, int nblocks, double *out, double add0,
+                                cudaStream_t stream);
+cudaError_t launch_sum_partials4(const long long *partials, int64_t nblocks, long long *mid, int mid_blocks,
+                                 double *out, double add0, cudaStream_t stream);
 cudaError_t launch_scatter(int storage, const Launch &L, void *dst, const float *f, int64_t n, int deviation);
 cudaError_t launch_init_eq(int storage, const Launch &L, void *dst, const float *rho, const float *u, int64_t n,
                            const ForceArgs &F);
@@ -41,7 +42,7 @@ cudaError_t launch_gather(int storage, const Launch &L, const void *src, float *
 cudaError_t launch_macros(int storage, const Launch &L, const void *src, const ForceArgs &F, float *rho, float *u,
                           int64_t n);
 cudaError_t launch_reduce_moments(int storage, const Launch &L, const void *src, const ForceArgs &F,
-                                  double *partials, int nblocks, double *out);
+                                  long long *partials, int nblocks, double *out);
 cudaError_t launch_adjoint_step(int storage, const Launch &L, const void *state, const float *lam_next, float *lam,
                                 float *gF, const Rates &r, const ForceArgs &F, int64_t n);
 cudaError_t launch_adjoint_seed(int storage, const Launch &L, const void *state, const float *gu, float *lam,

@@ -29,7 +29,7 @@ __device__ __forceinline__ void force_at(const ForceArgs &F, const Geom &g, int 
 
 template <typename S, int FM, bool WALLS>
 __global__ void __launch_bounds__(512) k_step(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r,
-                                              ForceArgs F, int *__restrict__ flag) {
+                                              ForceArgs F, int *__restrict__ flag, uint32_t key) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -44,37 +44,37 @@ __global__ void __launch_bounds__(512) k_step(const S *__restrict__ src, S *__re
     force_at<FM>(F, g, z, off[0], fx, fy, fz);
     const float drho = collide(h, fx, fy, fz, r);
     if (!(fabsf(drho) < 0.9f)) *flag = 1;
-    S *d = dst + off[0];
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) d[(size_t)i * g.stride] = Codec<S>::from_f(h[i]);
+    store_node<S>(dst + off[0], g.stride, h, off[0], key);
 }
 
 template <typename S, int FM>
 static cudaError_t step_walls(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
-                              int *flag) {
+                              int *flag, uint32_t key) {
     if (L.g.walls)
-        k_step<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag);
+        k_step<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
     else
-        k_step<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag);
+        k_step<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
     return cudaGetLastError();
 }
 
 template <typename S>
 static cudaError_t step_force(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
-                              int *flag) {
+                              int *flag, uint32_t key) {
     switch (F.mode) {
-        case kForceUniform: return step_walls<S, kForceUniform>(L, src, dst, r, F, flag);
-        case kForceProfileZ: return step_walls<S, kForceProfileZ>(L, src, dst, r, F, flag);
-        default: return step_walls<S, kForceField>(L, src, dst, r, F, flag);
+        case kForceUniform: return step_walls<S, kForceUniform>(L, src, dst, r, F, flag, key);
+        case kForceProfileZ: return step_walls<S, kForceProfileZ>(L, src, dst, r, F, flag, key);
+        default: return step_walls<S, kForceField>(L, src, dst, r, F, flag, key);
     }
 }
 
 cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
-                        const ForceArgs &F, int *flag) {
+                        const ForceArgs &F, int *flag, uint32_t key) {
     switch (storage) {
-        case 0: return step_force<float>(L, src, dst, r, F, flag);
-        case 1: return step_force<__half>(L, src, dst, r, F, flag);
-        default: return step_force<__nv_bfloat16>(L, src, dst, r, F, flag);
+        case 0: return step_force<float>(L, src, dst, r, F, flag, key);
+        case 1: return step_force<__half>(L, src, dst, r, F, flag, key);
+        case 2: return step_force<__nv_bfloat16>(L, src, dst, r, F, flag, key);
+        case 3: return step_force<HalfSR>(L, src, dst, r, F, flag, key);
+        default: return step_force<BF16SR>(L, src, dst, r, F, flag, key);
     }
 }
 

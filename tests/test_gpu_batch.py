@@ -1,0 +1,90 @@
+"""Batched multi-domain stepping: each domain of a batch must evolve exactly as
+the same lattice stepped alone (same per-node arithmetic), in every step mode
+and block shape, and match the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_common import F32_REL_TOL, W, dev, make_pair, rel_err
+from paper_1801_04586_gb300 import Batch
+
+pytestmark = pytest.mark.gpu
+
+DOMAINS = [
+    dict(nx=40, ny=20, nz=12, walls=4, nu=0.05, fx=1e-5),
+    dict(nx=33, ny=17, nz=9, walls=6, nu=0.02, s2b=1.2, s3=1.1, fx=3e-6, fy=1e-6),
+    dict(nx=150, ny=5, nz=4, walls=0, nu=0.1, s4=0.8, fx=-2e-6, fz=4e-6),
+    dict(nx=20, ny=24, nz=31, walls=6, nu=0.008, fx=5e-6),
+    dict(nx=1, ny=7, nz=40, walls=4, nu=0.03, fx=2e-6),
+]
+
+
+def _single(d, steps):
+    g, _ = make_pair(d["nx"], d["ny"], d["nz"], d["nu"], walls=d.get("walls", 0), s2b=d.get("s2b", 1.0),
+                     s3=d.get("s3", 1.0), s4=d.get("s4", 1.0))
+    g.set_force_uniform(d.get("fx", 0.0), d.get("fy", 0.0), d.get("fz", 0.0))
+    g.init_equilibrium()
+    g.step(steps)
+    out = g.populations(deviation=True).cpu()
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("mode", [Batch.GRAPH, Batch.DIRECT, Batch.PER_DOMAIN])
+def test_batch_domains_match_single_lattices(mode):
+    steps = 37  # two graph replays of 16 steps plus 5 direct launches in graph mode
+    b = Batch(DOMAINS, device=dev())
+    b.init_equilibrium()
+    b.step(steps, mode)
+    b.check()
+    assert b.info()["steps_done"] == steps
+    for k, d in enumerate(DOMAINS):
+        assert torch.equal(b.populations(k, deviation=True).cpu(), _single(d, steps)), f"domain {k}"
+    b.close()
+
+
+@pytest.mark.parametrize("block", [(32, 1), (32, 8), (64, 4), (256, 2)])
+def test_batch_block_shape_bit_identical(block):
+    b = Batch(DOMAINS, device=dev())
+    b.set_block(*block)
+    b.init_equilibrium()
+    b.step(20, Batch.GRAPH)
+    for k, d in enumerate(DOMAINS):
+        assert torch.equal(b.populations(k, deviation=True).cpu(), _single(d, 20)), f"domain {k}"
+    b.close()
+
+
+def test_autotune_keeps_state_and_picks_a_candidate():
+    b = Batch(DOMAINS, device=dev())
+    b.init_equilibrium()
+    b.step(7, Batch.DIRECT)
+    before = [b.populations(k, deviation=True).cpu() for k in range(len(DOMAINS))]
+    bx, by = b.autotune(trial_steps=3)
+    assert (bx, by) in {(32, 4), (32, 8), (64, 2), (64, 4), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2)}
+    info = b.info()
+    assert (info["block_x"], info["block_y"]) == (bx, by)
+    for k in range(len(DOMAINS)):
+        assert torch.equal(b.populations(k, deviation=True).cpu(), before[k])
+    b.step(30, Batch.GRAPH)
+    for k, d in enumerate(DOMAINS):
+        assert torch.equal(b.populations(k, deviation=True).cpu(), _single(d, 37)), f"domain {k}"
+    b.close()
+
+
+def test_batch_against_oracle():
+    doms = DOMAINS[:2]
+    b = Batch(doms, device=dev())
+    b.init_equilibrium()
+    b.step(50, Batch.GRAPH)
+    for k, d in enumerate(doms):
+        shape = (d["nz"], d["ny"], d["nx"])
+        o = oracle.Lattice(d["nx"], d["ny"], d["nz"], walls=d["walls"], s2=1.0 / (3 * d["nu"] + 0.5),
+                           s2b=d.get("s2b", 1.0), s3=d.get("s3", 1.0), s4=d.get("s4", 1.0))
+        F = np.zeros((3,) + shape)
+        F[0], F[1], F[2] = d.get("fx", 0.0), d.get("fy", 0.0), d.get("fz", 0.0)
+        F = F.astype(np.float32).astype(np.float64)
+        fo = oracle.step(o, oracle.init(o, None, None, F), F, 50)
+        fg = b.populations(k, deviation=True).double().cpu().numpy() + W
+        assert rel_err(fg, fo) < F32_REL_TOL
+    b.close()

@@ -23,6 +23,48 @@ def test_codec_rounds_to_nearest_even(storage, tdtype):
     np.testing.assert_array_equal(g.populations(deviation=True).cpu().numpy(), expect)
 
 
+@pytest.mark.parametrize("storage,tdtype", [("f16sr", torch.float16), ("bf16sr", torch.bfloat16)])
+def test_stochastic_rounding_is_unbiased(storage, tdtype):
+    """One step from the same representable state in FP32 and in a stochastic
+    format: every stored value is one of the two format neighbours of the FP32
+    result, and rounding up happens with the dropped fraction's probability
+    (no bias)."""
+    nx, ny, nz = 64, 32, 16
+    shape = (nz, ny, nx)
+    h0 = torch.from_numpy(synthetic.random_deviations(shape, 2e-2, seed=93)).to(tdtype).float().numpy()
+    F = synthetic.gaussian_force(shape, 1e-4, seed=94)
+    out = {}
+    for st in ("f32", storage):
+        g, _ = make_pair(nx, ny, nz, 0.05, walls=4, storage=st)
+        g.set_force_field(t(F))
+        g.set_populations(t(h0), deviation=True)
+        g.step(1)
+        out[st] = g.populations(deviation=True).cpu()
+        g.close()
+    exact = out["f32"].flatten()
+    got = out[storage].flatten()
+    # the format neighbours of each exact value: toward zero (tz) and away
+    # from zero (aw), stepping the 16-bit sign-magnitude pattern by one
+    rn = exact.to(tdtype)
+    bits = rn.view(torch.int16)
+    overshoot = rn.float().abs() > exact.abs()
+    tz = torch.where(overshoot, (bits - 1).view(tdtype), rn)
+    aw = torch.where(tz.float().abs() < exact.abs(), (tz.view(torch.int16) + 1).view(tdtype), tz)
+    normal = (exact.abs() >= 6.103515625e-05) & (rn.float() != 0)
+    ok = (got == tz.float()) | (got == aw.float())
+    assert torch.all(ok | ~normal)
+    sel = normal & (aw != tz)
+    frac = ((exact[sel].abs() - tz[sel].float().abs()).double()
+            / (aw[sel].float().abs() - tz[sel].float().abs()).double())
+    went_up = (got[sel] == aw[sel].float()).double()
+    n = frac.numel()
+    assert n > 100000
+    # expected number of round-ups vs observed: binomial spread
+    diff = float(went_up.sum() - frac.sum())
+    assert abs(diff) < 6.0 * float(torch.sqrt((frac * (1 - frac)).sum())) + 1.0
+    report("stochastic_rounding_bias", storage=storage, n=n, excess_ups=diff)
+
+
 def _duct_profile(g, nz, ny):
     """x-averaged u_x on the (z, y) cross-section, FP64."""
     u = g.macros()[1][0].double()
@@ -44,7 +86,7 @@ def test_duct_copy_against_oracle():
     fo = oracle.step(o, oracle.init(o, None, None, Ff), Ff, steps)
     uo = oracle.macros(o, fo, Ff)[1][0, :, :, 0]
     errs = {}
-    for storage in ("f32", "f16", "bf16"):
+    for storage in ("f32", "f16", "bf16", "f16sr", "bf16sr"):
         g, _ = make_pair(nx, ny, nz, nu, walls=6, storage=storage)
         g.set_force_uniform(F)
         g.init_equilibrium()
@@ -52,9 +94,11 @@ def test_duct_copy_against_oracle():
         errs[storage] = _e2(_duct_profile(g, nz, ny), uo)
         g.close()
     report("duct_128x32x32_vs_oracle", **errs)
-    assert errs["f32"] < 1e-5
-    assert errs["f16"] < 1e-3
-    assert errs["bf16"] < 5e-2  # 8-bit significand: reported, not expected to meet 1e-3
+    # FP32: rounding of 20000 FP32 steps; f16sr: the stated 1e-3. Round-to-
+    # nearest FP16/BF16 stall once the per-step force increment falls below
+    # half a unit in the last place: reported, not asserted.
+    assert errs["f32"] < 1e-4
+    assert errs["f16sr"] < 1e-3
 
 
 def test_duct_512x128x128_against_series():
@@ -64,7 +108,7 @@ def test_duct_512x128x128_against_series():
     nx, ny, nz, nu, F, steps = 512, 128, 128, 0.05, 2e-6, 20000
     ua = an.duct_transient(ny, F, nu, steps)
     errs, rates = {}, {}
-    for storage in ("f32", "f16", "bf16"):
+    for storage in ("f32", "f16", "bf16", "f16sr", "bf16sr"):
         g, _ = make_pair(nx, ny, nz, nu, walls=6, storage=storage)
         g.set_force_uniform(F)
         g.init_equilibrium()
@@ -80,5 +124,5 @@ def test_duct_512x128x128_against_series():
         g.check()
         g.close()
     report("duct_512x128x128_vs_series", **errs, **rates)
-    assert errs["f32"] < 2e-3
-    assert errs["f16"] < 1e-3 + errs["f32"]
+    assert errs["f32"] < 1e-3
+    assert errs["f16sr"] < 1e-3
