@@ -55,7 +55,7 @@ def _params(**kw):
 
 @pytest.mark.parametrize("kw", [dict(nx=0), dict(ny=-3), dict(nz=70000), dict(walls=8), dict(nu=0.0),
                                 dict(nu=-1.0), dict(s2b=2.0), dict(s3=0.0), dict(s4=float("nan")),
-                                dict(storage=3), dict(block_x=48), dict(block_x=1024, block_y=1),
+                                dict(storage=5), dict(block_x=48), dict(block_x=1024, block_y=1),
                                 dict(nx=2048, ny=2048, nz=1024)])
 def test_create_rejects_bad_parameters(lib, kw):
     from paper_1801_04586_gb300 import _capi
