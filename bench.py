@@ -328,10 +328,10 @@ def bench_batch(dev, steps, peak):
     doms = synthetic.batch_domains(64, seed=6)
     b = Batch(doms, device=dev)
     b.init_equilibrium()
-    bx, by = b.autotune(trial_steps=10)
+    threads = b.autotune(trial_steps=10)
     b.step(32, Batch.GRAPH)
     nodes = b.total_nodes
-    out = {"domains": len(doms), "total_nodes": nodes, "steps": steps, "block": [bx, by]}
+    out = {"domains": len(doms), "total_nodes": nodes, "steps": steps, "threads_per_block": threads}
     for name, mode in (("graph", Batch.GRAPH), ("direct", Batch.DIRECT), ("per_domain", Batch.PER_DOMAIN)):
         torch.cuda.synchronize()
         e0, e1 = _events()

@@ -257,8 +257,8 @@ int clbm_reduce_pair_noalloc(const float *a_dev, const float *b_dev, int64_t n, 
  * rates (as clbm_params) and uniform body force, all in one storage format.
  * Each domain follows exactly the per-node update of clbm_step. The batch
  * steps all domains with one launch per time step: a grid of (SMs x resident
- * blocks) walks a work list of tiles (block_x x block_y nodes of one z plane of
- * one domain). The batch owns its population buffers. */
+ * blocks) walks a work list of tiles, each `threads` consecutive nodes of one
+ * domain in its linear index. The batch owns its population buffers. */
 typedef struct clbm_domain {
     int32_t nx, ny, nz;
     uint32_t walls;
@@ -268,7 +268,7 @@ typedef struct clbm_domain {
 
 typedef struct clbm_batch_info {
     int32_t ndomains;
-    int32_t ntiles, grid, block_x, block_y, graph_steps;
+    int32_t ntiles, grid, threads, graph_steps;
     int64_t total_nodes;
     int64_t state_bytes;   /* both buffers: 2 x state_bytes are allocated */
     int64_t steps_done;
@@ -282,20 +282,20 @@ typedef struct clbm_batch_info {
 typedef struct clbm_batch clbm_batch;
 
 /* Create: validates every domain as clbm_create does, allocates the A/B
- * population buffers of all domains and a work list for block 128 x 2, binds
- * to `stream`. Populations start at rest (f = w). Errors: CLBM_ERR_ARG,
+ * population buffers of all domains and a work list for 256-thread tiles,
+ * binds to `stream`. Populations start at rest (f = w). Errors: CLBM_ERR_ARG,
  * CLBM_ERR_OOM, CLBM_ERR_CUDA. */
 int clbm_batch_create(const clbm_domain *domains, int32_t ndomains, int32_t storage, void *stream,
                       clbm_batch **out);
 int clbm_batch_destroy(clbm_batch *b);
 int clbm_batch_get_info(const clbm_batch *b, clbm_batch_info *info);
-/* Rebuild the work list for another block shape (block_x a multiple of 32,
- * block_x * block_y <= 512). Synchronises the stream. */
-int clbm_batch_set_block(clbm_batch *b, int32_t block_x, int32_t block_y);
-/* Time trial_steps launches for each of a fixed set of block shapes (trials
- * read the current state and write the other buffer, so the state is not
- * changed), keep the fastest and report it. Synchronises. */
-int clbm_batch_autotune(clbm_batch *b, int32_t trial_steps, int32_t *block_x_out, int32_t *block_y_out);
+/* Rebuild the work list for another block size (threads per block and
+ * nodes per tile: a multiple of 32 in [32, 512]). Synchronises the stream. */
+int clbm_batch_set_tile(clbm_batch *b, int32_t threads);
+/* Time trial_steps launches for each block size in {64, 128, 192, 256, 384,
+ * 512} (trials read the current state and write the other buffer, so the
+ * state is not changed), keep the fastest and report it. Synchronises. */
+int clbm_batch_autotune(clbm_batch *b, int32_t trial_steps, int32_t *threads_out);
 /* Every domain to the generalized equilibrium at rho = 1, u = 0 (u' = -F/2). */
 int clbm_batch_init_equilibrium(clbm_batch *b);
 /* Advance every domain by nsteps steps with the given CLBM_BATCH_* mode. The

@@ -38,7 +38,7 @@ class Domain(ctypes.Structure):
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("ndomains", ctypes.c_int32), ("ntiles", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
                 ("total_nodes", ctypes.c_int64), ("state_bytes", ctypes.c_int64), ("steps_done", ctypes.c_int64)]
 
 
@@ -85,8 +85,8 @@ SIGNATURES = {
     "clbm_batch_create": [P, I32, I32, P, ctypes.POINTER(P)],
     "clbm_batch_destroy": [P],
     "clbm_batch_get_info": [P, P],
-    "clbm_batch_set_block": [P, I32, I32],
-    "clbm_batch_autotune": [P, I32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+    "clbm_batch_set_tile": [P, I32],
+    "clbm_batch_autotune": [P, I32, ctypes.POINTER(ctypes.c_int32)],
     "clbm_batch_init_equilibrium": [P],
     "clbm_batch_step": [P, I64, I32],
     "clbm_batch_get_macros": [P, I32, P, P],

@@ -58,14 +58,14 @@ class Batch:
         check(self.lib.clbm_batch_get_info(self.h, ctypes.byref(i)), "clbm_batch_get_info")
         return {k: getattr(i, k) for k, _ in _capi.BatchInfo._fields_}
 
-    def set_block(self, bx: int, by: int):
-        check(self.lib.clbm_batch_set_block(self.h, int(bx), int(by)), "clbm_batch_set_block")
+    def set_tile(self, threads: int):
+        check(self.lib.clbm_batch_set_tile(self.h, int(threads)), "clbm_batch_set_tile")
 
-    def autotune(self, trial_steps: int = 10):
-        bx, by = ctypes.c_int32(), ctypes.c_int32()
-        check(self.lib.clbm_batch_autotune(self.h, int(trial_steps), ctypes.byref(bx), ctypes.byref(by)),
-              "clbm_batch_autotune")
-        return bx.value, by.value
+    def autotune(self, trial_steps: int = 10) -> int:
+        """Pick the fastest block size; returns threads per block."""
+        t = ctypes.c_int32()
+        check(self.lib.clbm_batch_autotune(self.h, int(trial_steps), ctypes.byref(t)), "clbm_batch_autotune")
+        return t.value
 
     def init_equilibrium(self):
         check(self.lib.clbm_batch_init_equilibrium(self.h), "clbm_batch_init_equilibrium")

@@ -6,10 +6,11 @@
 // kernel (pull, Eqs. 5, 7, 8, 9 in deviation form; see d3q19.cuh). The
 // domains' populations share two A/B allocations, domain after domain, each in
 // the single-lattice layout. A host-built work list cuts every domain into
-// tiles of one block (block_x nodes along x, block_y rows along y, one z
-// plane); a grid of (SMs x resident blocks) walks the list with a stride, so
-// one launch covers all domains with no tail per domain, and consecutive tiles
-// are consecutive in memory. Steps are replayed from a captured CUDA graph.
+// tiles of T consecutive nodes in its linear index (T = threads per block),
+// so every lane has a node whatever the domain's extents, a warp reads
+// contiguous memory, and only a domain's last tile is partial. A grid of
+// (SMs x resident blocks) walks the list with a stride: one launch covers all
+// domains. Steps are replayed from a captured CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,7 +31,8 @@ struct DomainDesc {
     Geom g;
     Rates r;
     float fx, fy, fz;
-    int64_t offset;  // element offset of the domain's 19 x stride block in A and in B
+    float inv_nx, inv_ny;  // 1/nx, 1/ny (FP32) for the tile coordinate decode
+    int64_t offset;        // element offset of the domain's 19 x stride block in A and in B
 };
 
 template <typename S>
@@ -39,11 +41,17 @@ __global__ void __launch_bounds__(512) k_batch_step(const S *__restrict__ A, S *
                                                     const int4 *__restrict__ tiles, int ntiles,
                                                     int *__restrict__ flag) {
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 tile = __ldg(tiles + t);  // (domain, x0, y0, z)
+        const int4 tile = __ldg(tiles + t);  // (domain, x, y, z) of the tile's first node
         const DomainDesc *D = doms + tile.x;
         const Geom g = D->g;
-        const int x = tile.y + threadIdx.x, y = tile.z + threadIdx.y, z = tile.w;
-        if (x >= g.nx || y >= g.ny) continue;
+        // node tile_start + threadIdx.x: carry x into y and y into z. The
+        // quotients are below 2^17, so floor((v + 0.5) * (1/n)) in FP32 is exact.
+        const int xt = tile.y + (int)threadIdx.x;
+        const int cy = (int)(((float)xt + 0.5f) * D->inv_nx);
+        const int yt = tile.z + cy;
+        const int cz = (int)(((float)yt + 0.5f) * D->inv_ny);
+        const int x = xt - cy * g.nx, y = yt - cz * g.ny, z = tile.w + cz;
+        if (z >= g.nz) continue;
         const S *src = A + D->offset;
         S *dst = B + D->offset;
         uint32_t off[kQ];
@@ -143,14 +151,18 @@ void *domain_ptr(const clbm_batch *b, int which, int d) {
     return (char *)b->buf[which] + (size_t)b->descs[d].offset * b->elem;
 }
 
-// Build and upload the work list for a block shape.
-int build_tiles(clbm_batch *b, int bx, int by) {
+// Build and upload the work list for T threads per block: tiles of T
+// consecutive linear nodes, domain after domain.
+int build_tiles(clbm_batch *b, int T) {
     std::vector<int4> tiles;
     for (int d = 0; d < b->ndom; ++d) {
         const Geom &g = b->descs[d].g;
-        for (int z = 0; z < g.nz; ++z)
-            for (int y0 = 0; y0 < g.ny; y0 += by)
-                for (int x0 = 0; x0 < g.nx; x0 += bx) tiles.push_back(make_int4(d, x0, y0, z));
+        const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+        for (int64_t s0 = 0; s0 < n; s0 += T) {
+            const int x = (int)(s0 % g.nx);
+            const int64_t r = s0 / g.nx;
+            tiles.push_back(make_int4(d, x, (int)(r % g.ny), (int)(r / g.ny)));
+        }
     }
     if (tiles.size() > (size_t)INT32_MAX) return bfail(CLBM_ERR_ARG, "clbm_batch: too many tiles");
     if ((int)tiles.size() > b->tiles_cap) {
@@ -169,11 +181,11 @@ int build_tiles(clbm_batch *b, int bx, int by) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(e, "clbm_batch: work list upload");
     b->ntiles = (int)tiles.size();
-    b->block = dim3(bx, by, 1);
+    b->block = dim3(T, 1, 1);
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->grid = std::max(1, std::min(b->ntiles, std::max(1, sms) * batch_occupancy(b->storage, bx * by)));
+    b->grid = std::max(1, std::min(b->ntiles, std::max(1, sms) * batch_occupancy(b->storage, T)));
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -245,6 +257,8 @@ int clbm_batch_create(const clbm_domain *doms, int32_t ndomains, int32_t storage
         D.r.c3 = (float)((1.0 - 0.5 * p.s3) / 3.0);
         D.r.om4 = (float)(1.0 - p.s4);
         D.fx = (float)p.fx; D.fy = (float)p.fy; D.fz = (float)p.fz;
+        D.inv_nx = 1.0f / (float)p.nx;
+        D.inv_ny = 1.0f / (float)p.ny;
         D.offset = off;
         off += (int64_t)kQ * D.g.stride;
         nodes += n;
@@ -278,7 +292,7 @@ int clbm_batch_create(const clbm_domain *doms, int32_t ndomains, int32_t storage
                         b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flag, 0, sizeof(int), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->buf[0], 0, 2 * (size_t)off * b->elem, b->stream);
-    int rc = e == cudaSuccess ? build_tiles(b, 128, 2) : bcuda(e, "clbm_batch_create");
+    int rc = e == cudaSuccess ? build_tiles(b, 256) : bcuda(e, "clbm_batch_create");
     if (rc != CLBM_OK) {
         clbm_batch_destroy(b);
         return rc;
@@ -306,31 +320,29 @@ int clbm_batch_get_info(const clbm_batch *b, clbm_batch_info *info) {
     info->state_bytes = (int64_t)b->total_elems * (int64_t)b->elem;
     info->ntiles = b->ntiles;
     info->grid = b->grid;
-    info->block_x = (int32_t)b->block.x;
-    info->block_y = (int32_t)b->block.y;
+    info->threads = (int32_t)b->block.x;
     info->graph_steps = b->graph_steps;
     info->steps_done = b->steps_done;
     return CLBM_OK;
 }
 
-int clbm_batch_set_block(clbm_batch *b, int32_t bx, int32_t by) {
-    if (!b || bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 512)
-        return bfail(CLBM_ERR_ARG, "clbm_batch_set_block: block_x a multiple of 32, block_x*block_y <= 512");
-    return build_tiles(b, bx, by);
+int clbm_batch_set_tile(clbm_batch *b, int32_t threads) {
+    if (!b || threads < 32 || threads % 32 != 0 || threads > 512)
+        return bfail(CLBM_ERR_ARG, "clbm_batch_set_tile: threads must be a multiple of 32 in [32, 512]");
+    return build_tiles(b, threads);
 }
 
-int clbm_batch_autotune(clbm_batch *b, int32_t trial_steps, int32_t *bx_out, int32_t *by_out) {
+int clbm_batch_autotune(clbm_batch *b, int32_t trial_steps, int32_t *threads_out) {
     if (!b || trial_steps < 1) return bfail(CLBM_ERR_ARG, "clbm_batch_autotune: bad argument");
-    static const int cand[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {128, 4}, {256, 1},
-                                  {256, 2}};
+    static const int cand[] = {64, 128, 192, 256, 384, 512};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bbx = 128, bby = 2;
+    int bt = 256;
     int rc = CLBM_OK;
-    for (const auto &c : cand) {
-        if ((rc = build_tiles(b, c[0], c[1])) != CLBM_OK) break;
+    for (int T : cand) {
+        if ((rc = build_tiles(b, T)) != CLBM_OK) break;
         // trials read the current buffer and write the other one: the state is unchanged
         cudaError_t e = launch_all(b, b->stream, b->cur);
         if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
@@ -345,16 +357,14 @@ int clbm_batch_autotune(clbm_batch *b, int32_t trial_steps, int32_t *bx_out, int
         }
         if (ms < best) {
             best = ms;
-            bbx = c[0];
-            bby = c[1];
+            bt = T;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != CLBM_OK) return rc;
-    if ((rc = build_tiles(b, bbx, bby)) != CLBM_OK) return rc;
-    if (bx_out) *bx_out = bbx;
-    if (by_out) *by_out = bby;
+    if ((rc = build_tiles(b, bt)) != CLBM_OK) return rc;
+    if (threads_out) *threads_out = bt;
     return CLBM_OK;
 }
 

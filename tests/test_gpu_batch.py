@@ -44,10 +44,10 @@ def test_batch_domains_match_single_lattices(mode):
     b.close()
 
 
-@pytest.mark.parametrize("block", [(32, 1), (32, 8), (64, 4), (256, 2)])
-def test_batch_block_shape_bit_identical(block):
+@pytest.mark.parametrize("threads", [32, 96, 256, 512])
+def test_batch_tile_size_bit_identical(threads):
     b = Batch(DOMAINS, device=dev())
-    b.set_block(*block)
+    b.set_tile(threads)
     b.init_equilibrium()
     b.step(20, Batch.GRAPH)
     for k, d in enumerate(DOMAINS):
@@ -60,10 +60,9 @@ def test_autotune_keeps_state_and_picks_a_candidate():
     b.init_equilibrium()
     b.step(7, Batch.DIRECT)
     before = [b.populations(k, deviation=True).cpu() for k in range(len(DOMAINS))]
-    bx, by = b.autotune(trial_steps=3)
-    assert (bx, by) in {(32, 4), (32, 8), (64, 2), (64, 4), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2)}
-    info = b.info()
-    assert (info["block_x"], info["block_y"]) == (bx, by)
+    threads = b.autotune(trial_steps=3)
+    assert threads in {64, 128, 192, 256, 384, 512}
+    assert b.info()["threads"] == threads
     for k in range(len(DOMAINS)):
         assert torch.equal(b.populations(k, deviation=True).cpu(), before[k])
     b.step(30, Batch.GRAPH)
