@@ -212,12 +212,13 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def bench_storage(storage, K, warmup, dev, side, prof, u0, peak):
-    """The same workload with populations stored as FP16/BF16 deviations."""
+def bench_storage(storage, K, warmup, dev, side, prof, u0, peak, variant=0):
+    """The same workload in another storage format or step-kernel form."""
     import torch
 
     from paper_1801_04586_gb300 import Lattice
-    lat = Lattice(side, side, side, NU, storage=storage, device=dev)
+    lat = Lattice(side, side, side, NU, storage=storage, device=dev, variant=variant)
+    npt = lat.info()["nodes_per_thread"]
     lat.set_force_profile_z(prof)
     lat.init_equilibrium(None, u0)
     lat.step(warmup)
@@ -231,9 +232,10 @@ def bench_storage(storage, K, warmup, dev, side, prof, u0, peak):
     ms = e0.elapsed_time(e1)
     n = lat.n
     lat.close()
-    achieved = 76 * n / (ms / K * 1e-3) / 1e9
-    return {"value": n * K / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / K, "bytes_per_node": 76,
-            "achieved_gbs": achieved, "frac": achieved / peak}
+    bpn = 152 if storage == "f32" else 76
+    achieved = bpn * n / (ms / K * 1e-3) / 1e9
+    return {"value": n * K / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / K, "bytes_per_node": bpn,
+            "achieved_gbs": achieved, "frac": achieved / peak, "nodes_per_thread": npt}
 
 
 def bench_adjoint(dev, side, K, peak):
@@ -452,8 +454,13 @@ def run_gb300(args):
     if not args.no_variants:
         import numpy as np  # noqa: F401
         variants = {
+            "f32_two_nodes_per_thread": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, variant=2),
             "f16_storage": bench_storage("f16", K, args.warmup, dev, side, prof, u0, peak),
             "bf16_storage": bench_storage("bf16", K, args.warmup, dev, side, prof, u0, peak),
+            "f16_storage_one_node_per_thread": bench_storage("f16", K, args.warmup, dev, side, prof, u0, peak,
+                                                             variant=1),
+            "f16_stochastic_storage": bench_storage("f16sr", K, args.warmup, dev, side, prof, u0, peak),
+            "bf16_stochastic_storage": bench_storage("bf16sr", K, args.warmup, dev, side, prof, u0, peak),
             "adjoint_kernel_256": bench_adjoint(dev, side, max(10, min(K, 100)), peak),
             "adjoint_unroll_64": bench_unroll(dev),
             "batched_64_domains": bench_batch(dev, args.batch_steps, peak),

@@ -71,7 +71,11 @@ extern "C" {
  * s0 = s1 = 1 (Sec. III); the method's result does not depend on them.
  * walls: CLBM_WALL_* bits; an axis without a bit is periodic.
  * block_x, block_y: CUDA block shape of the step kernel (block_x a multiple
- *      of 32, block_x*block_y <= 512); 0 selects the built-in default. */
+ *      of 32, block_x*block_y <= 512); 0 selects the built-in default.
+ * variant: step kernel form. 1: one node per thread; 2: two nodes per thread
+ *      (x and x + block_x), collided together with the FP32x2 instructions;
+ *      0: the default, 1 for FP32 storage and 2 for the 16-bit formats. The
+ *      forms give the same results up to the rounding of fused operations. */
 typedef struct clbm_params {
     int32_t nx, ny, nz;
     uint32_t walls;
@@ -79,7 +83,7 @@ typedef struct clbm_params {
     double s2b, s3, s4;
     int32_t storage;
     int32_t block_x, block_y;
-    int32_t reserved;
+    int32_t variant;
 } clbm_params;
 
 typedef struct clbm_info {
@@ -90,6 +94,8 @@ typedef struct clbm_info {
     int32_t storage;
     int32_t block_x, block_y; /* block shape in use */
     double s2;                /* 1/(3 nu + 1/2) */
+    int32_t nodes_per_thread; /* of the step kernel: 1 or 2 */
+    int32_t reserved;
 } clbm_info;
 
 typedef struct clbm_ctx clbm_ctx;
@@ -118,6 +124,15 @@ int clbm_get_info(const clbm_ctx *ctx, clbm_info *info);
 int clbm_set_force_uniform(clbm_ctx *ctx, double fx, double fy, double fz);
 int clbm_set_force_profile_z(clbm_ctx *ctx, const float *F_dev);
 int clbm_set_force_field(clbm_ctx *ctx, const float *F_dev);
+
+/* Time dependence of the body force: the force in use at time step t (in
+ * Eq. 9 on the state f(t) and in the collision that advances it) becomes
+ * F e^{-gamma t}, where F is the force set by clbm_set_force_* and t the
+ * context's steps_done. gamma = 0 (the default) keeps the force static. The
+ * decaying Taylor-Green force of Sec. III.D has this form. Initialisation uses
+ * t = 0. The recomputation and adjoint entry points require gamma = 0
+ * (CLBM_ERR_STATE otherwise). */
+int clbm_set_force_decay(clbm_ctx *ctx, double gamma);
 
 /* Initial state: at every node the generalized local equilibrium (Sec. II.B
  * after Eq. 15, central moments of Eq. A5) at density rho and velocity

@@ -6,6 +6,6 @@ may import this package. The GPU library never does.
 from .oracle import (  # noqa: F401
     Lattice, build, lib_path, velocities, moment_exponents, matrix_M, matrix_Minv,
     matrix_N, matrix_S, teq, cforce, central_moments, macros_node, collide,
-    equilibrium, init, step, macros, first_step_nodes, adjoint_step, adjoint_seed,
+    equilibrium, init, step, step_decay, macros, first_step_nodes, adjoint_step, adjoint_seed,
     num_threads,
 )

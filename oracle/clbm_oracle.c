@@ -294,8 +294,19 @@ int ora_init(const ora_lattice *L, const double *rho, const double *u, const dou
     return 0;
 }
 
-/* nsteps full time steps (Steps 1-4), in place on f (post-streaming state). */
+/* nsteps full time steps (Steps 1-4), in place on f (post-streaming state),
+ * with the force F(x) e^{-gamma t}, t = t0, t0 + 1, ... the time of each
+ * collision (gamma = 0: a static force). */
+int ora_step_decay(const ora_lattice *L, const double *F, double *f, int nsteps, int nthreads, double t0,
+                   double gamma);
+
 int ora_step(const ora_lattice *L, const double *F, double *f, int nsteps, int nthreads)
+{
+    return ora_step_decay(L, F, f, nsteps, nthreads, 0.0, 0.0);
+}
+
+int ora_step_decay(const ora_lattice *L, const double *F, double *f, int nsteps, int nthreads, double t0,
+                   double gamma)
 {
     ensure_ready();
     long N = lattice_n(L);
@@ -305,6 +316,7 @@ int ora_step(const ora_lattice *L, const double *F, double *f, int nsteps, int n
     if (!tmp) return -1;
     set_threads(nthreads);
     for (int t = 0; t < nsteps; ++t) {
+        const double decay = gamma == 0.0 ? 1.0 : exp(-gamma * (t0 + t));
 #pragma omp parallel for collapse(2) schedule(static)
         for (int z = 0; z < L->nz; ++z) {
             for (int y = 0; y < L->ny; ++y) {
@@ -312,7 +324,7 @@ int ora_step(const ora_lattice *L, const double *F, double *f, int nsteps, int n
                     long s = ((long)z * L->ny + y) * L->nx + x;
                     double fl[Q], Fl[3], fs[Q];
                     for (int i = 0; i < Q; ++i) fl[i] = f[i * N + s];
-                    for (int a = 0; a < 3; ++a) Fl[a] = F ? F[a * N + s] : 0.0;
+                    for (int a = 0; a < 3; ++a) Fl[a] = F ? F[a * N + s] * decay : 0.0;
                     collide_r(S, g_Minv, fl, Fl, fs);
                     for (int i = 0; i < Q; ++i) {
                         int d;

@@ -58,6 +58,7 @@ def _get():
             "ora_macros_node": [P, P, P, P], "ora_collide": [P, P, P, P],
             "ora_equilibrium": [D, P, P], "ora_init": [P, P, P, P, P],
             "ora_step": [P, P, P, I, I], "ora_macros": [P, P, P, P, P],
+            "ora_step_decay": [P, P, P, I, I, D, D],
             "ora_first_step_nodes": [P, P, P, P, I, P, P, I],
             "ora_adjoint_step": [P, P, P, P, P, P, I],
             "ora_adjoint_seed": [P, P, P, P, P, P],
@@ -67,7 +68,7 @@ def _get():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int if name in (
-                "ora_init", "ora_step", "ora_macros", "ora_first_step_nodes",
+                "ora_init", "ora_step", "ora_step_decay", "ora_macros", "ora_first_step_nodes",
                 "ora_adjoint_step", "ora_adjoint_seed", "ora_num_threads") else None
         _lib = lib
     return _lib
@@ -220,6 +221,18 @@ def step(lat: Lattice, f, F=None, nsteps: int = 1, nthreads: int = 0) -> np.ndar
     c = lat.c()
     rc = _get().ora_step(ctypes.byref(c), _ptr(_f64(F, (3,) + lat.shape)), _ptr(f), int(nsteps),
                          int(nthreads))
+    if rc != 0:
+        raise MemoryError("oracle step failed")
+    return f
+
+
+def step_decay(lat: Lattice, f, F, nsteps: int, t0: float, gamma: float, nthreads: int = 0) -> np.ndarray:
+    """As step, with the force F(x) exp(-gamma t) at each collision time
+    t = t0, t0 + 1, ..."""
+    f = _f64(f, (Q,) + lat.shape).copy()
+    c = lat.c()
+    rc = _get().ora_step_decay(ctypes.byref(c), _ptr(_f64(F, (3,) + lat.shape)), _ptr(f), int(nsteps), int(nthreads),
+                               float(t0), float(gamma))
     if rc != 0:
         raise MemoryError("oracle step failed")
     return f

@@ -26,7 +26,7 @@ class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("walls", ctypes.c_uint32), ("nu", ctypes.c_double), ("s2b", ctypes.c_double),
                 ("s3", ctypes.c_double), ("s4", ctypes.c_double), ("storage", ctypes.c_int32),
-                ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
 class Domain(ctypes.Structure):
@@ -48,7 +48,8 @@ BATCH_GRAPH, BATCH_DIRECT, BATCH_PER_DOMAIN = 0, 1, 2
 class Info(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("pop_stride", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
                 ("steps_done", ctypes.c_int64), ("storage", ctypes.c_int32), ("block_x", ctypes.c_int32),
-                ("block_y", ctypes.c_int32), ("s2", ctypes.c_double)]
+                ("block_y", ctypes.c_int32), ("s2", ctypes.c_double), ("nodes_per_thread", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 P = ctypes.c_void_p
@@ -64,6 +65,7 @@ SIGNATURES = {
     "clbm_set_force_uniform": [P, D, D, D],
     "clbm_set_force_profile_z": [P, P],
     "clbm_set_force_field": [P, P],
+    "clbm_set_force_decay": [P, D],
     "clbm_init_equilibrium": [P, P, P],
     "clbm_step": [P, I64],
     "clbm_get_macros": [P, P, P],

@@ -335,6 +335,9 @@ __device__ __forceinline__ void force_adj(const ForceArgs &F, const Geom &g, int
     } else {
         fx = __ldg(F.field + self); fy = __ldg(F.field + F.n + self); fz = __ldg(F.field + 2 * F.n + self);
     }
+    fx *= F.scale;
+    fy *= F.scale;
+    fz *= F.scale;
 }
 
 // One adjoint step. state: raw buffer whose pull gives f^t; lam_next: adjoint

@@ -15,6 +15,9 @@ __device__ __forceinline__ void force_node(const ForceArgs &F, const Geom &g, in
     } else {
         fx = F.field[self]; fy = F.field[F.n + self]; fz = F.field[2 * F.n + self];
     }
+    fx *= F.scale;
+    fy *= F.scale;
+    fz *= F.scale;
 }
 
 __device__ __forceinline__ bool node_of(const Geom &g, int &x, int &y, int &z) {

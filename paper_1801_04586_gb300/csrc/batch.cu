@@ -35,14 +35,26 @@ struct DomainDesc {
     int64_t offset;        // element offset of the domain's 19 x stride block in A and in B
 };
 
-template <typename S>
+// SMEM: the domain table is staged in shared memory once per launch (the
+// usual case); otherwise it is read through the read-only cache. The next
+// tile's entry is fetched while the current tile is processed.
+template <typename S, bool SMEM>
 __global__ void __launch_bounds__(512) k_batch_step(const S *__restrict__ A, S *__restrict__ B,
-                                                    const DomainDesc *__restrict__ doms,
+                                                    const DomainDesc *__restrict__ doms, int ndom,
                                                     const int4 *__restrict__ tiles, int ntiles,
                                                     int *__restrict__ flag) {
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 tile = __ldg(tiles + t);  // (domain, x, y, z) of the tile's first node
-        const DomainDesc *D = doms + tile.x;
+    extern __shared__ DomainDesc sdom[];
+    if (SMEM) {
+        for (int i = threadIdx.x; i < ndom; i += blockDim.x) sdom[i] = doms[i];
+        __syncthreads();
+    }
+    int t = blockIdx.x;
+    if (t >= ntiles) return;
+    int4 tile = __ldg(tiles + t);  // (domain, x, y, z) of the tile's first node
+    for (; t < ntiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        const int4 next = tn < ntiles ? __ldg(tiles + tn) : tile;
+        const DomainDesc *D = SMEM ? sdom + tile.x : doms + tile.x;
         const Geom g = D->g;
         // node tile_start + threadIdx.x: carry x into y and y into z. The
         // quotients are below 2^17, so floor((v + 0.5) * (1/n)) in FP32 is exact.
@@ -51,48 +63,63 @@ __global__ void __launch_bounds__(512) k_batch_step(const S *__restrict__ A, S *
         const int yt = tile.z + cy;
         const int cz = (int)(((float)yt + 0.5f) * D->inv_ny);
         const int x = xt - cy * g.nx, y = yt - cz * g.ny, z = tile.w + cz;
-        if (z >= g.nz) continue;
-        const S *src = A + D->offset;
-        S *dst = B + D->offset;
-        uint32_t off[kQ];
-        int pop[kQ];
-        pull_sources<true>(g, x, y, z, off, pop);
-        float h[kQ];
+        if (z < g.nz) {
+            const S *src = A + D->offset;
+            S *dst = B + D->offset;
+            uint32_t off[kQ];
+            int pop[kQ];
+            pull_sources<true>(g, x, y, z, off, pop);
+            float h[kQ];
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
-        const float drho = collide(h, D->fx, D->fy, D->fz, D->r);
-        if (!(fabsf(drho) < 0.9f)) *flag = 1;
-        store_node<S>(dst + off[0], g.stride, h, off[0], 0u);
+            for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
+            const float drho = collide(h, D->fx, D->fy, D->fz, D->r);
+            if (!(fabsf(drho) < 0.9f)) *flag = 1;
+            store_node<S>(dst + off[0], g.stride, h, off[0], 0u);
+        }
+        tile = next;
+    }
+}
+
+constexpr int kSmemDomains = 512;  // domain tables up to this size are staged in shared memory
+
+template <typename S>
+static cudaError_t batch_launch_t(const void *A, void *B, const DomainDesc *doms, int ndom, const int4 *tiles,
+                                  int ntiles, int grid, dim3 block, int *flag, cudaStream_t s) {
+    if (ndom <= kSmemDomains)
+        k_batch_step<S, true><<<grid, block, sizeof(DomainDesc) * ndom, s>>>((const S *)A, (S *)B, doms, ndom, tiles,
+                                                                            ntiles, flag);
+    else
+        k_batch_step<S, false><<<grid, block, 0, s>>>((const S *)A, (S *)B, doms, ndom, tiles, ntiles, flag);
+    return cudaGetLastError();
+}
+
+static cudaError_t batch_launch(int storage, const void *A, void *B, const DomainDesc *doms, int ndom,
+                                const int4 *tiles, int ntiles, int grid, dim3 block, int *flag, cudaStream_t s) {
+    switch (storage) {
+        case 0: return batch_launch_t<float>(A, B, doms, ndom, tiles, ntiles, grid, block, flag, s);
+        case 1: return batch_launch_t<__half>(A, B, doms, ndom, tiles, ntiles, grid, block, flag, s);
+        default: return batch_launch_t<__nv_bfloat16>(A, B, doms, ndom, tiles, ntiles, grid, block, flag, s);
     }
 }
 
 template <typename S>
-static cudaError_t batch_launch_t(const void *A, void *B, const DomainDesc *doms, const int4 *tiles, int ntiles,
-                                  int grid, dim3 block, int *flag, cudaStream_t s) {
-    k_batch_step<S><<<grid, block, 0, s>>>((const S *)A, (S *)B, doms, tiles, ntiles, flag);
-    return cudaGetLastError();
-}
-
-static cudaError_t batch_launch(int storage, const void *A, void *B, const DomainDesc *doms, const int4 *tiles,
-                                int ntiles, int grid, dim3 block, int *flag, cudaStream_t s) {
-    switch (storage) {
-        case 0: return batch_launch_t<float>(A, B, doms, tiles, ntiles, grid, block, flag, s);
-        case 1: return batch_launch_t<__half>(A, B, doms, tiles, ntiles, grid, block, flag, s);
-        default: return batch_launch_t<__nv_bfloat16>(A, B, doms, tiles, ntiles, grid, block, flag, s);
-    }
-}
-
-static int batch_occupancy(int storage, int threads) {
+static int occupancy_t(int threads, int ndom) {
     int per_sm = 0;
     cudaError_t e;
-    switch (storage) {
-        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<float>, threads, 0); break;
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<__half>, threads, 0); break;
-        default:
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<__nv_bfloat16>, threads, 0);
-            break;
-    }
+    if (ndom <= kSmemDomains)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<S, true>, threads,
+                                                          sizeof(DomainDesc) * ndom);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<S, false>, threads, 0);
     return (e == cudaSuccess && per_sm > 0) ? per_sm : 1;
+}
+
+static int batch_occupancy(int storage, int threads, int ndom) {
+    switch (storage) {
+        case 0: return occupancy_t<float>(threads, ndom);
+        case 1: return occupancy_t<__half>(threads, ndom);
+        default: return occupancy_t<__nv_bfloat16>(threads, ndom);
+    }
 }
 
 }  // namespace clbm
@@ -134,6 +161,7 @@ Launch domain_launch(const clbm_batch *b, int d) {
     L.block = dim3(bx, by, 1);
     L.grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
     L.stream = b->stream;
+    L.packed = false;
     return L;
 }
 
@@ -144,6 +172,7 @@ ForceArgs domain_force(const clbm_batch *b, int d) {
     F.profile = nullptr;
     F.field = nullptr;
     F.n = (int64_t)b->descs[d].g.nx * b->descs[d].g.ny * b->descs[d].g.nz;
+    F.scale = 1.0f;
     return F;
 }
 
@@ -185,7 +214,7 @@ int build_tiles(clbm_batch *b, int T) {
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->grid = std::max(1, std::min(b->ntiles, std::max(1, sms) * batch_occupancy(b->storage, T)));
+    b->grid = std::max(1, std::min(b->ntiles, std::max(1, sms) * batch_occupancy(b->storage, T, b->ndom)));
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -194,8 +223,8 @@ int build_tiles(clbm_batch *b, int T) {
 }
 
 cudaError_t launch_all(clbm_batch *b, cudaStream_t s, int from) {
-    return batch_launch(b->storage, b->buf[from], b->buf[from ^ 1], b->d_descs, b->d_tiles, b->ntiles, b->grid,
-                        b->block, b->d_flag, s);
+    return batch_launch(b->storage, b->buf[from], b->buf[from ^ 1], b->d_descs, b->ndom, b->d_tiles, b->ntiles,
+                        b->grid, b->block, b->d_flag, s);
 }
 
 // Capture graph_steps steps starting from buffer 0 (graph_steps is even, so

@@ -61,10 +61,25 @@ struct clbm_ctx {
     long long *d_diag;    //   4 fixed-point sums per step-kernel block
     int64_t diag_blocks;
     int64_t steps_done;
+    double gamma;         // force decay rate (clbm_set_force_decay)
+    bool packed;          // step kernel with two nodes per thread (FP32x2 arithmetic)
     dim3 block;
 };
 
 namespace {
+
+// The force in use at the context's current time step.
+ForceArgs force_at_zero(const clbm_ctx *c) {
+    ForceArgs F = c->force;
+    F.scale = 1.0f;
+    return F;
+}
+
+ForceArgs force_now(const clbm_ctx *c) {
+    ForceArgs F = c->force;
+    F.scale = c->gamma == 0.0 ? 1.0f : (float)std::exp(-c->gamma * (double)c->steps_done);
+    return F;
+}
 
 Launch launch_of(const clbm_ctx *c) {
     Launch L;
@@ -72,6 +87,17 @@ Launch launch_of(const clbm_ctx *c) {
     L.block = c->block;
     L.grid = dim3((c->g.nx + c->block.x - 1) / c->block.x, (c->g.ny + c->block.y - 1) / c->block.y, c->g.nz);
     L.stream = c->stream;
+    L.packed = false;
+    return L;
+}
+
+// The step launch: two nodes per thread when the context's variant says so.
+Launch step_launch_of(const clbm_ctx *c) {
+    Launch L = launch_of(c);
+    if (c->packed) {
+        L.packed = true;
+        L.grid.x = (c->g.nx + 2 * c->block.x - 1) / (2 * c->block.x);
+    }
     return L;
 }
 
@@ -109,6 +135,7 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
         return fail(CLBM_ERR_ARG, "clbm_create: relaxation rates must lie in (0, 2)");
     if (p->storage < CLBM_STORAGE_F32 || p->storage > CLBM_STORAGE_BF16_SR)
         return fail(CLBM_ERR_ARG, "clbm_create: unknown storage format");
+    if (p->variant < 0 || p->variant > 2) return fail(CLBM_ERR_ARG, "clbm_create: variant must be 0, 1 or 2");
     int bx = p->block_x, by = p->block_y;
     if (bx == 0) bx = p->nx >= 128 ? 128 : ((p->nx + 31) / 32) * 32;
     if (by == 0) by = std::max(1, std::min(p->ny, 256 / bx));
@@ -136,6 +163,9 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     c->force.profile = nullptr;
     c->force.field = nullptr;
     c->force.n = n;
+    c->force.scale = 1.0f;
+    c->gamma = 0.0;
+    c->packed = p->variant == 2 || (p->variant == 0 && p->storage != CLBM_STORAGE_F32);
     c->block = dim3(bx, by, 1);
     c->cur = 0;
     c->steps_done = 0;
@@ -187,6 +217,7 @@ int clbm_get_info(const clbm_ctx *c, clbm_info *info) {
     info->block_x = (int32_t)c->block.x;
     info->block_y = (int32_t)c->block.y;
     info->s2 = c->s2;
+    info->nodes_per_thread = c->packed ? 2 : 1;
     return CLBM_OK;
 }
 
@@ -213,9 +244,16 @@ int clbm_set_force_field(clbm_ctx *c, const float *F) {
     return CLBM_OK;
 }
 
+int clbm_set_force_decay(clbm_ctx *c, double gamma) {
+    if (!c) return fail(CLBM_ERR_ARG, "clbm_set_force_decay: null context");
+    if (!std::isfinite(gamma)) return fail(CLBM_ERR_ARG, "clbm_set_force_decay: non-finite rate");
+    c->gamma = gamma;
+    return CLBM_OK;
+}
+
 int clbm_init_equilibrium(clbm_ctx *c, const float *rho, const float *u) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_init_equilibrium: null context");
-    cudaError_t e = launch_init_eq(c->p.storage, launch_of(c), c->buf[c->cur], rho, u, c->n, c->force);
+    cudaError_t e = launch_init_eq(c->p.storage, launch_of(c), c->buf[c->cur], rho, u, c->n, force_at_zero(c));
     if (e != cudaSuccess) return cuda_fail(e, "clbm_init_equilibrium");
     c->steps_done = 0;
     return CLBM_OK;
@@ -224,9 +262,9 @@ int clbm_init_equilibrium(clbm_ctx *c, const float *rho, const float *u) {
 int clbm_step(clbm_ctx *c, int64_t nsteps) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_step: null context");
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_step: nsteps < 0");
-    const Launch L = launch_of(c);
+    const Launch L = step_launch_of(c);
     for (int64_t t = 0; t < nsteps; ++t) {
-        cudaError_t e = launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force,
+        cudaError_t e = launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),
                                     c->d_flag, step_key(c->steps_done));
         if (e != cudaSuccess) return cuda_fail(e, "clbm_step");
         c->cur ^= 1;
@@ -238,7 +276,7 @@ int clbm_step(clbm_ctx *c, int64_t nsteps) {
 int clbm_get_macros(clbm_ctx *c, float *rho, float *u) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_get_macros: null context");
     if (!rho && !u) return CLBM_OK;
-    cudaError_t e = launch_macros(c->p.storage, launch_of(c), c->buf[c->cur], c->force, rho, u, c->n);
+    cudaError_t e = launch_macros(c->p.storage, launch_of(c), c->buf[c->cur], force_now(c), rho, u, c->n);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_get_macros");
     return CLBM_OK;
 }
@@ -260,7 +298,7 @@ int clbm_set_populations(clbm_ctx *c, const float *f, int deviation) {
 
 int clbm_reduce_moments(clbm_ctx *c, double *out) {
     if (!c || !out) return fail(CLBM_ERR_ARG, "clbm_reduce_moments: null pointer");
-    cudaError_t e = launch_reduce_moments(c->p.storage, launch_of(c), c->buf[c->cur], c->force,
+    cudaError_t e = launch_reduce_moments(c->p.storage, launch_of(c), c->buf[c->cur], force_now(c),
                                           (long long *)c->d_partials, kReduceBlocks, out);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_reduce_moments");
     return CLBM_OK;
@@ -353,10 +391,11 @@ int clbm_load_state(clbm_ctx *c, const void *host, size_t bytes) {
 
 int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
     if (!c || !src || !dst) return fail(CLBM_ERR_ARG, "clbm_step_raw: null pointer");
+    if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_step_raw: needs a static force (decay 0)");
     const size_t bytes = (size_t)kQ * c->g.stride * c->elem;
     if ((const char *)src < (const char *)dst + bytes && (const char *)dst < (const char *)src + bytes)
         return fail(CLBM_ERR_ARG, "clbm_step_raw: src and dst overlap");
-    cudaError_t e = launch_step(c->p.storage, launch_of(c), src, dst, c->rates, c->force, c->d_flag, step_key(0));
+    cudaError_t e = launch_step(c->p.storage, step_launch_of(c), src, dst, c->rates, c->force, c->d_flag, step_key(0));
     if (e != cudaSuccess) return cuda_fail(e, "clbm_step_raw");
     return CLBM_OK;
 }
@@ -364,6 +403,7 @@ int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
 int clbm_adjoint_seed(clbm_ctx *c, const void *state, const float *gu, float *lam, float *gF) {
     if (!c || !gu || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: null pointer");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: FP32 storage only");
+    if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_adjoint_seed: needs a static force (decay 0)");
     cudaError_t e = launch_adjoint_seed(c->p.storage, launch_of(c), state ? state : c->buf[c->cur], gu, lam, gF,
                                         c->force, c->n);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_adjoint_seed");
@@ -373,6 +413,7 @@ int clbm_adjoint_seed(clbm_ctx *c, const void *state, const float *gu, float *la
 int clbm_adjoint_step(clbm_ctx *c, const void *state, const float *lam_next, float *lam, float *gF) {
     if (!c || !state || !lam_next || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: null pointer");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: FP32 storage only");
+    if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_adjoint_step: needs a static force (decay 0)");
     if (lam == lam_next) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: lam aliases lam_next");
     cudaError_t e =
         launch_adjoint_step(c->p.storage, launch_of(c), state, lam_next, lam, gF, c->rates, c->force, c->n);
@@ -385,6 +426,7 @@ int clbm_adjoint_segment(clbm_ctx *c, const void *ckpt, void *tape, int64_t k, f
     if (!c || !ckpt || !lam || !lam_tmp || !gF || k < 1 || (k > 1 && !tape) || lam == lam_tmp)
         return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: bad argument");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: FP32 storage only");
+    if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_adjoint_segment: needs a static force (decay 0)");
     const Launch L = launch_of(c);
     const size_t sb = (size_t)kQ * c->g.stride * c->elem;
     auto state = [&](int64_t j) -> const void * { return j == 0 ? ckpt : (const char *)tape + (j - 1) * sb; };
@@ -439,16 +481,16 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     for (int64_t t = 0; t < nsteps; ++t) {
         if (moments_h) {
             // fused step: FP64 sums of the state it pulls (state t) into per-block partials
-            e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force, c->d_flag,
-                                 c->d_diag, step_key(c->steps_done));
+            e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),
+                                 c->d_flag, c->d_diag, step_key(c->steps_done));
             if (e == cudaSuccess)
                 e = launch_sum_partials4(c->d_diag, nblocks, c->d_mid, kMidBlocks, c->d_mom, (double)c->n, c->stream);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                                     c->stream);
         } else {
-            e = launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, c->force, c->d_flag,
-                            step_key(c->steps_done));
+            e = launch_step(c->p.storage, step_launch_of(c), c->buf[c->cur], c->buf[c->cur ^ 1], c->rates,
+                            force_now(c), c->d_flag, step_key(c->steps_done));
         }
         if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: step");
         c->cur ^= 1;

@@ -205,42 +205,69 @@ struct Rates {
     float om4;  // 1 - s4
 };
 
+// Two nodes' values packed for the FP32x2 instructions of sm_100-class GPUs
+// (__fadd2_rn / __fmul2_rn / __ffma2_rn round each lane exactly like the
+// scalar operation). The collision templates below run on float or on f2.
+struct f2 {
+    float2 v;
+};
+__device__ __forceinline__ f2 mk2(float a) { return f2{make_float2(a, a)}; }
+__device__ __forceinline__ f2 mk2(float a, float b) { return f2{make_float2(a, b)}; }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2{__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)}; }
+__device__ __forceinline__ f2 operator-(f2 a) { return f2{make_float2(-a.v.x, -a.v.y)}; }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ f2 operator*(float s, f2 b) { return mk2(s) * b; }
+__device__ __forceinline__ f2 operator*(f2 b, float s) { return b * mk2(s); }
+__device__ __forceinline__ f2 operator+(float s, f2 b) { return mk2(s) + b; }
+__device__ __forceinline__ f2 operator+(f2 b, float s) { return b + mk2(s); }
+__device__ __forceinline__ f2 operator/(float s, f2 b) { return f2{make_float2(s / b.v.x, s / b.v.y)}; }
+__device__ __forceinline__ f2 &operator*=(f2 &a, float s) { return a = a * s; }
+using ::fmaf;
+__device__ __forceinline__ f2 fmaf(f2 a, f2 b, f2 c) { return f2{__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ f2 fmaf(float a, f2 b, f2 c) { return fmaf(mk2(a), b, c); }
+
 // Central shift of one triplet along an axis with velocity v (one factor of
 // N(u)): (k0, k1, k2) -> (k0, k1 - v k0, k2 - 2 v k1 + v^2 k0).
-__device__ __forceinline__ void shift3(float k0, float &k1, float &k2, float v) {
-    const float c1 = fmaf(-v, k0, k1);
+template <typename T>
+__device__ __forceinline__ void shift3(T k0, T &k1, T &k2, T v) {
+    const T c1 = fmaf(-v, k0, k1);
     k2 = fmaf(-v, k1 + c1, k2);
     k1 = c1;
 }
 // Its inverse (one factor of N(-u)): (c0, c1, c2) -> (c0, c1 + v c0, c2 + 2 v c1 + v^2 c0).
-__device__ __forceinline__ void unshift3(float c0, float &c1, float &c2, float v) {
-    const float k1 = fmaf(v, c0, c1);
+template <typename T>
+__device__ __forceinline__ void unshift3(T c0, T &c1, T &c2, T v) {
+    const T k1 = fmaf(v, c0, c1);
     c2 = fmaf(v, c1 + k1, c2);
     c1 = k1;
 }
 
 // Raw-moment deviations dT = M h, named by exponents (Eq. A2 with k~002 as the
 // tenth moment).
-struct Moments {
-    float m000, m100, m010, m001, m110, m101, m011, m200, m020, m002;
-    float m120, m102, m210, m201, m012, m021, m220, m202, m022;
+template <typename T>
+struct MomentsT {
+    T m000, m100, m010, m001, m110, m101, m011, m200, m020, m002;
+    T m120, m102, m210, m201, m012, m021, m220, m202, m022;
 };
+using Moments = MomentsT<float>;
 
-__device__ __forceinline__ void raw_moments(const float (&h)[kQ], Moments &k) {
+template <typename T>
+__device__ __forceinline__ void raw_moments(const T (&h)[kQ], MomentsT<T> &k) {
     // xy plane (7..10): four moments ex^a ey^b with a, b in {1, 2}
-    const float a = h[7] + h[8], b = h[9] + h[10], c = h[7] + h[9], d = h[8] + h[10];
-    const float e = h[7] + h[10], f = h[8] + h[9];
+    const T a = h[7] + h[8], b = h[9] + h[10], c = h[7] + h[9], d = h[8] + h[10];
+    const T e = h[7] + h[10], f = h[8] + h[9];
     k.m220 = a + b; k.m210 = a - b; k.m120 = c - d; k.m110 = e - f;
     // xz plane (11..14)
-    const float a2 = h[11] + h[12], b2 = h[13] + h[14], c2 = h[11] + h[13], d2 = h[12] + h[14];
-    const float e2 = h[11] + h[14], f2 = h[12] + h[13];
+    const T a2 = h[11] + h[12], b2 = h[13] + h[14], c2 = h[11] + h[13], d2 = h[12] + h[14];
+    const T e2 = h[11] + h[14], f2 = h[12] + h[13];
     k.m202 = a2 + b2; k.m201 = a2 - b2; k.m102 = c2 - d2; k.m101 = e2 - f2;
     // yz plane (15..18)
-    const float a3 = h[15] + h[16], b3 = h[17] + h[18], c3 = h[15] + h[17], d3 = h[16] + h[18];
-    const float e3 = h[15] + h[18], f3 = h[16] + h[17];
+    const T a3 = h[15] + h[16], b3 = h[17] + h[18], c3 = h[15] + h[17], d3 = h[16] + h[18];
+    const T e3 = h[15] + h[18], f3 = h[16] + h[17];
     k.m022 = a3 + b3; k.m021 = a3 - b3; k.m012 = c3 - d3; k.m011 = e3 - f3;
     // axes
-    const float s12 = h[1] + h[2], s34 = h[3] + h[4], s56 = h[5] + h[6];
+    const T s12 = h[1] + h[2], s34 = h[3] + h[4], s56 = h[5] + h[6];
     k.m200 = s12 + k.m220 + k.m202;
     k.m020 = s34 + k.m220 + k.m022;
     k.m002 = s56 + k.m202 + k.m022;
@@ -252,13 +279,15 @@ __device__ __forceinline__ void raw_moments(const float (&h)[kQ], Moments &k) {
 
 // Deviations of the generalized-equilibrium raw moments, rho G(u) - M w,
 // for the 15 moments other than the ones with a zero/first-order closed form.
-struct EqDev {
-    float d110, d101, d011, d200, d020, d002, d120, d102, d210, d201, d012, d021, d220, d202, d022;
+template <typename T>
+struct EqDevT {
+    T d110, d101, d011, d200, d020, d002, d120, d102, d210, d201, d012, d021, d220, d202, d022;
 };
+using EqDev = EqDevT<float>;
 
-__device__ __forceinline__ void eq_dev(float drho, float rho, float jx, float jy, float jz,
-                                       float ux, float uy, float uz, EqDev &q) {
-    const float X = ux * ux, Y = uy * uy, Z = uz * uz;
+template <typename T>
+__device__ __forceinline__ void eq_dev(T drho, T rho, T jx, T jy, T jz, T ux, T uy, T uz, EqDevT<T> &q) {
+    const T X = ux * ux, Y = uy * uy, Z = uz * uz;
     q.d110 = jx * uy; q.d101 = jx * uz; q.d011 = jy * uz;
     q.d200 = fmaf(jx, ux, drho * kC); q.d020 = fmaf(jy, uy, drho * kC); q.d002 = fmaf(jz, uz, drho * kC);
     q.d120 = jx * (Y + kC); q.d102 = jx * (Z + kC);
@@ -270,7 +299,8 @@ __device__ __forceinline__ void eq_dev(float drho, float rho, float jx, float jy
 }
 
 // h = M^-1 Q for raw-moment deviations Q (Eq. 7, M^-1 of Eq. A4).
-__device__ __forceinline__ void inverse_moments(const Moments &q, float (&h)[kQ]) {
+template <typename T>
+__device__ __forceinline__ void inverse_moments(const MomentsT<T> &q, T (&h)[kQ]) {
     h[7] = 0.25f * ((q.m220 + q.m210) + (q.m120 + q.m110));
     h[8] = 0.25f * ((q.m220 + q.m210) - (q.m120 + q.m110));
     h[9] = 0.25f * ((q.m220 - q.m210) + (q.m120 - q.m110));
@@ -283,9 +313,9 @@ __device__ __forceinline__ void inverse_moments(const Moments &q, float (&h)[kQ]
     h[16] = 0.25f * ((q.m022 + q.m021) - (q.m012 + q.m011));
     h[17] = 0.25f * ((q.m022 - q.m021) + (q.m012 - q.m011));
     h[18] = 0.25f * ((q.m022 - q.m021) - (q.m012 - q.m011));
-    const float px = q.m200 - q.m220 - q.m202, vx = q.m100 - q.m120 - q.m102;
-    const float py = q.m020 - q.m220 - q.m022, vy = q.m010 - q.m210 - q.m012;
-    const float pz = q.m002 - q.m202 - q.m022, vz = q.m001 - q.m201 - q.m021;
+    const T px = q.m200 - q.m220 - q.m202, vx = q.m100 - q.m120 - q.m102;
+    const T py = q.m020 - q.m220 - q.m022, vy = q.m010 - q.m210 - q.m012;
+    const T pz = q.m002 - q.m202 - q.m022, vz = q.m001 - q.m201 - q.m021;
     h[1] = 0.5f * (px + vx); h[2] = 0.5f * (px - vx);
     h[3] = 0.5f * (py + vy); h[4] = 0.5f * (py - vy);
     h[5] = 0.5f * (pz + vz); h[6] = 0.5f * (pz - vz);
@@ -295,26 +325,28 @@ __device__ __forceinline__ void inverse_moments(const Moments &q, float (&h)[kQ]
 // One collision (Steps 1-3 of Sec. II.B) on deviations h, in place.
 // Returns drho = rho - 1 of the pre-collision state (Eq. 9); if j_out is not
 // null it receives rho*u of Eq. 9 (momentum including F/2).
-__device__ __forceinline__ float collide(float (&h)[kQ], float Fx, float Fy, float Fz, const Rates &r,
-                                         float3 *j_out = nullptr) {
-    Moments k;
+template <typename T>
+__device__ __forceinline__ T collide(T (&h)[kQ], T Fx, T Fy, T Fz, const Rates &r, float3 *j_out = nullptr) {
+    MomentsT<T> k;
     raw_moments(h, k);
-    const float drho = k.m000;
-    const float rho = 1.0f + drho;
-    const float inv = 1.0f / rho;
-    const float jx = fmaf(0.5f, Fx, k.m100), jy = fmaf(0.5f, Fy, k.m010), jz = fmaf(0.5f, Fz, k.m001);
-    const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
-    if (j_out) *j_out = make_float3(jx, jy, jz);
-    EqDev e;
+    const T drho = k.m000;
+    const T rho = 1.0f + drho;
+    const T inv = 1.0f / rho;
+    const T jx = fmaf(0.5f, Fx, k.m100), jy = fmaf(0.5f, Fy, k.m010), jz = fmaf(0.5f, Fz, k.m001);
+    const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (j_out) *j_out = make_float3(jx, jy, jz);
+    }
+    EqDevT<T> e;
     eq_dev(drho, rho, jx, jy, jz, ux, uy, uz, e);
 
     // non-equilibrium raw moments R = dT - (rho G - M w); R000 = 0, R100 = -Fx/2, ...
-    const float hFx = 0.5f * Fx, hFy = 0.5f * Fy, hFz = 0.5f * Fz;
-    float r110 = k.m110 - e.d110, r101 = k.m101 - e.d101, r011 = k.m011 - e.d011;
-    float r200 = k.m200 - e.d200, r020 = k.m020 - e.d020, r002 = k.m002 - e.d002;
-    float r120 = k.m120 - e.d120, r102 = k.m102 - e.d102, r210 = k.m210 - e.d210;
-    float r201 = k.m201 - e.d201, r012 = k.m012 - e.d012, r021 = k.m021 - e.d021;
-    float r220 = k.m220 - e.d220, r202 = k.m202 - e.d202, r022 = k.m022 - e.d022;
+    const T hFx = 0.5f * Fx, hFy = 0.5f * Fy, hFz = 0.5f * Fz;
+    T r110 = k.m110 - e.d110, r101 = k.m101 - e.d101, r011 = k.m011 - e.d011;
+    T r200 = k.m200 - e.d200, r020 = k.m020 - e.d020, r002 = k.m002 - e.d002;
+    T r120 = k.m120 - e.d120, r102 = k.m102 - e.d102, r210 = k.m210 - e.d210;
+    T r201 = k.m201 - e.d201, r012 = k.m012 - e.d012, r021 = k.m021 - e.d021;
+    T r220 = k.m220 - e.d220, r202 = k.m202 - e.d202, r022 = k.m022 - e.d022;
 
     // D = N(u) R: x shift on (000,100,200) (010,110,210) (001,101,201) (020,120,220) (002,102,202)
     r200 = fmaf(ux, Fx, r200);                 // R000 = 0, R100 = -Fx/2
@@ -339,7 +371,7 @@ __device__ __forceinline__ float collide(float (&h)[kQ], float Fx, float Fy, flo
     // s0 = s1 = 1: D*000 = 0, D*100 = Fx/2, ...
     r110 *= r.om2; r101 *= r.om2; r011 *= r.om2;
     {
-        const float tr = r.cb * (r200 + r020 + r002);
+        const T tr = r.cb * (r200 + r020 + r002);
         r200 = fmaf(r.om2, r200, -tr);
         r020 = fmaf(r.om2, r020, -tr);
         r002 = fmaf(r.om2, r002, -tr);
@@ -370,7 +402,7 @@ __device__ __forceinline__ float collide(float (&h)[kQ], float Fx, float Fy, flo
     unshift3(r002, r102, r202, ux);
 
     // Q = R* + (rho G(u) - M w); first order: R*100 = Fx/2, so Q100 = jx + Fx/2.
-    Moments q;
+    MomentsT<T> q;
     q.m000 = drho;
     q.m100 = jx + hFx; q.m010 = jy + hFy; q.m001 = jz + hFz;
     q.m110 = r110 + e.d110; q.m101 = r101 + e.d101; q.m011 = r011 + e.d011;
@@ -384,12 +416,13 @@ __device__ __forceinline__ float collide(float (&h)[kQ], float Fx, float Fy, flo
 
 // Deviations of the generalized local equilibrium at (rho, u):
 // h = M^-1 (rho G(u) - M w).
-__device__ __forceinline__ void equilibrium_dev(float rho, float ux, float uy, float uz, float (&h)[kQ]) {
-    const float drho = rho - 1.0f;
-    const float jx = rho * ux, jy = rho * uy, jz = rho * uz;
-    EqDev e;
+template <typename T>
+__device__ __forceinline__ void equilibrium_dev(T rho, T ux, T uy, T uz, T (&h)[kQ]) {
+    const T drho = rho - 1.0f;
+    const T jx = rho * ux, jy = rho * uy, jz = rho * uz;
+    EqDevT<T> e;
     eq_dev(drho, rho, jx, jy, jz, ux, uy, uz, e);
-    Moments q;
+    MomentsT<T> q;
     q.m000 = drho; q.m100 = jx; q.m010 = jy; q.m001 = jz;
     q.m110 = e.d110; q.m101 = e.d101; q.m011 = e.d011;
     q.m200 = e.d200; q.m020 = e.d020; q.m002 = e.d002;
@@ -400,9 +433,9 @@ __device__ __forceinline__ void equilibrium_dev(float rho, float ux, float uy, f
 }
 
 // Eq. 9 on deviations: returns drho and writes rho*u (momentum incl. F/2).
-__device__ __forceinline__ float macros_dev(const float (&h)[kQ], float Fx, float Fy, float Fz,
-                                            float &jx, float &jy, float &jz) {
-    Moments k;
+template <typename T>
+__device__ __forceinline__ T macros_dev(const T (&h)[kQ], T Fx, T Fy, T Fz, T &jx, T &jy, T &jz) {
+    MomentsT<T> k;
     raw_moments(h, k);
     jx = fmaf(0.5f, Fx, k.m100);
     jy = fmaf(0.5f, Fy, k.m010);

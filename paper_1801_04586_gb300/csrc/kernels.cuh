@@ -17,12 +17,14 @@ struct ForceArgs {
     const float *profile;    // 3 x nz
     const float *field;      // 3 x N
     int64_t n;               // N, component stride of `field`
+    float scale;             // time factor e^{-gamma t} of the step (1 for a static force)
 };
 
 struct Launch {
     Geom g;
-    dim3 block, grid;
+    dim3 block, grid;  // grid of the one-node-per-thread kernels
     cudaStream_t stream;
+    bool packed;       // launch_step: two nodes per thread (grid.x halved)
 };
 
 // storage: 0 = f32, 1 = f16, 2 = bf16, 3 = f16 stochastic, 4 = bf16 stochastic

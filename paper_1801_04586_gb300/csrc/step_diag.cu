@@ -21,6 +21,9 @@ __device__ __forceinline__ void force_diag(const ForceArgs &F, const Geom &g, in
     } else {
         fx = __ldg(F.field + self); fy = __ldg(F.field + F.n + self); fz = __ldg(F.field + 2 * F.n + self);
     }
+    fx *= F.scale;
+    fy *= F.scale;
+    fz *= F.scale;
 }
 
 template <typename S, int FM, bool WALLS>

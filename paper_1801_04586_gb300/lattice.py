@@ -32,7 +32,7 @@ class Lattice:
 
     def __init__(self, nx: int, ny: int, nz: int, nu: float, walls: int = 0, s2b: float = 1.0,
                  s3: float = 1.0, s4: float = 1.0, storage: str = "f32", block: Tuple[int, int] = (0, 0),
-                 device=None, stream: Optional[torch.cuda.Stream] = None):
+                 device=None, stream: Optional[torch.cuda.Stream] = None, variant: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required: the lattice runs only in libclbm.so's kernels")
         self.lib = _capi.lib()
@@ -46,7 +46,7 @@ class Lattice:
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             p = _capi.Params(self.nx, self.ny, self.nz, self.walls, float(nu), float(s2b), float(s3), float(s4),
-                             _capi.STORAGE[storage], int(block[0]), int(block[1]), 0)
+                             _capi.STORAGE[storage], int(block[0]), int(block[1]), int(variant))
             h = ctypes.c_void_p()
             check(self.lib.clbm_create(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
                   "clbm_create")
@@ -95,6 +95,10 @@ class Lattice:
         self._dev(F, (3,) + self.shape, "F")
         check(self.lib.clbm_set_force_field(self.h, _ptr(F)), "clbm_set_force_field")
         self._force_ref = F
+
+    def set_force_decay(self, gamma: float):
+        """Force in use at step t becomes F exp(-gamma t) (gamma = 0: static)."""
+        check(self.lib.clbm_set_force_decay(self.h, float(gamma)), "clbm_set_force_decay")
 
     # ---- state
     def init_equilibrium(self, rho: Optional[torch.Tensor] = None, u: Optional[torch.Tensor] = None):

@@ -92,3 +92,35 @@ def shear_wave_amplitude(ux_y: np.ndarray) -> float:
     L = ux_y.shape[-1]
     y = np.arange(L)
     return 2.0 / L * float(np.sum(ux_y * np.sin(2 * np.pi * y / L)))
+
+
+def taylor_green(L: int, u0: float, nu: float, t: float):
+    """Sec. III.D: decaying Taylor-Green vortex on an L x L periodic box with
+    k1 = k2 = 2 pi / L, node positions x = 0..L-1. Returns (u_x, u_y) as [y, x]
+    arrays at time t."""
+    k = 2.0 * np.pi / L
+    x = np.arange(L)[None, :]
+    y = np.arange(L)[:, None]
+    d = np.exp(-2.0 * nu * k * k * t)
+    return -u0 * np.cos(k * x) * np.sin(k * y) * d, u0 * np.sin(k * x) * np.cos(k * y) * d
+
+
+def taylor_green_force(L: int, u0: float, rho: float = 1.0):
+    """The body force of Sec. III.D at t = 0, (F_x, F_y) as [y, x] arrays; it
+    decays as exp(-gamma t) with gamma = taylor_green_decay(L, nu)."""
+    k = 2.0 * np.pi / L
+    x = np.arange(L)[None, :] * np.ones((L, 1))
+    y = np.arange(L)[:, None] * np.ones((1, L))
+    return -(rho * k * u0 * u0 / 2.0) * np.sin(2.0 * k * x), -(rho * k * u0 * u0 / 2.0) * np.sin(2.0 * k * y)
+
+
+def taylor_green_decay(L: int, nu: float) -> float:
+    """Decay rate of the Taylor-Green force: 2 nu (k1^2 + k2^2)."""
+    k = 2.0 * np.pi / L
+    return 4.0 * nu * k * k
+
+
+def taylor_green_time(L: int, nu: float, tstar: float) -> int:
+    """Steps to reach T* = nu (k1^2 + k2^2) t / ln 2 (Sec. III.D)."""
+    k = 2.0 * np.pi / L
+    return int(round(tstar * np.log(2.0) / (2.0 * nu * k * k)))

@@ -31,8 +31,9 @@ def s2_of(nu):
     return 1.0 / (3.0 * nu + 0.5)
 
 
-def make_pair(nx, ny, nz, nu, walls=0, s2b=1.0, s3=1.0, s4=1.0, storage="f32", block=(0, 0)):
-    g = Lattice(nx, ny, nz, nu, walls=walls, s2b=s2b, s3=s3, s4=s4, storage=storage, block=block, device=dev())
+def make_pair(nx, ny, nz, nu, walls=0, s2b=1.0, s3=1.0, s4=1.0, storage="f32", block=(0, 0), variant=0):
+    g = Lattice(nx, ny, nz, nu, walls=walls, s2b=s2b, s3=s3, s4=s4, storage=storage, block=block, device=dev(),
+                variant=variant)
     o = oracle.Lattice(nx, ny, nz, walls=walls, s2=s2_of(nu), s2b=s2b, s3=s3, s4=s4)
     return g, o
 

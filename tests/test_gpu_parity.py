@@ -74,6 +74,25 @@ def test_100_steps_parity(case):
     np.testing.assert_allclose(rg.double().cpu().numpy(), ro, rtol=0, atol=1e-6)
 
 
+@pytest.mark.parametrize("shape_walls", [((150, 20, 12), 7), ((37, 19, 23), 0), ((1, 5, 9), 4), ((300, 3, 2), 2)])
+def test_two_nodes_per_thread_parity(shape_walls):
+    """The packed step (two nodes per thread, FP32x2 arithmetic) on FP32
+    storage, including row tails where the second lane has no node."""
+    (nx, ny, nz), walls = shape_walls
+    shape = (nz, ny, nx)
+    g, o = make_pair(nx, ny, nz, 0.03, walls=walls, s2b=1.2, s3=1.1, s4=0.9, variant=2)
+    assert g.info()["nodes_per_thread"] == 2
+    h0 = synthetic.random_deviations(shape, 2e-3, seed=33)
+    F = synthetic.gaussian_force(shape, 1e-4, seed=34)
+    g.set_force_field(t(F))
+    g.set_populations(t(h0), deviation=True)
+    g.step(100)
+    fo = oracle.step(o, h0.astype(np.float64) + W, F, 100)
+    report("parity_packed", shape=str(shape), rel=rel_err(gpu_f(g), fo))
+    assert rel_err(gpu_f(g), fo) < F32_REL_TOL
+    g.check()
+
+
 def test_random_state_parity():
     """An arbitrary non-equilibrium state (random deviations) set through the ABI."""
     nx, ny, nz = 32, 32, 32
