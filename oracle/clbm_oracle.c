@@ -8,12 +8,18 @@
  * test suite, the package smoke check and the benchmark's CPU-baseline leg may
  * load it. It shares no code, header, table or helper with the CUDA library.
  *
+ * Built twice from this one source: ORACLE_Q = 19 (Appendix A, exported as
+ * ora_*) and ORACLE_Q = 27 (Sec. II, the paper's main development, exported
+ * as ora27_*). The lattice enters only through the tables below.
+ *
  * What it computes (everything in double precision):
- *   - D3Q19 velocities in the order of Eq. A1, the simplified central-moment
- *     set of Eq. A2, M built from its definition (Eq. 4), M^-1 by Gauss-Jordan.
+ *   - The velocities in the order of Eq. A1 (Eq. 1), the simplified
+ *     central-moment set of Eq. A2 (Eq. 12), M built from its definition
+ *     (Eq. 4), M^-1 by Gauss-Jordan.
  *   - Per node, the algorithm of Sec. II.B: Step 1 central moments straight
  *     from Eq. 2 (no M, no N); Step 2 the collision of Eq. 5 with the dense
- *     block-diagonal S of Eq. A3, T~eq of Eq. A5 and C of Eq. A6; Step 3
+ *     block-diagonal S of Eq. A3 (Eq. 13), T~eq of Eq. A5 (Eq. 15) and C of
+ *     Eq. A6 (Eq. 16); Step 3
  *     T* = N(u)^-1 T~* by a dense solve and f* = M^-1 T*; Step 4 push streaming
  *     (Eq. 8) with periodic faces or halfway bounce-back walls, and Eq. 9.
  *   - An adjoint of one step: per-node Jacobians by complex-step
@@ -22,7 +28,8 @@
  *
  * Readings of points the paper leaves open or prints garbled:
  *   - Eq. 2 prints (e_iy - u_z)^p as the third factor; read (e_iz - u_z)^p.
- *   - Eq. A2 lists k~020 twice; the tenth moment is k~002 (M row 9 is e_z^2).
+ *   - Eqs. A2 and 12 list k~020 twice; the tenth moment is k~002 (M row 9 is
+ *     e_z^2 in both printed matrices).
  *   - S uses s_nu for k~110, k~101, k~011 and s_2 in the viscosity relation; we
  *     read s_nu = s_2 (the deviatoric eigenvalue of the 3x3 block is s_2).
  *   - Halfway bounce-back: a population whose streaming destination lies
@@ -41,9 +48,46 @@
 #include <omp.h>
 #endif
 
-#define Q 19
+#ifndef ORACLE_Q
+#define ORACLE_Q 19
+#endif
+#define Q ORACLE_Q
 #define CS2 (1.0 / 3.0)
 
+#if ORACLE_Q == 27
+#define ORA(name) ora27_##name
+/* Eq. 1 (D3Q27). */
+static const int EV[Q][3] = {
+    {0, 0, 0},
+    {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 0}, {-1, 1, 0}, {1, -1, 0}, {-1, -1, 0},
+    {1, 0, 1}, {-1, 0, 1}, {1, 0, -1}, {-1, 0, -1},
+    {0, 1, 1}, {0, -1, 1}, {0, 1, -1}, {0, -1, -1},
+    {1, 1, 1}, {-1, 1, 1}, {1, -1, 1}, {-1, -1, 1},
+    {1, 1, -1}, {-1, 1, -1}, {1, -1, -1}, {-1, -1, -1},
+};
+/* Eq. 12: exponents of the simplified central-moment set. */
+static const int MOM[Q][3] = {
+    {0, 0, 0},
+    {1, 0, 0}, {0, 1, 0}, {0, 0, 1},
+    {1, 1, 0}, {1, 0, 1}, {0, 1, 1},
+    {2, 0, 0}, {0, 2, 0}, {0, 0, 2},
+    {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {2, 0, 1}, {0, 1, 2}, {0, 2, 1},
+    {1, 1, 1},
+    {2, 2, 0}, {2, 0, 2}, {0, 2, 2},
+    {2, 1, 1}, {1, 2, 1}, {1, 1, 2},
+    {1, 2, 2}, {2, 1, 2}, {2, 2, 1},
+    {2, 2, 2},
+};
+/* Eq. 15: T~eq_j = rho c_s^(2 p) with p = TEQ_POW[j], 0 where p < 0. */
+static const int TEQ_POW[Q] = {0,  -1, -1, -1, -1, -1, -1, 1,  1,  1,  -1, -1, -1, -1,
+                               -1, -1, -1, 2,  2,  2,  -1, -1, -1, -1, -1, -1, 3};
+/* Eq. 16: C_j = F_a c_s^(2 p) with a = CF_AXIS[j] (-1: zero), p = CF_POW[j]. */
+static const int CF_AXIS[Q] = {-1, 0,  1,  2,  -1, -1, -1, -1, -1, -1, 0, 0, 1, 2,
+                               1,  2,  -1, -1, -1, -1, -1, -1, -1, 0,  1, 2, -1};
+static const int CF_POW[Q] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 0, 0, 0, 0, 0, 0, 0, 2, 2, 2, 0};
+#else
+#define ORA(name) ora_##name
 /* Eq. A1 (D3Q19): rest, +-x, +-y, +-z, xy, xz, yz diagonals. */
 static const int EV[Q][3] = {
     {0, 0, 0},
@@ -62,11 +106,18 @@ static const int MOM[Q][3] = {
     {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {2, 0, 1}, {0, 1, 2}, {0, 2, 1},
     {2, 2, 0}, {2, 0, 2}, {0, 2, 2},
 };
+/* Eq. A5: T~eq_j = rho c_s^(2 p) with p = TEQ_POW[j], 0 where p < 0. */
+static const int TEQ_POW[Q] = {0, -1, -1, -1, -1, -1, -1, 1, 1, 1, -1, -1, -1, -1, -1, -1, 2, 2, 2};
+/* Eq. A6: C_j = F_a c_s^(2 p) with a = CF_AXIS[j] (-1: zero), p = CF_POW[j]. */
+static const int CF_AXIS[Q] = {-1, 0, 1, 2, -1, -1, -1, -1, -1, -1, 0, 0, 1, 2, 1, 2, -1, -1, -1};
+static const int CF_POW[Q] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 0, 0, 0};
+#endif
 
 typedef struct {
     int nx, ny, nz;
     int walls;          /* bit 0: x faces are walls, bit 1: y, bit 2: z */
     double s0, s1, s2, s2b, s3, s4;
+    double s3b, s4b, s5, s6;  /* D3Q27 only (Eq. 13) */
 } ora_lattice;
 
 static int binom(int n, int k)
@@ -144,7 +195,8 @@ static void build_Minv(double Minv[Q][Q])
         for (int c = 0; c < Q; ++c) Minv[r][c] = A[r][Q + c];
 }
 
-/* Eq. A3 with s_nu read as s_2, s_+ = (s2b + 2 s2)/3, s_- = (s2b - s2)/3. */
+/* Eq. A3 (D3Q19) or Eq. 13 (D3Q27) with s_nu read as s_2,
+ * s_+ = (s2b + 2 s2)/3, s_- = (s2b - s2)/3. */
 static void build_S(const ora_lattice *L, double S[Q][Q])
 {
     memset(S, 0, sizeof(double) * Q * Q);
@@ -155,7 +207,15 @@ static void build_S(const ora_lattice *L, double S[Q][Q])
     for (int r = 7; r <= 9; ++r)
         for (int c = 7; c <= 9; ++c) S[r][c] = (r == c) ? sp : sm;
     for (int j = 10; j <= 15; ++j) S[j][j] = L->s3;
+#if ORACLE_Q == 27
+    S[16][16] = L->s3b;
+    for (int j = 17; j <= 19; ++j) S[j][j] = L->s4;
+    for (int j = 20; j <= 22; ++j) S[j][j] = L->s4b;
+    for (int j = 23; j <= 25; ++j) S[j][j] = L->s5;
+    S[26][26] = L->s6;
+#else
     for (int j = 16; j <= 18; ++j) S[j][j] = L->s4;
+#endif
 }
 
 static double g_Minv[Q][Q];
@@ -171,53 +231,53 @@ static void ensure_ready(void)
 
 /* ---- exported: tables and matrices ---- */
 
-void ora_velocities(int *e)
+void ORA(velocities)(int *e)
 {
     for (int i = 0; i < Q; ++i)
         for (int a = 0; a < 3; ++a) e[3 * i + a] = EV[i][a];
 }
 
-void ora_moment_exponents(int *m)
+void ORA(moment_exponents)(int *m)
 {
     for (int j = 0; j < Q; ++j)
         for (int a = 0; a < 3; ++a) m[3 * j + a] = MOM[j][a];
 }
 
-void ora_matrix_M(double *out)
+void ORA(matrix_M)(double *out)
 {
     double M[Q][Q];
     build_M(M);
     memcpy(out, M, sizeof(M));
 }
 
-void ora_matrix_Minv(double *out)
+void ORA(matrix_Minv)(double *out)
 {
     ensure_ready();
     memcpy(out, g_Minv, sizeof(g_Minv));
 }
 
-void ora_matrix_N(const double *u, double *out)
+void ORA(matrix_N)(const double *u, double *out)
 {
     double N[Q][Q];
     shift_matrix_r(u, N);
     memcpy(out, N, sizeof(N));
 }
 
-void ora_matrix_S(const ora_lattice *L, double *out)
+void ORA(matrix_S)(const ora_lattice *L, double *out)
 {
     double S[Q][Q];
     build_S(L, S);
     memcpy(out, S, sizeof(S));
 }
 
-void ora_teq(double rho, double *out) { teq_r(rho, out); }
-void ora_cforce(const double *F, double *out) { cforce_r(F, out); }
+void ORA(teq)(double rho, double *out) { teq_r(rho, out); }
+void ORA(cforce)(const double *F, double *out) { cforce_r(F, out); }
 
-void ora_central_moments(const double *f, const double *u, double *kt) { central_moments_r(f, u, kt); }
+void ORA(central_moments)(const double *f, const double *u, double *kt) { central_moments_r(f, u, kt); }
 
-void ora_macros_node(const double *f, const double *F, double *rho, double *u) { macros_r(f, F, rho, u); }
+void ORA(macros_node)(const double *f, const double *F, double *rho, double *u) { macros_r(f, F, rho, u); }
 
-void ora_collide(const ora_lattice *L, const double *f, const double *F, double *fs)
+void ORA(collide)(const ora_lattice *L, const double *f, const double *F, double *fs)
 {
     ensure_ready();
     double S[Q][Q];
@@ -225,7 +285,7 @@ void ora_collide(const ora_lattice *L, const double *f, const double *F, double 
     collide_r(S, g_Minv, f, F, fs);
 }
 
-void ora_equilibrium(double rho, const double *u, double *feq)
+void ORA(equilibrium)(double rho, const double *u, double *feq)
 {
     ensure_ready();
     equilibrium_r(g_Minv, rho, u, feq);
@@ -266,7 +326,7 @@ static void set_threads(int nthreads)
 #endif
 }
 
-int ora_num_threads(void)
+int ORA(num_threads)(void)
 {
 #ifdef _OPENMP
     return omp_get_max_threads();
@@ -276,7 +336,7 @@ int ora_num_threads(void)
 }
 
 /* Initial state: generalized equilibrium at (rho, u - F/(2 rho)). */
-int ora_init(const ora_lattice *L, const double *rho, const double *u, const double *F, double *f)
+int ORA(init)(const ora_lattice *L, const double *rho, const double *u, const double *F, double *f)
 {
     ensure_ready();
     long N = lattice_n(L);
@@ -297,15 +357,15 @@ int ora_init(const ora_lattice *L, const double *rho, const double *u, const dou
 /* nsteps full time steps (Steps 1-4), in place on f (post-streaming state),
  * with the force F(x) e^{-gamma t}, t = t0, t0 + 1, ... the time of each
  * collision (gamma = 0: a static force). */
-int ora_step_decay(const ora_lattice *L, const double *F, double *f, int nsteps, int nthreads, double t0,
+int ORA(step_decay)(const ora_lattice *L, const double *F, double *f, int nsteps, int nthreads, double t0,
                    double gamma);
 
-int ora_step(const ora_lattice *L, const double *F, double *f, int nsteps, int nthreads)
+int ORA(step)(const ora_lattice *L, const double *F, double *f, int nsteps, int nthreads)
 {
-    return ora_step_decay(L, F, f, nsteps, nthreads, 0.0, 0.0);
+    return ORA(step_decay)(L, F, f, nsteps, nthreads, 0.0, 0.0);
 }
 
-int ora_step_decay(const ora_lattice *L, const double *F, double *f, int nsteps, int nthreads, double t0,
+int ORA(step_decay)(const ora_lattice *L, const double *F, double *f, int nsteps, int nthreads, double t0,
                    double gamma)
 {
     ensure_ready();
@@ -341,7 +401,7 @@ int ora_step_decay(const ora_lattice *L, const double *F, double *f, int nsteps,
 }
 
 /* Eq. 9 over the lattice. */
-int ora_macros(const ora_lattice *L, const double *f, const double *F, double *rho, double *u)
+int ORA(macros)(const ora_lattice *L, const double *f, const double *F, double *rho, double *u)
 {
     long N = lattice_n(L);
     for (long s = 0; s < N; ++s) {
@@ -358,7 +418,7 @@ int ora_macros(const ora_lattice *L, const double *f, const double *F, double *r
 /* One step for a list of nodes only, starting from the initial state that
  * ora_init would build from (rho, u, F): out[k*Q + i] = f_i(node_k, t = 1).
  * Lets a test check sampled nodes of a lattice too large for ora_step. */
-int ora_first_step_nodes(const ora_lattice *L, const double *rho, const double *u, const double *F,
+int ORA(first_step_nodes)(const ora_lattice *L, const double *rho, const double *u, const double *F,
                          int nnodes, const long *nodes, double *out, int nthreads)
 {
     ensure_ready();
@@ -426,7 +486,7 @@ static void collide_jacobian(const double S[Q][Q], const double f[Q], const doub
  *   lam*_i(x) = lam^{t+1} at the slot that (x, i) streams into (P transposed),
  *   lam^t(x)  = J_f(x)^T lam*(x),   gF(x) += J_F(x)^T lam*(x).
  * f_t is the post-streaming state at t; gF is accumulated (3N SoA). */
-int ora_adjoint_step(const ora_lattice *L, const double *f_t, const double *F, const double *lam_next,
+int ORA(adjoint_step)(const ora_lattice *L, const double *f_t, const double *F, const double *lam_next,
                      double *lam_t, double *gF, int nthreads)
 {
     ensure_ready();
@@ -466,7 +526,7 @@ int ora_adjoint_step(const ora_lattice *L, const double *f_t, const double *F, c
 
 /* Seed of the adjoint from a cotangent g on the final velocity u(x,T) of Eq. 9:
  * lam^T_i(x) = sum_a g_a(x) du_a/df_i, gF_a(x) += g_a(x) du_a/dF_a. */
-int ora_adjoint_seed(const ora_lattice *L, const double *f_T, const double *F, const double *g,
+int ORA(adjoint_seed)(const ora_lattice *L, const double *f_T, const double *F, const double *g,
                      double *lam_T, double *gF)
 {
     long N = lattice_n(L);
