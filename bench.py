@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--block", default="0,0", help="step kernel block shape bx,by (0,0 = default)")
     ap.add_argument("--size", type=int, default=N_SIDE,
                     help="box side (the benchmark workload is 256; smaller sides are for profiling captures)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f16sr", "bf16sr"],
+                    help="storage of the timed lattice (the benchmark line is f32; others for profiling)")
+    ap.add_argument("--variant", type=int, default=0, help="step kernel form (0/1: one node per thread, 2: two)")
+    ap.add_argument("--lattice", type=int, default=19, choices=[19, 27])
     return ap.parse_args()
 
 
@@ -238,6 +242,30 @@ def bench_storage(storage, K, warmup, dev, side, prof, u0, peak, variant=0):
             "achieved_gbs": achieved, "frac": achieved / peak, "nodes_per_thread": npt}
 
 
+def bench_d3q27(K, warmup, dev, side, prof, u0, peak):
+    """The same workload on the D3Q27 lattice of Sec. II (FP32, 216 B/node)."""
+    import torch
+
+    from paper_1801_04586_gb300 import Lattice
+    lat = Lattice(side, side, side, NU, device=dev, lattice=27)
+    lat.set_force_profile_z(prof)
+    lat.init_equilibrium(None, u0)
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record(lat.stream)
+    lat.step(K)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    lat.check()
+    ms = e0.elapsed_time(e1)
+    n = lat.n
+    lat.close()
+    achieved = 216 * n / (ms / K * 1e-3) / 1e9
+    return {"value": n * K / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / K, "bytes_per_node": 216,
+            "achieved_gbs": achieved, "frac": achieved / peak}
+
+
 def bench_adjoint(dev, side, K, peak):
     """Adjoint step kernel versus forward step kernel on the same lattice with a
     force field (F ~ N(0, 1e-5^2), seed 3): per-launch times."""
@@ -374,7 +402,8 @@ def run_gb300(args):
     bx, by = (int(v) for v in args.block.split(","))
     side = args.size
     shape = (side, side, side)
-    lat = Lattice(side, side, side, NU, walls=0, storage="f32", block=(bx, by), device=dev)
+    lat = Lattice(side, side, side, NU, walls=0, storage=args.storage, block=(bx, by), device=dev,
+                  variant=args.variant, lattice=args.lattice)
     prof = torch.from_numpy(synthetic.kolmogorov_profile(side, F0)).to(dev)
     u0_np = synthetic.divfree_velocity(shape, seed=1, umax=UMAX)
     u0 = torch.from_numpy(u0_np).to(dev)
@@ -417,8 +446,9 @@ def run_gb300(args):
     value = ws * nodes * K / (elapsed_ms * 1e-3) / 1e6
     mean_launch_s = statistics.mean(per_launch) * 1e-3
     peak, peak_kind = measured_peaks()
-    achieved = BYTES_PER_NODE * nodes / mean_launch_s / 1e9
-    traffic = profiled_traffic()
+    bytes_per_node = (2 if args.storage != "f32" else 4) * 2 * args.lattice
+    achieved = bytes_per_node * nodes / mean_launch_s / 1e9
+    traffic = profiled_traffic() if (args.storage, args.lattice, side) == ("f32", 19, N_SIDE) else None
 
     e2e = None
     if not args.no_e2e:
@@ -461,6 +491,7 @@ def run_gb300(args):
                                                              variant=1),
             "f16_stochastic_storage": bench_storage("f16sr", K, args.warmup, dev, side, prof, u0, peak),
             "bf16_stochastic_storage": bench_storage("bf16sr", K, args.warmup, dev, side, prof, u0, peak),
+            "d3q27_f32": bench_d3q27(K, args.warmup, dev, side, prof, u0, peak),
             "adjoint_kernel_256": bench_adjoint(dev, side, max(10, min(K, 100)), peak),
             "adjoint_unroll_64": bench_unroll(dev),
             "batched_64_domains": bench_batch(dev, args.batch_steps, peak),
@@ -478,7 +509,8 @@ def run_gb300(args):
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": "f32" if args.storage == "f32" else f"f32 arithmetic, {args.storage} storage",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD if side == N_SIDE else WORKLOAD.replace("256", str(side)),
                        "nx": side, "ny": side, "nz": side, "nu": NU, "F0": F0,
                        "storage": "f32 A/B pull", "block": [info["block_x"], info["block_y"]],
@@ -486,7 +518,9 @@ def run_gb300(args):
                        "parallelism": f"{ws} independent replica(s), one per GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": BYTES_PER_NODE * nodes, "kernel": "k_step<float,1,false>"},
+                         "algorithmic_bytes_per_launch": bytes_per_node * nodes,
+                         "kernel": "k_step<float,1,false>" if (args.storage, args.lattice) == ("f32", 19)
+                         else f"step kernel, {args.storage} storage, D3Q{args.lattice}"},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "variants": variants,

@@ -13,7 +13,8 @@
  * - Lattice: nx x ny x nz nodes, node index s = (z*ny + y)*nx + x (x fastest),
  *   N = nx*ny*nz. Node spacing and time step are 1 (lattice units, c_s^2 = 1/3).
  * - Population arrays exchanged with the caller are float32, structure of
- *   arrays, f[i*N + s] for the 19 velocities in the order of Eq. A1. Vector
+ *   arrays, f[i*N + s] for the Q = 19 velocities in the order of Eq. A1 (or
+ *   Q = 27 in the order of Eq. 1, see clbm_params.lattice). Vector
  *   fields are 3 x N (component-major: F[a*N + s]); scalar fields are N.
  * - Every pointer marked _dev is a CUDA device pointer owned by the caller; it
  *   must stay valid until the work that uses it has finished on the context's
@@ -72,10 +73,18 @@ extern "C" {
  * walls: CLBM_WALL_* bits; an axis without a bit is periodic.
  * block_x, block_y: CUDA block shape of the step kernel (block_x a multiple
  *      of 32, block_x*block_y <= 512); 0 selects the built-in default.
- * variant: step kernel form. 1: one node per thread; 2: two nodes per thread
- *      (x and x + block_x), collided together with the FP32x2 instructions;
- *      0: the default, 1 for FP32 storage and 2 for the 16-bit formats. The
- *      forms give the same results up to the rounding of fused operations. */
+ * variant: step kernel form. 0 or 1: one node per thread (the default); 2:
+ *      two nodes per thread (x and x + block_x), collided together with the
+ *      FP32x2 instructions (D3Q19 only; measured slower on GB300 for every
+ *      storage format, kept as an option). The forms give the same results
+ *      up to the rounding of fused operations.
+ * lattice: 19 (or 0): D3Q19 of Appendix A (Eqs. A1-A6); 27: D3Q27 of Sec. II
+ *      (velocities Eq. 1, moments Eq. 12, S Eq. 13, T~eq Eq. 15, C Eq. 16).
+ *      D3Q27 runs the one-node-per-thread form (blocks of at most 256
+ *      threads); the recomputation/adjoint entry points and batches are D3Q19
+ *      only. Population arrays then hold 27 x N floats in the order of Eq. 1.
+ * s3b, s4b, s5, s6: the further D3Q27 rates of Eq. 13 (k~111; k~211, k~121,
+ *      k~112; k~122, k~212, k~221; k~222); 0 selects 1. Ignored for D3Q19. */
 typedef struct clbm_params {
     int32_t nx, ny, nz;
     uint32_t walls;
@@ -84,6 +93,9 @@ typedef struct clbm_params {
     int32_t storage;
     int32_t block_x, block_y;
     int32_t variant;
+    int32_t lattice;
+    int32_t reserved;
+    double s3b, s4b, s5, s6;
 } clbm_params;
 
 typedef struct clbm_info {
@@ -95,13 +107,13 @@ typedef struct clbm_info {
     int32_t block_x, block_y; /* block shape in use */
     double s2;                /* 1/(3 nu + 1/2) */
     int32_t nodes_per_thread; /* of the step kernel: 1 or 2 */
-    int32_t reserved;
+    int32_t q;                /* 19 or 27 */
 } clbm_info;
 
 typedef struct clbm_ctx clbm_ctx;
 
 /* Create a lattice context: validates p, allocates two population buffers
- * (A/B) of 19 * N elements each on the current CUDA device, and binds the
+ * (A/B) of Q * N elements each on the current CUDA device, and binds the
  * context to `stream` (a cudaStream_t; NULL = legacy default stream).
  * The populations are zero deviations (f = w, rest at rho = 1) until an init
  * call. *out receives the context (owned by the caller; free with
@@ -154,12 +166,12 @@ int clbm_step(clbm_ctx *ctx, int64_t nsteps);
  * either may be NULL. */
 int clbm_get_macros(clbm_ctx *ctx, float *rho_dev, float *u_dev);
 
-/* Copy the current post-streaming populations out (19 x N floats). With
+/* Copy the current post-streaming populations out (Q x N floats). With
  * deviation != 0 the values are f - w_i, else f. */
 int clbm_get_populations(clbm_ctx *ctx, float *f_dev, int deviation);
 
 /* Replace the current state by the given post-streaming populations
- * (19 x N floats, f - w_i if deviation != 0, else f). Values are rounded to
+ * (Q x N floats, f - w_i if deviation != 0, else f). Values are rounded to
  * the storage format. Resets steps_done. */
 int clbm_set_populations(clbm_ctx *ctx, const float *f_dev, int deviation);
 

@@ -26,7 +26,9 @@ class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("walls", ctypes.c_uint32), ("nu", ctypes.c_double), ("s2b", ctypes.c_double),
                 ("s3", ctypes.c_double), ("s4", ctypes.c_double), ("storage", ctypes.c_int32),
-                ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("variant", ctypes.c_int32)]
+                ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("lattice", ctypes.c_int32), ("reserved", ctypes.c_int32), ("s3b", ctypes.c_double),
+                ("s4b", ctypes.c_double), ("s5", ctypes.c_double), ("s6", ctypes.c_double)]
 
 
 class Domain(ctypes.Structure):
@@ -49,7 +51,7 @@ class Info(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("pop_stride", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
                 ("steps_done", ctypes.c_int64), ("storage", ctypes.c_int32), ("block_x", ctypes.c_int32),
                 ("block_y", ctypes.c_int32), ("s2", ctypes.c_double), ("nodes_per_thread", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("q", ctypes.c_int32)]
 
 
 P = ctypes.c_void_p

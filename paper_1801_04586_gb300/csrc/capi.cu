@@ -10,6 +10,7 @@
 #include <string>
 
 #include "../../include/clbm.h"
+#include "d3q27.cuh"
 #include "kernels.cuh"
 
 using namespace clbm;
@@ -34,7 +35,7 @@ constexpr int kMidBlocks = 152;         // first pass over the step kernel's blo
 
 struct StateHeader {
     char magic[8];
-    int32_t version, nx, ny, nz, walls, storage;
+    int32_t version, nx, ny, nz, walls, storage, q, pad;
     int64_t stride, steps_done, bytes;
 };
 
@@ -63,6 +64,8 @@ struct clbm_ctx {
     int64_t steps_done;
     double gamma;         // force decay rate (clbm_set_force_decay)
     bool packed;          // step kernel with two nodes per thread (FP32x2 arithmetic)
+    int q;                // 19 (Appendix A) or 27 (Sec. II)
+    Rates27 rates27;
     dim3 block;
 };
 
@@ -136,12 +139,22 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     if (p->storage < CLBM_STORAGE_F32 || p->storage > CLBM_STORAGE_BF16_SR)
         return fail(CLBM_ERR_ARG, "clbm_create: unknown storage format");
     if (p->variant < 0 || p->variant > 2) return fail(CLBM_ERR_ARG, "clbm_create: variant must be 0, 1 or 2");
+    if (p->lattice != 0 && p->lattice != 19 && p->lattice != 27)
+        return fail(CLBM_ERR_ARG, "clbm_create: lattice must be 19 or 27");
+    const int q = p->lattice == 27 ? 27 : 19;
+    auto or1 = [](double s) { return s == 0.0 ? 1.0 : s; };
+    const double s3b = or1(p->s3b), s4b = or1(p->s4b), s5 = or1(p->s5), s6 = or1(p->s6);
+    if (q == 27 && (!rate_ok(s3b) || !rate_ok(s4b) || !rate_ok(s5) || !rate_ok(s6)))
+        return fail(CLBM_ERR_ARG, "clbm_create: relaxation rates must lie in (0, 2)");
+    if (q == 27 && p->variant == 2)
+        return fail(CLBM_ERR_ARG, "clbm_create: the two-nodes-per-thread form is D3Q19 only");
     int bx = p->block_x, by = p->block_y;
     if (bx == 0) bx = p->nx >= 128 ? 128 : ((p->nx + 31) / 32) * 32;
     if (by == 0) by = std::max(1, std::min(p->ny, 256 / bx));
     if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 512)
         return fail(CLBM_ERR_ARG, "clbm_create: block_x must be a multiple of 32 and block_x*block_y <= 512");
     if ((p->ny + by - 1) / by > 65535) return fail(CLBM_ERR_ARG, "clbm_create: ny / block_y exceeds grid limit");
+    if (q == 27 && bx * by > 256) return fail(CLBM_ERR_ARG, "clbm_create: D3Q27 blocks hold at most 256 threads");
 
     clbm_ctx *c = new (std::nothrow) clbm_ctx();
     if (!c) return fail(CLBM_ERR_OOM, "clbm_create: host allocation failed");
@@ -165,11 +178,22 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     c->force.n = n;
     c->force.scale = 1.0f;
     c->gamma = 0.0;
-    c->packed = p->variant == 2 || (p->variant == 0 && p->storage != CLBM_STORAGE_F32);
+    c->q = q;
+    c->packed = q == 19 && p->variant == 2;
+    c->rates27.om2 = c->rates.om2;
+    c->rates27.cb = c->rates.cb;
+    c->rates27.om3 = c->rates.om3;
+    c->rates27.c3 = c->rates.c3;
+    c->rates27.om3b = (float)(1.0 - s3b);
+    c->rates27.om4 = c->rates.om4;
+    c->rates27.om4b = (float)(1.0 - s4b);
+    c->rates27.om5 = (float)(1.0 - s5);
+    c->rates27.c5 = (float)((1.0 - 0.5 * s5) / 9.0);
+    c->rates27.om6 = (float)(1.0 - s6);
     c->block = dim3(bx, by, 1);
     c->cur = 0;
     c->steps_done = 0;
-    const size_t bytes = (size_t)kQ * c->g.stride * c->elem;
+    const size_t bytes = (size_t)c->q * c->g.stride * c->elem;
     cudaError_t e = cudaMalloc(&c->buf[0], 2 * bytes);
     if (e != cudaSuccess) {
         delete c;
@@ -211,13 +235,14 @@ int clbm_get_info(const clbm_ctx *c, clbm_info *info) {
     if (!c || !info) return fail(CLBM_ERR_ARG, "clbm_get_info: null pointer");
     info->n_nodes = c->n;
     info->pop_stride = c->g.stride;
-    info->state_bytes = (int64_t)kQ * c->g.stride * (int64_t)c->elem;
+    info->state_bytes = (int64_t)c->q * c->g.stride * (int64_t)c->elem;
     info->steps_done = c->steps_done;
     info->storage = c->p.storage;
     info->block_x = (int32_t)c->block.x;
     info->block_y = (int32_t)c->block.y;
     info->s2 = c->s2;
     info->nodes_per_thread = c->packed ? 2 : 1;
+    info->q = c->q;
     return CLBM_OK;
 }
 
@@ -253,7 +278,9 @@ int clbm_set_force_decay(clbm_ctx *c, double gamma) {
 
 int clbm_init_equilibrium(clbm_ctx *c, const float *rho, const float *u) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_init_equilibrium: null context");
-    cudaError_t e = launch_init_eq(c->p.storage, launch_of(c), c->buf[c->cur], rho, u, c->n, force_at_zero(c));
+    cudaError_t e = c->q == 27
+        ? launch_init27(c->p.storage, launch_of(c), c->buf[c->cur], rho, u, c->n, force_at_zero(c))
+        : launch_init_eq(c->p.storage, launch_of(c), c->buf[c->cur], rho, u, c->n, force_at_zero(c));
     if (e != cudaSuccess) return cuda_fail(e, "clbm_init_equilibrium");
     c->steps_done = 0;
     return CLBM_OK;
@@ -264,8 +291,11 @@ int clbm_step(clbm_ctx *c, int64_t nsteps) {
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_step: nsteps < 0");
     const Launch L = step_launch_of(c);
     for (int64_t t = 0; t < nsteps; ++t) {
-        cudaError_t e = launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),
-                                    c->d_flag, step_key(c->steps_done));
+        cudaError_t e = c->q == 27
+            ? launch_step27(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates27, force_now(c), c->d_flag,
+                            step_key(c->steps_done))
+            : launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c), c->d_flag,
+                          step_key(c->steps_done));
         if (e != cudaSuccess) return cuda_fail(e, "clbm_step");
         c->cur ^= 1;
         ++c->steps_done;
@@ -276,21 +306,24 @@ int clbm_step(clbm_ctx *c, int64_t nsteps) {
 int clbm_get_macros(clbm_ctx *c, float *rho, float *u) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_get_macros: null context");
     if (!rho && !u) return CLBM_OK;
-    cudaError_t e = launch_macros(c->p.storage, launch_of(c), c->buf[c->cur], force_now(c), rho, u, c->n);
+    cudaError_t e = c->q == 27 ? launch_macros27(c->p.storage, launch_of(c), c->buf[c->cur], force_now(c), rho, u, c->n)
+                               : launch_macros(c->p.storage, launch_of(c), c->buf[c->cur], force_now(c), rho, u, c->n);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_get_macros");
     return CLBM_OK;
 }
 
 int clbm_get_populations(clbm_ctx *c, float *f, int deviation) {
     if (!c || !f) return fail(CLBM_ERR_ARG, "clbm_get_populations: null pointer");
-    cudaError_t e = launch_gather(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation);
+    cudaError_t e = c->q == 27 ? launch_gather27(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation)
+                               : launch_gather(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_get_populations");
     return CLBM_OK;
 }
 
 int clbm_set_populations(clbm_ctx *c, const float *f, int deviation) {
     if (!c || !f) return fail(CLBM_ERR_ARG, "clbm_set_populations: null pointer");
-    cudaError_t e = launch_scatter(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation);
+    cudaError_t e = c->q == 27 ? launch_scatter27(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation)
+                               : launch_scatter(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_set_populations");
     c->steps_done = 0;
     return CLBM_OK;
@@ -298,8 +331,10 @@ int clbm_set_populations(clbm_ctx *c, const float *f, int deviation) {
 
 int clbm_reduce_moments(clbm_ctx *c, double *out) {
     if (!c || !out) return fail(CLBM_ERR_ARG, "clbm_reduce_moments: null pointer");
-    cudaError_t e = launch_reduce_moments(c->p.storage, launch_of(c), c->buf[c->cur], force_now(c),
-                                          (long long *)c->d_partials, kReduceBlocks, out);
+    cudaError_t e = c->q == 27 ? launch_moments27(c->p.storage, launch_of(c), c->buf[c->cur], force_now(c),
+                                                  (long long *)c->d_partials, kReduceBlocks, out)
+                               : launch_reduce_moments(c->p.storage, launch_of(c), c->buf[c->cur], force_now(c),
+                                                       (long long *)c->d_partials, kReduceBlocks, out);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_reduce_moments");
     return CLBM_OK;
 }
@@ -327,7 +362,7 @@ int clbm_check(clbm_ctx *c, int clear) {
 
 int clbm_export_state(clbm_ctx *c, void *dst) {
     if (!c || !dst) return fail(CLBM_ERR_ARG, "clbm_export_state: null pointer");
-    const size_t bytes = (size_t)kQ * c->g.stride * c->elem;
+    const size_t bytes = (size_t)c->q * c->g.stride * c->elem;
     cudaError_t e = cudaMemcpyAsync(dst, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_export_state");
     return CLBM_OK;
@@ -335,7 +370,7 @@ int clbm_export_state(clbm_ctx *c, void *dst) {
 
 int clbm_import_state(clbm_ctx *c, const void *src, int64_t set_steps) {
     if (!c || !src) return fail(CLBM_ERR_ARG, "clbm_import_state: null pointer");
-    const size_t bytes = (size_t)kQ * c->g.stride * c->elem;
+    const size_t bytes = (size_t)c->q * c->g.stride * c->elem;
     cudaError_t e = cudaMemcpyAsync(c->buf[c->cur], src, bytes, cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_import_state");
     if (set_steps >= 0) c->steps_done = set_steps;
@@ -344,7 +379,7 @@ int clbm_import_state(clbm_ctx *c, const void *src, int64_t set_steps) {
 
 int clbm_save_state(clbm_ctx *c, void *host, size_t *bytes) {
     if (!c || !bytes) return fail(CLBM_ERR_ARG, "clbm_save_state: null pointer");
-    const size_t raw = (size_t)kQ * c->g.stride * c->elem;
+    const size_t raw = (size_t)c->q * c->g.stride * c->elem;
     const size_t need = sizeof(StateHeader) + raw;
     if (!host) {
         *bytes = need;
@@ -353,11 +388,12 @@ int clbm_save_state(clbm_ctx *c, void *host, size_t *bytes) {
     if (*bytes < need) return fail(CLBM_ERR_ARG, "clbm_save_state: buffer too small");
     StateHeader h;
     std::memset(&h, 0, sizeof(h));
-    std::memcpy(h.magic, "CLBMQ19", 8);
-    h.version = 1;
+    std::memcpy(h.magic, "CLBMLBM", 8);
+    h.version = 2;
     h.nx = c->g.nx; h.ny = c->g.ny; h.nz = c->g.nz;
     h.walls = (int32_t)c->g.walls;
     h.storage = c->p.storage;
+    h.q = c->q;
     h.stride = c->g.stride;
     h.steps_done = c->steps_done;
     h.bytes = (int64_t)raw;
@@ -374,11 +410,11 @@ int clbm_load_state(clbm_ctx *c, const void *host, size_t bytes) {
     if (bytes < sizeof(StateHeader)) return fail(CLBM_ERR_ARG, "clbm_load_state: buffer too small");
     StateHeader h;
     std::memcpy(&h, host, sizeof(h));
-    const size_t raw = (size_t)kQ * c->g.stride * c->elem;
-    if (std::memcmp(h.magic, "CLBMQ19", 8) != 0 || h.version != 1)
+    const size_t raw = (size_t)c->q * c->g.stride * c->elem;
+    if (std::memcmp(h.magic, "CLBMLBM", 8) != 0 || h.version != 2)
         return fail(CLBM_ERR_ARG, "clbm_load_state: not a state buffer");
     if (h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz || h.walls != (int32_t)c->g.walls ||
-        h.storage != c->p.storage || h.stride != c->g.stride || h.bytes != (int64_t)raw ||
+        h.storage != c->p.storage || h.q != c->q || h.stride != c->g.stride || h.bytes != (int64_t)raw ||
         bytes < sizeof(h) + raw)
         return fail(CLBM_ERR_ARG, "clbm_load_state: geometry, storage or size mismatch");
     cudaError_t e =
@@ -391,8 +427,9 @@ int clbm_load_state(clbm_ctx *c, const void *host, size_t bytes) {
 
 int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
     if (!c || !src || !dst) return fail(CLBM_ERR_ARG, "clbm_step_raw: null pointer");
+    if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_step_raw: D3Q19 only");
     if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_step_raw: needs a static force (decay 0)");
-    const size_t bytes = (size_t)kQ * c->g.stride * c->elem;
+    const size_t bytes = (size_t)c->q * c->g.stride * c->elem;
     if ((const char *)src < (const char *)dst + bytes && (const char *)dst < (const char *)src + bytes)
         return fail(CLBM_ERR_ARG, "clbm_step_raw: src and dst overlap");
     cudaError_t e = launch_step(c->p.storage, step_launch_of(c), src, dst, c->rates, c->force, c->d_flag, step_key(0));
@@ -402,6 +439,7 @@ int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
 
 int clbm_adjoint_seed(clbm_ctx *c, const void *state, const float *gu, float *lam, float *gF) {
     if (!c || !gu || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: null pointer");
+    if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: D3Q19 only");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: FP32 storage only");
     if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_adjoint_seed: needs a static force (decay 0)");
     cudaError_t e = launch_adjoint_seed(c->p.storage, launch_of(c), state ? state : c->buf[c->cur], gu, lam, gF,
@@ -412,6 +450,7 @@ int clbm_adjoint_seed(clbm_ctx *c, const void *state, const float *gu, float *la
 
 int clbm_adjoint_step(clbm_ctx *c, const void *state, const float *lam_next, float *lam, float *gF) {
     if (!c || !state || !lam_next || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: null pointer");
+    if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: D3Q19 only");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: FP32 storage only");
     if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_adjoint_step: needs a static force (decay 0)");
     if (lam == lam_next) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: lam aliases lam_next");
@@ -425,10 +464,11 @@ int clbm_adjoint_segment(clbm_ctx *c, const void *ckpt, void *tape, int64_t k, f
                          float *gF) {
     if (!c || !ckpt || !lam || !lam_tmp || !gF || k < 1 || (k > 1 && !tape) || lam == lam_tmp)
         return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: bad argument");
+    if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: D3Q19 only");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: FP32 storage only");
     if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_adjoint_segment: needs a static force (decay 0)");
     const Launch L = launch_of(c);
-    const size_t sb = (size_t)kQ * c->g.stride * c->elem;
+    const size_t sb = (size_t)c->q * c->g.stride * c->elem;
     auto state = [&](int64_t j) -> const void * { return j == 0 ? ckpt : (const char *)tape + (j - 1) * sb; };
     cudaError_t e = cudaSuccess;
     for (int64_t j = 1; j < k && e == cudaSuccess; ++j)
@@ -478,7 +518,16 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         return cuda_fail(e, "clbm_run_host: copy u");
     int rc = clbm_init_equilibrium(c, rho_h ? d_rho : nullptr, u_h ? d_u : nullptr);
     if (rc != CLBM_OK) return rc;
-    for (int64_t t = 0; t < nsteps; ++t) {
+    for (int64_t t = 0; t < nsteps && c->q == 27; ++t) {
+        // D3Q27: plain step, then the conservation sums of the new state's predecessor
+        if (moments_h) {
+            if ((rc = clbm_reduce_moments(c, c->d_mom)) != CLBM_OK) return rc;
+            e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: moments");
+        }
+        if ((rc = clbm_step(c, 1)) != CLBM_OK) return rc;
+    }
+    for (int64_t t = 0; t < nsteps && c->q == 19; ++t) {
         if (moments_h) {
             // fused step: FP64 sums of the state it pulls (state t) into per-block partials
             e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),

@@ -119,21 +119,22 @@ template <> struct Codec<BF16SR> {
     }
 };
 
-// Store the 19 post-collision deviations of one node (pull scheme: at the
-// node itself). key: per-step random key (stochastic formats only).
-template <typename S>
-__device__ __forceinline__ void store_node(S *d, int64_t stride, const float (&h)[19], uint32_t node, uint32_t key) {
+// Store the NQ post-collision deviations of one node (pull scheme: at the
+// node itself), h in population order. key: per-step random key (stochastic
+// formats only).
+template <typename S, int NQ = 19>
+__device__ __forceinline__ void store_node(S *d, int64_t stride, const float (&h)[NQ], uint32_t node, uint32_t key) {
     if constexpr (Codec<S>::kStochastic) {
         const uint32_t base = lowbias32(node ^ key);
 #pragma unroll
-        for (int i = 0; i < 19; i += 2) {
+        for (int i = 0; i < NQ; i += 2) {
             const uint32_t r = lowbias32(base + (uint32_t)i * 0x9e3779b9u);
             d[(size_t)i * stride] = Codec<S>::from_f_sr(h[i], r);
-            if (i + 1 < 19) d[(size_t)(i + 1) * stride] = Codec<S>::from_f_sr(h[i + 1], r >> 16);
+            if (i + 1 < NQ) d[(size_t)(i + 1) * stride] = Codec<S>::from_f_sr(h[i + 1], r >> 16);
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) d[(size_t)i * stride] = Codec<S>::from_f(h[i]);
+        for (int i = 0; i < NQ; ++i) d[(size_t)i * stride] = Codec<S>::from_f(h[i]);
     }
 }
 

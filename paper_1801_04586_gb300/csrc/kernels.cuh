@@ -52,6 +52,19 @@ cudaError_t launch_adjoint_seed(int storage, const Launch &L, const void *state,
 cudaError_t launch_reduce_pair(const float *a, const float *b, int64_t n, double *partials, int nblocks,
                                double *out, cudaStream_t stream);
 
+// D3Q27 (step27.cu); Rates27 in d3q27.cuh.
+struct Rates27;
+cudaError_t launch_step27(int storage, const Launch &L, const void *src, void *dst, const Rates27 &r,
+                          const ForceArgs &F, int *flag, uint32_t key);
+cudaError_t launch_init27(int storage, const Launch &L, void *dst, const float *rho, const float *u, int64_t n,
+                          const ForceArgs &F);
+cudaError_t launch_scatter27(int storage, const Launch &L, void *dst, const float *f, int64_t n, int deviation);
+cudaError_t launch_gather27(int storage, const Launch &L, const void *src, float *f, int64_t n, int deviation);
+cudaError_t launch_macros27(int storage, const Launch &L, const void *src, const ForceArgs &F, float *rho, float *u,
+                            int64_t n);
+cudaError_t launch_moments27(int storage, const Launch &L, const void *src, const ForceArgs &F, long long *partials,
+                             int nblocks, double *out);
+
 // Record `msg` as the calling thread's last error (clbm_last_error) and return code.
 int set_error(int code, const char *msg);
 

@@ -22,17 +22,20 @@ def _ptr(t: Optional[torch.Tensor]):
 
 
 class Lattice:
-    """D3Q19 CLBM lattice (Fei, Luo & Li, arXiv:1801.04586, Appendix A).
+    """CLBM lattice (Fei, Luo & Li, arXiv:1801.04586): D3Q19 of Appendix A
+    (lattice=19) or D3Q27 of Sec. II (lattice=27).
 
     nu sets s2 = 1/(3 nu + 1/2); s2b, s3, s4 are the bulk, third- and
-    fourth-order rates (Eq. A3); walls is a CLBM_WALL_* bit mask (x=1, y=2,
-    z=4; other axes periodic); storage is 'f32', 'f16' or 'bf16' (populations
-    stored as deviations f - w_i).
+    fourth-order rates (Eq. A3 / Eq. 13), s3b, s4b, s5, s6 the further D3Q27
+    rates; walls is a CLBM_WALL_* bit mask (x=1, y=2, z=4; other axes
+    periodic); storage is 'f32', 'f16', 'bf16', 'f16sr' or 'bf16sr'
+    (populations stored as deviations f - w_i).
     """
 
     def __init__(self, nx: int, ny: int, nz: int, nu: float, walls: int = 0, s2b: float = 1.0,
                  s3: float = 1.0, s4: float = 1.0, storage: str = "f32", block: Tuple[int, int] = (0, 0),
-                 device=None, stream: Optional[torch.cuda.Stream] = None, variant: int = 0):
+                 device=None, stream: Optional[torch.cuda.Stream] = None, variant: int = 0, lattice: int = 19,
+                 s3b: float = 1.0, s4b: float = 1.0, s5: float = 1.0, s6: float = 1.0):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required: the lattice runs only in libclbm.so's kernels")
         self.lib = _capi.lib()
@@ -43,10 +46,12 @@ class Lattice:
         self.n = self.nx * self.ny * self.nz
         self.walls = int(walls)
         self.storage = storage
+        self.q = 27 if int(lattice) == 27 else 19
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             p = _capi.Params(self.nx, self.ny, self.nz, self.walls, float(nu), float(s2b), float(s3), float(s4),
-                             _capi.STORAGE[storage], int(block[0]), int(block[1]), int(variant))
+                             _capi.STORAGE[storage], int(block[0]), int(block[1]), int(variant), int(lattice), 0,
+                             float(s3b), float(s4b), float(s5), float(s6))
             h = ctypes.c_void_p()
             check(self.lib.clbm_create(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
                   "clbm_create")
@@ -118,12 +123,12 @@ class Lattice:
         return rho, u
 
     def populations(self, deviation: bool = False, out: Optional[torch.Tensor] = None):
-        out = self.empty(19, *self.shape) if out is None else self._dev(out, (19,) + self.shape, "out")
+        out = self.empty(self.q, *self.shape) if out is None else self._dev(out, (self.q,) + self.shape, "out")
         check(self.lib.clbm_get_populations(self.h, _ptr(out), int(deviation)), "clbm_get_populations")
         return out
 
     def set_populations(self, f: torch.Tensor, deviation: bool = False):
-        self._dev(f, (19,) + self.shape, "f")
+        self._dev(f, (self.q,) + self.shape, "f")
         check(self.lib.clbm_set_populations(self.h, _ptr(f), int(deviation)), "clbm_set_populations")
 
     def reduce_moments(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:

@@ -48,7 +48,7 @@ def test_binding_covers_header():
 def _params(**kw):
     from paper_1801_04586_gb300 import _capi
     base = dict(nx=8, ny=8, nz=8, walls=0, nu=0.1, s2b=1.0, s3=1.0, s4=1.0, storage=0, block_x=0, block_y=0,
-                variant=0)
+                variant=0, lattice=0, reserved=0, s3b=0.0, s4b=0.0, s5=0.0, s6=0.0)
     base.update(kw)
     return _capi.Params(**base)
 
@@ -56,7 +56,9 @@ def _params(**kw):
 @pytest.mark.parametrize("kw", [dict(nx=0), dict(ny=-3), dict(nz=70000), dict(walls=8), dict(nu=0.0),
                                 dict(nu=-1.0), dict(s2b=2.0), dict(s3=0.0), dict(s4=float("nan")),
                                 dict(storage=5), dict(block_x=48), dict(block_x=1024, block_y=1),
-                                dict(nx=2048, ny=2048, nz=1024), dict(variant=3)])
+                                dict(nx=2048, ny=2048, nz=1024), dict(variant=3),
+                                dict(lattice=21), dict(lattice=27, s5=2.5), dict(lattice=27, variant=2),
+                                dict(lattice=27, block_x=512, block_y=1)])
 def test_create_rejects_bad_parameters(lib, kw):
     from paper_1801_04586_gb300 import _capi
     h = ctypes.c_void_p()
