@@ -25,6 +25,12 @@
  *   - An adjoint of one step: per-node Jacobians by complex-step
  *     differentiation of the same collision code, transposed, and the
  *     transposed streaming map.
+ *   - The two comparison collision models the paper sets beside the cascaded
+ *     one (model field of ora_lattice): the SRT-LBM with the discrete
+ *     equilibrium of Sec. II.B and Guo's forcing term (Sec. III.A), and the
+ *     non-orthogonal raw-moment MRT-LBM of Appendix B on the same M and S.
+ *     The lattice weights they use are the generalized equilibrium at rest,
+ *     rho = 1, u = 0.
  *
  * Readings of points the paper leaves open or prints garbled:
  *   - Eq. 2 prints (e_iy - u_z)^p as the third factor; read (e_iz - u_z)^p.
@@ -118,6 +124,8 @@ typedef struct {
     int walls;          /* bit 0: x faces are walls, bit 1: y, bit 2: z */
     double s0, s1, s2, s2b, s3, s4;
     double s3b, s4b, s5, s6;  /* D3Q27 only (Eq. 13) */
+    int model;          /* 0: cascaded (Sec. II); 1: SRT-LBM (rate s2); 2: non-orthogonal MRT (Appendix B) */
+    int pad;
 } ora_lattice;
 
 static int binom(int n, int k)
@@ -218,15 +226,37 @@ static void build_S(const ora_lattice *L, double S[Q][Q])
 #endif
 }
 
+static double g_M[Q][Q];
 static double g_Minv[Q][Q];
+static double g_w[Q];
 static int g_ready = 0;
 
 static void ensure_ready(void)
 {
     if (!g_ready) {
+        build_M(g_M);
         build_Minv(g_Minv);
+        double u0[3] = {0.0, 0.0, 0.0};
+        equilibrium_r(g_Minv, 1.0, u0, g_w);  /* lattice weights */
         g_ready = 1;
     }
+}
+
+/* One collision of the lattice's model. */
+static void collide_model_r(const ora_lattice *L, const double S[Q][Q], const double f[Q], const double F[3],
+                            double fs[Q])
+{
+    if (L->model == 1) collide_srt_r(L->s2, g_w, f, F, fs);
+    else if (L->model == 2) collide_mrt_r(S, g_M, g_Minv, g_w, f, F, fs);
+    else collide_r(S, g_Minv, f, F, fs);
+}
+
+static void collide_model_c(const ora_lattice *L, const double S[Q][Q], const double complex f[Q],
+                            const double complex F[3], double complex fs[Q])
+{
+    if (L->model == 1) collide_srt_c(L->s2, g_w, f, F, fs);
+    else if (L->model == 2) collide_mrt_c(S, g_M, g_Minv, g_w, f, F, fs);
+    else collide_c(S, g_Minv, f, F, fs);
 }
 
 /* ---- exported: tables and matrices ---- */
@@ -282,7 +312,20 @@ void ORA(collide)(const ora_lattice *L, const double *f, const double *F, double
     ensure_ready();
     double S[Q][Q];
     build_S(L, S);
-    collide_r(S, g_Minv, f, F, fs);
+    collide_model_r(L, S, f, F, fs);
+}
+
+/* The discrete equilibrium of Sec. II.B and Guo's forcing term (Appendix B). */
+void ORA(feq_discrete)(double rho, const double *u, double *feq)
+{
+    ensure_ready();
+    feq_discrete_r(g_w, rho, u, feq);
+}
+
+void ORA(guo_force)(const double *u, const double *F, double *R)
+{
+    ensure_ready();
+    guo_force_r(g_w, u, F, R);
 }
 
 void ORA(equilibrium)(double rho, const double *u, double *feq)
@@ -385,7 +428,7 @@ int ORA(step_decay)(const ora_lattice *L, const double *F, double *f, int nsteps
                     double fl[Q], Fl[3], fs[Q];
                     for (int i = 0; i < Q; ++i) fl[i] = f[i * N + s];
                     for (int a = 0; a < 3; ++a) Fl[a] = F ? F[a * N + s] * decay : 0.0;
-                    collide_r(S, g_Minv, fl, Fl, fs);
+                    collide_model_r(L, S, fl, Fl, fs);
                     for (int i = 0; i < Q; ++i) {
                         int d;
                         long t2 = push_target(L, x, y, z, i, &d);
@@ -452,7 +495,7 @@ int ORA(first_step_nodes)(const ora_lattice *L, const double *rho, const double 
                 up[a] = (u ? u[a * N + src] : 0.0) - Fl[a] / (2.0 * r);
             }
             equilibrium_r(g_Minv, r, up, feq);
-            collide_r(S, g_Minv, feq, Fl, fs);
+            collide_model_r(L, S, feq, Fl, fs);
             int d;
             int sx = (int)(src % L->nx), sy = (int)((src / L->nx) % L->ny), sz = (int)(src / ((long)L->nx * L->ny));
             long dest = push_target(L, sx, sy, sz, take, &d);
@@ -469,7 +512,8 @@ int ORA(first_step_nodes)(const ora_lattice *L, const double *rho, const double 
 
 /* Jacobian of the node collision f* = C(f, F): J[i][k], k < 19 w.r.t. f_k,
  * k = 19..21 w.r.t. F_{k-19}, by complex-step differentiation. */
-static void collide_jacobian(const double S[Q][Q], const double f[Q], const double F[3], double J[Q][Q + 3])
+static void collide_jacobian(const ora_lattice *L, const double S[Q][Q], const double f[Q], const double F[3],
+                             double J[Q][Q + 3])
 {
     for (int k = 0; k < Q + 3; ++k) {
         double complex fc[Q], Fc[3], out[Q];
@@ -477,7 +521,7 @@ static void collide_jacobian(const double S[Q][Q], const double f[Q], const doub
         for (int a = 0; a < 3; ++a) Fc[a] = F[a];
         if (k < Q) fc[k] += HCS * I;
         else Fc[k - Q] += HCS * I;
-        collide_c(S, g_Minv, fc, Fc, out);
+        collide_model_c(L, S, fc, Fc, out);
         for (int i = 0; i < Q; ++i) J[i][k] = cimag(out[i]) / HCS;
     }
 }
@@ -507,7 +551,7 @@ int ORA(adjoint_step)(const ora_lattice *L, const double *f_t, const double *F, 
                     long t2 = push_target(L, x, y, z, i, &d);
                     ls[i] = lam_next[d * N + t2];
                 }
-                collide_jacobian(S, fl, Fl, J);
+                collide_jacobian(L, S, fl, Fl, J);
                 for (int k = 0; k < Q; ++k) {
                     double acc = 0.0;
                     for (int i = 0; i < Q; ++i) acc += J[i][k] * ls[i];

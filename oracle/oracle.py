@@ -76,6 +76,7 @@ def _get(q: int = 19):
             "ora_adjoint_step": [P, P, P, P, P, P, I],
             "ora_adjoint_seed": [P, P, P, P, P, P],
             "ora_num_threads": [],
+            "ora_feq_discrete": [D, P, P], "ora_guo_force": [P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(lib, pre + name[len("ora_"):])
@@ -92,7 +93,8 @@ class _CLattice(ctypes.Structure):
                 ("walls", ctypes.c_int), ("s0", ctypes.c_double), ("s1", ctypes.c_double),
                 ("s2", ctypes.c_double), ("s2b", ctypes.c_double), ("s3", ctypes.c_double),
                 ("s4", ctypes.c_double), ("s3b", ctypes.c_double), ("s4b", ctypes.c_double),
-                ("s5", ctypes.c_double), ("s6", ctypes.c_double)]
+                ("s5", ctypes.c_double), ("s6", ctypes.c_double), ("model", ctypes.c_int),
+                ("pad", ctypes.c_int)]
 
 
 @dataclass
@@ -101,7 +103,10 @@ class Lattice:
     halfway bounce-back walls (else periodic). ``s2`` follows from the
     kinematic viscosity, nu = (1/s2 - 1/2)/3 (Sec. II.B). ``q`` selects D3Q19
     (Appendix A) or D3Q27 (Sec. II); s3b, s4b, s5, s6 are the extra D3Q27
-    rates of Eq. 13."""
+    rates of Eq. 13. ``model`` selects the collision: 0 the cascaded one
+    (Sec. II), 1 the SRT-LBM at rate s2 with the discrete equilibrium of
+    Sec. II.B and Guo's forcing, 2 the non-orthogonal raw-moment MRT of
+    Appendix B (same M and S)."""
     nx: int
     ny: int
     nz: int
@@ -117,6 +122,7 @@ class Lattice:
     s4b: float = 1.0
     s5: float = 1.0
     s6: float = 1.0
+    model: int = 0
 
     @staticmethod
     def from_nu(nx, ny, nz, nu, walls=0, **kw):
@@ -132,7 +138,8 @@ class Lattice:
 
     def c(self) -> _CLattice:
         return _CLattice(self.nx, self.ny, self.nz, self.walls, self.s0, self.s1,
-                         self.s2, self.s2b, self.s3, self.s4, self.s3b, self.s4b, self.s5, self.s6)
+                         self.s2, self.s2b, self.s3, self.s4, self.s3b, self.s4b, self.s5, self.s6,
+                         int(self.model), 0)
 
 
 def _ptr(a):
@@ -224,6 +231,20 @@ def collide(lat: Lattice, f, F=(0.0, 0.0, 0.0)) -> np.ndarray:
 def equilibrium(rho: float, u, q: int = 19) -> np.ndarray:
     out = np.zeros(q)
     _get(q).ora_equilibrium(float(rho), _ptr(_f64(u, (3,))), _ptr(out))
+    return out
+
+
+def feq_discrete(rho: float, u, q: int = 19) -> np.ndarray:
+    """The second-order discrete equilibrium of Sec. II.B at (rho, u)."""
+    out = np.zeros(q)
+    _get(q).ora_feq_discrete(float(rho), _ptr(_f64(u, (3,))), _ptr(out))
+    return out
+
+
+def guo_force(u, F, q: int = 19) -> np.ndarray:
+    """Guo's forcing term as Appendix B quotes it, at (u, F)."""
+    out = np.zeros(q)
+    _get(q).ora_guo_force(_ptr(_f64(u, (3,))), _ptr(_f64(F, (3,))), _ptr(out))
     return out
 
 

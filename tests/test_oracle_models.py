@@ -1,0 +1,144 @@
+"""Pins of the oracle's comparison collision models: the SRT-LBM with the
+discrete equilibrium of Sec. II.B and Guo's forcing term, and the
+non-orthogonal raw-moment MRT-LBM of Appendix B.
+
+What fixes them independently of the oracle's code:
+- textbook moments of the second-order discrete equilibrium and of Guo's
+  forcing term on isotropic lattices (closed forms written out here);
+- the GMRT statement of Sec. II.A: with all rates equal the MRT collision
+  is the SRT one;
+- the shear-wave viscosity nu = c_s^2 (1/s2 - 1/2);
+- the closed-form wall slip of halfway bounce-back in plane Poiseuille flow
+  for two-rate schemes, u_s = F (16 Lambda - 3) / (24 nu) with
+  Lambda = (1/s_even - 1/2)(1/s_odd - 1/2) (He, Zou, Luo & Dembo 1997 for
+  BGK; Ginzburg & d'Humieres 2003 for two rates), zero at Lambda = 3/16,
+  which is the paper's no-slip rule s3 = (16 - 8 s2)/(8 - s2).
+"""
+import numpy as np
+import pytest
+
+import analytic as an
+import oracle as o
+
+CS2 = 1.0 / 3.0
+RNG = np.random.default_rng(77)
+
+
+def weights(q):
+    return o.equilibrium(1.0, np.zeros(3), q)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_discrete_equilibrium_moments(q):
+    E = o.velocities(q).astype(float)
+    for _ in range(5):
+        rho, u = RNG.uniform(0.9, 1.1), RNG.uniform(-0.15, 0.15, 3)
+        fe = o.feq_discrete(rho, u, q)
+        assert fe.sum() == pytest.approx(rho, abs=1e-15)
+        np.testing.assert_allclose(E.T @ fe, rho * u, atol=1e-15)
+        P = np.einsum("i,ia,ib->ab", fe, E, E)
+        np.testing.assert_allclose(P, rho * (np.outer(u, u) + CS2 * np.eye(3)), atol=1e-15)
+        # third order: sum f e_x e_y^2 = rho c_s^2 u_x (lattice sums w e_x^2 e_y^2 = c_s^4)
+        k120 = (fe * E[:, 0] * E[:, 1] ** 2).sum()
+        assert k120 == pytest.approx(rho * CS2 * u[0], abs=1e-15)
+        # fourth order: D3Q19 has no corners (sum w e_x^2 e_y^2 e_z^2 = 0), D3Q27 has 1/27
+        k220 = (fe * E[:, 0] ** 2 * E[:, 1] ** 2).sum()
+        uu = u @ u
+        expect = (rho * (1 / 9 + (u[0] ** 2 + u[1] ** 2) / 2 - uu / 6) if q == 19
+                  else rho * (1 / 9 + (u[0] ** 2 + u[1] ** 2) / 3))
+        assert k220 == pytest.approx(expect, abs=1e-15)
+    np.testing.assert_allclose(o.feq_discrete(1.0, np.zeros(3), q), weights(q), atol=1e-16)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_guo_force_moments(q):
+    E = o.velocities(q).astype(float)
+    for _ in range(5):
+        u, F = RNG.uniform(-0.15, 0.15, 3), RNG.normal(size=3)
+        R = o.guo_force(u, F, q)
+        assert abs(R.sum()) < 1e-15
+        np.testing.assert_allclose(E.T @ R, F, atol=1e-15)
+        np.testing.assert_allclose(np.einsum("i,ia,ib->ab", R, E, E), np.outer(u, F) + np.outer(F, u), atol=1e-15)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("model", [1, 2])
+def test_conservation_and_equilibrium_fixed_point(q, model):
+    w = weights(q)
+    E = o.velocities(q).astype(float)
+    lat = o.Lattice(2, 2, 2, q=q, model=model, s2=1.4, s2b=0.9, s3=1.2, s4=0.7, s3b=1.1, s4b=1.3, s5=0.8, s6=1.6,
+                    s0=RNG.uniform(0.2, 1.8), s1=RNG.uniform(0.2, 1.8))
+    for _ in range(5):
+        f = w * (1 + RNG.uniform(-0.2, 0.2, q))
+        F = RNG.normal(scale=1e-3, size=3)
+        fs = o.collide(lat, f, F)
+        assert fs.sum() == pytest.approx(f.sum(), abs=2e-15)
+        np.testing.assert_allclose(E.T @ fs, E.T @ f + F, atol=2e-15)
+        rho, u = RNG.uniform(0.9, 1.1), RNG.uniform(-0.1, 0.1, 3)
+        fe = o.feq_discrete(rho, u, q)
+        np.testing.assert_allclose(o.collide(lat, fe), fe, atol=1e-15)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_srt_closed_form_and_mrt_reduces_to_srt(q):
+    """s = 1: f* = f_D + R/2 (the textbook BGK update at tau = 1); MRT with
+    all rates equal is the SRT collision (Sec. II.A)."""
+    w = weights(q)
+    f = w * (1 + RNG.uniform(-0.1, 0.1, q))
+    F = RNG.normal(scale=1e-3, size=3)
+    rho = f.sum()
+    u = (o.velocities(q).T @ f + F / 2) / rho
+    srt1 = o.Lattice(2, 2, 2, q=q, model=1, s2=1.0)
+    np.testing.assert_allclose(o.collide(srt1, f, F), o.feq_discrete(rho, u, q) + o.guo_force(u, F, q) / 2,
+                               atol=1e-16)
+    for s in (0.6, 1.3, 1.9):
+        srt = o.Lattice(2, 2, 2, q=q, model=1, s2=s)
+        mrt = o.Lattice(2, 2, 2, q=q, model=2, s2=s, s2b=s, s3=s, s4=s, s3b=s, s4b=s, s5=s, s6=s, s0=s, s1=s)
+        np.testing.assert_allclose(o.collide(mrt, f, F), o.collide(srt, f, F), atol=2e-16)
+
+
+@pytest.mark.parametrize("q,model", [(19, 1), (19, 2), (27, 2)])
+def test_shear_wave_viscosity(q, model):
+    L, nu = 101, 0.05
+    lat = o.Lattice(1, L, 1, q=q, model=model, s2=an.s2_from_nu(nu), s2b=0.8, s3=1.2, s4=1.1)
+    y = np.arange(L)
+    u = np.zeros((3, 1, L, 1))
+    u[0, 0, :, 0] = 1e-4 * np.sin(2 * np.pi * y / L)
+    f = o.step(lat, o.init(lat, None, u), None, 200)
+    a1 = an.shear_wave_amplitude(o.macros(lat, f)[1][0, 0, :, 0])
+    f = o.step(lat, f, None, 2000)
+    a2 = an.shear_wave_amplitude(o.macros(lat, f)[1][0, 0, :, 0])
+    assert np.log(a1 / a2) / ((2 * np.pi / L) ** 2 * 2000) == pytest.approx(nu, rel=1e-3)
+
+
+def poiseuille(q, model, n=20, F=1e-6, **rates):
+    lat = o.Lattice(1, 1, n, walls=4, q=q, model=model, **rates)
+    nu = an.nu_from_s2(lat.s2)
+    Ff = np.zeros((3, n, 1, 1))
+    Ff[0] = F
+    steps = int(40 * 4 * (n / 2) ** 2 / (np.pi ** 2 * nu))
+    f = o.step(lat, o.init(lat, None, None, Ff), Ff, steps)
+    return o.macros(lat, f, Ff)[1][0, :, 0, 0], an.poiseuille_steady(n, F, nu), nu
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("s", [0.7, 1.25, 8 - 4 * np.sqrt(3)])
+def test_srt_poiseuille_bounce_back_slip(q, s):
+    F = 1e-6
+    ux, ua, nu = poiseuille(q, 1, F=F, s2=s)
+    lam = (1 / s - 0.5) ** 2
+    slip = F * (16 * lam - 3) / (24 * nu)
+    np.testing.assert_allclose(ux - ua, slip, rtol=0, atol=1e-8 * ua.max())
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("s3", [1.0, "noslip"])
+def test_mrt_poiseuille_bounce_back_slip(q, s3):
+    F, s2 = 1e-6, an.s2_from_nu(0.1)
+    s3v = an.noslip_s3(s2) if s3 == "noslip" else s3
+    ux, ua, nu = poiseuille(q, 2, F=F, s2=s2, s2b=s2, s3=s3v)
+    lam = (1 / s2 - 0.5) * (1 / s3v - 0.5)
+    slip = F * (16 * lam - 3) / (24 * nu)
+    np.testing.assert_allclose(ux - ua, slip, rtol=0, atol=1e-8 * ua.max())
+    if s3 == "noslip":
+        assert np.sqrt(((ux - ua) ** 2).sum() / (ua ** 2).sum()) < 1e-8
