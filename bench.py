@@ -57,6 +57,10 @@ def parse():
                     help="storage of the timed lattice (the benchmark line is f32; others for profiling)")
     ap.add_argument("--variant", type=int, default=0, help="step kernel form (0/1: one node per thread, 2: two)")
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 27])
+    ap.add_argument("--model", default="cascaded", choices=["cascaded", "srt", "mrt"],
+                    help="collision of the timed lattice (the benchmark line is cascaded; others for profiling)")
+    ap.add_argument("--pattern", default="ab", choices=["ab", "aa"],
+                    help="storage pattern of the timed lattice (the benchmark line is ab; aa for profiling)")
     return ap.parse_args()
 
 
@@ -72,7 +76,8 @@ def measured_peaks():
 
 def kernel_source_digest():
     h = hashlib.sha256()
-    for rel in ("paper_1801_04586_gb300/csrc/step.cu", "paper_1801_04586_gb300/csrc/d3q19.cuh"):
+    for rel in ("paper_1801_04586_gb300/csrc/step.cu", "paper_1801_04586_gb300/csrc/step_kernels.cuh",
+                "paper_1801_04586_gb300/csrc/d3q19.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -216,13 +221,17 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def bench_storage(storage, K, warmup, dev, side, prof, u0, peak, variant=0):
-    """The same workload in another storage format or step-kernel form."""
+def bench_storage(storage, K, warmup, dev, side, prof, u0, peak, variant=0, lattice=19, pattern="ab",
+                  model="cascaded"):
+    """The same workload in another storage format, step-kernel form, lattice
+    (D3Q27 of Sec. II), storage pattern (in-place AA) or collision model (the
+    SRT and non-orthogonal MRT comparison models)."""
     import torch
 
     from paper_1801_04586_gb300 import Lattice
-    lat = Lattice(side, side, side, NU, storage=storage, device=dev, variant=variant)
-    npt = lat.info()["nodes_per_thread"]
+    lat = Lattice(side, side, side, NU, storage=storage, device=dev, variant=variant, lattice=lattice,
+                  pattern=pattern, model=model)
+    info = lat.info()
     lat.set_force_profile_z(prof)
     lat.init_equilibrium(None, u0)
     lat.step(warmup)
@@ -236,34 +245,11 @@ def bench_storage(storage, K, warmup, dev, side, prof, u0, peak, variant=0):
     ms = e0.elapsed_time(e1)
     n = lat.n
     lat.close()
-    bpn = 152 if storage == "f32" else 76
+    bpn = (4 if storage == "f32" else 2) * 2 * lattice
     achieved = bpn * n / (ms / K * 1e-3) / 1e9
     return {"value": n * K / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / K, "bytes_per_node": bpn,
-            "achieved_gbs": achieved, "frac": achieved / peak, "nodes_per_thread": npt}
-
-
-def bench_d3q27(K, warmup, dev, side, prof, u0, peak):
-    """The same workload on the D3Q27 lattice of Sec. II (FP32, 216 B/node)."""
-    import torch
-
-    from paper_1801_04586_gb300 import Lattice
-    lat = Lattice(side, side, side, NU, device=dev, lattice=27)
-    lat.set_force_profile_z(prof)
-    lat.init_equilibrium(None, u0)
-    lat.step(warmup)
-    torch.cuda.synchronize()
-    e0, e1 = _events()
-    e0.record(lat.stream)
-    lat.step(K)
-    e1.record(lat.stream)
-    torch.cuda.synchronize()
-    lat.check()
-    ms = e0.elapsed_time(e1)
-    n = lat.n
-    lat.close()
-    achieved = 216 * n / (ms / K * 1e-3) / 1e9
-    return {"value": n * K / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / K, "bytes_per_node": 216,
-            "achieved_gbs": achieved, "frac": achieved / peak}
+            "achieved_gbs": achieved, "frac": achieved / peak, "nodes_per_thread": info["nodes_per_thread"],
+            "buffers": info["buffers"], "state_gb": info["buffers"] * info["state_bytes"] / 1e9}
 
 
 def bench_adjoint(dev, side, K, peak):
@@ -403,7 +389,7 @@ def run_gb300(args):
     side = args.size
     shape = (side, side, side)
     lat = Lattice(side, side, side, NU, walls=0, storage=args.storage, block=(bx, by), device=dev,
-                  variant=args.variant, lattice=args.lattice)
+                  variant=args.variant, lattice=args.lattice, pattern=args.pattern, model=args.model)
     prof = torch.from_numpy(synthetic.kolmogorov_profile(side, F0)).to(dev)
     u0_np = synthetic.divfree_velocity(shape, seed=1, umax=UMAX)
     u0 = torch.from_numpy(u0_np).to(dev)
@@ -448,7 +434,9 @@ def run_gb300(args):
     peak, peak_kind = measured_peaks()
     bytes_per_node = (2 if args.storage != "f32" else 4) * 2 * args.lattice
     achieved = bytes_per_node * nodes / mean_launch_s / 1e9
-    traffic = profiled_traffic() if (args.storage, args.lattice, side) == ("f32", 19, N_SIDE) else None
+    default_case = (args.storage, args.lattice, args.pattern, args.variant, args.model) == (
+        "f32", 19, "ab", 0, "cascaded")
+    traffic = profiled_traffic() if default_case and side == N_SIDE else None
 
     e2e = None
     if not args.no_e2e:
@@ -491,7 +479,13 @@ def run_gb300(args):
                                                              variant=1),
             "f16_stochastic_storage": bench_storage("f16sr", K, args.warmup, dev, side, prof, u0, peak),
             "bf16_stochastic_storage": bench_storage("bf16sr", K, args.warmup, dev, side, prof, u0, peak),
-            "d3q27_f32": bench_d3q27(K, args.warmup, dev, side, prof, u0, peak),
+            "aa_in_place_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, pattern="aa"),
+            "aa_in_place_f16": bench_storage("f16", K, args.warmup, dev, side, prof, u0, peak, pattern="aa"),
+            "srt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, model="srt"),
+            "mrt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, model="mrt"),
+            "d3q27_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, lattice=27),
+            "d3q27_aa_in_place_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, lattice=27,
+                                                   pattern="aa"),
             "adjoint_kernel_256": bench_adjoint(dev, side, max(10, min(K, 100)), peak),
             "adjoint_unroll_64": bench_unroll(dev),
             "batched_64_domains": bench_batch(dev, args.batch_steps, peak),
@@ -519,8 +513,9 @@ def run_gb300(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": bytes_per_node * nodes,
-                         "kernel": "k_step<float,1,false>" if (args.storage, args.lattice) == ("f32", 19)
-                         else f"step kernel, {args.storage} storage, D3Q{args.lattice}"},
+                         "kernel": "k_step<float,1,false>" if default_case
+                         else f"step kernel, {args.model} collision, {args.storage} storage, D3Q{args.lattice}, "
+                              f"{args.pattern} pattern"},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "variants": variants,

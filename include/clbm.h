@@ -58,6 +58,36 @@ extern "C" {
 #define CLBM_STORAGE_F16_SR  3
 #define CLBM_STORAGE_BF16_SR 4
 
+/* ---- storage patterns of the population state ---- */
+/* Two buffers: each step pulls from one and writes the other (Eq. 8 read
+ * backwards). */
+#define CLBM_PATTERN_AB 0
+/* One buffer updated in place, alternating two step kinds: even steps read
+ * and write the node's own slots (writing population i into the slot of its
+ * opposite), odd steps read from and write to the neighbours' slots. Each node
+ * writes exactly the slots it read, so no other node races it. Same results,
+ * same bytes per node update, half the memory. The raw layout of the state
+ * depends on the parity of the step count: clbm_export_state and
+ * clbm_import_state move raw layouts, so import into a context whose step
+ * count has the same parity. Not available for the recomputation and adjoint
+ * entry points or in batches. */
+#define CLBM_PATTERN_AA 1
+
+/* ---- collision models ---- */
+/* The paper's method: the cascaded (central-moment) collision of Eq. 5 with
+ * the consistent forcing scheme (Eqs. A5-A6 / 15-16). */
+#define CLBM_MODEL_CASCADED 0
+/* Comparison models the paper measures against, on the same layout,
+ * streaming and storage formats (D3Q19 only; not in batches, not for the
+ * adjoint entry points):
+ * SRT-LBM (Sec. III.A): one rate s2 (from nu), the second-order discrete
+ * equilibrium written out in Sec. II.B and Guo's forcing term. */
+#define CLBM_MODEL_SRT      1
+/* Non-orthogonal MRT-LBM (Appendix B): the raw moments of Eq. A4 relaxed
+ * with the S of Eq. A3 (nu, s2b, s3, s4) towards M f_D, with the forcing
+ * moments M R_G of Guo's term. */
+#define CLBM_MODEL_MRT      2
+
 /* ---- wall axes: both faces of the axis are halfway bounce-back walls ---- */
 #define CLBM_WALL_X 1u
 #define CLBM_WALL_Y 2u
@@ -94,8 +124,10 @@ typedef struct clbm_params {
     int32_t block_x, block_y;
     int32_t variant;
     int32_t lattice;
-    int32_t reserved;
+    int32_t pattern;          /* CLBM_PATTERN_AB (0) or CLBM_PATTERN_AA */
     double s3b, s4b, s5, s6;
+    int32_t model;            /* CLBM_MODEL_CASCADED (0), CLBM_MODEL_SRT or CLBM_MODEL_MRT */
+    int32_t reserved;         /* must be 0 */
 } clbm_params;
 
 typedef struct clbm_info {
@@ -108,6 +140,10 @@ typedef struct clbm_info {
     double s2;                /* 1/(3 nu + 1/2) */
     int32_t nodes_per_thread; /* of the step kernel: 1 or 2 */
     int32_t q;                /* 19 or 27 */
+    int32_t pattern;          /* CLBM_PATTERN_AB or CLBM_PATTERN_AA */
+    int32_t buffers;          /* population buffers held: 2 (A/B) or 1 (AA) */
+    int32_t model;            /* CLBM_MODEL_* */
+    int32_t reserved;
 } clbm_info;
 
 typedef struct clbm_ctx clbm_ctx;
@@ -210,14 +246,16 @@ int clbm_load_state(clbm_ctx *ctx, const void *host_buf, size_t bytes);
  * final state back to rho_out_host / u_out_host (either may be NULL). If
  * moments_host is not NULL it receives 4 * (nsteps + 1) doubles: entry k
  * (k = 0..nsteps) holds the FP64 sums of clbm_reduce_moments for the state at
- * step k. For k < nsteps they are formed inside step k+1's kernel from the
- * state it pulls (block sums, no extra pass over the populations) and copied
- * back asynchronously after every step; the last comes from one reduction
- * after the final step. The call synchronises once, at the end, then returns
+ * step k. With the cascaded collision, the A/B pattern and D3Q19 they are
+ * formed inside step k+1's kernel from the state it pulls (exact fixed-point
+ * warp sums, no extra pass over the populations); otherwise by one
+ * clbm_reduce_moments pass before each step. They are copied back
+ * asynchronously after every step; the last comes from one reduction after
+ * the final step. The call synchronises once, at the end, then returns
  * CLBM_ERR_UNSTABLE if any mass sum is non-finite or the instability flag is
- * set. Device scratch for the staging fields and block sums is allocated on
- * first use and kept by the context. Host buffers should be pinned for full
- * copy speed and for the copies to overlap the steps. */
+ * set. Device scratch for the staging fields and partial sums is allocated
+ * on first use and kept by the context. Host buffers should be pinned for
+ * full copy speed and for the copies to overlap the steps. */
 int clbm_run_host(clbm_ctx *ctx, const float *rho_host, const float *u_host, int64_t nsteps,
                   float *rho_out_host, float *u_out_host, double *moments_host);
 

@@ -19,6 +19,8 @@ CLBM_ERR_UNSTABLE = -4
 CLBM_ERR_STATE = -5
 
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "f16sr": 3, "bf16sr": 4}
+PATTERN = {"ab": 0, "aa": 1}
+MODEL = {"cascaded": 0, "srt": 1, "mrt": 2}
 WALL_X, WALL_Y, WALL_Z = 1, 2, 4
 
 
@@ -27,8 +29,9 @@ class Params(ctypes.Structure):
                 ("walls", ctypes.c_uint32), ("nu", ctypes.c_double), ("s2b", ctypes.c_double),
                 ("s3", ctypes.c_double), ("s4", ctypes.c_double), ("storage", ctypes.c_int32),
                 ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("lattice", ctypes.c_int32), ("reserved", ctypes.c_int32), ("s3b", ctypes.c_double),
-                ("s4b", ctypes.c_double), ("s5", ctypes.c_double), ("s6", ctypes.c_double)]
+                ("lattice", ctypes.c_int32), ("pattern", ctypes.c_int32), ("s3b", ctypes.c_double),
+                ("s4b", ctypes.c_double), ("s5", ctypes.c_double), ("s6", ctypes.c_double),
+                ("model", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Domain(ctypes.Structure):
@@ -51,7 +54,8 @@ class Info(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("pop_stride", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
                 ("steps_done", ctypes.c_int64), ("storage", ctypes.c_int32), ("block_x", ctypes.c_int32),
                 ("block_y", ctypes.c_int32), ("s2", ctypes.c_double), ("nodes_per_thread", ctypes.c_int32),
-                ("q", ctypes.c_int32)]
+                ("q", ctypes.c_int32), ("pattern", ctypes.c_int32), ("buffers", ctypes.c_int32),
+                ("model", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 P = ctypes.c_void_p

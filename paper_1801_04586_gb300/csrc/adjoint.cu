@@ -21,49 +21,6 @@
 
 namespace clbm {
 
-// Targets of the 19 populations leaving node (x, y, z) under Eq. 8: (i, x + e_i)
-// with periodic wrap, or (ibar, x) when x + e_i lies beyond a wall face.
-template <bool WALLS>
-__device__ __forceinline__ void push_targets(const Geom &g, int x, int y, int z, uint32_t (&off)[kQ],
-                                             int (&pop)[kQ]) {
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-    const uint32_t unx = (uint32_t)nx, uny = (uint32_t)ny;
-    const uint32_t rc = ((uint32_t)z * uny + y) * unx;
-    const uint32_t rym = ((uint32_t)z * uny + ym) * unx, ryp = ((uint32_t)z * uny + yp) * unx;
-    const uint32_t rzm = ((uint32_t)zm * uny + y) * unx, rzp = ((uint32_t)zp * uny + y) * unx;
-    const uint32_t rmm = ((uint32_t)zm * uny + ym) * unx, rpm = ((uint32_t)zm * uny + yp) * unx;
-    const uint32_t rmp = ((uint32_t)zp * uny + ym) * unx, rpp = ((uint32_t)zp * uny + yp) * unx;
-    const uint32_t self = rc + x;
-    // destination x + e_i
-    off[0] = self;
-    off[1] = rc + xp;   off[2] = rc + xm;
-    off[3] = ryp + x;   off[4] = rym + x;
-    off[5] = rzp + x;   off[6] = rzm + x;
-    off[7] = ryp + xp;  off[8] = ryp + xm;  off[9] = rym + xp;  off[10] = rym + xm;
-    off[11] = rzp + xp; off[12] = rzp + xm; off[13] = rzm + xp; off[14] = rzm + xm;
-    off[15] = rpp + x;  off[16] = rmp + x;  off[17] = rpm + x;  off[18] = rmm + x;
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) pop[i] = i;
-    if (WALLS) {
-        const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
-        const bool xl = wx && x == 0, xh = wx && x == nx - 1;  // leaving through x- (ex = -1) / x+ (ex = +1)
-        const bool yl = wy && y == 0, yh = wy && y == ny - 1;
-        const bool zl = wz && z == 0, zh = wz && z == nz - 1;
-        const bool bb[kQ] = {false,
-                             xh, xl, yh, yl, zh, zl,
-                             xh || yh, xl || yh, xh || yl, xl || yl,
-                             xh || zh, xl || zh, xh || zl, xl || zl,
-                             yh || zh, yl || zh, yh || zl, yl || zl};
-#pragma unroll
-        for (int i = 1; i < kQ; ++i) {
-            if (bb[i]) { pop[i] = opposite(i); off[i] = self; }
-        }
-    }
-}
-
 // Transposed triplet factors. Unshift (c -> k with velocity v) has matrix
 // [[1,0,0],[v,1,0],[v^2,2v,1]]; its transpose maps (a0,a1,a2) to
 // (a0 + v a1 + v^2 a2, a1 + 2 v a2, a2). The shift is the unshift with -v.

@@ -27,29 +27,49 @@ __device__ __forceinline__ bool node_of(const Geom &g, int &x, int &y, int &z) {
     return x < g.nx && y < g.ny;
 }
 
+// Slots of the post-streaming populations of node (x,y,z) in a state buffer.
+// map 0: A/B pattern, the pull map; 1: in-place (AA) pattern after an even
+// number of steps, natural order at the node; 2: AA after an odd number of
+// steps, the swapped pull map of the odd step (step.cu).
+template <bool WALLS>
+__device__ __forceinline__ void state_slots(const Geom &g, int x, int y, int z, int map, uint32_t (&off)[kQ],
+                                            int (&pop)[kQ]) {
+    if (map == 1) {
+        const uint32_t self = ((uint32_t)z * g.ny + y) * g.nx + x;
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) { off[i] = self; pop[i] = i; }
+    } else if (map == 2) {
+        pull_sources<WALLS, true>(g, x, y, z, off, pop);
+    } else {
+        pull_sources<WALLS>(g, x, y, z, off, pop);
+    }
+}
+
 // Write a post-streaming state h (deviations) of node (x,y,z) where the next
-// pull will find it: the pull map used for writing.
+// step will find it.
 template <typename S, bool WALLS>
-__device__ __forceinline__ void scatter_node(S *dst, const Geom &g, int x, int y, int z, const float (&h)[kQ]) {
+__device__ __forceinline__ void scatter_node(S *dst, const Geom &g, int x, int y, int z, int map,
+                                             const float (&h)[kQ]) {
     uint32_t off[kQ];
     int pop[kQ];
-    pull_sources<WALLS>(g, x, y, z, off, pop);
+    state_slots<WALLS>(g, x, y, z, map, off, pop);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) dst[(size_t)pop[i] * g.stride + off[i]] = Codec<S>::from_f(h[i]);
 }
 
 template <typename S, bool WALLS>
-__device__ __forceinline__ uint32_t pull_node(const S *src, const Geom &g, int x, int y, int z, float (&h)[kQ]) {
+__device__ __forceinline__ uint32_t pull_node(const S *src, const Geom &g, int x, int y, int z, int map,
+                                              float (&h)[kQ]) {
     uint32_t off[kQ];
     int pop[kQ];
-    pull_sources<WALLS>(g, x, y, z, off, pop);
+    state_slots<WALLS>(g, x, y, z, map, off, pop);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load_plain(src + (size_t)pop[i] * g.stride + off[i]);
-    return off[0];
+    return ((uint32_t)z * g.ny + y) * g.nx + x;
 }
 
 template <typename S, bool WALLS>
-__global__ void k_scatter(S *dst, Geom g, const float *__restrict__ f, int64_t n, int deviation) {
+__global__ void k_scatter(S *dst, Geom g, int map, const float *__restrict__ f, int64_t n, int deviation) {
     int x, y, z;
     if (!node_of(g, x, y, z)) return;
     const uint32_t self = ((uint32_t)z * g.ny + y) * g.nx + x;
@@ -59,12 +79,12 @@ __global__ void k_scatter(S *dst, Geom g, const float *__restrict__ f, int64_t n
         const float v = f[(size_t)i * n + self];
         h[i] = deviation ? v : v - rest_weight(i);
     }
-    scatter_node<S, WALLS>(dst, g, x, y, z, h);
+    scatter_node<S, WALLS>(dst, g, x, y, z, map, h);
 }
 
 template <typename S, int FM, bool WALLS>
-__global__ void k_init_eq(S *dst, Geom g, const float *__restrict__ rho, const float *__restrict__ u, int64_t n,
-                          ForceArgs F) {
+__global__ void k_init_eq(S *dst, Geom g, int map, const float *__restrict__ rho, const float *__restrict__ u,
+                          int64_t n, ForceArgs F) {
     int x, y, z;
     if (!node_of(g, x, y, z)) return;
     const uint32_t self = ((uint32_t)z * g.ny + y) * g.nx + x;
@@ -77,26 +97,26 @@ __global__ void k_init_eq(S *dst, Geom g, const float *__restrict__ rho, const f
     const float uz = (u ? u[2 * n + self] : 0.0f) - fz * half_inv;
     float h[kQ];
     equilibrium_dev(r, ux, uy, uz, h);
-    scatter_node<S, WALLS>(dst, g, x, y, z, h);
+    scatter_node<S, WALLS>(dst, g, x, y, z, map, h);
 }
 
 template <typename S, bool WALLS>
-__global__ void k_gather(const S *src, Geom g, float *__restrict__ f, int64_t n, int deviation) {
+__global__ void k_gather(const S *src, Geom g, int map, float *__restrict__ f, int64_t n, int deviation) {
     int x, y, z;
     if (!node_of(g, x, y, z)) return;
     float h[kQ];
-    const uint32_t self = pull_node<S, WALLS>(src, g, x, y, z, h);
+    const uint32_t self = pull_node<S, WALLS>(src, g, x, y, z, map, h);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) f[(size_t)i * n + self] = deviation ? h[i] : h[i] + rest_weight(i);
 }
 
 template <typename S, int FM, bool WALLS>
-__global__ void k_macros(const S *src, Geom g, ForceArgs F, float *__restrict__ rho, float *__restrict__ u,
-                         int64_t n) {
+__global__ void k_macros(const S *src, Geom g, int map, ForceArgs F, float *__restrict__ rho,
+                         float *__restrict__ u, int64_t n) {
     int x, y, z;
     if (!node_of(g, x, y, z)) return;
     float h[kQ];
-    const uint32_t self = pull_node<S, WALLS>(src, g, x, y, z, h);
+    const uint32_t self = pull_node<S, WALLS>(src, g, x, y, z, map, h);
     float fx, fy, fz, jx, jy, jz;
     force_node<FM>(F, g, z, self, fx, fy, fz);
     const float drho = macros_dev(h, fx, fy, fz, jx, jy, jz);
@@ -142,7 +162,7 @@ __global__ void k_fixed_final4(const long long *partials, int nblocks, double *o
 }
 
 template <typename S, int FM, bool WALLS>
-__global__ void k_reduce_moments(const S *src, Geom g, ForceArgs F, long long *partials) {
+__global__ void k_reduce_moments(const S *src, Geom g, int map, ForceArgs F, long long *partials) {
     long long q[4] = {0ll, 0ll, 0ll, 0ll};
     const int64_t n = (int64_t)g.nx * g.ny * g.nz;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
@@ -150,7 +170,7 @@ __global__ void k_reduce_moments(const S *src, Geom g, ForceArgs F, long long *p
         const int64_t t = s / g.nx;
         const int y = (int)(t % g.ny), z = (int)(t / g.ny);
         float h[kQ];
-        const uint32_t self = pull_node<S, WALLS>(src, g, x, y, z, h);
+        const uint32_t self = pull_node<S, WALLS>(src, g, x, y, z, map, h);
         float fx, fy, fz, jx, jy, jz;
         force_node<FM>(F, g, z, self, fx, fy, fz);
         const float drho = macros_dev(h, fx, fy, fz, jx, jy, jz);
@@ -182,7 +202,7 @@ __global__ void k_reduce_pair(const float *__restrict__ a, const float *__restri
 
 template <typename S, bool W>
 static void scatter_t(const Launch &L, void *dst, const float *f, int64_t n, int dev) {
-    k_scatter<S, W><<<L.grid, L.block, 0, L.stream>>>((S *)dst, L.g, f, n, dev);
+    k_scatter<S, W><<<L.grid, L.block, 0, L.stream>>>((S *)dst, L.g, L.map, f, n, dev);
 }
 
 cudaError_t launch_scatter(int storage, const Launch &L, void *dst, const float *f, int64_t n, int deviation) {
@@ -195,8 +215,8 @@ cudaError_t launch_scatter(int storage, const Launch &L, void *dst, const float 
 
 template <typename S, int FM>
 static void init_t(const Launch &L, void *dst, const float *rho, const float *u, int64_t n, const ForceArgs &F) {
-    if (L.g.walls) k_init_eq<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((S *)dst, L.g, rho, u, n, F);
-    else k_init_eq<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((S *)dst, L.g, rho, u, n, F);
+    if (L.g.walls) k_init_eq<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((S *)dst, L.g, L.map, rho, u, n, F);
+    else k_init_eq<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((S *)dst, L.g, L.map, rho, u, n, F);
 }
 
 cudaError_t launch_init_eq(int storage, const Launch &L, void *dst, const float *rho, const float *u, int64_t n,
@@ -213,16 +233,16 @@ cudaError_t launch_init_eq(int storage, const Launch &L, void *dst, const float 
 
 cudaError_t launch_gather(int storage, const Launch &L, const void *src, float *f, int64_t n, int deviation) {
     CLBM_DISPATCH_STORAGE(storage, {
-        if (L.g.walls) k_gather<S, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, L.g, f, n, deviation);
-        else k_gather<S, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, L.g, f, n, deviation);
+        if (L.g.walls) k_gather<S, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, L.g, L.map, f, n, deviation);
+        else k_gather<S, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, L.g, L.map, f, n, deviation);
     })
     return cudaGetLastError();
 }
 
 template <typename S, int FM>
 static void macros_t(const Launch &L, const void *src, const ForceArgs &F, float *rho, float *u, int64_t n) {
-    if (L.g.walls) k_macros<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, L.g, F, rho, u, n);
-    else k_macros<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, L.g, F, rho, u, n);
+    if (L.g.walls) k_macros<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, L.g, L.map, F, rho, u, n);
+    else k_macros<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, L.g, L.map, F, rho, u, n);
 }
 
 cudaError_t launch_macros(int storage, const Launch &L, const void *src, const ForceArgs &F, float *rho, float *u,
@@ -239,8 +259,8 @@ cudaError_t launch_macros(int storage, const Launch &L, const void *src, const F
 
 template <typename S, int FM>
 static void moments_t(const Launch &L, const void *src, const ForceArgs &F, long long *partials, int nb) {
-    if (L.g.walls) k_reduce_moments<S, FM, true><<<nb, 256, 0, L.stream>>>((const S *)src, L.g, F, partials);
-    else k_reduce_moments<S, FM, false><<<nb, 256, 0, L.stream>>>((const S *)src, L.g, F, partials);
+    if (L.g.walls) k_reduce_moments<S, FM, true><<<nb, 256, 0, L.stream>>>((const S *)src, L.g, L.map, F, partials);
+    else k_reduce_moments<S, FM, false><<<nb, 256, 0, L.stream>>>((const S *)src, L.g, L.map, F, partials);
 }
 
 cudaError_t launch_reduce_moments(int storage, const Launch &L, const void *src, const ForceArgs &F,

@@ -162,6 +162,7 @@ Launch domain_launch(const clbm_batch *b, int d) {
     L.grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
     L.stream = b->stream;
     L.packed = false;
+    L.map = 0;
     return L;
 }
 

@@ -41,6 +41,19 @@ constexpr double kFixUnit = 1.0 / 68719476736.0;     // 2^-36
 
 __device__ __forceinline__ long long to_fixed(float v) { return __float2ll_rn(v * 68719476736.0f); }
 
+// Warp sum of fixed-point values, exact, with two 32-bit warp reductions
+// (redux.sync) instead of 64-bit shuffles: v is split into its low 20 bits
+// (non-negative) and the rest (arithmetic shift). Exact while every |v| <
+// 2^46 (|value| < 2^10): then 32 high parts sum below 2^31 and 32 low parts
+// below 2^25. All 32 lanes must call it.
+__device__ __forceinline__ long long warp_sum_fixed(long long v) {
+    const int lo = (int)(v & 0xfffffll);
+    const int hi = (int)(v >> 20);
+    const int slo = __reduce_add_sync(0xffffffffu, lo);
+    const int shi = __reduce_add_sync(0xffffffffu, hi);
+    return (long long)shi * 1048576ll + (long long)slo;
+}
+
 // Block sum of fixed-point values q; thread 0's warp writes the K totals to
 // dst[0..K-1]. Every thread of the block calls it.
 template <int K>

@@ -35,7 +35,7 @@ constexpr int kMidBlocks = 152;         // first pass over the step kernel's blo
 
 struct StateHeader {
     char magic[8];
-    int32_t version, nx, ny, nz, walls, storage, q, pad;
+    int32_t version, nx, ny, nz, walls, storage, q, pattern;
     int64_t stride, steps_done, bytes;
 };
 
@@ -59,12 +59,14 @@ struct clbm_ctx {
     float *d_io;          // clbm_run_host scratch (first use): 4 x N floats, then
     double *d_mom;        //   4 doubles of sums and
     long long *d_mid;     //   4 fixed-point sums per first-pass block and
-    long long *d_diag;    //   4 fixed-point sums per step-kernel block
-    int64_t diag_blocks;
+    long long *d_diag;    //   4 fixed-point sums per warp of the fused step kernel
+    int64_t diag_blocks;  // warp partial sets d_diag holds
     int64_t steps_done;
     double gamma;         // force decay rate (clbm_set_force_decay)
     bool packed;          // step kernel with two nodes per thread (FP32x2 arithmetic)
     int q;                // 19 (Appendix A) or 27 (Sec. II)
+    bool aa;              // in-place (AA) pattern: one population buffer, step kind by parity
+    int model;            // CLBM_MODEL_*
     Rates27 rates27;
     dim3 block;
 };
@@ -91,6 +93,9 @@ Launch launch_of(const clbm_ctx *c) {
     L.grid = dim3((c->g.nx + c->block.x - 1) / c->block.x, (c->g.ny + c->block.y - 1) / c->block.y, c->g.nz);
     L.stream = c->stream;
     L.packed = false;
+    // A/B: the pull map; AA: natural slots after an even number of steps, the
+    // odd step's swapped pull map after an odd number.
+    L.map = c->aa ? ((c->steps_done & 1) ? 2 : 1) : 0;
     return L;
 }
 
@@ -105,6 +110,24 @@ Launch step_launch_of(const clbm_ctx *c) {
 }
 
 bool rate_ok(double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; }
+
+// One D3Q19 step of the context's collision model and pattern.
+cudaError_t step19(const clbm_ctx *c, const Launch &L, const void *src, void *dst, const ForceArgs &F,
+                   uint32_t key) {
+    switch (c->model) {
+        case CLBM_MODEL_SRT: return launch_step_srt(c->p.storage, L, src, dst, c->rates, F, c->d_flag, key);
+        case CLBM_MODEL_MRT: return launch_step_mrt(c->p.storage, L, src, dst, c->rates, F, c->d_flag, key);
+        default: return launch_step(c->p.storage, L, src, dst, c->rates, F, c->d_flag, key);
+    }
+}
+
+cudaError_t step19_aa(const clbm_ctx *c, const Launch &L, void *f, const ForceArgs &F, uint32_t key, bool odd) {
+    switch (c->model) {
+        case CLBM_MODEL_SRT: return launch_step_aa_srt(c->p.storage, L, f, c->rates, F, c->d_flag, key, odd);
+        case CLBM_MODEL_MRT: return launch_step_aa_mrt(c->p.storage, L, f, c->rates, F, c->d_flag, key, odd);
+        default: return launch_step_aa(c->p.storage, L, f, c->rates, F, c->d_flag, key, odd);
+    }
+}
 
 }  // namespace
 
@@ -148,6 +171,14 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
         return fail(CLBM_ERR_ARG, "clbm_create: relaxation rates must lie in (0, 2)");
     if (q == 27 && p->variant == 2)
         return fail(CLBM_ERR_ARG, "clbm_create: the two-nodes-per-thread form is D3Q19 only");
+    if (p->pattern != CLBM_PATTERN_AB && p->pattern != CLBM_PATTERN_AA)
+        return fail(CLBM_ERR_ARG, "clbm_create: pattern must be CLBM_PATTERN_AB or CLBM_PATTERN_AA");
+    if (p->pattern == CLBM_PATTERN_AA && p->variant == 2)
+        return fail(CLBM_ERR_ARG, "clbm_create: the in-place pattern runs one node per thread (variant 0 or 1)");
+    if (p->model < CLBM_MODEL_CASCADED || p->model > CLBM_MODEL_MRT || p->reserved != 0)
+        return fail(CLBM_ERR_ARG, "clbm_create: model must be CLBM_MODEL_CASCADED, _SRT or _MRT (reserved 0)");
+    if (p->model != CLBM_MODEL_CASCADED && (q != 19 || p->variant == 2))
+        return fail(CLBM_ERR_ARG, "clbm_create: the SRT and MRT models are D3Q19, one node per thread");
     int bx = p->block_x, by = p->block_y;
     if (bx == 0) bx = p->nx >= 128 ? 128 : ((p->nx + 31) / 32) * 32;
     if (by == 0) by = std::max(1, std::min(p->ny, 256 / bx));
@@ -180,6 +211,8 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     c->gamma = 0.0;
     c->q = q;
     c->packed = q == 19 && p->variant == 2;
+    c->aa = p->pattern == CLBM_PATTERN_AA;
+    c->model = p->model;
     c->rates27.om2 = c->rates.om2;
     c->rates27.cb = c->rates.cb;
     c->rates27.om3 = c->rates.om3;
@@ -194,13 +227,14 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     c->cur = 0;
     c->steps_done = 0;
     const size_t bytes = (size_t)c->q * c->g.stride * c->elem;
-    cudaError_t e = cudaMalloc(&c->buf[0], 2 * bytes);
+    const size_t nbuf = c->aa ? 1 : 2;
+    cudaError_t e = cudaMalloc(&c->buf[0], nbuf * bytes);
     if (e != cudaSuccess) {
         delete c;
         cudaGetLastError();
         return fail(CLBM_ERR_OOM, std::string("clbm_create: cudaMalloc: ") + cudaGetErrorString(e));
     }
-    c->buf[1] = (char *)c->buf[0] + bytes;
+    c->buf[1] = c->aa ? c->buf[0] : (char *)c->buf[0] + bytes;
     e = cudaMalloc(&c->d_flag, 256 + sizeof(double) * 4 * kReduceBlocks);
     if (e != cudaSuccess) {
         cudaFree(c->buf[0]);
@@ -209,8 +243,8 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
         return fail(CLBM_ERR_OOM, std::string("clbm_create: cudaMalloc: ") + cudaGetErrorString(e));
     }
     c->d_partials = (double *)((char *)c->d_flag + 256);
-    // rest state: zero deviations in both buffers (zero bits are zero in all formats)
-    if ((e = cudaMemsetAsync(c->buf[0], 0, 2 * bytes, c->stream)) != cudaSuccess ||
+    // rest state: zero deviations in every buffer (zero bits are zero in all formats)
+    if ((e = cudaMemsetAsync(c->buf[0], 0, nbuf * bytes, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream)) != cudaSuccess) {
         cudaFree(c->d_flag);
         cudaFree(c->buf[0]);
@@ -243,6 +277,10 @@ int clbm_get_info(const clbm_ctx *c, clbm_info *info) {
     info->s2 = c->s2;
     info->nodes_per_thread = c->packed ? 2 : 1;
     info->q = c->q;
+    info->pattern = c->aa ? CLBM_PATTERN_AA : CLBM_PATTERN_AB;
+    info->buffers = c->aa ? 1 : 2;
+    info->model = c->model;
+    info->reserved = 0;
     return CLBM_OK;
 }
 
@@ -278,11 +316,11 @@ int clbm_set_force_decay(clbm_ctx *c, double gamma) {
 
 int clbm_init_equilibrium(clbm_ctx *c, const float *rho, const float *u) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_init_equilibrium: null context");
+    c->steps_done = 0;  // before launch_of: the in-place pattern starts in natural order
     cudaError_t e = c->q == 27
         ? launch_init27(c->p.storage, launch_of(c), c->buf[c->cur], rho, u, c->n, force_at_zero(c))
         : launch_init_eq(c->p.storage, launch_of(c), c->buf[c->cur], rho, u, c->n, force_at_zero(c));
     if (e != cudaSuccess) return cuda_fail(e, "clbm_init_equilibrium");
-    c->steps_done = 0;
     return CLBM_OK;
 }
 
@@ -290,12 +328,20 @@ int clbm_step(clbm_ctx *c, int64_t nsteps) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_step: null context");
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_step: nsteps < 0");
     const Launch L = step_launch_of(c);
-    for (int64_t t = 0; t < nsteps; ++t) {
+    for (int64_t t = 0; t < nsteps && c->aa; ++t) {
+        const bool odd = (c->steps_done & 1) != 0;
+        cudaError_t e = c->q == 27
+            ? launch_step27_aa(c->p.storage, L, c->buf[0], c->rates27, force_now(c), c->d_flag,
+                               step_key(c->steps_done), odd)
+            : step19_aa(c, L, c->buf[0], force_now(c), step_key(c->steps_done), odd);
+        if (e != cudaSuccess) return cuda_fail(e, "clbm_step");
+        ++c->steps_done;
+    }
+    for (int64_t t = 0; t < nsteps && !c->aa; ++t) {
         cudaError_t e = c->q == 27
             ? launch_step27(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates27, force_now(c), c->d_flag,
                             step_key(c->steps_done))
-            : launch_step(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c), c->d_flag,
-                          step_key(c->steps_done));
+            : step19(c, L, c->buf[c->cur], c->buf[c->cur ^ 1], force_now(c), step_key(c->steps_done));
         if (e != cudaSuccess) return cuda_fail(e, "clbm_step");
         c->cur ^= 1;
         ++c->steps_done;
@@ -322,10 +368,10 @@ int clbm_get_populations(clbm_ctx *c, float *f, int deviation) {
 
 int clbm_set_populations(clbm_ctx *c, const float *f, int deviation) {
     if (!c || !f) return fail(CLBM_ERR_ARG, "clbm_set_populations: null pointer");
+    c->steps_done = 0;  // before launch_of: the in-place pattern restarts in natural order
     cudaError_t e = c->q == 27 ? launch_scatter27(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation)
                                : launch_scatter(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_set_populations");
-    c->steps_done = 0;
     return CLBM_OK;
 }
 
@@ -394,6 +440,7 @@ int clbm_save_state(clbm_ctx *c, void *host, size_t *bytes) {
     h.walls = (int32_t)c->g.walls;
     h.storage = c->p.storage;
     h.q = c->q;
+    h.pattern = c->aa ? CLBM_PATTERN_AA : CLBM_PATTERN_AB;
     h.stride = c->g.stride;
     h.steps_done = c->steps_done;
     h.bytes = (int64_t)raw;
@@ -414,7 +461,8 @@ int clbm_load_state(clbm_ctx *c, const void *host, size_t bytes) {
     if (std::memcmp(h.magic, "CLBMLBM", 8) != 0 || h.version != 2)
         return fail(CLBM_ERR_ARG, "clbm_load_state: not a state buffer");
     if (h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz || h.walls != (int32_t)c->g.walls ||
-        h.storage != c->p.storage || h.q != c->q || h.stride != c->g.stride || h.bytes != (int64_t)raw ||
+        h.storage != c->p.storage || h.q != c->q || h.pattern != (c->aa ? CLBM_PATTERN_AA : CLBM_PATTERN_AB) ||
+        h.stride != c->g.stride || h.bytes != (int64_t)raw ||
         bytes < sizeof(h) + raw)
         return fail(CLBM_ERR_ARG, "clbm_load_state: geometry, storage or size mismatch");
     cudaError_t e =
@@ -428,6 +476,8 @@ int clbm_load_state(clbm_ctx *c, const void *host, size_t bytes) {
 int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
     if (!c || !src || !dst) return fail(CLBM_ERR_ARG, "clbm_step_raw: null pointer");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_step_raw: D3Q19 only");
+    if (c->aa) return fail(CLBM_ERR_ARG, "clbm_step_raw: A/B pattern only");
+    if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_step_raw: cascaded model only");
     if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_step_raw: needs a static force (decay 0)");
     const size_t bytes = (size_t)c->q * c->g.stride * c->elem;
     if ((const char *)src < (const char *)dst + bytes && (const char *)dst < (const char *)src + bytes)
@@ -440,6 +490,8 @@ int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
 int clbm_adjoint_seed(clbm_ctx *c, const void *state, const float *gu, float *lam, float *gF) {
     if (!c || !gu || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: null pointer");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: D3Q19 only");
+    if (c->aa) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: A/B pattern only");
+    if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: cascaded model only");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: FP32 storage only");
     if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_adjoint_seed: needs a static force (decay 0)");
     cudaError_t e = launch_adjoint_seed(c->p.storage, launch_of(c), state ? state : c->buf[c->cur], gu, lam, gF,
@@ -451,6 +503,8 @@ int clbm_adjoint_seed(clbm_ctx *c, const void *state, const float *gu, float *la
 int clbm_adjoint_step(clbm_ctx *c, const void *state, const float *lam_next, float *lam, float *gF) {
     if (!c || !state || !lam_next || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: null pointer");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: D3Q19 only");
+    if (c->aa) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: A/B pattern only");
+    if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: cascaded model only");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: FP32 storage only");
     if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_adjoint_step: needs a static force (decay 0)");
     if (lam == lam_next) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: lam aliases lam_next");
@@ -465,6 +519,8 @@ int clbm_adjoint_segment(clbm_ctx *c, const void *ckpt, void *tape, int64_t k, f
     if (!c || !ckpt || !lam || !lam_tmp || !gF || k < 1 || (k > 1 && !tape) || lam == lam_tmp)
         return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: bad argument");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: D3Q19 only");
+    if (c->aa) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: A/B pattern only");
+    if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: cascaded model only");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: FP32 storage only");
     if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_adjoint_segment: needs a static force (decay 0)");
     const Launch L = launch_of(c);
@@ -490,12 +546,13 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     if (!c) return fail(CLBM_ERR_ARG, "clbm_run_host: null context");
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_run_host: nsteps < 0");
     const Launch L = launch_of(c);
-    const int64_t nblocks = (int64_t)L.grid.x * L.grid.y * L.grid.z;
+    // one fixed-point partial set per warp of the fused step kernel
+    const int64_t nparts = (int64_t)L.grid.x * L.grid.y * L.grid.z * ((L.block.x * L.block.y) / 32);
     cudaError_t e;
-    if (!c->d_io || c->diag_blocks < nblocks) {
+    if (!c->d_io || c->diag_blocks < nparts) {
         if (c->d_io) cudaFree(c->d_io);
         const size_t bytes =
-            sizeof(float) * 4 * (size_t)c->n + 256 + sizeof(double) * (4 * (size_t)nblocks + 4 + 4 * kMidBlocks);
+            sizeof(float) * 4 * (size_t)c->n + 256 + sizeof(double) * (4 * (size_t)nparts + 4 + 4 * kMidBlocks);
         void *p = nullptr;
         if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) {
             c->d_io = nullptr;
@@ -508,7 +565,7 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         c->d_mom = (double *)((char *)p + io);
         c->d_mid = (long long *)(c->d_mom + 4);
         c->d_diag = c->d_mid + 4 * kMidBlocks;
-        c->diag_blocks = nblocks;
+        c->diag_blocks = nparts;
     }
     float *d_rho = c->d_io, *d_u = c->d_io + c->n;
     const size_t nb = sizeof(float) * (size_t)c->n;
@@ -518,8 +575,9 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         return cuda_fail(e, "clbm_run_host: copy u");
     int rc = clbm_init_equilibrium(c, rho_h ? d_rho : nullptr, u_h ? d_u : nullptr);
     if (rc != CLBM_OK) return rc;
-    for (int64_t t = 0; t < nsteps && c->q == 27; ++t) {
-        // D3Q27: plain step, then the conservation sums of the new state's predecessor
+    const bool fused = c->q == 19 && !c->aa && c->model == CLBM_MODEL_CASCADED;
+    for (int64_t t = 0; t < nsteps && !fused; ++t) {
+        // D3Q27 and the in-place pattern: the sums of state t, then a plain step
         if (moments_h) {
             if ((rc = clbm_reduce_moments(c, c->d_mom)) != CLBM_OK) return rc;
             e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
@@ -527,19 +585,19 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         }
         if ((rc = clbm_step(c, 1)) != CLBM_OK) return rc;
     }
-    for (int64_t t = 0; t < nsteps && c->q == 19; ++t) {
+    for (int64_t t = 0; t < nsteps && fused; ++t) {
         if (moments_h) {
             // fused step: FP64 sums of the state it pulls (state t) into per-block partials
             e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),
                                  c->d_flag, c->d_diag, step_key(c->steps_done));
             if (e == cudaSuccess)
-                e = launch_sum_partials4(c->d_diag, nblocks, c->d_mid, kMidBlocks, c->d_mom, (double)c->n, c->stream);
+                e = launch_sum_partials4(c->d_diag, nparts, c->d_mid, kMidBlocks, c->d_mom, (double)c->n, c->stream);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                                     c->stream);
         } else {
-            e = launch_step(c->p.storage, step_launch_of(c), c->buf[c->cur], c->buf[c->cur ^ 1], c->rates,
-                            force_now(c), c->d_flag, step_key(c->steps_done));
+            e = step19(c, step_launch_of(c), c->buf[c->cur], c->buf[c->cur ^ 1], force_now(c),
+                       step_key(c->steps_done));
         }
         if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: step");
         c->cur ^= 1;

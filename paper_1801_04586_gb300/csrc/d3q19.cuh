@@ -48,6 +48,20 @@ __host__ __device__ constexpr int opposite(int i) {
     return i == 0 ? 0 : (i <= 6 ? ((i & 1) ? i + 1 : i - 1) : (2 * (7 + 4 * ((i - 7) / 4)) + 3 - i));
 }
 
+// Velocity components of the D3Q19 set in the order of Eq. A1.
+__host__ __device__ constexpr int ex19(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey19(int i) {
+    return (i == 3 || i == 7 || i == 8 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 9 || i == 10 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int ez19(int i) {
+    return (i == 5 || i == 11 || i == 12 || i == 15 || i == 16) ? 1
+         : (i == 6 || i == 13 || i == 14 || i == 17 || i == 18) ? -1 : 0;
+}
+
 // ---------------------------------------------------------------- storage
 // Counter-based hash "lowbias32" (C. Wellons, hash-prospector, 2018): an
 // invertible 32-bit mixer; used to draw the dither of stochastic rounding
@@ -119,23 +133,39 @@ template <> struct Codec<BF16SR> {
     }
 };
 
-// Store the NQ post-collision deviations of one node (pull scheme: at the
-// node itself), h in population order. key: per-step random key (stochastic
-// formats only).
-template <typename S, int NQ = 19>
-__device__ __forceinline__ void store_node(S *d, int64_t stride, const float (&h)[NQ], uint32_t node, uint32_t key) {
+// Encode the NQ post-collision deviations h (population order) of one node
+// in the storage format. key: per-step random key (stochastic formats only);
+// the dither of population i depends on (key, node, i) alone, so every
+// storage pattern and staging path stores the same values.
+template <typename S, int NQ>
+__device__ __forceinline__ void encode_each(const float (&h)[NQ], uint32_t node, uint32_t key, S (&e)[NQ]) {
     if constexpr (Codec<S>::kStochastic) {
         const uint32_t base = lowbias32(node ^ key);
 #pragma unroll
         for (int i = 0; i < NQ; i += 2) {
             const uint32_t r = lowbias32(base + (uint32_t)i * 0x9e3779b9u);
-            d[(size_t)i * stride] = Codec<S>::from_f_sr(h[i], r);
-            if (i + 1 < NQ) d[(size_t)(i + 1) * stride] = Codec<S>::from_f_sr(h[i + 1], r >> 16);
+            e[i] = Codec<S>::from_f_sr(h[i], r);
+            if (i + 1 < NQ) e[i + 1] = Codec<S>::from_f_sr(h[i + 1], r >> 16);
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) d[(size_t)i * stride] = Codec<S>::from_f(h[i]);
+        for (int i = 0; i < NQ; ++i) e[i] = Codec<S>::from_f(h[i]);
     }
+}
+
+// Store them: population i goes to addr(i).
+template <typename S, int NQ, typename Addr>
+__device__ __forceinline__ void store_each(const float (&h)[NQ], uint32_t node, uint32_t key, Addr addr) {
+    S e[NQ];
+    encode_each<S, NQ>(h, node, key, e);
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) *addr(i) = e[i];
+}
+
+// Pull scheme: the node's own slots, population i in array i.
+template <typename S, int NQ = 19>
+__device__ __forceinline__ void store_node(S *d, int64_t stride, const float (&h)[NQ], uint32_t node, uint32_t key) {
+    store_each<S, NQ>(h, node, key, [&](int i) { return d + (size_t)i * stride; });
 }
 
 // Per-step key of the stochastic dither.
@@ -156,7 +186,10 @@ struct Geom {
 // pop[i] is the population array index and off[i] the node offset to read.
 // The same map, used to write instead of read, turns a post-streaming state
 // into the post-collision buffer a later pull reproduces it from.
-template <bool WALLS>
+// SWAP = true gives the same offsets with the opposite array index, (ibar,
+// x - e_i) or (i, x): the slots of the in-place (AA) pattern's odd step, which
+// reads population i there and writes post-collision population ibar there.
+template <bool WALLS, bool SWAP = false>
 __device__ __forceinline__ void pull_sources(const Geom &g, int x, int y, int z,
                                              uint32_t (&off)[kQ], int (&pop)[kQ]) {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -178,7 +211,7 @@ __device__ __forceinline__ void pull_sources(const Geom &g, int x, int y, int z,
     off[11] = rzm + xm; off[12] = rzm + xp; off[13] = rzp + xm; off[14] = rzp + xp;
     off[15] = rmm + x;  off[16] = rpm + x;  off[17] = rmp + x;  off[18] = rpp + x;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) pop[i] = i;
+    for (int i = 0; i < kQ; ++i) pop[i] = SWAP ? opposite(i) : i;
     if (WALLS) {
         const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
         const bool xl = wx && x == 0, xh = wx && x == nx - 1;  // ex = +1 / -1 bounce
@@ -190,6 +223,51 @@ __device__ __forceinline__ void pull_sources(const Geom &g, int x, int y, int z,
                              xl || yl, xh || yl, xl || yh, xh || yh,
                              xl || zl, xh || zl, xl || zh, xh || zh,
                              yl || zl, yh || zl, yl || zh, yh || zh};
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) {
+            if (bb[i]) { pop[i] = SWAP ? i : opposite(i); off[i] = self; }
+        }
+    }
+}
+
+// Targets of the 19 populations leaving node (x, y, z) under Eq. 8: (i, x + e_i)
+// with periodic wrap, or (ibar, x) when x + e_i lies beyond a wall face. The
+// adjoint gathers through this map; the in-place pattern's odd step writes
+// through it.
+template <bool WALLS>
+__device__ __forceinline__ void push_targets(const Geom &g, int x, int y, int z, uint32_t (&off)[kQ],
+                                             int (&pop)[kQ]) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    const uint32_t unx = (uint32_t)nx, uny = (uint32_t)ny;
+    const uint32_t rc = ((uint32_t)z * uny + y) * unx;
+    const uint32_t rym = ((uint32_t)z * uny + ym) * unx, ryp = ((uint32_t)z * uny + yp) * unx;
+    const uint32_t rzm = ((uint32_t)zm * uny + y) * unx, rzp = ((uint32_t)zp * uny + y) * unx;
+    const uint32_t rmm = ((uint32_t)zm * uny + ym) * unx, rpm = ((uint32_t)zm * uny + yp) * unx;
+    const uint32_t rmp = ((uint32_t)zp * uny + ym) * unx, rpp = ((uint32_t)zp * uny + yp) * unx;
+    const uint32_t self = rc + x;
+    // destination x + e_i
+    off[0] = self;
+    off[1] = rc + xp;   off[2] = rc + xm;
+    off[3] = ryp + x;   off[4] = rym + x;
+    off[5] = rzp + x;   off[6] = rzm + x;
+    off[7] = ryp + xp;  off[8] = ryp + xm;  off[9] = rym + xp;  off[10] = rym + xm;
+    off[11] = rzp + xp; off[12] = rzp + xm; off[13] = rzm + xp; off[14] = rzm + xm;
+    off[15] = rpp + x;  off[16] = rmp + x;  off[17] = rpm + x;  off[18] = rmm + x;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) pop[i] = i;
+    if (WALLS) {
+        const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
+        const bool xl = wx && x == 0, xh = wx && x == nx - 1;  // leaving through x- (ex = -1) / x+ (ex = +1)
+        const bool yl = wy && y == 0, yh = wy && y == ny - 1;
+        const bool zl = wz && z == 0, zh = wz && z == nz - 1;
+        const bool bb[kQ] = {false,
+                             xh, xl, yh, yl, zh, zl,
+                             xh || yh, xl || yh, xh || yl, xl || yl,
+                             xh || zh, xl || zh, xh || zl, xl || zl,
+                             yh || zh, yl || zh, yh || zl, yl || zl};
 #pragma unroll
         for (int i = 1; i < kQ; ++i) {
             if (bb[i]) { pop[i] = opposite(i); off[i] = self; }

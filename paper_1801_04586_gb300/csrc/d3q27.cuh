@@ -52,8 +52,10 @@ struct Rates27 {
 
 // Pull sources of the 27 populations arriving at (x, y, z), population index
 // by cube code: periodic wrap, or halfway bounce-back (the opposite population
-// at the node itself) when x - e lies beyond a wall face.
-template <bool WALLS>
+// at the node itself) when x - e lies beyond a wall face. SWAP = true gives
+// the opposite population index at the same offsets: the slots of the
+// in-place (AA) pattern's odd step (as pull_sources in d3q19.cuh).
+template <bool WALLS, bool SWAP = false>
 __device__ __forceinline__ void pull_sources27(const Geom &g, int x, int y, int z, uint32_t (&off)[3][3][3],
                                                int (&pop)[3][3][3]) {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -78,7 +80,7 @@ __device__ __forceinline__ void pull_sources27(const Geom &g, int x, int y, int 
                 const bool bb = WALLS && (bx[ix] || by[iy] || bz[iz]);
                 // opposite: swap codes 1 <-> 2 on every axis
                 const int ox = ix == 0 ? 0 : 3 - ix, oy = iy == 0 ? 0 : 3 - iy, oz = iz == 0 ? 0 : 3 - iz;
-                pop[ix][iy][iz] = bb ? q27_index(ox, oy, oz) : q27_index(ix, iy, iz);
+                pop[ix][iy][iz] = (bb != SWAP) ? q27_index(ox, oy, oz) : q27_index(ix, iy, iz);
                 off[ix][iy][iz] = bb ? self : row + xs[ix];
             }
         }

@@ -25,12 +25,28 @@ struct Launch {
     dim3 block, grid;  // grid of the one-node-per-thread kernels
     cudaStream_t stream;
     bool packed;       // launch_step: two nodes per thread (grid.x halved)
+    int map;           // state kernels: slots of the post-streaming state (0 A/B pull map,
+                       // 1 in-place pattern after even steps, 2 after odd steps)
 };
 
 // storage: 0 = f32, 1 = f16, 2 = bf16, 3 = f16 stochastic, 4 = bf16 stochastic
 // (CLBM_STORAGE_*). key: per-step dither key (stochastic formats).
 cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
                         const ForceArgs &F, int *flag, uint32_t key);
+// In-place (AA) pattern: one step on the single population array f; odd
+// selects the odd step kind (step.cu).
+cudaError_t launch_step_aa(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,
+                           uint32_t key, bool odd);
+// The comparison collision models (models.cuh): SRT-LBM and non-orthogonal
+// MRT, A/B and in-place forms (step_srt.cu, step_mrt.cu).
+cudaError_t launch_step_srt(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
+                            const ForceArgs &F, int *flag, uint32_t key);
+cudaError_t launch_step_mrt(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
+                            const ForceArgs &F, int *flag, uint32_t key);
+cudaError_t launch_step_aa_srt(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,
+                               uint32_t key, bool odd);
+cudaError_t launch_step_aa_mrt(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,
+                               uint32_t key, bool odd);
 cudaError_t launch_step_diag(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
                              const ForceArgs &F, int *flag, long long *partials, uint32_t key);
 cudaError_t launch_fixed_final4(const long long *partials, int nblocks, double *out, double add0,
@@ -62,6 +78,8 @@ cudaError_t launch_scatter27(int storage, const Launch &L, void *dst, const floa
 cudaError_t launch_gather27(int storage, const Launch &L, const void *src, float *f, int64_t n, int deviation);
 cudaError_t launch_macros27(int storage, const Launch &L, const void *src, const ForceArgs &F, float *rho, float *u,
                             int64_t n);
+cudaError_t launch_step27_aa(int storage, const Launch &L, void *f, const Rates27 &r, const ForceArgs &F, int *flag,
+                             uint32_t key, bool odd);
 cudaError_t launch_moments27(int storage, const Launch &L, const void *src, const ForceArgs &F, long long *partials,
                              int nblocks, double *out);
 

@@ -1,54 +1,17 @@
-// step.cu -- the fused pull stream-and-collide kernel (one launch per time step).
-//
-// Per node (x, y, z): gather the 19 post-collision populations of the previous
-// step from the neighbours x - e_i (Eq. 8; periodic wrap or halfway
-// bounce-back), collide them (Eqs. 5, 7, 9 with A3, A5, A6; see d3q19.cuh)
-// and store the 19 post-collision values at the node itself. Loads use the
-// read-only path so that the +-1 x-shifted reads of neighbouring threads share
-// L1 sectors; stores are coalesced and aligned. One thread per node, x
-// fastest, so each warp touches 19 contiguous 128-byte segments per direction.
-#include "kernels.cuh"
+// step.cu -- the cascaded collision's step kernels (Eqs. 5, 7, 9 with A3, A5,
+// A6; collision in d3q19.cuh, kernels in step_kernels.cuh), plus the form
+// with two nodes per thread on the FP32x2 instructions.
+#include "step_kernels.cuh"
 
 namespace clbm {
 
-template <int FM>
-__device__ __forceinline__ void force_at(const ForceArgs &F, const Geom &g, int z, uint32_t self, float &fx,
-                                         float &fy, float &fz) {
-    if (FM == kForceUniform) {
-        fx = F.fx; fy = F.fy; fz = F.fz;
-    } else if (FM == kForceProfileZ) {
-        fx = __ldg(F.profile + z);
-        fy = __ldg(F.profile + g.nz + z);
-        fz = __ldg(F.profile + 2 * g.nz + z);
-    } else {
-        fx = __ldg(F.field + self);
-        fy = __ldg(F.field + F.n + self);
-        fz = __ldg(F.field + 2 * F.n + self);
+// The paper's cascaded collision with the consistent forcing scheme.
+struct Cascaded {
+    template <typename T>
+    static __device__ __forceinline__ T run(T (&h)[kQ], T Fx, T Fy, T Fz, const Rates &r) {
+        return collide(h, Fx, Fy, Fz, r);
     }
-    fx *= F.scale;
-    fy *= F.scale;
-    fz *= F.scale;
-}
-
-template <typename S, int FM, bool WALLS>
-__global__ void __launch_bounds__(512) k_step(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r,
-                                              ForceArgs F, int *__restrict__ flag, uint32_t key) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= g.nx || y >= g.ny) return;
-    uint32_t off[kQ];
-    int pop[kQ];
-    pull_sources<WALLS>(g, x, y, z, off, pop);
-    float h[kQ];
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
-    float fx, fy, fz;
-    force_at<FM>(F, g, z, off[0], fx, fy, fz);
-    const float drho = collide(h, fx, fy, fz, r);
-    if (!(fabsf(drho) < 0.9f)) *flag = 1;
-    store_node<S>(dst + off[0], g.stride, h, off[0], key);
-}
+};
 
 // Two nodes per thread: x and x + blockDim.x of a 2 * blockDim.x segment of a
 // row, collided together with the FP32x2 instructions (f2 in d3q19.cuh), which
@@ -90,41 +53,40 @@ __global__ void __launch_bounds__(256) k_step2(const S *__restrict__ src, S *__r
 }
 
 template <typename S, int FM>
-static cudaError_t step_walls(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
-                              int *flag, uint32_t key) {
-    if (L.packed) {
-        if (L.g.walls)
-            k_step2<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
-        else
-            k_step2<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
-    } else {
-        if (L.g.walls)
-            k_step<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
-        else
-            k_step<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
-    }
+static cudaError_t step2_walls(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
+                               int *flag, uint32_t key) {
+    if (L.g.walls)
+        k_step2<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
+    else
+        k_step2<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
     return cudaGetLastError();
 }
 
 template <typename S>
-static cudaError_t step_force(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
-                              int *flag, uint32_t key) {
+static cudaError_t step2_force(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
+                               int *flag, uint32_t key) {
     switch (F.mode) {
-        case kForceUniform: return step_walls<S, kForceUniform>(L, src, dst, r, F, flag, key);
-        case kForceProfileZ: return step_walls<S, kForceProfileZ>(L, src, dst, r, F, flag, key);
-        default: return step_walls<S, kForceField>(L, src, dst, r, F, flag, key);
+        case kForceUniform: return step2_walls<S, kForceUniform>(L, src, dst, r, F, flag, key);
+        case kForceProfileZ: return step2_walls<S, kForceProfileZ>(L, src, dst, r, F, flag, key);
+        default: return step2_walls<S, kForceField>(L, src, dst, r, F, flag, key);
     }
 }
 
 cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
                         const ForceArgs &F, int *flag, uint32_t key) {
+    if (!L.packed) return launch_step_with<Cascaded>(storage, L, src, dst, r, F, flag, key);
     switch (storage) {
-        case 0: return step_force<float>(L, src, dst, r, F, flag, key);
-        case 1: return step_force<__half>(L, src, dst, r, F, flag, key);
-        case 2: return step_force<__nv_bfloat16>(L, src, dst, r, F, flag, key);
-        case 3: return step_force<HalfSR>(L, src, dst, r, F, flag, key);
-        default: return step_force<BF16SR>(L, src, dst, r, F, flag, key);
+        case 0: return step2_force<float>(L, src, dst, r, F, flag, key);
+        case 1: return step2_force<__half>(L, src, dst, r, F, flag, key);
+        case 2: return step2_force<__nv_bfloat16>(L, src, dst, r, F, flag, key);
+        case 3: return step2_force<HalfSR>(L, src, dst, r, F, flag, key);
+        default: return step2_force<BF16SR>(L, src, dst, r, F, flag, key);
     }
+}
+
+cudaError_t launch_step_aa(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,
+                           uint32_t key, bool odd) {
+    return launch_step_aa_with<Cascaded>(storage, L, f, r, F, flag, key, odd);
 }
 
 }  // namespace clbm

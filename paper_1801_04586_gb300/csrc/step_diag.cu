@@ -2,10 +2,12 @@
 // jobs that read mass and momentum back after every step.
 //
 // Same per-node work as k_step (pull, collide, store). In addition every
-// block sums the Eq. 9 density deviation and momentum of the state it pulls
+// warp sums the Eq. 9 density deviation and momentum of the state it pulls
 // (the state before the step) as exact fixed-point integers (block_reduce.cuh),
-// so the totals equal clbm_reduce_moments' bit for bit. Block partials are
-// added by a two-level integer reduction; only the final totals become FP64.
+// so the totals equal clbm_reduce_moments' bit for bit. Lane 0 of each warp
+// writes its 4 sums (32 bytes per 32 nodes): no block barrier holds the
+// warps of a block together. The warp partials are added by a two-level
+// integer reduction; only the final totals become FP64.
 #include "block_reduce.cuh"
 #include "kernels.cuh"
 
@@ -34,7 +36,7 @@ __global__ void __launch_bounds__(512) k_step_diag(const S *__restrict__ src, S 
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     long long q[4] = {0ll, 0ll, 0ll, 0ll};
-    if (x < g.nx && y < g.ny) {
+    if (x < g.nx && y < g.ny) {  // no early return: every lane joins the warp sums
         uint32_t off[kQ];
         int pop[kQ];
         pull_sources<WALLS>(g, x, y, z, off, pop);
@@ -49,8 +51,18 @@ __global__ void __launch_bounds__(512) k_step_diag(const S *__restrict__ src, S 
         store_node<S>(dst + off[0], g.stride, h, off[0], key);
         q[0] = to_fixed(drho); q[1] = to_fixed(j.x); q[2] = to_fixed(j.y); q[3] = to_fixed(j.z);
     }
+    // blockDim.x is a multiple of 32, so a warp is 32 threads of one row
     const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    block_sum_fixed<4>(q, partials + 4 * b);
+    const unsigned wpb = (blockDim.x * blockDim.y) >> 5;
+    const unsigned w = (threadIdx.x + blockDim.x * threadIdx.y) >> 5;
+    long long s[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s[k] = warp_sum_fixed(q[k]);
+    if ((threadIdx.x & 31) == 0) {
+        long long *d = partials + 4 * (b * wpb + w);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = s[k];
+    }
 }
 
 template <typename S, int FM>

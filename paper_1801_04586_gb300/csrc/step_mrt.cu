@@ -1,0 +1,25 @@
+// step_mrt.cu -- step kernels of the non-orthogonal MRT comparison model
+// (models.cuh, Appendix B) on the layout, streaming and storage formats of
+// the cascaded step.
+#include "models.cuh"
+#include "step_kernels.cuh"
+
+namespace clbm {
+
+struct Mrt {
+    static __device__ __forceinline__ float run(float (&h)[kQ], float Fx, float Fy, float Fz, const Rates &r) {
+        return collide_mrt(h, Fx, Fy, Fz, r);
+    }
+};
+
+cudaError_t launch_step_mrt(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
+                            const ForceArgs &F, int *flag, uint32_t key) {
+    return launch_step_with<Mrt>(storage, L, src, dst, r, F, flag, key);
+}
+
+cudaError_t launch_step_aa_mrt(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,
+                               uint32_t key, bool odd) {
+    return launch_step_aa_with<Mrt>(storage, L, f, r, F, flag, key, odd);
+}
+
+}  // namespace clbm

@@ -29,13 +29,17 @@ class Lattice:
     fourth-order rates (Eq. A3 / Eq. 13), s3b, s4b, s5, s6 the further D3Q27
     rates; walls is a CLBM_WALL_* bit mask (x=1, y=2, z=4; other axes
     periodic); storage is 'f32', 'f16', 'bf16', 'f16sr' or 'bf16sr'
-    (populations stored as deviations f - w_i).
+    (populations stored as deviations f - w_i); pattern is 'ab' (two
+    buffers, pull) or 'aa' (one buffer updated in place); model is
+    'cascaded' (the paper's collision), or one of the comparison models
+    'srt' (SRT-LBM at s2) and 'mrt' (non-orthogonal MRT of Appendix B).
     """
 
     def __init__(self, nx: int, ny: int, nz: int, nu: float, walls: int = 0, s2b: float = 1.0,
                  s3: float = 1.0, s4: float = 1.0, storage: str = "f32", block: Tuple[int, int] = (0, 0),
                  device=None, stream: Optional[torch.cuda.Stream] = None, variant: int = 0, lattice: int = 19,
-                 s3b: float = 1.0, s4b: float = 1.0, s5: float = 1.0, s6: float = 1.0):
+                 s3b: float = 1.0, s4b: float = 1.0, s5: float = 1.0, s6: float = 1.0, pattern: str = "ab",
+                 model: str = "cascaded"):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required: the lattice runs only in libclbm.so's kernels")
         self.lib = _capi.lib()
@@ -46,12 +50,15 @@ class Lattice:
         self.n = self.nx * self.ny * self.nz
         self.walls = int(walls)
         self.storage = storage
+        self.pattern = pattern
+        self.model = model
         self.q = 27 if int(lattice) == 27 else 19
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             p = _capi.Params(self.nx, self.ny, self.nz, self.walls, float(nu), float(s2b), float(s3), float(s4),
-                             _capi.STORAGE[storage], int(block[0]), int(block[1]), int(variant), int(lattice), 0,
-                             float(s3b), float(s4b), float(s5), float(s6))
+                             _capi.STORAGE[storage], int(block[0]), int(block[1]), int(variant), int(lattice),
+                             _capi.PATTERN[pattern],
+                             float(s3b), float(s4b), float(s5), float(s6), _capi.MODEL[model], 0)
             h = ctypes.c_void_p()
             check(self.lib.clbm_create(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
                   "clbm_create")

@@ -48,7 +48,8 @@ def test_binding_covers_header():
 def _params(**kw):
     from paper_1801_04586_gb300 import _capi
     base = dict(nx=8, ny=8, nz=8, walls=0, nu=0.1, s2b=1.0, s3=1.0, s4=1.0, storage=0, block_x=0, block_y=0,
-                variant=0, lattice=0, reserved=0, s3b=0.0, s4b=0.0, s5=0.0, s6=0.0)
+                variant=0, lattice=0, pattern=0, s3b=0.0, s4b=0.0, s5=0.0, s6=0.0, model=0,
+                reserved=0)
     base.update(kw)
     return _capi.Params(**base)
 
@@ -58,7 +59,9 @@ def _params(**kw):
                                 dict(storage=5), dict(block_x=48), dict(block_x=1024, block_y=1),
                                 dict(nx=2048, ny=2048, nz=1024), dict(variant=3),
                                 dict(lattice=21), dict(lattice=27, s5=2.5), dict(lattice=27, variant=2),
-                                dict(lattice=27, block_x=512, block_y=1)])
+                                dict(lattice=27, block_x=512, block_y=1), dict(pattern=2),
+                                dict(pattern=-1), dict(pattern=1, variant=2), dict(model=3), dict(model=-1),
+                                dict(reserved=1), dict(model=1, lattice=27), dict(model=2, variant=2)])
 def test_create_rejects_bad_parameters(lib, kw):
     from paper_1801_04586_gb300 import _capi
     h = ctypes.c_void_p()
