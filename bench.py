@@ -484,6 +484,8 @@ def run_gb300(args):
             "srt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, model="srt"),
             "mrt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, model="mrt"),
             "d3q27_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, lattice=27),
+            "d3q27_srt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, lattice=27, model="srt"),
+            "d3q27_mrt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, lattice=27, model="mrt"),
             "d3q27_aa_in_place_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, lattice=27,
                                                    pattern="aa"),
             "adjoint_kernel_256": bench_adjoint(dev, side, max(10, min(K, 100)), peak),

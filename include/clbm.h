@@ -78,14 +78,15 @@ extern "C" {
  * the consistent forcing scheme (Eqs. A5-A6 / 15-16). */
 #define CLBM_MODEL_CASCADED 0
 /* Comparison models the paper measures against, on the same layout,
- * streaming and storage formats (D3Q19 only; not in batches, not for the
- * adjoint entry points):
+ * streaming and storage formats, for both lattices (one node per thread;
+ * not in batches, not for the adjoint entry points):
  * SRT-LBM (Sec. III.A): one rate s2 (from nu), the second-order discrete
  * equilibrium written out in Sec. II.B and Guo's forcing term. */
 #define CLBM_MODEL_SRT      1
-/* Non-orthogonal MRT-LBM (Appendix B): the raw moments of Eq. A4 relaxed
- * with the S of Eq. A3 (nu, s2b, s3, s4) towards M f_D, with the forcing
- * moments M R_G of Guo's term. */
+/* Non-orthogonal MRT-LBM (Appendix B): the raw moments of Eq. A4 (Eq. 14 for
+ * D3Q27) relaxed with the S of Eq. A3 (Eq. 13: nu, s2b, s3, s4 and for D3Q27
+ * s3b, s4b, s5, s6) towards M f_D, with the forcing moments M R_G of Guo's
+ * term. */
 #define CLBM_MODEL_MRT      2
 
 /* ---- wall axes: both faces of the axis are halfway bounce-back walls ---- */

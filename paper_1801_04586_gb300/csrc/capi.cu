@@ -31,7 +31,6 @@ int cuda_fail(cudaError_t e, const char *where) {
 size_t elem_size(int storage) { return storage == CLBM_STORAGE_F32 ? 4 : 2; }
 
 constexpr int kReduceBlocks = 4 * 152;  // fixed reduction grid: deterministic sums
-constexpr int kMidBlocks = 152;         // first pass over the step kernel's block sums
 
 struct StateHeader {
     char magic[8];
@@ -56,11 +55,9 @@ struct clbm_ctx {
     ForceArgs force;
     int *d_flag;
     double *d_partials;
-    float *d_io;          // clbm_run_host scratch (first use): 4 x N floats, then
-    double *d_mom;        //   4 doubles of sums and
-    long long *d_mid;     //   4 fixed-point sums per first-pass block and
-    long long *d_diag;    //   4 fixed-point sums per warp of the fused step kernel
-    int64_t diag_blocks;  // warp partial sets d_diag holds
+    float *d_io;               // clbm_run_host scratch (first use): 4 x N floats, then
+    double *d_mom;             //   4 doubles of sums and
+    unsigned long long *d_acc; //   kDiagSlots x 4 fixed-point accumulators (kept zero between steps)
     int64_t steps_done;
     double gamma;         // force decay rate (clbm_set_force_decay)
     bool packed;          // step kernel with two nodes per thread (FP32x2 arithmetic)
@@ -121,6 +118,23 @@ cudaError_t step19(const clbm_ctx *c, const Launch &L, const void *src, void *ds
     }
 }
 
+cudaError_t step27(const clbm_ctx *c, const Launch &L, const void *src, void *dst, const ForceArgs &F,
+                   uint32_t key) {
+    switch (c->model) {
+        case CLBM_MODEL_SRT: return launch_step27_srt(c->p.storage, L, src, dst, c->rates27, F, c->d_flag, key);
+        case CLBM_MODEL_MRT: return launch_step27_mrt(c->p.storage, L, src, dst, c->rates27, F, c->d_flag, key);
+        default: return launch_step27(c->p.storage, L, src, dst, c->rates27, F, c->d_flag, key);
+    }
+}
+
+cudaError_t step27_aa(const clbm_ctx *c, const Launch &L, void *f, const ForceArgs &F, uint32_t key, bool odd) {
+    switch (c->model) {
+        case CLBM_MODEL_SRT: return launch_step27_aa_srt(c->p.storage, L, f, c->rates27, F, c->d_flag, key, odd);
+        case CLBM_MODEL_MRT: return launch_step27_aa_mrt(c->p.storage, L, f, c->rates27, F, c->d_flag, key, odd);
+        default: return launch_step27_aa(c->p.storage, L, f, c->rates27, F, c->d_flag, key, odd);
+    }
+}
+
 cudaError_t step19_aa(const clbm_ctx *c, const Launch &L, void *f, const ForceArgs &F, uint32_t key, bool odd) {
     switch (c->model) {
         case CLBM_MODEL_SRT: return launch_step_aa_srt(c->p.storage, L, f, c->rates, F, c->d_flag, key, odd);
@@ -177,8 +191,8 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
         return fail(CLBM_ERR_ARG, "clbm_create: the in-place pattern runs one node per thread (variant 0 or 1)");
     if (p->model < CLBM_MODEL_CASCADED || p->model > CLBM_MODEL_MRT || p->reserved != 0)
         return fail(CLBM_ERR_ARG, "clbm_create: model must be CLBM_MODEL_CASCADED, _SRT or _MRT (reserved 0)");
-    if (p->model != CLBM_MODEL_CASCADED && (q != 19 || p->variant == 2))
-        return fail(CLBM_ERR_ARG, "clbm_create: the SRT and MRT models are D3Q19, one node per thread");
+    if (p->model != CLBM_MODEL_CASCADED && p->variant == 2)
+        return fail(CLBM_ERR_ARG, "clbm_create: the SRT and MRT models run one node per thread");
     int bx = p->block_x, by = p->block_y;
     if (bx == 0) bx = p->nx >= 128 ? 128 : ((p->nx + 31) / 32) * 32;
     if (by == 0) by = std::max(1, std::min(p->ny, 256 / bx));
@@ -330,17 +344,14 @@ int clbm_step(clbm_ctx *c, int64_t nsteps) {
     const Launch L = step_launch_of(c);
     for (int64_t t = 0; t < nsteps && c->aa; ++t) {
         const bool odd = (c->steps_done & 1) != 0;
-        cudaError_t e = c->q == 27
-            ? launch_step27_aa(c->p.storage, L, c->buf[0], c->rates27, force_now(c), c->d_flag,
-                               step_key(c->steps_done), odd)
-            : step19_aa(c, L, c->buf[0], force_now(c), step_key(c->steps_done), odd);
+        cudaError_t e = c->q == 27 ? step27_aa(c, L, c->buf[0], force_now(c), step_key(c->steps_done), odd)
+                                   : step19_aa(c, L, c->buf[0], force_now(c), step_key(c->steps_done), odd);
         if (e != cudaSuccess) return cuda_fail(e, "clbm_step");
         ++c->steps_done;
     }
     for (int64_t t = 0; t < nsteps && !c->aa; ++t) {
         cudaError_t e = c->q == 27
-            ? launch_step27(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates27, force_now(c), c->d_flag,
-                            step_key(c->steps_done))
+            ? step27(c, L, c->buf[c->cur], c->buf[c->cur ^ 1], force_now(c), step_key(c->steps_done))
             : step19(c, L, c->buf[c->cur], c->buf[c->cur ^ 1], force_now(c), step_key(c->steps_done));
         if (e != cudaSuccess) return cuda_fail(e, "clbm_step");
         c->cur ^= 1;
@@ -546,26 +557,22 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     if (!c) return fail(CLBM_ERR_ARG, "clbm_run_host: null context");
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_run_host: nsteps < 0");
     const Launch L = launch_of(c);
-    // one fixed-point partial set per warp of the fused step kernel
-    const int64_t nparts = (int64_t)L.grid.x * L.grid.y * L.grid.z * ((L.block.x * L.block.y) / 32);
     cudaError_t e;
-    if (!c->d_io || c->diag_blocks < nparts) {
-        if (c->d_io) cudaFree(c->d_io);
-        const size_t bytes =
-            sizeof(float) * 4 * (size_t)c->n + 256 + sizeof(double) * (4 * (size_t)nparts + 4 + 4 * kMidBlocks);
+    if (!c->d_io) {
+        const size_t io = (sizeof(float) * 4 * (size_t)c->n + 255) / 256 * 256;
+        const size_t acc = sizeof(unsigned long long) * 4 * kDiagSlots;
+        const size_t bytes = io + 256 + acc;
         void *p = nullptr;
         if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) {
             c->d_io = nullptr;
-            c->diag_blocks = 0;
             cudaGetLastError();
             return fail(CLBM_ERR_OOM, "clbm_run_host: cudaMalloc failed");
         }
         c->d_io = (float *)p;
-        const size_t io = (sizeof(float) * 4 * (size_t)c->n + 255) / 256 * 256;
         c->d_mom = (double *)((char *)p + io);
-        c->d_mid = (long long *)(c->d_mom + 4);
-        c->d_diag = c->d_mid + 4 * kMidBlocks;
-        c->diag_blocks = nparts;
+        c->d_acc = (unsigned long long *)((char *)p + io + 256);
+        if ((e = cudaMemsetAsync(c->d_acc, 0, acc, c->stream)) != cudaSuccess)
+            return cuda_fail(e, "clbm_run_host: clear accumulators");
     }
     float *d_rho = c->d_io, *d_u = c->d_io + c->n;
     const size_t nb = sizeof(float) * (size_t)c->n;
@@ -585,13 +592,15 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         }
         if ((rc = clbm_step(c, 1)) != CLBM_OK) return rc;
     }
+    if (fused && moments_h && nsteps > 0 &&
+        (e = cudaMemsetAsync(c->d_acc, 0, sizeof(unsigned long long) * 4 * kDiagSlots, c->stream)) != cudaSuccess)
+        return cuda_fail(e, "clbm_run_host: clear accumulators");
     for (int64_t t = 0; t < nsteps && fused; ++t) {
         if (moments_h) {
-            // fused step: FP64 sums of the state it pulls (state t) into per-block partials
+            // fused step: exact sums of the state it pulls (state t) into the accumulators
             e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),
-                                 c->d_flag, c->d_diag, step_key(c->steps_done));
-            if (e == cudaSuccess)
-                e = launch_sum_partials4(c->d_diag, nparts, c->d_mid, kMidBlocks, c->d_mom, (double)c->n, c->stream);
+                                 c->d_flag, c->d_acc, step_key(c->steps_done));
+            if (e == cudaSuccess) e = launch_drain4(c->d_acc, c->d_mom, (double)c->n, c->stream);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                                     c->stream);

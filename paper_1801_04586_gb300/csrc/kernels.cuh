@@ -47,12 +47,15 @@ cudaError_t launch_step_aa_srt(int storage, const Launch &L, void *f, const Rate
                                uint32_t key, bool odd);
 cudaError_t launch_step_aa_mrt(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,
                                uint32_t key, bool odd);
+// Fused step + fixed-point conservation sums of the pulled state into the
+// kDiagSlots x 4 accumulators acc (zero on entry); launch_drain4 turns them
+// into 4 FP64 totals and clears them (step_diag.cu).
+constexpr int kDiagSlots = 1024;
 cudaError_t launch_step_diag(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
-                             const ForceArgs &F, int *flag, long long *partials, uint32_t key);
+                             const ForceArgs &F, int *flag, unsigned long long *acc, uint32_t key);
+cudaError_t launch_drain4(unsigned long long *acc, double *out, double add0, cudaStream_t stream);
 cudaError_t launch_fixed_final4(const long long *partials, int nblocks, double *out, double add0,
                                 cudaStream_t stream);
-cudaError_t launch_sum_partials4(const long long *partials, int64_t nblocks, long long *mid, int mid_blocks,
-                                 double *out, double add0, cudaStream_t stream);
 cudaError_t launch_scatter(int storage, const Launch &L, void *dst, const float *f, int64_t n, int deviation);
 cudaError_t launch_init_eq(int storage, const Launch &L, void *dst, const float *rho, const float *u, int64_t n,
                            const ForceArgs &F);
@@ -80,6 +83,15 @@ cudaError_t launch_macros27(int storage, const Launch &L, const void *src, const
                             int64_t n);
 cudaError_t launch_step27_aa(int storage, const Launch &L, void *f, const Rates27 &r, const ForceArgs &F, int *flag,
                              uint32_t key, bool odd);
+// The comparison models on D3Q27 (models27.cuh; step27_srt.cu, step27_mrt.cu).
+cudaError_t launch_step27_srt(int storage, const Launch &L, const void *src, void *dst, const Rates27 &r,
+                              const ForceArgs &F, int *flag, uint32_t key);
+cudaError_t launch_step27_mrt(int storage, const Launch &L, const void *src, void *dst, const Rates27 &r,
+                              const ForceArgs &F, int *flag, uint32_t key);
+cudaError_t launch_step27_aa_srt(int storage, const Launch &L, void *f, const Rates27 &r, const ForceArgs &F,
+                                 int *flag, uint32_t key, bool odd);
+cudaError_t launch_step27_aa_mrt(int storage, const Launch &L, void *f, const Rates27 &r, const ForceArgs &F,
+                                 int *flag, uint32_t key, bool odd);
 cudaError_t launch_moments27(int storage, const Launch &L, const void *src, const ForceArgs &F, long long *partials,
                              int nblocks, double *out);
 

@@ -1,49 +1,30 @@
-// step27.cu -- D3Q27 kernels: the fused pull stream-and-collide step
-// (collision in d3q27.cuh) and the state kernels around it (initial
-// equilibrium, import / export of post-streaming populations, Eq. 9 read-out,
-// fixed-point conservation sums). Same layout and conventions as the D3Q19
-// kernels: structure of arrays, 27 arrays of `stride` elements, deviations
-// from the rest weights in the storage format S.
+// step27.cu -- D3Q27 kernels: the cascaded collision's step kernels (collision
+// in d3q27.cuh, kernels in step27_kernels.cuh) and the state kernels around
+// them (initial equilibrium, import / export of post-streaming populations,
+// Eq. 9 read-out, fixed-point conservation sums). Same layout and conventions
+// as the D3Q19 kernels: structure of arrays, 27 arrays of `stride` elements,
+// deviations from the rest weights in the storage format S.
 #include "block_reduce.cuh"
-#include "d3q27.cuh"
-#include "kernels.cuh"
+#include "step27_kernels.cuh"
 
 namespace clbm {
 
-template <int FM>
-__device__ __forceinline__ void force27(const ForceArgs &F, const Geom &g, int z, uint32_t self, float &fx, float &fy,
-                                        float &fz) {
-    if (FM == kForceUniform) {
-        fx = F.fx; fy = F.fy; fz = F.fz;
-    } else if (FM == kForceProfileZ) {
-        fx = __ldg(F.profile + z); fy = __ldg(F.profile + g.nz + z); fz = __ldg(F.profile + 2 * g.nz + z);
-    } else {
-        fx = __ldg(F.field + self); fy = __ldg(F.field + F.n + self); fz = __ldg(F.field + 2 * F.n + self);
+// The paper's cascaded collision on D3Q27 (Sec. II).
+struct Cascaded27 {
+    static __device__ __forceinline__ float run(float (&h)[3][3][3], float Fx, float Fy, float Fz,
+                                                const Rates27 &r) {
+        return collide27(h, Fx, Fy, Fz, r);
     }
-    fx *= F.scale;
-    fy *= F.scale;
-    fz *= F.scale;
+};
+
+cudaError_t launch_step27(int storage, const Launch &L, const void *src, void *dst, const Rates27 &r,
+                          const ForceArgs &F, int *flag, uint32_t key) {
+    return launch_step27_with<Cascaded27>(storage, L, src, dst, r, F, flag, key);
 }
 
-__device__ __forceinline__ bool node27(const Geom &g, int &x, int &y, int &z) {
-    x = blockIdx.x * blockDim.x + threadIdx.x;
-    y = blockIdx.y * blockDim.y + threadIdx.y;
-    z = blockIdx.z;
-    return x < g.nx && y < g.ny;
-}
-
-template <typename S, bool WALLS>
-__device__ __forceinline__ uint32_t pull27(const S *src, const Geom &g, int x, int y, int z, float (&h)[3][3][3]) {
-    uint32_t off[3][3][3];
-    int pop[3][3][3];
-    pull_sources27<WALLS>(g, x, y, z, off, pop);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) h[a][b][c] = Codec<S>::load(src + (size_t)pop[a][b][c] * g.stride + off[a][b][c]);
-    return ((uint32_t)z * g.ny + y) * g.nx + x;
+cudaError_t launch_step27_aa(int storage, const Launch &L, void *f, const Rates27 &r, const ForceArgs &F, int *flag,
+                             uint32_t key, bool odd) {
+    return launch_step27_aa_with<Cascaded27>(storage, L, f, r, F, flag, key, odd);
 }
 
 // Slots of the post-streaming populations of (x, y, z) in a state buffer, by
@@ -81,141 +62,6 @@ __device__ __forceinline__ uint32_t state_load27(const S *src, const Geom &g, in
             for (int c = 0; c < 3; ++c)
                 h[a][b][c] = Codec<S>::load_plain(src + (size_t)pop[a][b][c] * g.stride + off[a][b][c]);
     return ((uint32_t)z * g.ny + y) * g.nx + x;
-}
-
-// cube (by velocity code) -> population order of Eq. 1
-__device__ __forceinline__ void flatten27(const float (&h)[3][3][3], float (&f)[kQ27]) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) f[q27_index(a, b, c)] = h[a][b][c];
-}
-
-template <typename S, int FM, bool WALLS>
-__global__ void __launch_bounds__(256, 4) k_step27(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates27 r,
-                                                ForceArgs F, int *__restrict__ flag, uint32_t key) {
-    int x, y, z;
-    if (!node27(g, x, y, z)) return;
-    float h[3][3][3];
-    const uint32_t self = pull27<S, WALLS>(src, g, x, y, z, h);
-    float fx, fy, fz;
-    force27<FM>(F, g, z, self, fx, fy, fz);
-    const float drho = collide27(h, fx, fy, fz, r);
-    if (!(fabsf(drho) < 0.9f)) *flag = 1;
-    float f[kQ27];
-    flatten27(h, f);
-    store_node<S, kQ27>(dst + self, g.stride, f, self, key);
-}
-
-// In-place (AA) pattern, as k_step_aa in step_kernels.cuh: the even kind
-// reads the node's natural slots and writes population (a,b,c) to the
-// opposite slot at the node; the odd kind reads the swapped pull slots and
-// writes population (a,b,c) to the slot the opposite direction was read from.
-// A node writes exactly the slots it read; a slot is read once, by the thread
-// that later overwrites it, so loads may take the read-only path. The odd
-// kind stages the 18 populations with e_x != 0 in shared memory so that the
-// thread whose own x is the destination stores them (aligned warp stores);
-// values whose destination leaves the block row, wraps around a periodic x
-// face or bounces back are stored directly.
-template <typename S, int FM, bool WALLS, bool ODD>
-__global__ void __launch_bounds__(256, 3) k_step27_aa(S *f, Geom g, Rates27 r, ForceArgs F, int *__restrict__ flag,
-                                                   uint32_t key) {
-    int x, y, z;
-    const bool active = node27(g, x, y, z);
-    if (!ODD && !active) return;
-    const uint32_t self = ((uint32_t)z * g.ny + y) * g.nx + x;
-    const int tx = threadIdx.x, bx = blockDim.x;
-    const int tid = tx + bx * threadIdx.y;
-    __shared__ S stage[ODD ? 18 : 1][ODD ? 256 : 1];
-    if (active) {
-        uint32_t off[3][3][3];
-        int pop[3][3][3];
-        if (ODD) {
-            pull_sources27<WALLS, true>(g, x, y, z, off, pop);
-        } else {
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = 0; b < 3; ++b)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) { off[a][b][c] = self; pop[a][b][c] = q27_index(a, b, c); }
-        }
-        float h[3][3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    h[a][b][c] = Codec<S>::load(f + (size_t)pop[a][b][c] * g.stride + off[a][b][c]);
-        float fx, fy, fz;
-        force27<FM>(F, g, z, self, fx, fy, fz);
-        const float drho = collide27(h, fx, fy, fz, r);
-        if (!(fabsf(drho) < 0.9f)) *flag = 1;
-        if (ODD) {
-            // recompute the slots from coordinates the compiler must treat as new,
-            // so that 27 offsets do not stay live through the collision
-            int xs = x, ys = y, zs = z;
-            asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs));
-            pull_sources27<WALLS, true>(g, xs, ys, zs, off, pop);
-        }
-        // destination of population q27_index(a,b,c): the slot read for the opposite code
-        float v[kQ27];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) v[q27_index(a, b, c)] = h[a][b][c];
-        S e[kQ27];
-        encode_each<S, kQ27>(v, self, key, e);
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int p = q27_index(a, b, c);
-                    const int oa = a ? 3 - a : 0, ob = b ? 3 - b : 0, oc = c ? 3 - c : 0;
-                    S *dst = f + (size_t)pop[oa][ob][oc] * g.stride + off[oa][ob][oc];
-                    if (!ODD || a == 0) {
-                        *dst = e[p];
-                    } else {
-                        const int ex = e_of(a);
-                        stage[ODD ? (a - 1) * 9 + b * 3 + c : 0][ODD ? tid : 0] = e[p];
-                        const bool handed = pop[oa][ob][oc] == p && x + ex >= 0 && x + ex < g.nx &&
-                                            tx + ex >= 0 && tx + ex < bx;
-                        if (!handed) *dst = e[p];
-                    }
-                }
-    }
-    if (ODD) {
-        __syncthreads();
-        if (active) {
-            const bool wy = WALLS && (g.walls & 2u), wz = WALLS && (g.walls & 4u);
-            const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
-            const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
-#pragma unroll
-            for (int a = 1; a < 3; ++a)
-#pragma unroll
-                for (int b = 0; b < 3; ++b)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const int ex = e_of(a), ey = e_of(b), ez = e_of(c);
-                        // the source x - e_x of this row sends population (a,b,c) to x
-                        const bool row_bb = (wy && ((ey == 1 && y == g.ny - 1) || (ey == -1 && y == 0))) ||
-                                            (wz && ((ez == 1 && z == g.nz - 1) || (ez == -1 && z == 0)));
-                        if (x - ex >= 0 && x - ex < g.nx && tx - ex >= 0 && tx - ex < bx && !row_bb) {
-                            const int yd = ey == 0 ? y : (ey > 0 ? yp : ym), zd = ez == 0 ? z : (ez > 0 ? zp : zm);
-                            const uint32_t dst = ((uint32_t)zd * g.ny + yd) * g.nx + x;
-                            f[(size_t)q27_index(a, b, c) * g.stride + dst] =
-                                stage[ODD ? (a - 1) * 9 + b * 3 + c : 0][ODD ? tid - ex : 0];
-                        }
-                    }
-        }
-    }
 }
 
 // Write a post-streaming state (cube by velocity code) where the next step finds it.
@@ -317,53 +163,6 @@ __global__ void k_moments27(const S *src, Geom g, int map, ForceArgs F, long lon
         q[0] += to_fixed(drho); q[1] += to_fixed(jx); q[2] += to_fixed(jy); q[3] += to_fixed(jz);
     }
     block_sum_fixed<4>(q, partials + (size_t)blockIdx.x * 4);
-}
-
-// ---- dispatch: storage x force mode x walls
-#define CLBM_Q27_STORE(storage, ...)                                                  \
-    switch (storage) {                                                                \
-        case 0: { using S = float; __VA_ARGS__; } break;                              \
-        case 1: { using S = __half; __VA_ARGS__; } break;                             \
-        case 2: { using S = __nv_bfloat16; __VA_ARGS__; } break;                      \
-        case 3: { using S = HalfSR; __VA_ARGS__; } break;                             \
-        default: { using S = BF16SR; __VA_ARGS__; } break;                            \
-    }
-// state kernels round to nearest: stochastic formats share the 16-bit bits
-#define CLBM_Q27_STATE(storage, ...)                                                  \
-    switch (storage) {                                                                \
-        case 0: { using S = float; __VA_ARGS__; } break;                              \
-        case 1: case 3: { using S = __half; __VA_ARGS__; } break;                     \
-        default: { using S = __nv_bfloat16; __VA_ARGS__; } break;                     \
-    }
-#define CLBM_Q27_FM(mode, ...)                                                        \
-    switch (mode) {                                                                   \
-        case kForceUniform: { constexpr int FM = kForceUniform; __VA_ARGS__; } break; \
-        case kForceProfileZ: { constexpr int FM = kForceProfileZ; __VA_ARGS__; } break; \
-        default: { constexpr int FM = kForceField; __VA_ARGS__; } break;              \
-    }
-
-cudaError_t launch_step27(int storage, const Launch &L, const void *src, void *dst, const Rates27 &r,
-                          const ForceArgs &F, int *flag, uint32_t key) {
-    CLBM_Q27_STORE(storage, CLBM_Q27_FM(F.mode, {
-        if (L.g.walls)
-            k_step27<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
-        else
-            k_step27<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
-    }))
-    return cudaGetLastError();
-}
-
-cudaError_t launch_step27_aa(int storage, const Launch &L, void *f, const Rates27 &r, const ForceArgs &F, int *flag,
-                             uint32_t key, bool odd) {
-    CLBM_Q27_STORE(storage, CLBM_Q27_FM(F.mode, {
-        if (!odd)
-            k_step27_aa<S, FM, false, false><<<L.grid, L.block, 0, L.stream>>>((S *)f, L.g, r, F, flag, key);
-        else if (L.g.walls)
-            k_step27_aa<S, FM, true, true><<<L.grid, L.block, 0, L.stream>>>((S *)f, L.g, r, F, flag, key);
-        else
-            k_step27_aa<S, FM, false, true><<<L.grid, L.block, 0, L.stream>>>((S *)f, L.g, r, F, flag, key);
-    }))
-    return cudaGetLastError();
 }
 
 cudaError_t launch_init27(int storage, const Launch &L, void *dst, const float *rho, const float *u, int64_t n,

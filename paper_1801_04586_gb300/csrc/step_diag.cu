@@ -5,9 +5,11 @@
 // warp sums the Eq. 9 density deviation and momentum of the state it pulls
 // (the state before the step) as exact fixed-point integers (block_reduce.cuh),
 // so the totals equal clbm_reduce_moments' bit for bit. Lane 0 of each warp
-// writes its 4 sums (32 bytes per 32 nodes): no block barrier holds the
-// warps of a block together. The warp partials are added by a two-level
-// integer reduction; only the final totals become FP64.
+// adds its 4 sums into one of kDiagSlots accumulator slots with 64-bit
+// integer atomics: integer addition is exact and order-independent, so the
+// totals do not depend on scheduling, and no block barrier holds the warps of
+// a block together. A one-block kernel then adds the slots, converts the
+// totals to FP64 and clears the slots for the next step.
 #include "block_reduce.cuh"
 #include "kernels.cuh"
 
@@ -31,7 +33,7 @@ __device__ __forceinline__ void force_diag(const ForceArgs &F, const Geom &g, in
 template <typename S, int FM, bool WALLS>
 __global__ void __launch_bounds__(512) k_step_diag(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r,
                                                    ForceArgs F, int *__restrict__ flag,
-                                                   long long *__restrict__ partials, uint32_t key) {
+                                                   unsigned long long *__restrict__ acc, uint32_t key) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -59,65 +61,66 @@ __global__ void __launch_bounds__(512) k_step_diag(const S *__restrict__ src, S 
 #pragma unroll
     for (int k = 0; k < 4; ++k) s[k] = warp_sum_fixed(q[k]);
     if ((threadIdx.x & 31) == 0) {
-        long long *d = partials + 4 * (b * wpb + w);
+        unsigned long long *d = acc + 4 * ((b * wpb + w) & (kDiagSlots - 1));
 #pragma unroll
-        for (int k = 0; k < 4; ++k) d[k] = s[k];
+        for (int k = 0; k < 4; ++k) atomicAdd(d + k, (unsigned long long)s[k]);  // two's complement: signed sum
     }
 }
 
 template <typename S, int FM>
 static cudaError_t diag_walls(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
-                              int *flag, long long *partials, uint32_t key) {
+                              int *flag, unsigned long long *acc, uint32_t key) {
     if (L.g.walls)
-        k_step_diag<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag,
-                                                                   partials, key);
+        k_step_diag<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, acc,
+                                                                   key);
     else
-        k_step_diag<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag,
-                                                                    partials, key);
+        k_step_diag<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, acc,
+                                                                    key);
     return cudaGetLastError();
 }
 
 template <typename S>
 static cudaError_t diag_force(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
-                              int *flag, long long *partials, uint32_t key) {
+                              int *flag, unsigned long long *acc, uint32_t key) {
     switch (F.mode) {
-        case kForceUniform: return diag_walls<S, kForceUniform>(L, src, dst, r, F, flag, partials, key);
-        case kForceProfileZ: return diag_walls<S, kForceProfileZ>(L, src, dst, r, F, flag, partials, key);
-        default: return diag_walls<S, kForceField>(L, src, dst, r, F, flag, partials, key);
+        case kForceUniform: return diag_walls<S, kForceUniform>(L, src, dst, r, F, flag, acc, key);
+        case kForceProfileZ: return diag_walls<S, kForceProfileZ>(L, src, dst, r, F, flag, acc, key);
+        default: return diag_walls<S, kForceField>(L, src, dst, r, F, flag, acc, key);
     }
 }
 
 cudaError_t launch_step_diag(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
-                             const ForceArgs &F, int *flag, long long *partials, uint32_t key) {
+                             const ForceArgs &F, int *flag, unsigned long long *acc, uint32_t key) {
     switch (storage) {
-        case 0: return diag_force<float>(L, src, dst, r, F, flag, partials, key);
-        case 1: return diag_force<__half>(L, src, dst, r, F, flag, partials, key);
-        case 2: return diag_force<__nv_bfloat16>(L, src, dst, r, F, flag, partials, key);
-        case 3: return diag_force<HalfSR>(L, src, dst, r, F, flag, partials, key);
-        default: return diag_force<BF16SR>(L, src, dst, r, F, flag, partials, key);
+        case 0: return diag_force<float>(L, src, dst, r, F, flag, acc, key);
+        case 1: return diag_force<__half>(L, src, dst, r, F, flag, acc, key);
+        case 2: return diag_force<__nv_bfloat16>(L, src, dst, r, F, flag, acc, key);
+        case 3: return diag_force<HalfSR>(L, src, dst, r, F, flag, acc, key);
+        default: return diag_force<BF16SR>(L, src, dst, r, F, flag, acc, key);
     }
 }
 
-// Sum nblocks fixed-point partials of 4 values: each block of the first pass
-// adds a contiguous chunk, the second pass adds the chunk sums and writes the
-// FP64 totals (plus add0 on the first).
-__global__ void k_sum_partials4(const long long *__restrict__ partials, int64_t nblocks, int64_t chunk,
-                                long long *__restrict__ mid) {
+// Totals of the kDiagSlots accumulator slots as FP64 (plus add0 on the
+// first), then the slots are cleared for the next step. One block.
+__global__ void k_drain4(unsigned long long *acc, double *out, double add0) {
     long long q[4] = {0ll, 0ll, 0ll, 0ll};
-    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(nblocks, lo + chunk);
-    for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x)
+    for (int s = threadIdx.x; s < kDiagSlots; s += blockDim.x)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) q[k] += partials[4 * b + k];
-    block_sum_fixed<4>(q, mid + 4 * (size_t)blockIdx.x);
+        for (int k = 0; k < 4; ++k) {
+            q[k] += (long long)acc[4 * s + k];
+            acc[4 * s + k] = 0ull;
+        }
+    __shared__ long long tot[4];
+    block_sum_fixed<4>(q, tot);
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = (double)tot[k] * kFixUnit + (k == 0 ? add0 : 0.0);
 }
 
-cudaError_t launch_sum_partials4(const long long *partials, int64_t nblocks, long long *mid, int mid_blocks,
-                                 double *out, double add0, cudaStream_t stream) {
-    const int64_t chunk = (nblocks + mid_blocks - 1) / mid_blocks;
-    k_sum_partials4<<<mid_blocks, 256, 0, stream>>>(partials, nblocks, chunk, mid);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_fixed_final4(mid, mid_blocks, out, add0, stream);
+cudaError_t launch_drain4(unsigned long long *acc, double *out, double add0, cudaStream_t stream) {
+    k_drain4<<<1, 1024, 0, stream>>>(acc, out, add0);
+    return cudaGetLastError();
 }
 
 }  // namespace clbm

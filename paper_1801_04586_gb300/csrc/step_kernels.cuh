@@ -74,21 +74,33 @@ __global__ void __launch_bounds__(512) k_step(const S *__restrict__ src, S *__re
 // touches them, so the update is race-free in place. Loads may take the
 // read-only path: a slot is read once, by the thread that later overwrites
 // it, and never after a write within the launch.
-// The k-th population with e_x != 0 (Eq. A1 order: 1, 2, 7..14): the stores
-// of the odd AA step that land one node to the side.
-__host__ __device__ constexpr int shift19(int k) { return k < 2 ? k + 1 : k + 5; }
-
 template <typename C, typename S, int FM, bool WALLS, bool ODD>
 __global__ void __launch_bounds__(512) k_step_aa(S *f, Geom g, Rates r, ForceArgs F, int *__restrict__ flag,
                                                  uint32_t key) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    const bool active = x < g.nx && y < g.ny;
+    if (x >= g.nx || y >= g.ny) return;
     const uint32_t self = ((uint32_t)z * g.ny + y) * g.nx + x;
     float h[kQ];
-    if constexpr (!ODD) {
-        if (!active) return;
+    if (ODD) {
+        uint32_t off[kQ];
+        int pop[kQ];
+        pull_sources<WALLS, true>(g, x, y, z, off, pop);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(f + (size_t)pop[i] * g.stride + off[i]);
+        float fx, fy, fz;
+        force_at<FM>(F, g, z, self, fx, fy, fz);
+        const float drho = C::run(h, fx, fy, fz, r);
+        if (!(fabsf(drho) < 0.9f)) *flag = 1;
+        // The slots read for the opposite directions are the push targets of
+        // Eq. 8. They are recomputed from coordinates the compiler must treat
+        // as new, so that 19 offsets do not stay live through the collision.
+        int xs = x, ys = y, zs = z;
+        asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs));
+        push_targets<WALLS>(g, xs, ys, zs, off, pop);
+        store_each<S, kQ>(h, self, key, [&](int i) { return f + (size_t)pop[i] * g.stride + off[i]; });
+    } else {
 #pragma unroll
         for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(f + (size_t)i * g.stride + self);
         float fx, fy, fz;
@@ -96,63 +108,6 @@ __global__ void __launch_bounds__(512) k_step_aa(S *f, Geom g, Rates r, ForceArg
         const float drho = C::run(h, fx, fy, fz, r);
         if (!(fabsf(drho) < 0.9f)) *flag = 1;
         store_each<S, kQ>(h, self, key, [&](int i) { return f + (size_t)opposite(i) * g.stride + self; });
-    } else {
-        // A store to x + e_i with e_x = +-1 straddles two 128-byte lines per
-        // warp. Those values are staged in shared memory and stored by the
-        // thread whose own x is the destination, so each warp writes aligned
-        // lines; values whose destination lies outside the block row, wraps
-        // around a periodic face or bounces back are stored directly.
-        __shared__ S stage[10][512];
-        const int tx = threadIdx.x, bx = blockDim.x;
-        const int tid = tx + bx * threadIdx.y;
-        if (active) {
-            uint32_t off[kQ];
-            int pop[kQ];
-            pull_sources<WALLS, true>(g, x, y, z, off, pop);
-#pragma unroll
-            for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(f + (size_t)pop[i] * g.stride + off[i]);
-            float fx, fy, fz;
-            force_at<FM>(F, g, z, self, fx, fy, fz);
-            const float drho = C::run(h, fx, fy, fz, r);
-            if (!(fabsf(drho) < 0.9f)) *flag = 1;
-            S e[kQ];
-            encode_each<S, kQ>(h, self, key, e);
-            // The slots read for the opposite directions are the push targets of
-            // Eq. 8. They are recomputed from coordinates the compiler must treat
-            // as new, so that 19 offsets do not stay live through the collision.
-            int xs = x, ys = y, zs = z;
-            asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs));
-            push_targets<WALLS>(g, xs, ys, zs, off, pop);
-#pragma unroll
-            for (int i = 0; i < kQ; ++i)
-                if (ex19(i) == 0) f[(size_t)pop[i] * g.stride + off[i]] = e[i];
-#pragma unroll
-            for (int k = 0; k < 10; ++k) {
-                const int i = shift19(k), ex = ex19(i);
-                stage[k][tid] = e[i];
-                const bool handed = pop[i] == i && x + ex >= 0 && x + ex < g.nx && tx + ex >= 0 && tx + ex < bx;
-                if (!handed) f[(size_t)pop[i] * g.stride + off[i]] = e[i];
-            }
-        }
-        __syncthreads();
-        if (active) {
-            const bool wy = WALLS && (g.walls & 2u), wz = WALLS && (g.walls & 4u);
-            const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
-            const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
-#pragma unroll
-            for (int k = 0; k < 10; ++k) {
-                const int i = shift19(k), ex = ex19(i), ey = ey19(i), ez = ez19(i);
-                // the source x - e_x of this row sends population i to x
-                const bool row_bb = (wy && ((ey == 1 && y == g.ny - 1) || (ey == -1 && y == 0))) ||
-                                    (wz && ((ez == 1 && z == g.nz - 1) || (ez == -1 && z == 0)));
-                const bool from = x - ex >= 0 && x - ex < g.nx && tx - ex >= 0 && tx - ex < bx && !row_bb;
-                if (from) {
-                    const int yd = ey == 0 ? y : (ey > 0 ? yp : ym), zd = ez == 0 ? z : (ez > 0 ? zp : zm);
-                    const uint32_t dst = ((uint32_t)zd * g.ny + yd) * g.nx + x;
-                    f[(size_t)i * g.stride + dst] = stage[k][tid - ex];
-                }
-            }
-        }
     }
 }
 

@@ -114,60 +114,3 @@ def test_aa_sequence_reproduces_pull_streaming(q, n, walls):
             got = np.array([buf[sl] for sl in rmap[c]])
             np.testing.assert_allclose(got, pull_states[s][c], rtol=0, atol=1e-12)
 
-
-def staged_odd_stores(q, n, walls, bx, by, E, opp):
-    """The odd step's store rule of the GPU kernels, restated: a value whose
-    destination is x + e_i with e_x != 0 is written by the thread at the
-    destination x (same block row) from shared memory, unless the
-    destination bounces back, wraps around a periodic x face or lies outside
-    the block row; then the sending thread writes it. Returns a list of
-    (writer node, slot, (source node, direction))."""
-    nx, ny, nz = n
-    wy, wz = bool(walls & 2), bool(walls & 4)
-    out = []
-    for z in range(nz):
-        for y in range(ny):
-            for x in range(nx):
-                tx = x % bx
-                for i in range(q):
-                    ex, ey, ez = E[i]
-                    c = (x, y, z)
-                    bb = beyond(c, -E[i], n, walls)
-                    target = (opp[i], c) if bb else (i, wrap(np.add(c, E[i]), n))
-                    if ex == 0:
-                        out.append((c, target, (c, i)))
-                        continue
-                    handed = (not bb) and 0 <= x + ex < nx and 0 <= tx + ex < bx
-                    if not handed:
-                        out.append((c, target, (c, i)))
-                # receiver side: this thread writes (i, dest row, x) for each shifted i
-                for i in range(q):
-                    ex, ey, ez = E[i]
-                    if ex == 0:
-                        continue
-                    row_bb = (wy and ((ey == 1 and y == ny - 1) or (ey == -1 and y == 0))) or \
-                             (wz and ((ez == 1 and z == nz - 1) or (ez == -1 and z == 0)))
-                    if 0 <= x - ex < nx and 0 <= tx - ex < bx and not row_bb:
-                        yd, zd = (y + ey) % ny, (z + ez) % nz
-                        out.append(((x, y, z), (i, (x, yd, zd)), ((x - ex, y, z), i)))
-    return out
-
-
-@pytest.mark.parametrize("q,n,walls,bx", [(19, (7, 4, 3), 0, 4), (19, (9, 3, 4), 7, 4), (19, (5, 4, 3), 6, 8),
-                                          (19, (12, 2, 2), 1, 4), (19, (1, 3, 4), 4, 4), (27, (7, 3, 3), 7, 4),
-                                          (27, (6, 4, 2), 0, 4), (27, (9, 2, 3), 3, 8)])
-def test_staged_odd_stores_write_each_value_once_to_its_slot(q, n, walls, bx):
-    E = velocity_set(q)
-    opp = opposite(E)
-    stores = staged_odd_stores(q, n, walls, bx, 1, E, opp)
-    written = {}
-    for writer, slot, val in stores:
-        assert slot not in written, f"slot {slot} written twice"
-        written[slot] = val
-    total = q * int(np.prod(n))
-    assert len(written) == total
-    # every value lands where the odd step's write map sends it
-    _, writes = slots(q, n, walls, True, E, opp)
-    for c in writes:
-        for i, sl in enumerate(writes[c]):
-            assert written[sl] == (c, i)

@@ -61,7 +61,7 @@ def _params(**kw):
                                 dict(lattice=21), dict(lattice=27, s5=2.5), dict(lattice=27, variant=2),
                                 dict(lattice=27, block_x=512, block_y=1), dict(pattern=2),
                                 dict(pattern=-1), dict(pattern=1, variant=2), dict(model=3), dict(model=-1),
-                                dict(reserved=1), dict(model=1, lattice=27), dict(model=2, variant=2)])
+                                dict(reserved=1), dict(model=2, variant=2)])
 def test_create_rejects_bad_parameters(lib, kw):
     from paper_1801_04586_gb300 import _capi
     h = ctypes.c_void_p()
