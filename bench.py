@@ -37,6 +37,7 @@ NU = 0.01
 F0 = 1e-5
 UMAX = 0.02
 BYTES_PER_NODE = 152  # 19 x 4 B read + 19 x 4 B written (FP32 A/B)
+NOMINAL_HBM_GBS = 7900.0  # HBM3e nominal, context beside the measured copy peak
 WORKLOAD = "periodic 256^3 Kolmogorov box, F_x = 1e-5 sin(2 pi z/256), nu = 0.01, FP32 populations"
 
 
@@ -177,9 +178,18 @@ def cpu_oracle_rate(seconds: float = 10.0, max_steps: int = 20):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": lat.n * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # one thread on a thinner slab (the thread count is set last: it stays set)
+    lat1 = oracle.Lattice.from_nu(N_SIDE, N_SIDE, 2, NU)
+    F1, f1 = np.ascontiguousarray(F[:, :2]), np.ascontiguousarray(f[:, :2])
+    t1 = time.perf_counter()
+    oracle.step(lat1, f1, F1, 2, nthreads=1)
+    dt1 = time.perf_counter() - t1
+    return {"value": lat.n * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"{steps} steps of a 256x256x16 periodic slab of the workload ({lat.n} nodes), "
-                      f"FP64, OpenMP over rows, {dt:.1f} s"}
+                      f"FP64, OpenMP over rows, {dt:.1f} s",
+            "value_1_thread": lat1.n * 2 / dt1 / 1e6,
+            "sample_1_thread": f"2 steps of a 256x256x2 slab ({lat1.n} nodes), one thread, {dt1:.1f} s"}
 
 
 def run_reference(args):
@@ -222,7 +232,7 @@ def _events():
 
 
 def bench_storage(storage, K, warmup, dev, side, prof, u0, peak, variant=0, lattice=19, pattern="ab",
-                  model="cascaded"):
+                  model="cascaded", walls=0):
     """The same workload in another storage format, step-kernel form, lattice
     (D3Q27 of Sec. II), storage pattern (in-place AA) or collision model (the
     SRT and non-orthogonal MRT comparison models)."""
@@ -230,7 +240,7 @@ def bench_storage(storage, K, warmup, dev, side, prof, u0, peak, variant=0, latt
 
     from paper_1801_04586_gb300 import Lattice
     lat = Lattice(side, side, side, NU, storage=storage, device=dev, variant=variant, lattice=lattice,
-                  pattern=pattern, model=model)
+                  pattern=pattern, model=model, walls=walls)
     info = lat.info()
     lat.set_force_profile_z(prof)
     lat.init_equilibrium(None, u0)
@@ -481,6 +491,7 @@ def run_gb300(args):
             "bf16_stochastic_storage": bench_storage("bf16sr", K, args.warmup, dev, side, prof, u0, peak),
             "aa_in_place_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, pattern="aa"),
             "aa_in_place_f16": bench_storage("f16", K, args.warmup, dev, side, prof, u0, peak, pattern="aa"),
+            "walls_yz_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, walls=6),
             "srt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, model="srt"),
             "mrt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, model="mrt"),
             "d3q27_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, lattice=27),
@@ -514,8 +525,9 @@ def run_gb300(args):
                        "parallelism": f"{ws} independent replica(s), one per GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                          "algorithmic_bytes_per_launch": bytes_per_node * nodes,
-                         "kernel": "k_step<float,1,false>" if default_case
+                         "kernel": "k_step<Cascaded,float,1,false>" if default_case
                          else f"step kernel, {args.model} collision, {args.storage} storage, D3Q{args.lattice}, "
                               f"{args.pattern} pattern"},
             "cpu_baseline": cpu,
