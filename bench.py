@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16, adjoint and batched lines")
     ap.add_argument("--batch-steps", type=int, default=5000, help="steps per mode of the 64-domain batch")
+    ap.add_argument("--batch-only", type=int, default=0, metavar="NDOMAINS",
+                    help="profiling: run only the batched sweep over the first NDOMAINS domains and print it")
     ap.add_argument("--block", default="0,0", help="step kernel block shape bx,by (0,0 = default)")
     ap.add_argument("--size", type=int, default=N_SIDE,
                     help="box side (the benchmark workload is 256; smaller sides are for profiling captures)")
@@ -343,15 +345,16 @@ def bench_unroll(dev, reps=3):
             "note": "64^3 is L2-resident: time ratio, not a roofline figure"}
 
 
-def bench_batch(dev, steps, peak):
+def bench_batch(dev, steps, peak, ndomains=64):
     """64 independent channels/ducts (sides U{32..128}, nu U[0.005, 0.1],
     F_x U[1e-7, 1e-5], seed 6): autotuned block, then the whole batch stepped
     with one launch per step replayed from a CUDA graph, one launch per step
-    issued directly, and one launch per domain per step."""
+    issued directly, and one launch per domain per step. A smaller ndomains
+    (the first of the same draw) is for profiling captures."""
     import torch
 
     from paper_1801_04586_gb300 import Batch, synthetic
-    doms = synthetic.batch_domains(64, seed=6)
+    doms = synthetic.batch_domains(64, seed=6)[:ndomains]
     b = Batch(doms, device=dev)
     b.init_equilibrium()
     threads = b.autotune(trial_steps=10)
@@ -543,10 +546,25 @@ def run_gb300(args):
     return 0
 
 
+def run_batch_only(args):
+    """Profiling aid: the batched sweep alone over the first --batch-only domains."""
+    import torch
+
+    from paper_1801_04586_gb300.builder import build
+    build()
+    torch.cuda.set_device(0)
+    peak, _ = measured_peaks()
+    out = bench_batch(torch.device("cuda", 0), args.batch_steps, peak, ndomains=args.batch_only)
+    print(json.dumps({"batch_only": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_only:
+        return run_batch_only(args)
     return run_gb300(args)
 
 

@@ -31,26 +31,41 @@ __device__ __forceinline__ void block_sum_store(double (&v)[K], double *dst) {
 }
 
 // Fixed-point conservation sums. Each FP32 value is rounded to a multiple of
-// 2^-36 and held as a 64-bit integer, so the sums are exact, independent of
-// the order of addition and need no FP64 arithmetic (which issues at a small
-// fraction of the FP32 rate on this GPU). Values must stay below 2^27 in
-// magnitude and a sum of up to 2^24 values below 1 fits with room to spare;
-// a state that breaks this has already tripped the instability flag.
+// 2^-36 and held as an integer, so the sums are exact, independent of the
+// order of addition and need no FP64 arithmetic (which issues at a small
+// fraction of the FP32 rate on this GPU). The rounding is done with FP32
+// additions only (no 64-bit conversion): v * 2^36 rounded to nearest even is
+// returned as hi * 2^20 + lo with hi = round(v * 2^16) and lo = round((v *
+// 2^16 - hi) * 2^20), both taken from the mantissa of a sum with 1.5 * 2^23.
+// Exact for |v| < 2^6; density deviations and momenta of any state that has
+// not tripped the instability flag are far below that. A sum of up to 2^24
+// values below 1 fits in 64 bits with room to spare.
 constexpr double kFixScale = 68719476736.0;          // 2^36
 constexpr double kFixUnit = 1.0 / 68719476736.0;     // 2^-36
 
-__device__ __forceinline__ long long to_fixed(float v) { return __float2ll_rn(v * 68719476736.0f); }
+__device__ __forceinline__ void to_fixed_parts(float v, int &hi, int &lo) {
+    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: the ulp of the sum is 1
+    const float t = fmaf(v, 65536.0f, kMagic);          // 1.5 * 2^23 + round(v * 2^16)
+    const float r = fmaf(v, 65536.0f, -(t - kMagic));   // v * 2^16 - round(v * 2^16), exact, |r| <= 1/2
+    const float l = fmaf(r, 1048576.0f, kMagic);        // 1.5 * 2^23 + round(r * 2^20)
+    hi = __float_as_int(t) - __float_as_int(kMagic);
+    lo = __float_as_int(l) - __float_as_int(kMagic);
+}
 
-// Warp sum of fixed-point values, exact, with two 32-bit warp reductions
-// (redux.sync) instead of 64-bit shuffles: v is split into its low 20 bits
-// (non-negative) and the rest (arithmetic shift). Exact while every |v| <
-// 2^46 (|value| < 2^10): then 32 high parts sum below 2^31 and 32 low parts
-// below 2^25. All 32 lanes must call it.
-__device__ __forceinline__ long long warp_sum_fixed(long long v) {
-    const int lo = (int)(v & 0xfffffll);
-    const int hi = (int)(v >> 20);
-    const int slo = __reduce_add_sync(0xffffffffu, lo);
+__device__ __forceinline__ long long to_fixed(float v) {
+    int hi, lo;
+    to_fixed_parts(v, hi, lo);
+    return (long long)hi * 1048576ll + (long long)lo;
+}
+
+// Warp sum of the fixed-point value of v (to_fixed), exact, with two 32-bit
+// warp reductions (redux.sync) of its parts: 32 high parts (|hi| < 2^22) sum
+// below 2^27, 32 low parts (|lo| <= 2^19) below 2^24. All 32 lanes must call it.
+__device__ __forceinline__ long long warp_sum_fixed(float v) {
+    int hi, lo;
+    to_fixed_parts(v, hi, lo);
     const int shi = __reduce_add_sync(0xffffffffu, hi);
+    const int slo = __reduce_add_sync(0xffffffffu, lo);
     return (long long)shi * 1048576ll + (long long)slo;
 }
 

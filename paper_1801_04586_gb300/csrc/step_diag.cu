@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(512) k_step_diag(const S *__restrict__ src, S 
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    long long q[4] = {0ll, 0ll, 0ll, 0ll};
+    float q[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // to_fixed(0) = 0
     if (x < g.nx && y < g.ny) {  // no early return: every lane joins the warp sums
         uint32_t off[kQ];
         int pop[kQ];
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(512) k_step_diag(const S *__restrict__ src, S 
         const float drho = collide(h, fx, fy, fz, r, &j);
         if (!(fabsf(drho) < 0.9f)) *flag = 1;
         store_node<S>(dst + off[0], g.stride, h, off[0], key);
-        q[0] = to_fixed(drho); q[1] = to_fixed(j.x); q[2] = to_fixed(j.y); q[3] = to_fixed(j.z);
+        q[0] = drho; q[1] = j.x; q[2] = j.y; q[3] = j.z;
     }
     // blockDim.x is a multiple of 32, so a warp is 32 threads of one row
     const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
