@@ -27,6 +27,36 @@ using namespace clbm;
 
 namespace clbm {
 
+// Does the pull of node (x, y, z) meet a wall (a node on a wall face)?
+__device__ __forceinline__ bool on_wall_face(const Geom &g, int x, int y, int z) {
+    return ((g.walls & 1u) && (x == 0 || x == g.nx - 1)) || ((g.walls & 2u) && (y == 0 || y == g.ny - 1)) ||
+           ((g.walls & 4u) && (z == 0 || z == g.nz - 1));
+}
+
+// Load the 19 populations arriving at (x, y, z) (pull map of Eq. 8). With
+// walls, a warp none of whose nodes lies on a wall face takes the periodic
+// map, whose array indices are constants; only warps that touch a wall face
+// evaluate the bounce-back substitutions. Returns the node's offset. (On the
+// single-lattice step the two code paths measured 2 % slower than the
+// bounce-back map alone; on the batched step, whose domains all have walls,
+// 1 % faster.)
+template <typename S, bool WALLS>
+__device__ __forceinline__ uint32_t pull_load(const S *__restrict__ src, const Geom &g, int x, int y, int z,
+                                              float (&h)[kQ]) {
+    uint32_t off[kQ];
+    int pop[kQ];
+    if (WALLS && __any_sync(__activemask(), on_wall_face(g, x, y, z))) {
+        pull_sources<true>(g, x, y, z, off, pop);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
+    } else {
+        pull_sources<false>(g, x, y, z, off, pop);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)i * g.stride + off[i]);
+    }
+    return off[0];
+}
+
 struct DomainDesc {
     Geom g;
     Rates r;
@@ -66,15 +96,11 @@ __global__ void __launch_bounds__(512) k_batch_step(const S *__restrict__ A, S *
         if (z < g.nz) {
             const S *src = A + D->offset;
             S *dst = B + D->offset;
-            uint32_t off[kQ];
-            int pop[kQ];
-            pull_sources<true>(g, x, y, z, off, pop);
             float h[kQ];
-#pragma unroll
-            for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
+            const uint32_t self = pull_load<S, true>(src, g, x, y, z, h);
             const float drho = collide(h, D->fx, D->fy, D->fz, D->r);
             if (!(fabsf(drho) < 0.9f)) *flag = 1;
-            store_node<S>(dst + off[0], g.stride, h, off[0], 0u);
+            store_node<S>(dst + self, g.stride, h, self, 0u);
         }
         tile = next;
     }
