@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16, adjoint and batched lines")
     ap.add_argument("--batch-steps", type=int, default=5000, help="steps per mode of the 64-domain batch")
+    ap.add_argument("--only", default="", metavar="LINE",
+                    help="profiling: of the variant lines run only LINE (e.g. d3q27_f32, adjoint_kernel_256)")
     ap.add_argument("--batch-only", type=int, default=0, metavar="NDOMAINS",
                     help="profiling: run only the batched sweep over the first NDOMAINS domains and print it")
     ap.add_argument("--block", default="0,0", help="step kernel block shape bx,by (0,0 = default)")
@@ -483,29 +485,31 @@ def run_gb300(args):
 
     variants = None
     if not args.no_variants:
-        import numpy as np  # noqa: F401
-        variants = {
-            "f32_two_nodes_per_thread": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, variant=2),
-            "f16_storage": bench_storage("f16", K, args.warmup, dev, side, prof, u0, peak),
-            "bf16_storage": bench_storage("bf16", K, args.warmup, dev, side, prof, u0, peak),
-            "f16_storage_one_node_per_thread": bench_storage("f16", K, args.warmup, dev, side, prof, u0, peak,
-                                                             variant=1),
-            "f16_stochastic_storage": bench_storage("f16sr", K, args.warmup, dev, side, prof, u0, peak),
-            "bf16_stochastic_storage": bench_storage("bf16sr", K, args.warmup, dev, side, prof, u0, peak),
-            "aa_in_place_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, pattern="aa"),
-            "aa_in_place_f16": bench_storage("f16", K, args.warmup, dev, side, prof, u0, peak, pattern="aa"),
-            "walls_yz_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, walls=6),
-            "srt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, model="srt"),
-            "mrt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, model="mrt"),
-            "d3q27_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, lattice=27),
-            "d3q27_srt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, lattice=27, model="srt"),
-            "d3q27_mrt_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, lattice=27, model="mrt"),
-            "d3q27_aa_in_place_f32": bench_storage("f32", K, args.warmup, dev, side, prof, u0, peak, lattice=27,
-                                                   pattern="aa"),
-            "adjoint_kernel_256": bench_adjoint(dev, side, max(10, min(K, 100)), peak),
-            "adjoint_unroll_64": bench_unroll(dev),
-            "batched_64_domains": bench_batch(dev, args.batch_steps, peak),
+        S = lambda storage, **kw: (lambda: bench_storage(storage, K, args.warmup, dev, side, prof, u0, peak,  # noqa
+                                                          **kw))
+        lines = {
+            "f32_two_nodes_per_thread": S("f32", variant=2),
+            "f16_storage": S("f16"),
+            "bf16_storage": S("bf16"),
+            "f16_storage_one_node_per_thread": S("f16", variant=1),
+            "f16_stochastic_storage": S("f16sr"),
+            "bf16_stochastic_storage": S("bf16sr"),
+            "aa_in_place_f32": S("f32", pattern="aa"),
+            "aa_in_place_f16": S("f16", pattern="aa"),
+            "walls_yz_f32": S("f32", walls=6),
+            "srt_f32": S("f32", model="srt"),
+            "mrt_f32": S("f32", model="mrt"),
+            "d3q27_f32": S("f32", lattice=27),
+            "d3q27_srt_f32": S("f32", lattice=27, model="srt"),
+            "d3q27_mrt_f32": S("f32", lattice=27, model="mrt"),
+            "d3q27_aa_in_place_f32": S("f32", lattice=27, pattern="aa"),
+            "adjoint_kernel_256": lambda: bench_adjoint(dev, side, max(10, min(K, 100)), peak),
+            "adjoint_unroll_64": lambda: bench_unroll(dev),
+            "batched_64_domains": lambda: bench_batch(dev, args.batch_steps, peak),
         }
+        if args.only and args.only not in lines:
+            raise SystemExit(f"--only: unknown line {args.only!r}; one of {sorted(lines)}")
+        variants = {name: fn() for name, fn in lines.items() if not args.only or name == args.only}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
