@@ -57,7 +57,7 @@ struct clbm_ctx {
     double *d_partials;
     float *d_io;               // clbm_run_host scratch (first use): 4 x N floats, then
     double *d_mom;             //   4 doubles of sums and
-    unsigned long long *d_acc; //   kDiagSlots x 4 fixed-point accumulators (kept zero between steps)
+    unsigned long long *d_acc; //   2 sets of kDiagSlots x 4 fixed-point accumulators (kept zero between steps)
     int64_t steps_done;
     double gamma;         // force decay rate (clbm_set_force_decay)
     bool packed;          // step kernel with two nodes per thread (FP32x2 arithmetic)
@@ -560,7 +560,7 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     cudaError_t e;
     if (!c->d_io) {
         const size_t io = (sizeof(float) * 4 * (size_t)c->n + 255) / 256 * 256;
-        const size_t acc = sizeof(unsigned long long) * 4 * kDiagSlots;
+        const size_t acc = sizeof(unsigned long long) * 2 * 4 * kDiagSlots;
         const size_t bytes = io + 256 + acc;
         void *p = nullptr;
         if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) {
@@ -593,17 +593,42 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         if ((rc = clbm_step(c, 1)) != CLBM_OK) return rc;
     }
     if (fused && moments_h && nsteps > 0 &&
-        (e = cudaMemsetAsync(c->d_acc, 0, sizeof(unsigned long long) * 4 * kDiagSlots, c->stream)) != cudaSuccess)
+        (e = cudaMemsetAsync(c->d_acc, 0, sizeof(unsigned long long) * 2 * 4 * kDiagSlots, c->stream)) !=
+            cudaSuccess)
         return cuda_fail(e, "clbm_run_host: clear accumulators");
+    // Sums of step t are written straight into moments_h when the device can
+    // address it (pinned host memory under unified addressing); otherwise into
+    // d_mom and copied back after the launch that drains them.
+    double *mom_dev = nullptr;
+    if (fused && moments_h) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, moments_h) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+            a.devicePointer)
+            mom_dev = (double *)a.devicePointer;
+        cudaGetLastError();
+    }
+    const double add0 = (double)c->n;
     for (int64_t t = 0; t < nsteps && fused; ++t) {
         if (moments_h) {
-            // fused step: exact sums of the state it pulls (state t) into the accumulators
+            // fused step: exact sums of the state it pulls (state t) into slot set t % 2; its block 0
+            // first drains set (t - 1) % 2 into the totals of state t - 1
+            DiagSums d;
+            d.acc = c->d_acc + (t & 1) * 4 * kDiagSlots;
+            d.acc_prev = t > 0 ? c->d_acc + ((t - 1) & 1) * 4 * kDiagSlots : nullptr;
+            d.out_prev = mom_dev ? mom_dev + 4 * (t - 1) : c->d_mom;
+            d.add0 = add0;
             e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),
-                                 c->d_flag, c->d_acc, step_key(c->steps_done));
-            if (e == cudaSuccess) e = launch_drain4(c->d_acc, c->d_mom, (double)c->n, c->stream);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                                 c->d_flag, d, step_key(c->steps_done));
+            if (e == cudaSuccess && t > 0 && !mom_dev)
+                e = cudaMemcpyAsync(moments_h + 4 * (t - 1), c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                                     c->stream);
+            if (e == cudaSuccess && t == nsteps - 1) {  // the last step's set
+                double *out = mom_dev ? mom_dev + 4 * t : c->d_mom;
+                e = launch_drain4(c->d_acc + (t & 1) * 4 * kDiagSlots, out, add0, c->stream);
+                if (e == cudaSuccess && !mom_dev)
+                    e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                                        c->stream);
+            }
         } else {
             e = step19(c, step_launch_of(c), c->buf[c->cur], c->buf[c->cur ^ 1], force_now(c),
                        step_key(c->steps_done));

@@ -48,11 +48,19 @@ cudaError_t launch_step_aa_srt(int storage, const Launch &L, void *f, const Rate
 cudaError_t launch_step_aa_mrt(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,
                                uint32_t key, bool odd);
 // Fused step + fixed-point conservation sums of the pulled state into the
-// kDiagSlots x 4 accumulators acc (zero on entry); launch_drain4 turns them
-// into 4 FP64 totals and clears them (step_diag.cu).
+// kDiagSlots x 4 accumulators acc (zero on entry). If acc_prev is not null,
+// the launch first drains that set (the previous step's) into out_prev[0..3]
+// (FP64 totals, add0 added to the first; device memory or mapped host
+// memory) and clears it. launch_drain4 drains a set on its own (step_diag.cu).
 constexpr int kDiagSlots = 1024;
+struct DiagSums {
+    unsigned long long *acc;
+    unsigned long long *acc_prev;
+    double *out_prev;
+    double add0;
+};
 cudaError_t launch_step_diag(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
-                             const ForceArgs &F, int *flag, unsigned long long *acc, uint32_t key);
+                             const ForceArgs &F, int *flag, const DiagSums &d, uint32_t key);
 cudaError_t launch_drain4(unsigned long long *acc, double *out, double add0, cudaStream_t stream);
 cudaError_t launch_fixed_final4(const long long *partials, int nblocks, double *out, double add0,
                                 cudaStream_t stream);

@@ -8,12 +8,34 @@
 // adds its 4 sums into one of kDiagSlots accumulator slots with 64-bit
 // integer atomics: integer addition is exact and order-independent, so the
 // totals do not depend on scheduling, and no block barrier holds the warps of
-// a block together. A one-block kernel then adds the slots, converts the
-// totals to FP64 and clears the slots for the next step.
+// a block together. The slots come in two sets used by alternate steps:
+// block 0 of each step first drains the set the previous step filled (adds
+// the slots, writes the FP64 totals, clears the set), so no separate launch
+// sits between steps. k_drain4 drains the last step's set.
 #include "block_reduce.cuh"
 #include "kernels.cuh"
 
 namespace clbm {
+
+// Totals of a slot set as FP64 (plus add0 on the first) to out[0..3], then
+// the set is cleared. Every thread of the block calls it.
+__device__ __forceinline__ void drain_slots(unsigned long long *acc, double *out, double add0) {
+    const int nt = blockDim.x * blockDim.y;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    long long q[4] = {0ll, 0ll, 0ll, 0ll};
+    for (int s = tid; s < kDiagSlots; s += nt)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            q[k] += (long long)acc[4 * s + k];
+            acc[4 * s + k] = 0ull;
+        }
+    __shared__ long long tot[4];
+    block_sum_fixed<4>(q, tot);
+    __syncthreads();
+    if (tid == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = (double)tot[k] * kFixUnit + (k == 0 ? add0 : 0.0);
+}
 
 template <int FM>
 __device__ __forceinline__ void force_diag(const ForceArgs &F, const Geom &g, int z, uint32_t self, float &fx,
@@ -33,10 +55,13 @@ __device__ __forceinline__ void force_diag(const ForceArgs &F, const Geom &g, in
 template <typename S, int FM, bool WALLS>
 __global__ void __launch_bounds__(512) k_step_diag(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r,
                                                    ForceArgs F, int *__restrict__ flag,
-                                                   unsigned long long *__restrict__ acc, uint32_t key) {
+                                                   unsigned long long *__restrict__ acc,
+                                                   unsigned long long *__restrict__ acc_prev, double *out_prev,
+                                                   double add0, uint32_t key) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
+    if (acc_prev && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) drain_slots(acc_prev, out_prev, add0);
     float q[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // to_fixed(0) = 0
     if (x < g.nx && y < g.ny) {  // no early return: every lane joins the warp sums
         uint32_t off[kQ];
@@ -69,54 +94,39 @@ __global__ void __launch_bounds__(512) k_step_diag(const S *__restrict__ src, S 
 
 template <typename S, int FM>
 static cudaError_t diag_walls(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
-                              int *flag, unsigned long long *acc, uint32_t key) {
+                              int *flag, const DiagSums &d, uint32_t key) {
     if (L.g.walls)
-        k_step_diag<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, acc,
-                                                                   key);
+        k_step_diag<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, d.acc,
+                                                                   d.acc_prev, d.out_prev, d.add0, key);
     else
-        k_step_diag<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, acc,
-                                                                    key);
+        k_step_diag<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag,
+                                                                    d.acc, d.acc_prev, d.out_prev, d.add0, key);
     return cudaGetLastError();
 }
 
 template <typename S>
 static cudaError_t diag_force(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
-                              int *flag, unsigned long long *acc, uint32_t key) {
+                              int *flag, const DiagSums &d, uint32_t key) {
     switch (F.mode) {
-        case kForceUniform: return diag_walls<S, kForceUniform>(L, src, dst, r, F, flag, acc, key);
-        case kForceProfileZ: return diag_walls<S, kForceProfileZ>(L, src, dst, r, F, flag, acc, key);
-        default: return diag_walls<S, kForceField>(L, src, dst, r, F, flag, acc, key);
+        case kForceUniform: return diag_walls<S, kForceUniform>(L, src, dst, r, F, flag, d, key);
+        case kForceProfileZ: return diag_walls<S, kForceProfileZ>(L, src, dst, r, F, flag, d, key);
+        default: return diag_walls<S, kForceField>(L, src, dst, r, F, flag, d, key);
     }
 }
 
 cudaError_t launch_step_diag(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
-                             const ForceArgs &F, int *flag, unsigned long long *acc, uint32_t key) {
+                             const ForceArgs &F, int *flag, const DiagSums &d, uint32_t key) {
     switch (storage) {
-        case 0: return diag_force<float>(L, src, dst, r, F, flag, acc, key);
-        case 1: return diag_force<__half>(L, src, dst, r, F, flag, acc, key);
-        case 2: return diag_force<__nv_bfloat16>(L, src, dst, r, F, flag, acc, key);
-        case 3: return diag_force<HalfSR>(L, src, dst, r, F, flag, acc, key);
-        default: return diag_force<BF16SR>(L, src, dst, r, F, flag, acc, key);
+        case 0: return diag_force<float>(L, src, dst, r, F, flag, d, key);
+        case 1: return diag_force<__half>(L, src, dst, r, F, flag, d, key);
+        case 2: return diag_force<__nv_bfloat16>(L, src, dst, r, F, flag, d, key);
+        case 3: return diag_force<HalfSR>(L, src, dst, r, F, flag, d, key);
+        default: return diag_force<BF16SR>(L, src, dst, r, F, flag, d, key);
     }
 }
 
-// Totals of the kDiagSlots accumulator slots as FP64 (plus add0 on the
-// first), then the slots are cleared for the next step. One block.
-__global__ void k_drain4(unsigned long long *acc, double *out, double add0) {
-    long long q[4] = {0ll, 0ll, 0ll, 0ll};
-    for (int s = threadIdx.x; s < kDiagSlots; s += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            q[k] += (long long)acc[4 * s + k];
-            acc[4 * s + k] = 0ull;
-        }
-    __shared__ long long tot[4];
-    block_sum_fixed<4>(q, tot);
-    __syncthreads();
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) out[k] = (double)tot[k] * kFixUnit + (k == 0 ? add0 : 0.0);
-}
+// Drain one slot set (the last step's). One block.
+__global__ void k_drain4(unsigned long long *acc, double *out, double add0) { drain_slots(acc, out, add0); }
 
 cudaError_t launch_drain4(unsigned long long *acc, double *out, double add0, cudaStream_t stream) {
     k_drain4<<<1, 1024, 0, stream>>>(acc, out, add0);
