@@ -108,12 +108,25 @@ def test_run_host_job_matches_device_path():
     g3, _ = make_pair(nx, ny, nz, 0.05, walls=4)
     g3.set_force_uniform(1e-5)
     g3.init_equilibrium(t(rho), t(u))
-    m0 = g3.reduce_moments().cpu().numpy()
     m = mom.numpy().reshape(steps + 1, 4)
-    np.testing.assert_array_equal(m[0], m0)
+    m0 = g3.reduce_moments().cpu().numpy()
     assert np.all(np.abs(m[:, 0] - m0[0]) < 1e-6)
-    g3.step(steps - 1)
-    np.testing.assert_array_equal(m[steps - 1], g3.reduce_moments().cpu().numpy())
+    for k in range(steps + 1):  # every step's sums, written by the next launch
+        np.testing.assert_array_equal(m[k], g3.reduce_moments().cpu().numpy())
+        g3.step(1)
+    # pageable host buffers take the copy path: same values
+    g4, _ = make_pair(nx, ny, nz, 0.05, walls=4)
+    g4.set_force_uniform(1e-5)
+    mom2 = torch.empty(4 * (steps + 1), dtype=torch.float64)
+    g4.run_host(torch.from_numpy(rho), torch.from_numpy(u), steps, None, None, mom2)
+    assert torch.equal(mom2, mom)
+    # one step and no steps
+    for n in (1, 0):
+        g5, _ = make_pair(nx, ny, nz, 0.05, walls=4)
+        g5.set_force_uniform(1e-5)
+        m5 = torch.empty(4 * (n + 1), dtype=torch.float64).pin_memory()
+        g5.run_host(rho_h, u_h, n, None, None, m5)
+        assert torch.equal(m5, mom[: 4 * (n + 1)])
 
 
 def test_instability_flag():
