@@ -95,8 +95,11 @@ def test_models_poiseuille_slip(q, model):
 def test_shear_wave_moving_frame_gpu(q):
     """Sec. III.A on the GPU: shear wave of Eq. 17 on a frame moving at
     Ma = B/c_s = 0.3. The cascaded collision keeps the imposed viscosity
-    (paper: 0.08 % error); the SRT-LBM loses 8.91 % (paper), nu (1 - 3 B^2)."""
-    L, nu, A, t1, t2 = 101, 0.05, 1e-3, 200, 5200
+    (paper: 0.08 % error); the SRT-LBM loses 8.91 % (paper), nu (1 - 3 B^2).
+    The wave amplitude is 1e-2 of the 0.17 background so that FP32 rounding
+    over 5000 steps stays far below the measured effect (at 1e-3 it moved
+    the D3Q27 SRT value by 0.1 percentage point)."""
+    L, nu, A, t1, t2 = 101, 0.05, 1e-2, 200, 5200
     B = 0.3 * np.sqrt(1.0 / 3.0)
     phi = 2 * np.pi / L
     y = np.arange(L)

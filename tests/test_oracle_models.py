@@ -150,7 +150,7 @@ def test_mrt_poiseuille_bounce_back_slip(q, s3):
         assert np.sqrt(((ux - ua) ** 2).sum() / (ua ** 2).sum()) < 1e-8
 
 
-def shear_wave_viscosity(q, model, B, L=101, nu=0.05, A=1e-3, t1=200, t2=5200):
+def shear_wave_viscosity(q, model, B, L=101, nu=0.05, A=1e-2, t1=200, t2=5200):
     """Viscosity measured from the decay of the first Fourier mode of u_x(y)
     for the shear wave of Eq. 17 on a frame moving at B along y (reading:
     u = (A sin(2 pi y / L), B, 0)); the lattice is x- and z-invariant, so one
