@@ -249,11 +249,10 @@ int clbm_load_state(clbm_ctx *ctx, const void *host_buf, size_t bytes);
  * (k = 0..nsteps) holds the FP64 sums of clbm_reduce_moments for the state at
  * step k. With the cascaded collision, the A/B pattern and D3Q19 they are
  * formed inside step k+1's kernel from the state it pulls (exact fixed-point
- * warp sums, no extra pass over the populations) and written to moments_host
- * by the next launch: directly when moments_host is pinned memory the device
- * can address, else through an asynchronous copy. Otherwise they come from
- * one clbm_reduce_moments pass before each step, copied back
- * asynchronously. The last comes from one reduction after the final step. The call synchronises once, at the end, then returns
+ * warp sums, no extra pass over the populations), totalled by the next
+ * step's launch and copied back asynchronously. Otherwise they come from one
+ * clbm_reduce_moments pass before each step, copied back asynchronously.
+ * The last comes from one reduction after the final step. The call synchronises once, at the end, then returns
  * CLBM_ERR_UNSTABLE if any mass sum is non-finite or the instability flag is
  * set. Device scratch for the staging fields and partial sums is allocated
  * on first use and kept by the context. Host buffers should be pinned for

@@ -596,17 +596,10 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         (e = cudaMemsetAsync(c->d_acc, 0, sizeof(unsigned long long) * 2 * 4 * kDiagSlots, c->stream)) !=
             cudaSuccess)
         return cuda_fail(e, "clbm_run_host: clear accumulators");
-    // Sums of step t are written straight into moments_h when the device can
-    // address it (pinned host memory under unified addressing); otherwise into
-    // d_mom and copied back after the launch that drains them.
-    double *mom_dev = nullptr;
-    if (fused && moments_h) {
-        cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, moments_h) == cudaSuccess && a.type == cudaMemoryTypeHost &&
-            a.devicePointer)
-            mom_dev = (double *)a.devicePointer;
-        cudaGetLastError();
-    }
+    // The sums of step t - 1 land in d_mom during step t and are copied back
+    // after it. (Writing them from the kernel straight into pinned host memory
+    // made every step's kernel wait for that write: 9 us per step, more than
+    // the copy.)
     const double add0 = (double)c->n;
     for (int64_t t = 0; t < nsteps && fused; ++t) {
         if (moments_h) {
@@ -615,17 +608,16 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
             DiagSums d;
             d.acc = c->d_acc + (t & 1) * 4 * kDiagSlots;
             d.acc_prev = t > 0 ? c->d_acc + ((t - 1) & 1) * 4 * kDiagSlots : nullptr;
-            d.out_prev = mom_dev ? mom_dev + 4 * (t - 1) : c->d_mom;
+            d.out_prev = c->d_mom;
             d.add0 = add0;
             e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),
                                  c->d_flag, d, step_key(c->steps_done));
-            if (e == cudaSuccess && t > 0 && !mom_dev)
+            if (e == cudaSuccess && t > 0)
                 e = cudaMemcpyAsync(moments_h + 4 * (t - 1), c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                                     c->stream);
             if (e == cudaSuccess && t == nsteps - 1) {  // the last step's set
-                double *out = mom_dev ? mom_dev + 4 * t : c->d_mom;
-                e = launch_drain4(c->d_acc + (t & 1) * 4 * kDiagSlots, out, add0, c->stream);
-                if (e == cudaSuccess && !mom_dev)
+                e = launch_drain4(c->d_acc + (t & 1) * 4 * kDiagSlots, c->d_mom, add0, c->stream);
+                if (e == cudaSuccess)
                     e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                                         c->stream);
             }

@@ -136,14 +136,20 @@ template <> struct Codec<BF16SR> {
 // Encode the NQ post-collision deviations h (population order) of one node
 // in the storage format. key: per-step random key (stochastic formats only);
 // the dither of population i depends on (key, node, i) alone, so every
-// storage pattern and staging path stores the same values.
+// storage pattern and staging path stores the same values. The node's hash
+// is the full lowbias32 mix of (node, key); each pair of populations then
+// takes one xorshift-multiply round of it offset by a Weyl step (the first
+// round of the same mixer): a bijection of a uniform word, so every dither
+// stays uniform, at a third of the cost of a full mix per pair.
 template <typename S, int NQ>
 __device__ __forceinline__ void encode_each(const float (&h)[NQ], uint32_t node, uint32_t key, S (&e)[NQ]) {
     if constexpr (Codec<S>::kStochastic) {
         const uint32_t base = lowbias32(node ^ key);
 #pragma unroll
         for (int i = 0; i < NQ; i += 2) {
-            const uint32_t r = lowbias32(base + (uint32_t)i * 0x9e3779b9u);
+            uint32_t r = base + (uint32_t)i * 0x9e3779b9u;
+            r ^= r >> 16;
+            r *= 0x7feb352du;
             e[i] = Codec<S>::from_f_sr(h[i], r);
             if (i + 1 < NQ) e[i + 1] = Codec<S>::from_f_sr(h[i + 1], r >> 16);
         }

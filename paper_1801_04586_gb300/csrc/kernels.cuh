@@ -50,8 +50,7 @@ cudaError_t launch_step_aa_mrt(int storage, const Launch &L, void *f, const Rate
 // Fused step + fixed-point conservation sums of the pulled state into the
 // kDiagSlots x 4 accumulators acc (zero on entry). If acc_prev is not null,
 // the launch first drains that set (the previous step's) into out_prev[0..3]
-// (FP64 totals, add0 added to the first; device memory or mapped host
-// memory) and clears it. launch_drain4 drains a set on its own (step_diag.cu).
+// (FP64 totals, add0 added to the first) and clears it. launch_drain4 drains a set on its own (step_diag.cu).
 constexpr int kDiagSlots = 1024;
 struct DiagSums {
     unsigned long long *acc;

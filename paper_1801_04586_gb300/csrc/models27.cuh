@@ -130,44 +130,24 @@ __device__ __forceinline__ float collide_mrt27(float (&h)[3][3][3], float Fx, fl
     return drho;
 }
 
-// SRT on D3Q27 deviations: h* = h + s (f_D - w - h) + (1 - s/2) R_G, s = s2.
+// SRT on D3Q27 deviations: the MRT collision with every rate equal to s2
+// (Sec. II.A), so mass and momentum come out exactly (see collide_srt in
+// models.cuh for why not per population).
 __device__ __forceinline__ float collide_srt27(float (&h)[3][3][3], float Fx, float Fy, float Fz,
                                                const Rates27 &r) {
-    float d = 0.0f, ax = 0.0f, ay = 0.0f, az = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float v = h[a][b][c];
-                d += v;
-                if (a) ax += e_of(a) > 0 ? v : -v;
-                if (b) ay += e_of(b) > 0 ? v : -v;
-                if (c) az += e_of(c) > 0 ? v : -v;
-            }
-    const float drho = d, rho = 1.0f + drho, inv = 1.0f / rho;
-    const float ux = fmaf(0.5f, Fx, ax) * inv, uy = fmaf(0.5f, Fy, ay) * inv, uz = fmaf(0.5f, Fz, az) * inv;
-    const float uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-    const float uF = fmaf(ux, Fx, fmaf(uy, Fy, uz * Fz));
-    const float base = fmaf(-1.5f * rho, uu, drho);
-    const float s = 1.0f - r.om2, cf = 1.0f - 0.5f * s;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float w = rest_weight27_code(a, b, c);
-                float eu = 0.0f, eF = 0.0f;
-                if (a) { eu += e_of(a) * ux; eF += e_of(a) * Fx; }
-                if (b) { eu += e_of(b) * uy; eF += e_of(b) * Fy; }
-                if (c) { eu += e_of(c) * uz; eF += e_of(c) * Fz; }
-                const float heq = w * fmaf(rho * eu, fmaf(4.5f, eu, 3.0f), base);
-                const float R = w * fmaf(9.0f * eu, eF, 3.0f * (eF - uF));
-                h[a][b][c] = fmaf(cf, R, fmaf(s, heq - h[a][b][c], h[a][b][c]));
-            }
-    return drho;
+    const float om = r.om2;
+    Rates27 e;
+    e.om2 = om;
+    e.cb = 0.0f;
+    e.om3 = om;
+    e.c3 = 0.5f * (1.0f + om) * kC;
+    e.om3b = om;
+    e.om4 = om;
+    e.om4b = om;
+    e.om5 = om;
+    e.c5 = 0.5f * (1.0f + om) * kC2;
+    e.om6 = om;
+    return collide_mrt27(h, Fx, Fy, Fz, e);
 }
 
 }  // namespace clbm
