@@ -99,3 +99,30 @@ def test_noslip_rule_constants():
     assert an.noslip_s3(5 / 4) == pytest.approx(8 / 9)
     assert an.s2_from_nu(0.2) == pytest.approx(10 / 11)
     assert an.noslip_s3(10 / 11) == pytest.approx(16 / 13)
+
+
+def test_duct_cross_section_error_minimal_near_the_noslip_rate():
+    """Sec. III.C: the local error E(z) over a duct cross-section is smallest
+    near the no-slip s3 for the central and intermediate sections (the rule
+    is exact only for unidirectional flow, so near, not at: the scan's
+    minimum sits at 1.18-1.23). At nu = 0.2 that rate is 16/13 = 1.23077;
+    the paper prints 1.33077, whose error is at least 1.3 times larger
+    (reading of the printed value)."""
+    n, nu, F = 16, 0.2, 2e-4
+    s2 = an.s2_from_nu(nu)
+    target = an.noslip_s3(s2)
+    assert target == pytest.approx(16 / 13, rel=1e-12)
+    ua = an.duct_steady(n, F, nu)
+    Ff = np.zeros((3, n, n, 1))
+    Ff[0] = F
+    steps = int(24 * n * n / (np.pi ** 2 * nu))
+    sections = (n // 2, n // 2 + 3)  # z = 0.5 and 3.5 spacings from the centre
+    E = {}
+    for s3 in (1.10, 1.18, target, 1.28, 1.33077, 1.40):
+        lat = o.Lattice(1, n, n, walls=6, s2=s2, s2b=s2, s3=s3)
+        ux = o.macros(lat, o.step(lat, o.init(lat, None, None, Ff), Ff, steps), Ff)[1][0, :, :, 0]
+        E[s3] = [np.sqrt(((ux[z] - ua[z]) ** 2).sum() / (ua[z] ** 2).sum()) for z in sections]
+    for k in range(len(sections)):
+        best = min(e[k] for e in E.values())
+        assert E[target][k] < 1.25 * best
+        assert E[1.33077][k] > 1.3 * E[target][k]
