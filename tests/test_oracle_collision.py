@@ -181,3 +181,49 @@ def test_first_step_nodes_matches_full_step(walls):
     nodes = RNG.choice(lat.n, 25, replace=False)
     np.testing.assert_allclose(o.first_step_nodes(lat, nodes, rho, u, F), full[:, nodes].T,
                                rtol=0, atol=1e-15)
+
+
+def _rest_jacobian(lat):
+    """Jacobian of the oracle collision at the rest state (central differences)."""
+    q = lat.q
+    w = o.equilibrium(1.0, np.zeros(3), q)
+    J = np.zeros((q, q))
+    h = 1e-7
+    for k in range(q):
+        d = np.zeros(q)
+        d[k] = h
+        J[:, k] = (o.collide(lat, w + d) - o.collide(lat, w - d)) / (2 * h)
+    return J
+
+
+def _spectral_radius(lat, nk=9):
+    """Largest |eigenvalue| of one linearised step (streaming in Fourier space
+    times the rest-state collision Jacobian) over a grid of wavevectors."""
+    E = o.velocities(lat.q).astype(float)
+    J = _rest_jacobian(lat)
+    ks = np.linspace(0.0, np.pi, nk)
+    r = 0.0
+    for kx in ks:
+        for ky in ks:
+            for kz in ks:
+                P = np.diag(np.exp(-1j * (E @ np.array([kx, ky, kz]))))
+                r = max(r, float(np.abs(np.linalg.eigvals(P @ J)).max()))
+    return r
+
+
+def test_linear_stability_at_rest():
+    """Von Neumann analysis of the oracle's step at the rest state: at k = 0
+    the 4 conserved modes have eigenvalue 1 and the others 1 - s; at every
+    wavevector the step does not amplify for the rates the tests use, and it
+    does amplify when the bulk rate nears 2 (s2b = 1.9 at nu = 0.1), which is
+    why no configuration here goes there."""
+    s2 = 1.0 / (3 * 0.1 + 0.5)
+    lat = o.Lattice(1, 1, 1, s2=s2, s2b=1.2, s3=1.1, s4=0.9)
+    ev = np.sort(np.abs(np.linalg.eigvals(_rest_jacobian(lat))))[::-1]
+    np.testing.assert_allclose(ev[:4], 1.0, atol=1e-7)
+    expected = sorted([1.0] * 4 + [abs(1 - s2)] * 5 + [abs(1 - 1.2)] + [abs(1 - 1.1)] * 6 + [abs(1 - 0.9)] * 3,
+                      reverse=True)
+    np.testing.assert_allclose(ev, expected, atol=1e-7)
+    for kw in (dict(s2b=1.2, s3=1.1, s4=0.9), dict(s2b=s2, s3=(16 - 8 * s2) / (8 - s2), s4=1.0)):
+        assert _spectral_radius(o.Lattice(1, 1, 1, s2=s2, **kw)) < 1 + 1e-7
+    assert _spectral_radius(o.Lattice(1, 1, 1, s2=s2, s2b=1.9, s3=(16 - 8 * s2) / (8 - s2), s4=1.0)) > 1.05
