@@ -143,3 +143,23 @@ def test_instability_flag():
     g.init_equilibrium()
     g.step(2)
     g.check()
+
+
+def test_bulk_rate_instability_is_flagged():
+    """A physical blow-up, not an injected NaN: at nu = 0.1 with the bulk rate
+    at 1.9 the rest state is linearly unstable (von Neumann spectral radius
+    1.11, tests/test_oracle_collision.py); a small perturbation grows until a
+    density leaves (0.1, 1.9) and the step kernel raises the flag. With the
+    bulk rate at 1.2 the same perturbation decays."""
+    shape = (16, 16, 16)
+    h0 = synthetic.rng(71).uniform(-1e-5, 1e-5, (19,) + shape).astype(np.float32)
+    for s2b, unstable in ((1.2, False), (1.9, True)):
+        g, _ = make_pair(16, 16, 16, 0.1, s2b=s2b)
+        g.set_populations(t(h0), deviation=True)
+        g.step(400)
+        if unstable:
+            with pytest.raises(UnstableError):
+                g.check()
+        else:
+            g.check()
+            assert float(g.populations(deviation=True).abs().max()) < 1e-4  # no growth
