@@ -20,9 +20,9 @@ DOMAINS = [
 ]
 
 
-def _single(d, steps):
+def _single(d, steps, storage="f32"):
     g, _ = make_pair(d["nx"], d["ny"], d["nz"], d["nu"], walls=d.get("walls", 0), s2b=d.get("s2b", 1.0),
-                     s3=d.get("s3", 1.0), s4=d.get("s4", 1.0))
+                     s3=d.get("s3", 1.0), s4=d.get("s4", 1.0), storage=storage)
     g.set_force_uniform(d.get("fx", 0.0), d.get("fy", 0.0), d.get("fz", 0.0))
     g.init_equilibrium()
     g.step(steps)
@@ -86,4 +86,17 @@ def test_batch_against_oracle():
         fo = oracle.step(o, oracle.init(o, None, None, F), F, 50)
         fg = b.populations(k, deviation=True).double().cpu().numpy() + W
         assert rel_err(fg, fo) < F32_REL_TOL
+    b.close()
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_batch_16bit_storage_matches_single_lattices(storage):
+    """FP16/BF16 deviation storage in a batch: the same stored bits as each
+    lattice stepped alone in that format."""
+    b = Batch(DOMAINS, storage=storage, device=dev())
+    b.init_equilibrium()
+    b.step(21, Batch.GRAPH)
+    b.check()
+    for k, d in enumerate(DOMAINS):
+        assert torch.equal(b.populations(k, deviation=True).cpu(), _single(d, 21, storage)), f"domain {k}"
     b.close()

@@ -110,8 +110,11 @@ def test_random_state_parity():
 
 
 @pytest.mark.parametrize("shape_walls", [((1, 1, 1), 0), ((1, 1, 1), 7), ((1, 1, 40), 4), ((5, 1, 1), 0),
-                                         ((2, 3, 2), 7), ((64, 1, 3), 2)])
+                                         ((2, 3, 2), 7), ((64, 1, 3), 2), ((65535, 1, 1), 1), ((1, 65535, 1), 0),
+                                         ((1, 1, 65535), 4)])
 def test_degenerate_lattices(shape_walls):
+    """Single nodes, single rows and the longest extents the ABI accepts
+    (65535 along one axis: the grid's z limit, and ny / block_y rows)."""
     (nx, ny, nz), walls = shape_walls
     shape = (nz, ny, nx)
     g, o = make_pair(nx, ny, nz, 0.1, walls=walls, s2b=0.9, s3=1.2)
