@@ -66,6 +66,8 @@ struct clbm_ctx {
     int model;            // CLBM_MODEL_*
     Rates27 rates27;
     dim3 block;
+    cudaStream_t cap_stream;   // private stream for graph capture (first use)
+    cudaGraphExec_t graph;     // kGraphSteps steps from phase 0; null until built, dropped when the force changes
 };
 
 namespace {
@@ -77,10 +79,23 @@ ForceArgs force_at_zero(const clbm_ctx *c) {
     return F;
 }
 
-ForceArgs force_now(const clbm_ctx *c) {
+ForceArgs force_at(const clbm_ctx *c, int64_t step) {
     ForceArgs F = c->force;
-    F.scale = c->gamma == 0.0 ? 1.0f : (float)std::exp(-c->gamma * (double)c->steps_done);
+    F.scale = c->gamma == 0.0 ? 1.0f : (float)std::exp(-c->gamma * (double)step);
     return F;
+}
+
+ForceArgs force_now(const clbm_ctx *c) { return force_at(c, c->steps_done); }
+
+// Steps replayed from one captured CUDA graph (even, so a replay ends in the
+// phase it started from).
+constexpr int kGraphSteps = 16;
+
+void drop_graph(clbm_ctx *c) {
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
 }
 
 Launch launch_of(const clbm_ctx *c) {
@@ -141,6 +156,47 @@ cudaError_t step19_aa(const clbm_ctx *c, const Launch &L, void *f, const ForceAr
         case CLBM_MODEL_MRT: return launch_step_aa_mrt(c->p.storage, L, f, c->rates, F, c->d_flag, key, odd);
         default: return launch_step_aa(c->p.storage, L, f, c->rates, F, c->d_flag, key, odd);
     }
+}
+
+// One time step `step` of the context's lattice, pattern and model, from
+// buffer cur (A/B) or in place (AA), launched with L.
+cudaError_t one_step(const clbm_ctx *c, const Launch &L, int cur, int64_t step) {
+    const ForceArgs F = force_at(c, step);
+    const uint32_t key = step_key(step);
+    if (c->aa) {
+        const bool odd = (step & 1) != 0;
+        return c->q == 27 ? step27_aa(c, L, c->buf[0], F, key, odd) : step19_aa(c, L, c->buf[0], F, key, odd);
+    }
+    return c->q == 27 ? step27(c, L, c->buf[cur], c->buf[cur ^ 1], F, key)
+                      : step19(c, L, c->buf[cur], c->buf[cur ^ 1], F, key);
+}
+
+// Capture kGraphSteps steps starting from phase 0 (A/B: from buffer 0; AA: an
+// even step) on a private stream. Only for launches whose arguments do not
+// change from step to step: a static force and no stochastic dither key.
+int ensure_graph(clbm_ctx *c) {
+    if (c->graph) return CLBM_OK;
+    cudaError_t e = cudaSuccess;
+    if (!c->cap_stream && (e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        c->cap_stream = nullptr;
+        return cuda_fail(e, "clbm_step: capture stream");
+    }
+    Launch L = step_launch_of(c);
+    L.stream = c->cap_stream;
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "clbm_step: begin capture");
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) e = one_step(c, L, k & 1, k);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        cudaGetLastError();
+        return cuda_fail(e, "clbm_step: graph capture");
+    }
+    return CLBM_OK;
 }
 
 }  // namespace
@@ -272,6 +328,8 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
 int clbm_destroy(clbm_ctx *c) {
     if (!c) return CLBM_OK;
     cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     cudaFree(c->buf[0]);
     cudaFree(c->d_flag);
     if (c->d_io) cudaFree(c->d_io);
@@ -304,6 +362,7 @@ int clbm_set_force_uniform(clbm_ctx *c, double fx, double fy, double fz) {
         return fail(CLBM_ERR_ARG, "clbm_set_force_uniform: non-finite force");
     c->force.mode = kForceUniform;
     c->force.fx = (float)fx; c->force.fy = (float)fy; c->force.fz = (float)fz;
+    drop_graph(c);
     return CLBM_OK;
 }
 
@@ -311,6 +370,7 @@ int clbm_set_force_profile_z(clbm_ctx *c, const float *F) {
     if (!c || !F) return fail(CLBM_ERR_ARG, "clbm_set_force_profile_z: null pointer");
     c->force.mode = kForceProfileZ;
     c->force.profile = F;
+    drop_graph(c);
     return CLBM_OK;
 }
 
@@ -318,6 +378,7 @@ int clbm_set_force_field(clbm_ctx *c, const float *F) {
     if (!c || !F) return fail(CLBM_ERR_ARG, "clbm_set_force_field: null pointer");
     c->force.mode = kForceField;
     c->force.field = F;
+    drop_graph(c);
     return CLBM_OK;
 }
 
@@ -325,6 +386,7 @@ int clbm_set_force_decay(clbm_ctx *c, double gamma) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_set_force_decay: null context");
     if (!std::isfinite(gamma)) return fail(CLBM_ERR_ARG, "clbm_set_force_decay: non-finite rate");
     c->gamma = gamma;
+    drop_graph(c);
     return CLBM_OK;
 }
 
@@ -342,20 +404,35 @@ int clbm_step(clbm_ctx *c, int64_t nsteps) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_step: null context");
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_step: nsteps < 0");
     const Launch L = step_launch_of(c);
-    for (int64_t t = 0; t < nsteps && c->aa; ++t) {
-        const bool odd = (c->steps_done & 1) != 0;
-        cudaError_t e = c->q == 27 ? step27_aa(c, L, c->buf[0], force_now(c), step_key(c->steps_done), odd)
-                                   : step19_aa(c, L, c->buf[0], force_now(c), step_key(c->steps_done), odd);
+    auto advance = [&]() -> int {
+        cudaError_t e = one_step(c, L, c->cur, c->steps_done);
         if (e != cudaSuccess) return cuda_fail(e, "clbm_step");
+        if (!c->aa) c->cur ^= 1;
         ++c->steps_done;
+        return CLBM_OK;
+    };
+    int64_t t = 0;
+    // Long runs with static launch arguments replay a captured graph of
+    // kGraphSteps steps: one launch call per 16 steps instead of 16.
+    const bool stochastic = c->p.storage == CLBM_STORAGE_F16_SR || c->p.storage == CLBM_STORAGE_BF16_SR;
+    if (!stochastic && c->gamma == 0.0 && nsteps >= 2 * kGraphSteps) {
+        const int phase = c->aa ? (int)(c->steps_done & 1) : c->cur;
+        if (phase != 0) {
+            int rc = advance();
+            if (rc != CLBM_OK) return rc;
+            ++t;
+        }
+        int rc = ensure_graph(c);
+        if (rc != CLBM_OK) return rc;
+        for (; t + kGraphSteps <= nsteps; t += kGraphSteps) {
+            cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "clbm_step: graph launch");
+            c->steps_done += kGraphSteps;
+        }
     }
-    for (int64_t t = 0; t < nsteps && !c->aa; ++t) {
-        cudaError_t e = c->q == 27
-            ? step27(c, L, c->buf[c->cur], c->buf[c->cur ^ 1], force_now(c), step_key(c->steps_done))
-            : step19(c, L, c->buf[c->cur], c->buf[c->cur ^ 1], force_now(c), step_key(c->steps_done));
-        if (e != cudaSuccess) return cuda_fail(e, "clbm_step");
-        c->cur ^= 1;
-        ++c->steps_done;
+    for (; t < nsteps; ++t) {
+        int rc = advance();
+        if (rc != CLBM_OK) return rc;
     }
     return CLBM_OK;
 }

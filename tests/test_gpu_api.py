@@ -163,3 +163,34 @@ def test_bulk_rate_instability_is_flagged():
         else:
             g.check()
             assert float(g.populations(deviation=True).abs().max()) < 1e-4  # no growth
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(pattern="aa"), dict(lattice=27), dict(model="mrt"),
+                                dict(storage="f16sr")])
+def test_long_steps_replay_graph_bit_identical(kw):
+    """step(n) for n >= 32 replays a captured 16-step graph when the launch
+    arguments are static (not for stochastic rounding or a decaying force):
+    bit-identical to single steps, from either phase, and rebuilt when the
+    force changes."""
+    from paper_1801_04586_gb300 import Lattice
+    nx, ny, nz = 40, 12, 10
+    shape = (nz, ny, nx)
+    u0 = t(synthetic.divfree_velocity(shape, seed=81, umax=0.03))
+    a = Lattice(nx, ny, nz, 0.05, walls=4, device=dev(), **kw)
+    b = Lattice(nx, ny, nz, 0.05, walls=4, device=dev(), **kw)
+    for g in (a, b):
+        g.set_force_uniform(1e-5)
+        g.init_equilibrium(None, u0)
+    a.step(1)  # odd phase: the next long run first takes one plain step
+    b.step(1)
+    a.step(53)
+    for _ in range(53):
+        b.step(1)
+    assert a.steps_done == b.steps_done == 54
+    assert torch.equal(a.populations(deviation=True), b.populations(deviation=True))
+    for g in (a, b):
+        g.set_force_uniform(-2e-5, 1e-5)
+    a.step(40)
+    for _ in range(40):
+        b.step(1)
+    assert torch.equal(a.populations(deviation=True), b.populations(deviation=True))
