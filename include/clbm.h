@@ -196,7 +196,10 @@ int clbm_init_equilibrium(clbm_ctx *ctx, const float *rho_dev, const float *u_de
  * a wall face), forms rho and u (Eq. 9), raw moments T = M f (Eq. A4),
  * central moments N(u) T (Eq. 4), relaxes them with S, T~eq and C
  * (Eqs. 5, A3, A5, A6), maps back with N(u)^-1 = N(-u) and M^-1 (Eq. 7) and
- * stores f*. Asynchronous. */
+ * stores f*. Asynchronous. For nsteps >= 32 with a static force and a storage
+ * format without stochastic rounding, the steps are replayed from a CUDA graph
+ * of 16 launches captured on first use (bit-identical results; the graph is
+ * dropped when the force changes). */
 int clbm_step(clbm_ctx *ctx, int64_t nsteps);
 
 /* Eq. 9 on the current state: rho_dev (N floats) and u_dev (3 x N floats);
