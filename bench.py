@@ -477,10 +477,25 @@ def run_gb300(args):
             dt = float(t.item())
         h2d = (rho_h.numel() + u_h.numel()) * 4
         d2h = (rho_o.numel() + u_o.numel()) * 4 + mom.numel() * 8
+        # the same field copies alone, outside the timed region: how much of the
+        # e2e time is the one-off host traffic
+        d_u = torch.empty((3,) + shape, dtype=torch.float32, device=dev)
+        c0, c1 = _events()
+        c2 = torch.cuda.Event(enable_timing=True)
+        c0.record()
+        d_u.copy_(u_h, non_blocking=True)
+        c1.record()
+        u_o.copy_(d_u, non_blocking=True)
+        c2.record()
+        torch.cuda.synchronize()
+        ub = u_h.numel() * 4
         e2e = {"value": ws * nodes * K / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / K,
                "d2h_bytes_per_step": d2h / K,
                "what": "clbm_run_host: pinned host rho,u -> init -> K steps, each step's FP64 mass/momentum "
-                       "sums (formed in the step kernel) copied back, final rho,u read back"}
+                       "sums (formed in the step kernel) copied back, final rho,u read back",
+               "h2d_gbs": ub / (c0.elapsed_time(c1) * 1e-3) / 1e9, "d2h_gbs": ub / (c1.elapsed_time(c2) * 1e-3) / 1e9,
+               "ms_total": dt * 1e3}
+        del d_u
         lat_e.close()
 
     variants = None
