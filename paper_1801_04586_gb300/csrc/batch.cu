@@ -437,6 +437,7 @@ int clbm_batch_init_equilibrium(clbm_batch *b) {
 
 int clbm_batch_step(clbm_batch *b, int64_t nsteps, int32_t mode) {
     if (!b || nsteps < 0 || mode < 0 || mode > 2) return bfail(CLBM_ERR_ARG, "clbm_batch_step: bad argument");
+    Range range("clbm_batch_step");
     cudaError_t e = cudaSuccess;
     int64_t t = 0;
     if (mode == CLBM_BATCH_GRAPH && nsteps >= b->graph_steps) {

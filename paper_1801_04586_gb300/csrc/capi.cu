@@ -1,6 +1,7 @@
 // capi.cu -- the extern "C" boundary declared in include/clbm.h: context
 // lifetime, argument validation, A/B buffer bookkeeping and launches.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -41,6 +42,24 @@ struct StateHeader {
 }  // namespace
 
 int clbm::set_error(int code, const char *msg) { return fail(code, msg); }
+
+namespace {
+nvtxDomainHandle_t nvtx_domain() {
+    static nvtxDomainHandle_t d = nvtxDomainCreateA("clbm");
+    return d;
+}
+}  // namespace
+
+clbm::Range::Range(const char *name) {
+    nvtxEventAttributes_t a = {};
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = name;
+    nvtxDomainRangePushEx(nvtx_domain(), &a);
+}
+
+clbm::Range::~Range() { nvtxDomainRangePop(nvtx_domain()); }
 
 struct clbm_ctx {
     clbm_params p;
@@ -176,6 +195,7 @@ cudaError_t one_step(const clbm_ctx *c, const Launch &L, int cur, int64_t step) 
 // change from step to step: a static force and no stochastic dither key.
 int ensure_graph(clbm_ctx *c) {
     if (c->graph) return CLBM_OK;
+    Range range("clbm_step: graph capture");
     cudaError_t e = cudaSuccess;
     if (!c->cap_stream && (e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
         c->cap_stream = nullptr;
@@ -403,6 +423,7 @@ int clbm_init_equilibrium(clbm_ctx *c, const float *rho, const float *u) {
 int clbm_step(clbm_ctx *c, int64_t nsteps) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_step: null context");
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_step: nsteps < 0");
+    Range range("clbm_step");
     const Launch L = step_launch_of(c);
     auto advance = [&]() -> int {
         cudaError_t e = one_step(c, L, c->cur, c->steps_done);
@@ -609,6 +630,7 @@ int clbm_adjoint_segment(clbm_ctx *c, const void *ckpt, void *tape, int64_t k, f
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: D3Q19 only");
     if (c->aa) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: A/B pattern only");
     if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: cascaded model only");
+    Range range("clbm_adjoint_segment");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: FP32 storage only");
     if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_adjoint_segment: needs a static force (decay 0)");
     const Launch L = launch_of(c);
@@ -632,6 +654,7 @@ int clbm_adjoint_segment(clbm_ctx *c, const void *ckpt, void *tape, int64_t k, f
 int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nsteps, float *rho_out,
                   float *u_out, double *moments_h) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_run_host: null context");
+    Range range("clbm_run_host");
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_run_host: nsteps < 0");
     const Launch L = launch_of(c);
     cudaError_t e;

@@ -105,4 +105,13 @@ cudaError_t launch_moments27(int storage, const Launch &L, const void *src, cons
 // Record `msg` as the calling thread's last error (clbm_last_error) and return code.
 int set_error(int code, const char *msg);
 
+// NVTX range for the span of one entry point (shown by profilers that
+// record NVTX; a no-op otherwise), in the "clbm" domain.
+struct Range {
+    explicit Range(const char *name);
+    ~Range();
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+
 }  // namespace clbm

@@ -194,3 +194,18 @@ def test_long_steps_replay_graph_bit_identical(kw):
     for _ in range(40):
         b.step(1)
     assert torch.equal(a.populations(deviation=True), b.populations(deviation=True))
+
+
+def test_allocation_failure_is_reported():
+    """A real allocation failure, not a GPU fault: 2047 x 2047 x 512 nodes
+    (within the ABI's 2^31 - 1 limit) need 326 GB for the FP32 A/B pair, more
+    than the device holds. clbm_create returns CLBM_ERR_OOM, leaves nothing
+    allocated, and the next lattice works."""
+    from paper_1801_04586_gb300 import CLBMError, Lattice
+    with pytest.raises(CLBMError) as exc:
+        Lattice(2047, 2047, 512, 0.05, device=dev())
+    assert "status -2" in str(exc.value)
+    g, _ = make_pair(8, 8, 8, 0.05)
+    g.init_equilibrium()
+    g.step(3)
+    g.check()
