@@ -58,17 +58,6 @@ __device__ __forceinline__ long long to_fixed(float v) {
     return (long long)hi * 1048576ll + (long long)lo;
 }
 
-// Warp sum of the fixed-point value of v (to_fixed), exact, with two 32-bit
-// warp reductions (redux.sync) of its parts: 32 high parts (|hi| < 2^22) sum
-// below 2^27, 32 low parts (|lo| <= 2^19) below 2^24. All 32 lanes must call it.
-__device__ __forceinline__ long long warp_sum_fixed(float v) {
-    int hi, lo;
-    to_fixed_parts(v, hi, lo);
-    const int shi = __reduce_add_sync(0xffffffffu, hi);
-    const int slo = __reduce_add_sync(0xffffffffu, lo);
-    return (long long)shi * 1048576ll + (long long)slo;
-}
-
 // Block sum of fixed-point values q; thread 0's warp writes the K totals to
 // dst[0..K-1]. Every thread of the block calls it.
 template <int K>

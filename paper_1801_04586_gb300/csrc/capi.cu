@@ -75,8 +75,10 @@ struct clbm_ctx {
     int *d_flag;
     double *d_partials;
     float *d_io;               // clbm_run_host scratch (first use): 4 x N floats, then
-    double *d_mom;             //   4 doubles of sums and
+    double *d_mom;             //   kMomRing x 4 doubles of per-step sums and
     unsigned long long *d_acc; //   2 sets of kDiagSlots x 4 fixed-point accumulators (kept zero between steps)
+    cudaStream_t copy_stream;  // clbm_run_host: per-step sums copied back beside the steps (first use)
+    cudaEvent_t ev_step, ev_copy;
     int64_t steps_done;
     double gamma;         // force decay rate (clbm_set_force_decay)
     bool packed;          // step kernel with two nodes per thread (FP32x2 arithmetic)
@@ -105,6 +107,14 @@ ForceArgs force_at(const clbm_ctx *c, int64_t step) {
 }
 
 ForceArgs force_now(const clbm_ctx *c) { return force_at(c, c->steps_done); }
+
+// clbm_run_host's fused path: the totals of step t land in slot t % kMomRing
+// and are copied back on a second stream while the next steps run; every
+// kMomSync steps the step stream waits for the copies issued kMomSync steps
+// earlier, so no slot is overwritten before its copy (kMomRing >= 2 kMomSync).
+constexpr int kMomRing = 64;
+constexpr int kMomSync = 32;
+static_assert(kMomRing >= 2 * kMomSync, "slot reuse needs two sync periods");
 
 // Steps replayed from one captured CUDA graph (even, so a replay ends in the
 // phase it started from).
@@ -350,6 +360,12 @@ int clbm_destroy(clbm_ctx *c) {
     cudaStreamSynchronize(c->stream);
     drop_graph(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+        cudaEventDestroy(c->ev_step);
+        cudaEventDestroy(c->ev_copy);
+    }
     cudaFree(c->buf[0]);
     cudaFree(c->d_flag);
     if (c->d_io) cudaFree(c->d_io);
@@ -661,7 +677,8 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     if (!c->d_io) {
         const size_t io = (sizeof(float) * 4 * (size_t)c->n + 255) / 256 * 256;
         const size_t acc = sizeof(unsigned long long) * 2 * 4 * kDiagSlots;
-        const size_t bytes = io + 256 + acc;
+        const size_t mom = sizeof(double) * 4 * kMomRing;
+        const size_t bytes = io + mom + acc;
         void *p = nullptr;
         if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) {
             c->d_io = nullptr;
@@ -670,7 +687,7 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         }
         c->d_io = (float *)p;
         c->d_mom = (double *)((char *)p + io);
-        c->d_acc = (unsigned long long *)((char *)p + io + 256);
+        c->d_acc = (unsigned long long *)((char *)p + io + mom);
         if ((e = cudaMemsetAsync(c->d_acc, 0, acc, c->stream)) != cudaSuccess)
             return cuda_fail(e, "clbm_run_host: clear accumulators");
     }
@@ -683,6 +700,20 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     int rc = clbm_init_equilibrium(c, rho_h ? d_rho : nullptr, u_h ? d_u : nullptr);
     if (rc != CLBM_OK) return rc;
     const bool fused = c->q == 19 && !c->aa && c->model == CLBM_MODEL_CASCADED;
+    if (fused && moments_h && !c->copy_stream) {
+        cudaStream_t cs = nullptr;
+        cudaEvent_t e1 = nullptr, e2 = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&e2, cudaEventDisableTiming)) != cudaSuccess) {
+            if (cs) cudaStreamDestroy(cs);
+            if (e1) cudaEventDestroy(e1);
+            return cuda_fail(e, "clbm_run_host: copy stream");
+        }
+        c->copy_stream = cs;
+        c->ev_step = e1;
+        c->ev_copy = e2;
+    }
     for (int64_t t = 0; t < nsteps && !fused; ++t) {
         // D3Q27 and the in-place pattern: the sums of state t, then a plain step
         if (moments_h) {
@@ -696,30 +727,43 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         (e = cudaMemsetAsync(c->d_acc, 0, sizeof(unsigned long long) * 2 * 4 * kDiagSlots, c->stream)) !=
             cudaSuccess)
         return cuda_fail(e, "clbm_run_host: clear accumulators");
-    // The sums of step t - 1 land in d_mom during step t and are copied back
-    // after it. (Writing them from the kernel straight into pinned host memory
-    // made every step's kernel wait for that write: 9 us per step, more than
-    // the copy.)
+    // The sums of step t - 1 land in ring slot (t - 1) % kMomRing during step t
+    // and are copied back on copy_stream after it, beside the following
+    // steps. (Writing them from the kernel straight into pinned host memory
+    // made every step's kernel wait for that write: 9 us per step; a copy on
+    // the step stream held each next step for 5 us.)
     const double add0 = (double)c->n;
+    auto slot = [c](int64_t t) { return c->d_mom + 4 * (t % kMomRing); };
     for (int64_t t = 0; t < nsteps && fused; ++t) {
         if (moments_h) {
+            if (t % kMomSync == 0) {
+                // the copies issued up to kMomSync steps ago are done before slots are reused
+                e = cudaStreamWaitEvent(c->stream, c->ev_copy, 0);
+                if (e == cudaSuccess) e = cudaEventRecord(c->ev_copy, c->copy_stream);
+                if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: copy sync");
+            }
             // fused step: exact sums of the state it pulls (state t) into slot set t % 2; its block 0
             // first drains set (t - 1) % 2 into the totals of state t - 1
             DiagSums d;
             d.acc = c->d_acc + (t & 1) * 4 * kDiagSlots;
             d.acc_prev = t > 0 ? c->d_acc + ((t - 1) & 1) * 4 * kDiagSlots : nullptr;
-            d.out_prev = c->d_mom;
+            d.out_prev = t > 0 ? slot(t - 1) : nullptr;
             d.add0 = add0;
             e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),
                                  c->d_flag, d, step_key(c->steps_done));
+            if (e == cudaSuccess && t == nsteps - 1)  // the last step's set
+                e = launch_drain4(c->d_acc + (t & 1) * 4 * kDiagSlots, slot(t), add0, c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_step, c->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->ev_step, 0);
             if (e == cudaSuccess && t > 0)
-                e = cudaMemcpyAsync(moments_h + 4 * (t - 1), c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
-                                    c->stream);
-            if (e == cudaSuccess && t == nsteps - 1) {  // the last step's set
-                e = launch_drain4(c->d_acc + (t & 1) * 4 * kDiagSlots, c->d_mom, add0, c->stream);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(moments_h + 4 * t, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost,
-                                        c->stream);
+                e = cudaMemcpyAsync(moments_h + 4 * (t - 1), slot(t - 1), sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                                    c->copy_stream);
+            if (e == cudaSuccess && t == nsteps - 1)
+                e = cudaMemcpyAsync(moments_h + 4 * t, slot(t), sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                                    c->copy_stream);
+            if (e == cudaSuccess && t == nsteps - 1) {  // the step stream reuses slot 0 below
+                e = cudaEventRecord(c->ev_copy, c->copy_stream);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_copy, 0);
             }
         } else {
             e = step19(c, step_launch_of(c), c->buf[c->cur], c->buf[c->cur ^ 1], force_now(c),

@@ -1,14 +1,17 @@
 // step_diag.cu -- the fused step kernel with in-kernel conservation sums, for
 // jobs that read mass and momentum back after every step.
 //
-// Same per-node work as k_step (pull, collide, store). In addition every
-// warp sums the Eq. 9 density deviation and momentum of the state it pulls
-// (the state before the step) as exact fixed-point integers (block_reduce.cuh),
-// so the totals equal clbm_reduce_moments' bit for bit. Lane 0 of each warp
-// adds its 4 sums into one of kDiagSlots accumulator slots with 64-bit
-// integer atomics: integer addition is exact and order-independent, so the
+// Same per-node work as k_step (pull, collide, store), for kDiagZ nodes per
+// thread along z. In addition every warp sums the Eq. 9 density deviation and
+// momentum of the state it pulls (the state before the step) as exact
+// fixed-point integers (block_reduce.cuh), so the totals equal
+// clbm_reduce_moments' bit for bit. Each thread adds the fixed-point parts of
+// its nodes in registers; then two warp reductions per quantity and lane 0's
+// four 64-bit integer atomics into one of kDiagSlots accumulator slots cover
+// 32 x kDiagZ nodes. Integer addition is exact and order-independent, so the
 // totals do not depend on scheduling, and no block barrier holds the warps of
-// a block together. The slots come in two sets used by alternate steps:
+// a block together. (With one node per thread the reductions and atomics
+// cost 6 % of the step at 256^3; with four they are lost in the memory time.) The slots come in two sets used by alternate steps:
 // block 0 of each step first drains the set the previous step filled (adds
 // the slots, writes the FP64 totals, clears the set), so no separate launch
 // sits between steps. k_drain4 drains the last step's set.
@@ -52,31 +55,45 @@ __device__ __forceinline__ void force_diag(const ForceArgs &F, const Geom &g, in
     fz *= F.scale;
 }
 
+// Nodes per thread along z. The per-thread part sums stay in 32 bits:
+// kDiagZ x 32 high parts below 2^22 sum below 2^29.
+constexpr int kDiagZ = 4;
+
 template <typename S, int FM, bool WALLS>
-__global__ void __launch_bounds__(512) k_step_diag(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r,
-                                                   ForceArgs F, int *__restrict__ flag,
-                                                   unsigned long long *__restrict__ acc,
-                                                   unsigned long long *__restrict__ acc_prev, double *out_prev,
-                                                   double add0, uint32_t key) {
+__global__ void __launch_bounds__(512, 2) k_step_diag(const S *__restrict__ src, S *__restrict__ dst, Geom g,
+                                                      Rates r, ForceArgs F, int *__restrict__ flag,
+                                                      unsigned long long *__restrict__ acc,
+                                                      unsigned long long *__restrict__ acc_prev, double *out_prev,
+                                                      double add0, uint32_t key) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int z0 = blockIdx.z * kDiagZ;
     if (acc_prev && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) drain_slots(acc_prev, out_prev, add0);
-    float q[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // to_fixed(0) = 0
+    int hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};  // fixed-point parts of the sums (to_fixed_parts)
     if (x < g.nx && y < g.ny) {  // no early return: every lane joins the warp sums
-        uint32_t off[kQ];
-        int pop[kQ];
-        pull_sources<WALLS>(g, x, y, z, off, pop);
-        float h[kQ];
+#pragma unroll 1
+        for (int z = z0; z < z0 + kDiagZ && z < g.nz; ++z) {
+            uint32_t off[kQ];
+            int pop[kQ];
+            pull_sources<WALLS>(g, x, y, z, off, pop);
+            float h[kQ];
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
-        float fx, fy, fz;
-        force_diag<FM>(F, g, z, off[0], fx, fy, fz);
-        float3 j;
-        const float drho = collide(h, fx, fy, fz, r, &j);
-        if (!(fabsf(drho) < 0.9f)) *flag = 1;
-        store_node<S>(dst + off[0], g.stride, h, off[0], key);
-        q[0] = drho; q[1] = j.x; q[2] = j.y; q[3] = j.z;
+            for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
+            float fx, fy, fz;
+            force_diag<FM>(F, g, z, off[0], fx, fy, fz);
+            float3 j;
+            const float drho = collide(h, fx, fy, fz, r, &j);
+            if (!(fabsf(drho) < 0.9f)) *flag = 1;
+            store_node<S>(dst + off[0], g.stride, h, off[0], key);
+            const float q[4] = {drho, j.x, j.y, j.z};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                int a, b;
+                to_fixed_parts(q[k], a, b);
+                hi[k] += a;
+                lo[k] += b;
+            }
+        }
     }
     // blockDim.x is a multiple of 32, so a warp is 32 threads of one row
     const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -84,7 +101,9 @@ __global__ void __launch_bounds__(512) k_step_diag(const S *__restrict__ src, S 
     const unsigned w = (threadIdx.x + blockDim.x * threadIdx.y) >> 5;
     long long s[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) s[k] = warp_sum_fixed(q[k]);
+    for (int k = 0; k < 4; ++k)
+        s[k] = (long long)__reduce_add_sync(0xffffffffu, hi[k]) * 1048576ll +
+               (long long)__reduce_add_sync(0xffffffffu, lo[k]);
     if ((threadIdx.x & 31) == 0) {
         unsigned long long *d = acc + 4 * ((b * wpb + w) & (kDiagSlots - 1));
 #pragma unroll
@@ -95,12 +114,13 @@ __global__ void __launch_bounds__(512) k_step_diag(const S *__restrict__ src, S 
 template <typename S, int FM>
 static cudaError_t diag_walls(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
                               int *flag, const DiagSums &d, uint32_t key) {
+    const dim3 grid(L.grid.x, L.grid.y, (L.grid.z + kDiagZ - 1) / kDiagZ);
     if (L.g.walls)
-        k_step_diag<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, d.acc,
-                                                                   d.acc_prev, d.out_prev, d.add0, key);
+        k_step_diag<S, FM, true><<<grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, d.acc,
+                                                                 d.acc_prev, d.out_prev, d.add0, key);
     else
-        k_step_diag<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag,
-                                                                    d.acc, d.acc_prev, d.out_prev, d.add0, key);
+        k_step_diag<S, FM, false><<<grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, d.acc,
+                                                                  d.acc_prev, d.out_prev, d.add0, key);
     return cudaGetLastError();
 }
 
