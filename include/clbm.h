@@ -253,7 +253,8 @@ int clbm_load_state(clbm_ctx *ctx, const void *host_buf, size_t bytes);
  * step k. With the cascaded collision, the A/B pattern and D3Q19 they are
  * formed inside step k+1's kernel from the state it pulls (exact fixed-point
  * warp sums, no extra pass over the populations), totalled by the next
- * step's launch and copied back asynchronously. Otherwise they come from one
+ * step's launch and copied back on a second stream of the context while
+ * the following steps run. Otherwise they come from one
  * clbm_reduce_moments pass before each step, copied back asynchronously.
  * The last comes from one reduction after the final step. The call synchronises once, at the end, then returns
  * CLBM_ERR_UNSTABLE if any mass sum is non-finite or the instability flag is
