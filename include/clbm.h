@@ -44,6 +44,7 @@ extern "C" {
 #define CLBM_ERR_CUDA     -3  /* a CUDA runtime call or kernel launch failed */
 #define CLBM_ERR_UNSTABLE -4  /* a node's density left (0.1, 1.9) or became non-finite */
 #define CLBM_ERR_STATE    -5  /* call not valid in the context's current state */
+#define CLBM_ERR_TIMEOUT  -6  /* a step kernel's wait for its staged copies gave up (about 2 s); the state is invalid */
 
 /* ---- storage formats of the populations (deviations f - w_i) ---- */
 #define CLBM_STORAGE_F32     0
@@ -104,11 +105,15 @@ extern "C" {
  * walls: CLBM_WALL_* bits; an axis without a bit is periodic.
  * block_x, block_y: CUDA block shape of the step kernel (block_x a multiple
  *      of 32, block_x*block_y <= 512); 0 selects the built-in default.
- * variant: step kernel form. 0 or 1: one node per thread (the default); 2:
- *      two nodes per thread (x and x + block_x), collided together with the
- *      FP32x2 instructions (D3Q19 only; measured slower on GB300 for every
- *      storage format, kept as an option). The forms give the same results
- *      up to the rounding of fused operations.
+ * variant: step kernel form. 0 (the default): D3Q19 A/B steps with 16-bit
+ *      storage stage the pulled rows in shared memory with bulk asynchronous
+ *      copies where the geometry allows (nx <= 1024, nx a multiple of 8),
+ *      one node per thread otherwise; 1: always one node per thread,
+ *      plain loads (block_x, block_y apply); 2: two nodes per thread (x and
+ *      x + block_x), collided together with the FP32x2 instructions (D3Q19
+ *      only; measured slower on GB300 for every storage format, kept as an
+ *      option). Forms 0 and 1 give bit-identical results; form 2 the same up
+ *      to the rounding of fused operations.
  * lattice: 19 (or 0): D3Q19 of Appendix A (Eqs. A1-A6); 27: D3Q27 of Sec. II
  *      (velocities Eq. 1, moments Eq. 12, S Eq. 13, T~eq Eq. 15, C Eq. 16).
  *      D3Q27 runs the one-node-per-thread form (blocks of at most 256
@@ -144,7 +149,7 @@ typedef struct clbm_info {
     int32_t pattern;          /* CLBM_PATTERN_AB or CLBM_PATTERN_AA */
     int32_t buffers;          /* population buffers held: 2 (A/B) or 1 (AA) */
     int32_t model;            /* CLBM_MODEL_* */
-    int32_t reserved;
+    int32_t staged;           /* 1: steps stage the pulled rows in shared memory (variant 0, see clbm_params) */
 } clbm_info;
 
 typedef struct clbm_ctx clbm_ctx;

@@ -17,6 +17,7 @@ CLBM_ERR_OOM = -2
 CLBM_ERR_CUDA = -3
 CLBM_ERR_UNSTABLE = -4
 CLBM_ERR_STATE = -5
+CLBM_ERR_TIMEOUT = -6
 
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "f16sr": 3, "bf16sr": 4}
 PATTERN = {"ab": 0, "aa": 1}
@@ -55,7 +56,7 @@ class Info(ctypes.Structure):
                 ("steps_done", ctypes.c_int64), ("storage", ctypes.c_int32), ("block_x", ctypes.c_int32),
                 ("block_y", ctypes.c_int32), ("s2", ctypes.c_double), ("nodes_per_thread", ctypes.c_int32),
                 ("q", ctypes.c_int32), ("pattern", ctypes.c_int32), ("buffers", ctypes.c_int32),
-                ("model", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("model", ctypes.c_int32), ("staged", ctypes.c_int32)]
 
 
 P = ctypes.c_void_p

@@ -82,6 +82,7 @@ struct clbm_ctx {
     int64_t steps_done;
     double gamma;         // force decay rate (clbm_set_force_decay)
     bool packed;          // step kernel with two nodes per thread (FP32x2 arithmetic)
+    bool staged;          // A/B D3Q19 step with rows staged in shared memory by bulk copies (variant 0)
     int q;                // 19 (Appendix A) or 27 (Sec. II)
     bool aa;              // in-place (AA) pattern: one population buffer, step kind by parity
     int model;            // CLBM_MODEL_*
@@ -134,6 +135,7 @@ Launch launch_of(const clbm_ctx *c) {
     L.grid = dim3((c->g.nx + c->block.x - 1) / c->block.x, (c->g.ny + c->block.y - 1) / c->block.y, c->g.nz);
     L.stream = c->stream;
     L.packed = false;
+    L.staged = c->staged;
     // A/B: the pull map; AA: natural slots after an even number of steps, the
     // odd step's swapped pull map after an odd number.
     L.map = c->aa ? ((c->steps_done & 1) ? 2 : 1) : 0;
@@ -241,6 +243,7 @@ const char *clbm_status_string(int status) {
         case CLBM_ERR_CUDA: return "CUDA error";
         case CLBM_ERR_UNSTABLE: return "unstable: density out of range or non-finite";
         case CLBM_ERR_STATE: return "invalid state";
+        case CLBM_ERR_TIMEOUT: return "timeout: a staged copy did not complete";
         default: return "unknown status";
     }
 }
@@ -311,6 +314,7 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     c->gamma = 0.0;
     c->q = q;
     c->packed = q == 19 && p->variant == 2;
+    c->staged = q == 19 && p->variant == 0 && p->pattern != CLBM_PATTERN_AA;
     c->aa = p->pattern == CLBM_PATTERN_AA;
     c->model = p->model;
     c->rates27.om2 = c->rates.om2;
@@ -388,7 +392,7 @@ int clbm_get_info(const clbm_ctx *c, clbm_info *info) {
     info->pattern = c->aa ? CLBM_PATTERN_AA : CLBM_PATTERN_AB;
     info->buffers = c->aa ? 1 : 2;
     info->model = c->model;
-    info->reserved = 0;
+    info->staged = c->staged && step_staged(c->g, c->elem, c->buf[0]) ? 1 : 0;
     return CLBM_OK;
 }
 
@@ -527,6 +531,8 @@ int clbm_check(clbm_ctx *c, int clear) {
         e = cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "clbm_check");
     }
+    if (h & 2)
+        return fail(CLBM_ERR_TIMEOUT, "clbm_check: a staged step's bulk copy did not complete; the state is invalid");
     if (h) return fail(CLBM_ERR_UNSTABLE, "clbm_check: a node's density left (0.1, 1.9) or became non-finite");
     return CLBM_OK;
 }

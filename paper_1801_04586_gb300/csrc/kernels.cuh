@@ -25,6 +25,8 @@ struct Launch {
     dim3 block, grid;  // grid of the one-node-per-thread kernels
     cudaStream_t stream;
     bool packed;       // launch_step: two nodes per thread (grid.x halved)
+    bool staged;       // launch_step (A/B, one node per thread): rows staged by bulk copies where they apply
+                       // (step_tma.cuh)
     int map;           // state kernels: slots of the post-streaming state (0 A/B pull map,
                        // 1 in-place pattern after even steps, 2 after odd steps)
 };
@@ -33,6 +35,9 @@ struct Launch {
 // (CLBM_STORAGE_*). key: per-step dither key (stochastic formats).
 cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
                         const ForceArgs &F, int *flag, uint32_t key);
+// Whether an A/B step from a state buffer at src (elem bytes per value) runs
+// the shared-memory staged kernel (step_tma.cuh) when the launch asks for it.
+bool step_staged(const Geom &g, size_t elem, const void *src);
 // In-place (AA) pattern: one step on the single population array f; odd
 // selects the odd step kind (step.cu).
 cudaError_t launch_step_aa(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,

@@ -84,6 +84,11 @@ cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst
     }
 }
 
+bool step_staged(const Geom &g, size_t elem, const void *src) {
+    TilePlan p;
+    return tile_plan(g, elem, src, 0, p);
+}
+
 cudaError_t launch_step_aa(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,
                            uint32_t key, bool odd) {
     return launch_step_aa_with<Cascaded>(storage, L, f, r, F, flag, key, odd);

@@ -41,6 +41,12 @@ __device__ __forceinline__ void force_at(const ForceArgs &F, const Geom &g, int 
     fz *= F.scale;
 }
 
+}  // namespace clbm
+
+#include "step_tma.cuh"
+
+namespace clbm {
+
 template <typename C, typename S, int FM, bool WALLS>
 __global__ void __launch_bounds__(512) k_step(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r,
                                               ForceArgs F, int *__restrict__ flag, uint32_t key) {
@@ -114,6 +120,10 @@ __global__ void __launch_bounds__(512) k_step_aa(S *f, Geom g, Rates r, ForceArg
 template <typename C, typename S, int FM>
 static cudaError_t step_walls_t(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
                                 int *flag, uint32_t key) {
+    if constexpr (sizeof(S) == 2) {  // 16-bit storage: rows staged in shared memory where they apply
+        cudaError_t e = cudaSuccess;
+        if (L.staged && launch_step_tma<C, S, FM>(L, src, dst, r, F, flag, key, e)) return e;
+    }
     if (L.g.walls)
         k_step<C, S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
     else

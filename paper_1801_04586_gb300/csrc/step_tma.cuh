@@ -1,0 +1,383 @@
+// step_tma.cuh -- the D3Q19 A/B step for 16-bit storage with the pulled rows
+// staged in shared memory by bulk asynchronous copies (cp.async.bulk: the TMA
+// unit), templated on the collision like k_step.
+//
+// Why: k_step with 16-bit storage is bound by instruction issue, not DRAM:
+// a node's 19 loads each need 64-bit address arithmetic (pull offsets with
+// periodic wrap), and each load holds a register until its data arrive, so
+// the warps alternate between waiting and computing. Here the TMA unit moves
+// whole rows into shared memory a tile ahead of the threads, which read
+// their 19 values from shared memory at three addresses (x - 1, x, x + 1)
+// plus constant offsets, collide and store exactly as k_step does: the
+// results are bit-identical, with a tenth fewer instructions per node. FP32
+// storage stays on k_step, which already runs at the DRAM bound.
+//
+// Tile: `rows` consecutive x-rows (y0 .. y0 + rows - 1) of one z-plane, at
+// most kTileNodes nodes. Under the pull map of Eq. 8, population i of the
+// tile's nodes comes from the same rows shifted by (-e_iy, -e_iz), each read
+// at x - e_ix. The y/z shift is applied when copying (one or two contiguous
+// runs of rows per population, two where the shift wraps around a periodic
+// face); the x shift, with its periodic wrap, when reading shared memory.
+// Every source row of every population is copied once per step, so the DRAM
+// traffic is the algorithmic 2 x 19 values per node.
+//
+// Walls (halfway bounce-back): a source row beyond a wall face is not
+// copied; the nodes that would pull from it, and the nodes at an x wall, read
+// their own opposite population from global memory instead.
+//
+// Pipeline: a persistent grid; block b walks tiles b, b + gridDim.x, ... with
+// kTmaStages shared buffers and one mbarrier each. A warp arms a buffer's
+// barrier with the tile's byte count and issues its copies (lane i:
+// population i). Every warp waits on the barrier of its next tile, computes
+// its nodes and counts itself done with the buffer; the last warp to finish
+// refills the buffer with the tile kTmaStages ahead. There is no block
+// barrier in the loop, so warps drift apart by up to kTmaStages tiles instead
+// of waiting for the slowest. Every wait is bounded (kWaitCycles); on expiry
+// the block sets bit 1 of the flag (reported as CLBM_ERR_TIMEOUT), its warps
+// leave the loop, and one thread waits, again bounded, for the copies still
+// in flight before the block ends.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace clbm {
+
+constexpr int kTmaThreads = 512;   // threads per block (two blocks per SM)
+constexpr int kTmaStages = 2;      // shared buffers per block
+constexpr int kTileNodes = 1024;   // nodes per tile, and the element pitch of a population's rows in a buffer:
+                                   // a buffer of 19 populations of 16-bit values is 38 KB, so two blocks of
+                                   // two buffers fit an SM
+constexpr long long kWaitCycles = 4000000000ll;  // bound of one barrier wait, about 2 s at 2 GHz
+
+struct TilePlan {
+    int rows;       // x-rows per tile
+    int tiles_y;    // tiles per z-plane
+    int ntiles;     // tiles_y * nz
+    int dz, dy;     // a block's step of gridDim.x tiles as (planes, tiles) : gridDim.x = dz tiles_y + dy
+    uint32_t rdiv;  // ceil(2^32 / nx): the row of tile node n is umulhi(n, rdiv), exact for n, nx <= 1024
+};
+
+// Bytes of one buffer: kQ x kTileNodes stored values, then the force on the
+// tile's nodes: for a field its three components (3 x kTileNodes floats),
+// for a z-profile the tile plane's three values.
+template <typename S, int FM>
+__host__ __device__ constexpr size_t stage_bytes() {
+    return (size_t)kQ * kTileNodes * sizeof(S) +
+           (FM == kForceField ? 3 * kTileNodes * sizeof(float) : (FM == kForceProfileZ ? 16 : 0));
+}
+
+// Shared memory of one block: the barriers, then kTmaStages buffers.
+template <typename S, int FM>
+constexpr size_t tile_smem_bytes() {
+    return 128 + kTmaStages * stage_bytes<S, FM>();
+}
+
+// Whether the staged step applies, and its plan for a grid of `grid` blocks
+// (0: eligibility only). The copies need 16-byte aligned rows (nx x elem and
+// stride x elem multiples of 16, src 16-byte aligned) and a row must fit a
+// tile.
+inline bool tile_plan(const Geom &g, size_t elem, const void *src, int grid, TilePlan &p) {
+    const int tn = kTileNodes;
+    if (elem != 2) return false;  // FP32 steps stay on k_step, which already runs at the DRAM bound
+    if (g.nx > tn || ((size_t)g.nx * elem) % 16 != 0 || ((size_t)g.stride * elem) % 16 != 0 ||
+        ((uintptr_t)src & 15u) != 0)
+        return false;
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    if (n >= (int64_t(1) << 31)) return false;
+    p.rows = g.ny < tn / g.nx ? g.ny : tn / g.nx;
+    p.tiles_y = (g.ny + p.rows - 1) / p.rows;
+    p.ntiles = p.tiles_y * g.nz;
+    p.dz = grid / p.tiles_y;
+    p.dy = grid - p.dz * p.tiles_y;
+    p.rdiv = 0xffffffffu / (uint32_t)g.nx + 1u;
+    return true;
+}
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Make the initialised barriers and the generic-proxy use of the buffers
+// visible to the asynchronous proxy (the bulk copies).
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for the phase of `parity` to complete; false after about kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// e_iy + 1 and e_iz + 1 of population i in two bits each.
+__host__ __device__ constexpr uint64_t pack_shift(int axis) {
+    uint64_t t = 0;
+    for (int i = 0; i < kQ; ++i) t |= (uint64_t)((axis == 1 ? ey19(i) : ez19(i)) + 1) << (2 * i);
+    return t;
+}
+constexpr uint64_t kEyBits = pack_shift(1), kEzBits = pack_shift(2);
+
+// Arm `bar` with the tile's byte count and copy its source rows into the
+// buffer `stage`: population i's rows land at element i * kTileNodes, slot
+// row r at r * nx; after the populations, the force: for a field, component
+// c of the tile's own rows at float c * kTileNodes (bulk copies), for a
+// z-profile the plane's three values (plain shared stores). Called by all 32
+// lanes of one warp; lane i < 19 handles population i, lanes 19-21 the force
+// components.
+template <typename S, int FM, bool WALLS>
+__device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, const Geom &g, const TilePlan &p,
+                                           int t, unsigned char *stage, uint64_t *bar, int lane) {
+    const int z = t / p.tiles_y;
+    const int y0 = (t - z * p.tiles_y) * p.rows;
+    const int rows = min(p.rows, g.ny - y0);
+    int src_a = 0, slot_a = 0, n_a = 0, src_b = 0, slot_b = 0, n_b = 0, zs = 0;
+    if (lane < kQ) {
+        const int ey = (int)((kEyBits >> (2 * lane)) & 3u) - 1, ez = (int)((kEzBits >> (2 * lane)) & 3u) - 1;
+        const bool wy = WALLS && (g.walls & 2u), wz = WALLS && (g.walls & 4u);
+        zs = z - ez;
+        bool plane = true;
+        if (zs < 0 || zs >= g.nz) {
+            if (wz) plane = false;              // beyond a z wall: bounce-back, read from global
+            else zs = zs < 0 ? zs + g.nz : zs - g.nz;
+        }
+        if (plane) {
+            const int start = y0 - ey;
+            if (start < 0) {                    // first slot row from row ny - 1 (periodic) or none (wall)
+                if (!wy) { src_a = g.ny - 1; slot_a = 0; n_a = 1; }
+                src_b = 0; slot_b = 1; n_b = rows - 1;
+            } else if (start + rows > g.ny) {   // last slot row from row 0 (periodic) or none (wall)
+                src_a = start; slot_a = 0; n_a = g.ny - start;
+                if (!wy) { src_b = 0; slot_b = g.ny - start; n_b = rows - (g.ny - start); }
+                } else {
+                src_a = start; slot_a = 0; n_a = rows;
+            }
+        }
+    }
+    const bool force_lane = FM == kForceField && lane >= kQ && lane < kQ + 3;
+    const uint32_t row_bytes = (uint32_t)g.nx * (uint32_t)sizeof(S);
+    const uint32_t bytes = force_lane ? (uint32_t)rows * (uint32_t)g.nx * 4u : (uint32_t)(n_a + n_b) * row_bytes;
+    const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
+    if (FM == kForceProfileZ && lane >= kQ && lane < kQ + 3) {
+        // the plane's force: a plain shared store, published to the waiting warps by the arrive below
+        float *fdst = reinterpret_cast<float *>(stage + (size_t)kQ * kTileNodes * sizeof(S));
+        fdst[lane - kQ] = __ldg(F.profile + (size_t)(lane - kQ) * g.nz + z);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive_expect_tx(bar, total);
+    __syncwarp();
+    if (lane < kQ) {
+        const S *pop = src + (size_t)lane * g.stride + (size_t)zs * g.ny * g.nx;
+        S *dst = reinterpret_cast<S *>(stage) + lane * kTileNodes;
+        if (n_a > 0)
+            bulk_copy_g2s(dst + slot_a * g.nx, pop + (size_t)src_a * g.nx, (uint32_t)n_a * row_bytes, bar);
+        if (n_b > 0)
+            bulk_copy_g2s(dst + slot_b * g.nx, pop + (size_t)src_b * g.nx, (uint32_t)n_b * row_bytes, bar);
+    } else if (force_lane) {
+        const int c = lane - kQ;
+        float *dst = reinterpret_cast<float *>(stage + (size_t)kQ * kTileNodes * sizeof(S)) + c * kTileNodes;
+        bulk_copy_g2s(dst, F.field + (size_t)c * F.n + ((size_t)z * g.ny + y0) * g.nx, bytes, bar);
+    }
+}
+
+// Collide and store the nodes of the tile of rows y0 .. y0 + rows - 1 of
+// plane z from its staged rows.
+template <typename C, typename S, int FM, bool WALLS>
+__device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__restrict__ dst, const Geom &g,
+                                             const Rates &r, const ForceArgs &F, int *flag, uint32_t key,
+                                             const TilePlan &p, int z, int y0, const unsigned char *buf,
+                                             float tfx, float tfy, float tfz) {
+    const S *stage = reinterpret_cast<const S *>(buf);
+    const float *fst = reinterpret_cast<const float *>(buf + (size_t)kQ * kTileNodes * sizeof(S));
+    constexpr int TN = kTileNodes;
+    const int rows = min(p.rows, g.ny - y0);
+    const uint32_t nx = (uint32_t)g.nx;
+    const uint32_t tile = (uint32_t)rows * nx;
+    const uint32_t base = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y0) * nx;
+    for (uint32_t n = threadIdx.x; n < tile; n += kTmaThreads) {
+        const uint32_t rr = __umulhi(n, p.rdiv);
+        const uint32_t x = n - rr * nx;
+        const uint32_t self = base + n;
+        // slots of x - 1 and x + 1 in the node's staged row, periodic in x
+        const uint32_t sm = x == 0 ? n + nx - 1u : n - 1u;
+        const uint32_t sp = x == nx - 1u ? n + 1u - nx : n + 1u;
+        float h[kQ];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const uint32_t j = ex19(i) > 0 ? sm : (ex19(i) < 0 ? sp : n);
+            h[i] = Codec<S>::load_plain(stage + i * TN + j);
+        }
+        if (WALLS) {
+            const int y = y0 + (int)rr;
+            const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
+            const bool xl = wx && x == 0, xh = wx && x == nx - 1u;
+            const bool yl = wy && y == 0, yh = wy && y == g.ny - 1;
+            const bool zl = wz && z == 0, zh = wz && z == g.nz - 1;
+            // nodes next to a wall are few: the warps without one skip this
+            if (__any_sync(__activemask(), xl || xh || yl || yh || zl || zh)) {
+                const bool bb[kQ] = {false,
+                                     xl, xh, yl, yh, zl, zh,
+                                     xl || yl, xh || yl, xl || yh, xh || yh,
+                                     xl || zl, xh || zl, xl || zh, xh || zh,
+                                     yl || zl, yh || zl, yl || zh, yh || zh};
+#pragma unroll
+                for (int i = 1; i < kQ; ++i)
+                    if (bb[i]) h[i] = Codec<S>::load(src + (size_t)opposite(i) * g.stride + self);
+            }
+        }
+        float fx = tfx, fy = tfy, fz = tfz;
+        if (FM == kForceField) {  // the staged field, scaled as force_at does
+            fx = fst[n] * F.scale;
+            fy = fst[TN + n] * F.scale;
+            fz = fst[2 * TN + n] * F.scale;
+        } else if (FM == kForceProfileZ) {
+            fx = fst[0] * F.scale;
+            fy = fst[1] * F.scale;
+            fz = fst[2] * F.scale;
+        }
+        const float drho = C::run(h, fx, fy, fz, r);
+        if (!(fabsf(drho) < 0.9f)) atomicOr(flag, 1);
+        store_node<S>(dst + self, g.stride, h, self, key);
+    }
+}
+
+template <typename C, typename S, int FM, bool WALLS>
+__global__ void __launch_bounds__(kTmaThreads, 2)
+    k_step_tma(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r, ForceArgs F, int *__restrict__ flag,
+               uint32_t key, TilePlan p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);     // [stages]: copies of the buffer's tile arrived
+    int *done = reinterpret_cast<int *>(smem + 64);         // [stages]: warps finished with the buffer's tile
+    int *issued = reinterpret_cast<int *>(smem + 96);       // [stages]: tiles copied into the buffer so far
+    volatile int *abort = reinterpret_cast<volatile int *>(smem + 124);
+    unsigned char *buf = smem + 128;
+    constexpr size_t SB = stage_bytes<S, FM>();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTmaStages; ++s) {
+            mbar_init(&bar[s], 1);
+            done[s] = 0;
+            issued[s] = 0;
+        }
+        *abort = 0;
+        fence_proxy_async();
+    }
+    __syncthreads();
+    if (warp == 0)
+        for (int k = 0; k < kTmaStages; ++k) {
+            const int t = blockIdx.x + k * gridDim.x;
+            if (t < p.ntiles) {
+                issue_tile<S, FM, WALLS>(src, F, g, p, t, buf + k * SB, &bar[k], lane);
+                if (lane == 0) issued[k] = 1;
+            }
+        }
+    // No block barrier inside the loop: each warp takes the tiles in order,
+    // waiting only for their copies; the last warp to finish with a buffer
+    // refills it with the tile kTmaStages ahead.
+    int z = blockIdx.x / p.tiles_y, yt = blockIdx.x - z * p.tiles_y;  // tile t = z tiles_y + yt
+    int k = 0;
+    for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++k) {
+        const int s = k & (kTmaStages - 1);
+        float tfx = 0.0f, tfy = 0.0f, tfz = 0.0f;  // a uniform force (the others come staged)
+        if (FM == kForceUniform) force_at<FM>(F, g, z, 0u, tfx, tfy, tfz);
+        const bool ok = mbar_wait(&bar[s], (uint32_t)(k / kTmaStages) & 1u);
+        if (!ok || *abort) {
+            if (!ok && lane == 0) {
+                *abort = 1;
+                atomicOr(flag, 2);
+            }
+            break;
+        }
+        compute_tile<C, S, FM, WALLS>(src, dst, g, r, F, flag, key, p, z, yt * p.rows, buf + s * SB, tfx, tfy, tfz);
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence_block();  // this warp's reads of the buffer precede the count
+            last = atomicAdd(&done[s], 1) == nwarps - 1;
+            if (last) done[s] = 0;
+        }
+        if (__shfl_sync(0xffffffffu, last, 0)) {
+            const int tn = t + kTmaStages * gridDim.x;
+            if (tn < p.ntiles) {
+                fence_proxy_async();  // the buffer's reads by every warp precede the copies into it
+                issue_tile<S, FM, WALLS>(src, F, g, p, tn, buf + s * SB, &bar[s], lane);
+                if (lane == 0) ++issued[s];
+            }
+        }
+        z += p.dz;
+        yt += p.dy;
+        if (yt >= p.tiles_y) {
+            yt -= p.tiles_y;
+            ++z;
+        }
+    }
+    __syncthreads();
+    if (*abort && threadIdx.x == 0) {
+        // a copy did not arrive in time: before the block's shared memory is
+        // released, wait (bounded) for the last copy issued into each buffer
+        for (int s = 0; s < kTmaStages; ++s)
+            if (issued[s] > 0) mbar_wait(&bar[s], (uint32_t)(issued[s] - 1) & 1u);
+    }
+}
+
+// Launch the staged step if it applies to this geometry and buffer; returns
+// false (nothing launched) otherwise.
+template <typename C, typename S, int FM>
+bool launch_step_tma(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F, int *flag,
+                     uint32_t key, cudaError_t &err) {
+    TilePlan p;
+    if (!tile_plan(L.g, sizeof(S), src, 0, p)) return false;
+    if (FM == kForceField && ((((uintptr_t)F.field) & 15u) != 0 || (F.n & 3) != 0)) return false;
+    int dev = 0, sms = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return true;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return true;
+    const size_t smem = tile_smem_bytes<S, FM>();
+    const int grid = p.ntiles < 2 * sms ? p.ntiles : 2 * sms;
+    tile_plan(L.g, sizeof(S), src, grid, p);
+    if (L.g.walls) {
+        auto kern = k_step_tma<C, S, FM, true>;
+        if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return true;
+        kern<<<grid, kTmaThreads, smem, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key, p);
+    } else {
+        auto kern = k_step_tma<C, S, FM, false>;
+        if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return true;
+        kern<<<grid, kTmaThreads, smem, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key, p);
+    }
+    err = cudaGetLastError();
+    return true;
+}
+
+}  // namespace clbm

@@ -79,3 +79,4 @@ def test_null_pointers_rejected(lib):
     assert lib.clbm_get_macros(None, None, None) == _capi.CLBM_ERR_ARG
     assert lib.clbm_destroy(None) == _capi.CLBM_OK
     assert lib.clbm_status_string(_capi.CLBM_ERR_UNSTABLE).decode().startswith("unstable")
+    assert lib.clbm_status_string(_capi.CLBM_ERR_TIMEOUT).decode().startswith("timeout")

@@ -1,0 +1,117 @@
+"""The shared-memory staged A/B step for 16-bit storage (step_tma.cuh)
+against the one-node-per-thread step (k_step), and against the FP64 oracle.
+
+The staged kernel copies the pulled rows into shared memory with bulk
+asynchronous copies and reads them back shifted along x; it performs the same
+collision on the same values, so its populations must equal k_step's bit for
+bit, for every 16-bit format, collision model, wall set and tile shape: tiles
+of several rows with a partial last tile, one row per tile (nx = 1024), a
+single row (ny = 1), a single plane (nz = 1), and x walls, whose nodes read
+their bounce-back partners from global memory.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_common import W, dev, report, s2_of, t
+from paper_1801_04586_gb300 import Lattice, synthetic
+
+pytestmark = pytest.mark.gpu
+
+RATES = dict(s2b=1.2, s3=1.1, s4=0.9)
+
+CASES = [
+    # (nx, ny, nz), walls, storage, model
+    ((64, 20, 9), 0, "f16", "cascaded"),     # 16 rows per tile, partial last tile, y wrap runs
+    ((40, 33, 7), 6, "bf16", "cascaded"),    # y and z walls, 25 rows per tile
+    ((40, 33, 7), 6, "f16", "srt"),
+    ((40, 33, 7), 6, "f16sr", "mrt"),
+    ((8, 70, 5), 7, "f16", "cascaded"),      # walls on every axis, one tile per plane
+    ((1024, 3, 4), 2, "f16", "cascaded"),    # one row per tile
+    ((512, 5, 3), 0, "bf16", "mrt"),         # two rows per tile, partial last tile
+    ((256, 1, 3), 0, "bf16sr", "cascaded"),  # ny = 1: the y shift maps a row onto itself
+    ((24, 50, 1), 4, "f16", "cascaded"),     # nz = 1 between two z walls
+    ((48, 16, 16), 1, "f16sr", "srt"),       # x walls
+    ((32, 32, 32), 0, "bf16", "mrt"),
+]
+
+
+def pair(shape_xyz, walls, storage, model):
+    nx, ny, nz = shape_xyz
+    kw = dict(walls=walls, storage=storage, model=model, device=dev(), **RATES)
+    return Lattice(nx, ny, nz, 0.02, variant=0, **kw), Lattice(nx, ny, nz, 0.02, variant=1, **kw)
+
+
+@pytest.mark.parametrize("shape_xyz,walls,storage,model", CASES)
+def test_staged_step_equals_plain_step(shape_xyz, walls, storage, model):
+    nx, ny, nz = shape_xyz
+    shape = (nz, ny, nx)
+    staged, plain = pair(shape_xyz, walls, storage, model)
+    assert staged.info()["staged"] == 1 and plain.info()["staged"] == 0
+    rho = synthetic.density_perturbation(shape, 0.01, seed=501)
+    u = synthetic.divfree_velocity(shape, seed=502, umax=0.04)
+    F = t(synthetic.gaussian_force(shape, 1e-4, seed=503))
+    for g in (staged, plain):
+        g.set_force_field(F)
+        g.init_equilibrium(t(rho), t(u))
+    for n in (1, 6):
+        staged.step(n)
+        plain.step(n)
+        assert torch.equal(staged.populations(deviation=True), plain.populations(deviation=True))
+    staged.check()
+
+
+@pytest.mark.parametrize("force", ["uniform", "profile"])
+def test_staged_step_force_modes(force):
+    nx, ny, nz = 96, 24, 12
+    staged, plain = pair((nx, ny, nz), 4, "f16", "cascaded")
+    prof = torch.zeros(3, nz, device=dev())
+    prof[0] = torch.linspace(-1e-4, 1e-4, nz, device=dev())
+    for g in (staged, plain):
+        if force == "uniform":
+            g.set_force_uniform(1e-5, -2e-5, 3e-6)
+        else:
+            g.set_force_profile_z(prof)
+        g.init_equilibrium()
+    staged.step(9)
+    plain.step(9)
+    assert torch.equal(staged.populations(deviation=True), plain.populations(deviation=True))
+
+
+@pytest.mark.parametrize("shape_xyz,storage", [((64, 16, 8), "f32"), ((36, 19, 11), "f16"), ((1040, 4, 4), "f16"),
+                                               ((12, 9, 5), "bf16")])
+def test_geometries_without_staging_fall_back(shape_xyz, storage):
+    """FP32 storage, rows that are not a multiple of 16 bytes, and rows longer
+    than a tile run the one-node-per-thread step."""
+    g = Lattice(*shape_xyz, 0.02, storage=storage, device=dev())
+    assert g.info()["staged"] == 0
+
+
+def ulp16(v):
+    """Spacing of FP16 numbers at |v| (subnormal spacing below 2^-14)."""
+    e = np.floor(np.log2(np.maximum(np.abs(v), 2.0 ** -14)))
+    return 2.0 ** (e - 10)
+
+
+def test_staged_step_against_oracle():
+    """One staged FP16 step from an FP16-representable state against the
+    FP64 oracle's step: each stored deviation is the oracle's rounded to
+    FP16, within half a unit in the last place plus the FP32 arithmetic's
+    error (about 1e-9 absolute, at most a few hundredths of an FP16 unit in
+    the subnormal range)."""
+    nx, ny, nz, walls = 64, 24, 18, 6
+    shape = (nz, ny, nx)
+    g = Lattice(nx, ny, nz, 0.03, walls=walls, storage="f16", device=dev(), **RATES)
+    assert g.info()["staged"] == 1
+    o = oracle.Lattice(nx, ny, nz, walls=walls, s2=s2_of(0.03), **RATES)
+    h0 = torch.from_numpy(synthetic.rng(511).uniform(-2e-3, 2e-3, (19,) + shape)).half().float().numpy()
+    F = synthetic.gaussian_force(shape, 1e-4, seed=512)
+    g.set_force_field(t(F))
+    g.set_populations(t(h0), deviation=True)
+    g.step(1)
+    ho = oracle.step(o, h0.astype(np.float64) + W, F, 1) - W
+    hg = g.populations(deviation=True).double().cpu().numpy()
+    err = np.abs(hg - ho) / ulp16(np.maximum(np.abs(hg), np.abs(ho)))
+    report("staged_f16_one_step_ulp", shape=str(shape), walls=walls, max_ulp=float(err.max()))
+    assert err.max() <= 0.55
