@@ -41,6 +41,16 @@ NOMINAL_HBM_GBS = 7900.0  # HBM3e nominal, context beside the measured copy peak
 WORKLOAD = "periodic 256^3 Kolmogorov box, F_x = 1e-5 sin(2 pi z/256), nu = 0.01, FP32 populations"
 
 
+def workload_name(side, args):
+    """The bench workload's name for this run's size, storage and lattice."""
+    w = WORKLOAD.replace("256", str(side))
+    if args.storage != "f32":
+        w = w.replace("FP32 populations", f"{args.storage} populations")
+    if args.lattice == 27:
+        w = w.replace("Kolmogorov box", "Kolmogorov box, D3Q27")
+    return w
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -540,10 +550,13 @@ def run_gb300(args):
             "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.storage == "f32" else f"f32 arithmetic, {args.storage} storage",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if side == N_SIDE else WORKLOAD.replace("256", str(side)),
+            "config": {"workload": workload_name(side, args),
                        "nx": side, "ny": side, "nz": side, "nu": NU, "F0": F0,
-                       "storage": "f32 A/B pull", "block": [info["block_x"], info["block_y"]],
-                       "l2": "inputs larger than L2: two 1.27 GB population buffers vs 129 MB L2, no flush",
+                       "storage": f"{args.storage} {args.pattern.upper()} "
+                                  + ("staged in shared memory" if info["staged"] else "one node per thread"),
+                       "block": [info["block_x"], info["block_y"]],
+                       "l2": f"inputs larger than L2: {info['buffers']} population buffer(s) of "
+                             f"{info['state_bytes'] / 1e9:.2f} GB vs 129 MB L2, no flush",
                        "parallelism": f"{ws} independent replica(s), one per GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,

@@ -9,7 +9,7 @@
 // whole rows into shared memory a tile ahead of the threads, which read
 // their 19 values from shared memory at three addresses (x - 1, x, x + 1)
 // plus constant offsets, collide and store exactly as k_step does: the
-// results are bit-identical, with a tenth fewer instructions per node. FP32
+// results are bit-identical, with a fifth fewer instructions per node. FP32
 // storage stays on k_step, which already runs at the DRAM bound.
 //
 // Tile: `rows` consecutive x-rows (y0 .. y0 + rows - 1) of one z-plane, at
@@ -42,8 +42,9 @@
 
 namespace clbm {
 
-constexpr int kTmaThreads = 512;   // threads per block (two blocks per SM)
-constexpr int kTmaStages = 2;      // shared buffers per block
+constexpr int kTmaThreads = 512;   // threads per block
+constexpr int kTmaBlocksPerSM = 2; // resident blocks per SM (registers and shared memory sized for it)
+constexpr int kTmaStages = 2;      // shared buffers per block (at most 7)
 constexpr int kTileNodes = 1024;   // nodes per tile, and the element pitch of a population's rows in a buffer:
                                    // a buffer of 19 populations of 16-bit values is 38 KB, so two blocks of
                                    // two buffers fit an SM
@@ -272,7 +273,7 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
 }
 
 template <typename C, typename S, int FM, bool WALLS>
-__global__ void __launch_bounds__(kTmaThreads, 2)
+__global__ void __launch_bounds__(kTmaThreads, kTmaBlocksPerSM)
     k_step_tma(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r, ForceArgs F, int *__restrict__ flag,
                uint32_t key, TilePlan p) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     int z = blockIdx.x / p.tiles_y, yt = blockIdx.x - z * p.tiles_y;  // tile t = z tiles_y + yt
     int k = 0;
     for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++k) {
-        const int s = k & (kTmaStages - 1);
+        const int s = k % kTmaStages;
         float tfx = 0.0f, tfy = 0.0f, tfz = 0.0f;  // a uniform force (the others come staged)
         if (FM == kForceUniform) force_at<FM>(F, g, z, 0u, tfx, tfy, tfz);
         const bool ok = mbar_wait(&bar[s], (uint32_t)(k / kTmaStages) & 1u);
@@ -363,7 +364,7 @@ bool launch_step_tma(const Launch &L, const void *src, void *dst, const Rates &r
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return true;
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return true;
     const size_t smem = tile_smem_bytes<S, FM>();
-    const int grid = p.ntiles < 2 * sms ? p.ntiles : 2 * sms;
+    const int grid = p.ntiles < kTmaBlocksPerSM * sms ? p.ntiles : kTmaBlocksPerSM * sms;
     tile_plan(L.g, sizeof(S), src, grid, p);
     if (L.g.walls) {
         auto kern = k_step_tma<C, S, FM, true>;
