@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(512) k_batch_step(const S *__restrict__ A, S *
             S *dst = B + D->offset;
             float h[kQ];
             const uint32_t self = pull_load<S, true>(src, g, x, y, z, h);
-            const float drho = collide(h, D->fx, D->fy, D->fz, D->r);
+            const float drho = collide<sizeof(S) == 2>(h, D->fx, D->fy, D->fz, D->r);
             if (!(fabsf(drho) < 0.9f)) *flag = 1;
             store_node<S>(dst + self, g.stride, h, self, 0u);
         }

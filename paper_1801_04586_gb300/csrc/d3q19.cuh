@@ -312,6 +312,31 @@ using ::fmaf;
 __device__ __forceinline__ f2 fmaf(f2 a, f2 b, f2 c) { return f2{__ffma2_rn(a.v, b.v, c.v)}; }
 __device__ __forceinline__ f2 fmaf(float a, f2 b, f2 c) { return fmaf(mk2(a), b, c); }
 
+// 1/x for x near 1 (the density): the hardware reciprocal estimate
+// (rcp.approx, relative error below 2^-23) refined by one Newton-Raphson
+// step, e = 1 - x r, r' = r + r e, which leaves it within an ulp of the
+// correctly rounded quotient in three instructions.
+__device__ __forceinline__ float recip_nr(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    const float e = fmaf(-x, r, 1.0f);
+    return fmaf(r, e, r);
+}
+__device__ __forceinline__ f2 recip_nr(f2 x) { return mk2(recip_nr(x.v.x), recip_nr(x.v.y)); }
+
+// The collision's 1/rho: recip_nr when FR (16-bit storage, whose steps are
+// bound by instruction issue: 3 to 6 % faster), the IEEE division otherwise
+// (FP32 steps are bound by DRAM; there the shorter sequence let the compiler
+// stretch live ranges, 58 -> 81 registers in the in-place odd step, and
+// measured 1-4 % slower).
+template <bool FR, typename T>
+__device__ __forceinline__ T recip_of(T x) {
+    if constexpr (FR)
+        return recip_nr(x);
+    else
+        return 1.0f / x;
+}
+
 // Central shift of one triplet along an axis with velocity v (one factor of
 // N(u)): (k0, k1, k2) -> (k0, k1 - v k0, k2 - 2 v k1 + v^2 k0).
 template <typename T>
@@ -383,40 +408,46 @@ __device__ __forceinline__ void eq_dev(T drho, T rho, T jx, T jy, T jz, T ux, T 
     q.d022 = fmaf(rho, fmaf(Y, Z, kC * (Y + Z)), drho * kC2);
 }
 
+// The four populations of one diagonal plane from its moments (22, 21, 12,
+// 11 in the plane's two axes): 1/4 ((m22 +- m21) +- (m12 +- m11)).
+template <typename T>
+__device__ __forceinline__ void plane_inverse(T m22, T m21, T m12, T m11, T &pp, T &pm, T &mp, T &mm) {
+    const T a = 0.25f * (m22 + m21), c = 0.25f * (m22 - m21);
+    const T b = m12 + m11, d = m12 - m11;
+    pp = fmaf(0.25f, b, a);
+    pm = fmaf(-0.25f, b, a);
+    mp = fmaf(0.25f, d, c);
+    mm = fmaf(-0.25f, d, c);
+}
+
 // h = M^-1 Q for raw-moment deviations Q (Eq. 7, M^-1 of Eq. A4).
 template <typename T>
 __device__ __forceinline__ void inverse_moments(const MomentsT<T> &q, T (&h)[kQ]) {
-    h[7] = 0.25f * ((q.m220 + q.m210) + (q.m120 + q.m110));
-    h[8] = 0.25f * ((q.m220 + q.m210) - (q.m120 + q.m110));
-    h[9] = 0.25f * ((q.m220 - q.m210) + (q.m120 - q.m110));
-    h[10] = 0.25f * ((q.m220 - q.m210) - (q.m120 - q.m110));
-    h[11] = 0.25f * ((q.m202 + q.m201) + (q.m102 + q.m101));
-    h[12] = 0.25f * ((q.m202 + q.m201) - (q.m102 + q.m101));
-    h[13] = 0.25f * ((q.m202 - q.m201) + (q.m102 - q.m101));
-    h[14] = 0.25f * ((q.m202 - q.m201) - (q.m102 - q.m101));
-    h[15] = 0.25f * ((q.m022 + q.m021) + (q.m012 + q.m011));
-    h[16] = 0.25f * ((q.m022 + q.m021) - (q.m012 + q.m011));
-    h[17] = 0.25f * ((q.m022 - q.m021) + (q.m012 - q.m011));
-    h[18] = 0.25f * ((q.m022 - q.m021) - (q.m012 - q.m011));
+    // Each pair s (a + b), s (a - b) is taken as s a +- s b with s a exact, so
+    // the results are the same bits with one multiply fewer per pair.
+    plane_inverse(q.m220, q.m210, q.m120, q.m110, h[7], h[8], h[9], h[10]);
+    plane_inverse(q.m202, q.m201, q.m102, q.m101, h[11], h[12], h[13], h[14]);
+    plane_inverse(q.m022, q.m021, q.m012, q.m011, h[15], h[16], h[17], h[18]);
     const T px = q.m200 - q.m220 - q.m202, vx = q.m100 - q.m120 - q.m102;
     const T py = q.m020 - q.m220 - q.m022, vy = q.m010 - q.m210 - q.m012;
     const T pz = q.m002 - q.m202 - q.m022, vz = q.m001 - q.m201 - q.m021;
-    h[1] = 0.5f * (px + vx); h[2] = 0.5f * (px - vx);
-    h[3] = 0.5f * (py + vy); h[4] = 0.5f * (py - vy);
-    h[5] = 0.5f * (pz + vz); h[6] = 0.5f * (pz - vz);
+    const T px2 = 0.5f * px, py2 = 0.5f * py, pz2 = 0.5f * pz;
+    h[1] = fmaf(0.5f, vx, px2); h[2] = fmaf(-0.5f, vx, px2);
+    h[3] = fmaf(0.5f, vy, py2); h[4] = fmaf(-0.5f, vy, py2);
+    h[5] = fmaf(0.5f, vz, pz2); h[6] = fmaf(-0.5f, vz, pz2);
     h[0] = q.m000 - (q.m200 + q.m020 + q.m002) + (q.m220 + q.m202 + q.m022);
 }
 
 // One collision (Steps 1-3 of Sec. II.B) on deviations h, in place.
 // Returns drho = rho - 1 of the pre-collision state (Eq. 9); if j_out is not
 // null it receives rho*u of Eq. 9 (momentum including F/2).
-template <typename T>
+template <bool FR = false, typename T>
 __device__ __forceinline__ T collide(T (&h)[kQ], T Fx, T Fy, T Fz, const Rates &r, float3 *j_out = nullptr) {
     MomentsT<T> k;
     raw_moments(h, k);
     const T drho = k.m000;
     const T rho = 1.0f + drho;
-    const T inv = 1.0f / rho;
+    const T inv = recip_of<FR>(rho);
     const T jx = fmaf(0.5f, Fx, k.m100), jy = fmaf(0.5f, Fy, k.m010), jz = fmaf(0.5f, Fz, k.m001);
     const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
     if constexpr (sizeof(T) == sizeof(float)) {

@@ -158,6 +158,7 @@ __device__ __forceinline__ void eq_dev27(float drho, float ux, float uy, float u
 
 // One collision on deviations h (cube by velocity code), in place; returns
 // drho of the pre-collision state (Eq. 9).
+template <bool FR = false>
 __device__ __forceinline__ float collide27(float (&h)[3][3][3], float Fx, float Fy, float Fz, const Rates27 &r) {
     float m[3][3][3];
 #pragma unroll
@@ -171,7 +172,7 @@ __device__ __forceinline__ float collide27(float (&h)[3][3][3], float Fx, float 
     raw_axis<2>(m);
     const float drho = m[0][0][0];
     const float rho = 1.0f + drho;
-    const float inv = 1.0f / rho;
+    const float inv = recip_of<FR>(rho);
     const float jx = fmaf(0.5f, Fx, m[1][0][0]), jy = fmaf(0.5f, Fy, m[0][1][0]), jz = fmaf(0.5f, Fz, m[0][0][1]);
     const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
     float e[3][3][3];

@@ -31,11 +31,12 @@ namespace clbm {
 //         (k_220 alike);
 //   R_G:  u_a F_b + u_b F_a, 2 u_a F_a, F_x / 3, u_x F_x + u_y F_y - u.F / 3;
 // then T* = T_eq + (I - S)(T - T_eq) + (I - S/2) G and h* = M^-1 (T* - M w).
+template <bool FR = false>
 __device__ __forceinline__ float collide_mrt(float (&h)[kQ], float Fx, float Fy, float Fz, const Rates &r) {
     Moments k;
     raw_moments(h, k);
     const float drho = k.m000;
-    const float rho = 1.0f + drho, inv = 1.0f / rho;
+    const float rho = 1.0f + drho, inv = recip_of<FR>(rho);
     const float jx = fmaf(0.5f, Fx, k.m100), jy = fmaf(0.5f, Fy, k.m010), jz = fmaf(0.5f, Fz, k.m001);
     const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
     const float X = ux * ux, Y = uy * uy, Z = uz * uz;
@@ -90,6 +91,7 @@ __device__ __forceinline__ float collide_mrt(float (&h)[kQ], float Fx, float Fy,
 // the equilibrium's mass and momentum in FP32 the same way every step on a
 // nearly steady flow, and drifted from the FP64 oracle by 3e-5 in 1000 steps
 // of a shear wave at u = 0.17.)
+template <bool FR = false>
 __device__ __forceinline__ float collide_srt(float (&h)[kQ], float Fx, float Fy, float Fz, const Rates &r) {
     Rates e;
     e.om2 = r.om2;
@@ -97,7 +99,7 @@ __device__ __forceinline__ float collide_srt(float (&h)[kQ], float Fx, float Fy,
     e.om3 = r.om2;
     e.c3 = 0.5f * (1.0f + r.om2) * kC;
     e.om4 = r.om2;
-    return collide_mrt(h, Fx, Fy, Fz, e);
+    return collide_mrt<FR>(h, Fx, Fy, Fz, e);
 }
 
 }  // namespace clbm

@@ -67,6 +67,7 @@ __device__ __forceinline__ float om27(int a, int b, int c, const Rates27 &r) {
 
 // Non-orthogonal MRT on D3Q27 deviations h (cube by velocity code), in place:
 // T* = T_eq + (I - S)(T - T_eq) + (I - S/2) G, h* = M^-1 (T* - M w).
+template <bool FR = false>
 __device__ __forceinline__ float collide_mrt27(float (&h)[3][3][3], float Fx, float Fy, float Fz,
                                                const Rates27 &r) {
     float m[3][3][3];
@@ -80,7 +81,7 @@ __device__ __forceinline__ float collide_mrt27(float (&h)[3][3][3], float Fx, fl
     raw_axis<1>(m);
     raw_axis<2>(m);
     const float drho = m[0][0][0];
-    const float rho = 1.0f + drho, inv = 1.0f / rho;
+    const float rho = 1.0f + drho, inv = recip_of<FR>(rho);
     const float jx = fmaf(0.5f, Fx, m[1][0][0]), jy = fmaf(0.5f, Fy, m[0][1][0]), jz = fmaf(0.5f, Fz, m[0][0][1]);
     const float u[3] = {jx * inv, jy * inv, jz * inv};
     const float F[3] = {Fx, Fy, Fz};
@@ -133,6 +134,7 @@ __device__ __forceinline__ float collide_mrt27(float (&h)[3][3][3], float Fx, fl
 // SRT on D3Q27 deviations: the MRT collision with every rate equal to s2
 // (Sec. II.A), so mass and momentum come out exactly (see collide_srt in
 // models.cuh for why not per population).
+template <bool FR = false>
 __device__ __forceinline__ float collide_srt27(float (&h)[3][3][3], float Fx, float Fy, float Fz,
                                                const Rates27 &r) {
     const float om = r.om2;
@@ -147,7 +149,7 @@ __device__ __forceinline__ float collide_srt27(float (&h)[3][3][3], float Fx, fl
     e.om5 = om;
     e.c5 = 0.5f * (1.0f + om) * kC2;
     e.om6 = om;
-    return collide_mrt27(h, Fx, Fy, Fz, e);
+    return collide_mrt27<FR>(h, Fx, Fy, Fz, e);
 }
 
 }  // namespace clbm

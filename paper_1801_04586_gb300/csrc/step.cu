@@ -7,9 +7,9 @@ namespace clbm {
 
 // The paper's cascaded collision with the consistent forcing scheme.
 struct Cascaded {
-    template <typename T>
+    template <bool FR = false, typename T>
     static __device__ __forceinline__ T run(T (&h)[kQ], T Fx, T Fy, T Fz, const Rates &r) {
-        return collide(h, Fx, Fy, Fz, r);
+        return collide<FR>(h, Fx, Fy, Fz, r);
     }
 };
 
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) k_step2(const S *__restrict__ src, S *__r
     float fxa, fya, fza, fxb, fyb, fzb;
     force_at<FM>(F, g, z, oa[0], fxa, fya, fza);
     force_at<FM>(F, g, z, ob[0], fxb, fyb, fzb);
-    const f2 drho = collide(h, mk2(fxa, fxb), mk2(fya, fyb), mk2(fza, fzb), r);
+    const f2 drho = collide<sizeof(S) == 2>(h, mk2(fxa, fxb), mk2(fya, fyb), mk2(fza, fzb), r);
     if (!(fabsf(drho.v.x) < 0.9f) || !(fabsf(drho.v.y) < 0.9f)) *flag = 1;
     float ha[kQ], hb[kQ];
 #pragma unroll

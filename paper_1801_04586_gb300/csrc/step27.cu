@@ -11,9 +11,10 @@ namespace clbm {
 
 // The paper's cascaded collision on D3Q27 (Sec. II).
 struct Cascaded27 {
+    template <bool FR = false>
     static __device__ __forceinline__ float run(float (&h)[3][3][3], float Fx, float Fy, float Fz,
                                                 const Rates27 &r) {
-        return collide27(h, Fx, Fy, Fz, r);
+        return collide27<FR>(h, Fx, Fy, Fz, r);
     }
 };
 

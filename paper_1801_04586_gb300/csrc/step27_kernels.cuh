@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256, 4) k_step27(const S *__restrict__ src, S 
     const uint32_t self = pull27<S, WALLS>(src, g, x, y, z, h);
     float fx, fy, fz;
     force27<FM>(F, g, z, self, fx, fy, fz);
-    const float drho = C::run(h, fx, fy, fz, r);
+    const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
     if (!(fabsf(drho) < 0.9f)) *flag = 1;
     float f[kQ27];
     flatten27(h, f);
@@ -107,13 +107,14 @@ __global__ void __launch_bounds__(256) k_step27_aa(S *f, Geom g, Rates27 r, Forc
             for (int c = 0; c < 3; ++c) h[a][b][c] = Codec<S>::load(f + (size_t)pop[a][b][c] * g.stride + off[a][b][c]);
     float fx, fy, fz;
     force27<FM>(F, g, z, self, fx, fy, fz);
-    const float drho = C::run(h, fx, fy, fz, r);
+    const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
     if (!(fabsf(drho) < 0.9f)) *flag = 1;
     if (ODD) {
-        // recompute the slots from coordinates the compiler must treat as new,
-        // so that 27 offsets do not stay live through the collision
+        // recompute the slots from coordinates the compiler must treat as new
+        // and as depending on the collision's outputs, so that 27 offsets do
+        // not stay live through the collision
         int xs = x, ys = y, zs = z;
-        asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs));
+        asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs) : "f"(h[0][0][0]), "f"(h[2][2][2]));
         pull_sources27<WALLS, true>(g, xs, ys, zs, off, pop);
     }
     // destination of population q27_index(a,b,c): the slot read for the opposite code

@@ -7,9 +7,10 @@
 namespace clbm {
 
 struct Mrt27 {
+    template <bool FR = false>
     static __device__ __forceinline__ float run(float (&h)[3][3][3], float Fx, float Fy, float Fz,
                                                 const Rates27 &r) {
-        return collide_mrt27(h, Fx, Fy, Fz, r);
+        return collide_mrt27<FR>(h, Fx, Fy, Fz, r);
     }
 };
 

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(512, 2) k_step_diag(const S *__restrict__ src,
             float fx, fy, fz;
             force_diag<FM>(F, g, z, off[0], fx, fy, fz);
             float3 j;
-            const float drho = collide(h, fx, fy, fz, r, &j);
+            const float drho = collide<sizeof(S) == 2>(h, fx, fy, fz, r, &j);
             if (!(fabsf(drho) < 0.9f)) *flag = 1;
             store_node<S>(dst + off[0], g.stride, h, off[0], key);
             const float q[4] = {drho, j.x, j.y, j.z};

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(512) k_step(const S *__restrict__ src, S *__re
     for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
     float fx, fy, fz;
     force_at<FM>(F, g, z, off[0], fx, fy, fz);
-    const float drho = C::run(h, fx, fy, fz, r);
+    const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
     if (!(fabsf(drho) < 0.9f)) *flag = 1;
     store_node<S>(dst + off[0], g.stride, h, off[0], key);
 }
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(512) k_step(const S *__restrict__ src, S *__re
 // read-only path: a slot is read once, by the thread that later overwrites
 // it, and never after a write within the launch.
 template <typename C, typename S, int FM, bool WALLS, bool ODD>
-__global__ void __launch_bounds__(512) k_step_aa(S *f, Geom g, Rates r, ForceArgs F, int *__restrict__ flag,
+__global__ void __launch_bounds__(512, sizeof(S) == 2 ? 2 : 0) k_step_aa(S *f, Geom g, Rates r, ForceArgs F, int *__restrict__ flag,
                                                  uint32_t key) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -97,13 +97,14 @@ __global__ void __launch_bounds__(512) k_step_aa(S *f, Geom g, Rates r, ForceArg
         for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(f + (size_t)pop[i] * g.stride + off[i]);
         float fx, fy, fz;
         force_at<FM>(F, g, z, self, fx, fy, fz);
-        const float drho = C::run(h, fx, fy, fz, r);
+        const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
         if (!(fabsf(drho) < 0.9f)) *flag = 1;
         // The slots read for the opposite directions are the push targets of
         // Eq. 8. They are recomputed from coordinates the compiler must treat
-        // as new, so that 19 offsets do not stay live through the collision.
+        // as new and as depending on the collision's outputs, so that 19
+        // offsets do not stay live through the collision.
         int xs = x, ys = y, zs = z;
-        asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs));
+        asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs) : "f"(h[0]), "f"(h[kQ - 1]));
         push_targets<WALLS>(g, xs, ys, zs, off, pop);
         store_each<S, kQ>(h, self, key, [&](int i) { return f + (size_t)pop[i] * g.stride + off[i]; });
     } else {
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(512) k_step_aa(S *f, Geom g, Rates r, ForceArg
         for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(f + (size_t)i * g.stride + self);
         float fx, fy, fz;
         force_at<FM>(F, g, z, self, fx, fy, fz);
-        const float drho = C::run(h, fx, fy, fz, r);
+        const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
         if (!(fabsf(drho) < 0.9f)) *flag = 1;
         store_each<S, kQ>(h, self, key, [&](int i) { return f + (size_t)opposite(i) * g.stride + self; });
     }

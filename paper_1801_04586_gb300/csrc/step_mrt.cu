@@ -7,8 +7,9 @@
 namespace clbm {
 
 struct Mrt {
+    template <bool FR = false>
     static __device__ __forceinline__ float run(float (&h)[kQ], float Fx, float Fy, float Fz, const Rates &r) {
-        return collide_mrt(h, Fx, Fy, Fz, r);
+        return collide_mrt<FR>(h, Fx, Fy, Fz, r);
     }
 };
 

@@ -6,8 +6,9 @@
 namespace clbm {
 
 struct Srt {
+    template <bool FR = false>
     static __device__ __forceinline__ float run(float (&h)[kQ], float Fx, float Fy, float Fz, const Rates &r) {
-        return collide_srt(h, Fx, Fy, Fz, r);
+        return collide_srt<FR>(h, Fx, Fy, Fz, r);
     }
 };
 

@@ -266,7 +266,7 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
             fy = fst[1] * F.scale;
             fz = fst[2] * F.scale;
         }
-        const float drho = C::run(h, fx, fy, fz, r);
+        const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
         if (!(fabsf(drho) < 0.9f)) atomicOr(flag, 1);
         store_node<S>(dst + self, g.stride, h, self, key);
     }

@@ -62,6 +62,25 @@ def test_staged_step_equals_plain_step(shape_xyz, walls, storage, model):
     staged.check()
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16sr"])
+def test_staged_step_full_size(storage):
+    """The 256^3 Kolmogorov workload of the benchmark, in its launch
+    configuration (persistent grid, 4-row tiles): two staged steps equal two
+    one-node-per-thread steps bit for bit."""
+    n = 256
+    staged, plain = pair((n, n, n), 0, storage, "cascaded")
+    prof = torch.zeros(3, n, device=dev())
+    prof[0] = 1e-5 * torch.sin(2 * np.pi * torch.arange(n, device=dev()) / n)
+    u = t(synthetic.divfree_velocity((n, n, n), seed=1, umax=0.02))
+    for g in (staged, plain):
+        g.set_force_profile_z(prof)
+        g.init_equilibrium(None, u)
+        g.step(2)
+    assert torch.equal(staged.populations(deviation=True), plain.populations(deviation=True))
+    staged.close()
+    plain.close()
+
+
 @pytest.mark.parametrize("force", ["uniform", "profile"])
 def test_staged_step_force_modes(force):
     nx, ny, nz = 96, 24, 12
