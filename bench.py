@@ -528,6 +528,7 @@ def run_gb300(args):
             "d3q27_srt_f32": S("f32", lattice=27, model="srt"),
             "d3q27_mrt_f32": S("f32", lattice=27, model="mrt"),
             "d3q27_aa_in_place_f32": S("f32", lattice=27, pattern="aa"),
+            "d3q27_f16_storage": S("f16", lattice=27),
             "adjoint_kernel_256": lambda: bench_adjoint(dev, side, max(10, min(K, 100)), peak),
             "adjoint_unroll_64": lambda: bench_unroll(dev),
             "batched_64_domains": lambda: bench_batch(dev, args.batch_steps, peak),

@@ -105,10 +105,10 @@ extern "C" {
  * walls: CLBM_WALL_* bits; an axis without a bit is periodic.
  * block_x, block_y: CUDA block shape of the step kernel (block_x a multiple
  *      of 32, block_x*block_y <= 512); 0 selects the built-in default.
- * variant: step kernel form. 0 (the default): D3Q19 A/B steps with 16-bit
- *      storage stage the pulled rows in shared memory with bulk asynchronous
- *      copies where the geometry allows (nx <= 1024, nx a multiple of 8),
- *      one node per thread otherwise; 1: always one node per thread,
+ * variant: step kernel form. 0 (the default): A/B steps with 16-bit storage
+ *      stage the pulled rows in shared memory with bulk asynchronous copies
+ *      where the geometry allows (nx <= 1024, nx a multiple of 8; D3Q27 not
+ *      with a force field), one node per thread otherwise; 1: always one node per thread,
  *      plain loads (block_x, block_y apply); 2: two nodes per thread (x and
  *      x + block_x), collided together with the FP32x2 instructions (D3Q19
  *      only; measured slower on GB300 for every storage format, kept as an

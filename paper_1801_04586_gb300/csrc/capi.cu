@@ -314,7 +314,7 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     c->gamma = 0.0;
     c->q = q;
     c->packed = q == 19 && p->variant == 2;
-    c->staged = q == 19 && p->variant == 0 && p->pattern != CLBM_PATTERN_AA;
+    c->staged = p->variant == 0 && p->pattern != CLBM_PATTERN_AA;
     c->aa = p->pattern == CLBM_PATTERN_AA;
     c->model = p->model;
     c->rates27.om2 = c->rates.om2;
@@ -392,7 +392,7 @@ int clbm_get_info(const clbm_ctx *c, clbm_info *info) {
     info->pattern = c->aa ? CLBM_PATTERN_AA : CLBM_PATTERN_AB;
     info->buffers = c->aa ? 1 : 2;
     info->model = c->model;
-    info->staged = c->staged && step_staged(c->g, c->elem, c->buf[0]) ? 1 : 0;
+    info->staged = c->staged && step_staged(c->g, c->elem, c->buf[0], c->q, c->force.mode) ? 1 : 0;
     return CLBM_OK;
 }
 

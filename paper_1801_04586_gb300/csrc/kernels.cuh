@@ -35,9 +35,10 @@ struct Launch {
 // (CLBM_STORAGE_*). key: per-step dither key (stochastic formats).
 cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
                         const ForceArgs &F, int *flag, uint32_t key);
-// Whether an A/B step from a state buffer at src (elem bytes per value) runs
-// the shared-memory staged kernel (step_tma.cuh) when the launch asks for it.
-bool step_staged(const Geom &g, size_t elem, const void *src);
+// Whether an A/B step of a q-population lattice from a state buffer at src
+// (elem bytes per value) with force mode force_mode runs the shared-memory
+// staged kernel (step_tma.cuh) when the launch asks for it.
+bool step_staged(const Geom &g, size_t elem, const void *src, int q, int force_mode);
 // In-place (AA) pattern: one step on the single population array f; odd
 // selects the odd step kind (step.cu).
 cudaError_t launch_step_aa(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,

@@ -84,9 +84,8 @@ cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst
     }
 }
 
-bool step_staged(const Geom &g, size_t elem, const void *src) {
-    TilePlan p;
-    return tile_plan(g, elem, src, 0, p);
+bool step_staged(const Geom &g, size_t elem, const void *src, int q, int force_mode) {
+    return step_staged_for(g, elem, src, q, force_mode);
 }
 
 cudaError_t launch_step_aa(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,

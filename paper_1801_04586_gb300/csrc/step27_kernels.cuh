@@ -9,6 +9,7 @@
 
 #include "d3q27.cuh"
 #include "kernels.cuh"
+#include "step_tma.cuh"
 
 namespace clbm {
 
@@ -163,7 +164,15 @@ template <typename C>
 cudaError_t launch_step27_with(int storage, const Launch &L, const void *src, void *dst, const Rates27 &r,
                                const ForceArgs &F, int *flag, uint32_t key) {
     CLBM_Q27_STORE(storage, CLBM_Q27_FM(F.mode, {
-        if (L.g.walls)
+        bool staged = false;
+        if constexpr (sizeof(S) == 2) {  // 16-bit storage: rows staged in shared memory where they apply
+            cudaError_t e = cudaSuccess;
+            staged = L.staged && launch_step_tma<27, C, S, FM>(L, src, dst, r, F, flag, key, e);
+            if (staged && e != cudaSuccess) return e;
+        }
+        if (staged)
+            ;
+        else if (L.g.walls)
             k_step27<C, S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);
         else
             k_step27<C, S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);

@@ -123,7 +123,7 @@ static cudaError_t step_walls_t(const Launch &L, const void *src, void *dst, con
                                 int *flag, uint32_t key) {
     if constexpr (sizeof(S) == 2) {  // 16-bit storage: rows staged in shared memory where they apply
         cudaError_t e = cudaSuccess;
-        if (L.staged && launch_step_tma<C, S, FM>(L, src, dst, r, F, flag, key, e)) return e;
+        if (L.staged && launch_step_tma<19, C, S, FM>(L, src, dst, r, F, flag, key, e)) return e;
     }
     if (L.g.walls)
         k_step<C, S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key);

@@ -26,25 +26,31 @@
 // their own opposite population from global memory instead.
 //
 // Pipeline: a persistent grid; block b walks tiles b, b + gridDim.x, ... with
-// kTmaStages shared buffers and one mbarrier each. A warp arms a buffer's
+// a few shared buffers (TmaShape) and one mbarrier each. A warp arms a buffer's
 // barrier with the tile's byte count and issues its copies (lane i:
 // population i). Every warp waits on the barrier of its next tile, computes
 // its nodes and counts itself done with the buffer; the last warp to finish
-// refills the buffer with the tile kTmaStages ahead. There is no block
-// barrier in the loop, so warps drift apart by up to kTmaStages tiles instead
+// refills the buffer with the tile as many tiles ahead as there are buffers.
+// There is no block barrier in the loop, so warps drift apart by up to that
+// many tiles instead
 // of waiting for the slowest. Every wait is bounded (kWaitCycles); on expiry
 // the block sets bit 1 of the flag (reported as CLBM_ERR_TIMEOUT), its warps
 // leave the loop, and one thread waits, again bounded, for the copies still
 // in flight before the block ends.
 #pragma once
 
+#include "d3q27.cuh"
 #include "kernels.cuh"
 
 namespace clbm {
 
-constexpr int kTmaThreads = 512;   // threads per block
-constexpr int kTmaBlocksPerSM = 2; // resident blocks per SM (registers and shared memory sized for it)
-constexpr int kTmaStages = 2;      // shared buffers per block (at most 7)
+// Launch shape per lattice: threads per block, resident blocks per SM
+// (registers and shared memory are sized for it) and shared buffers per block
+// (at most 7).
+template <int Q>
+struct TmaShape {
+    static constexpr int threads = 512, blocks = 2, stages = 2;
+};
 constexpr int kTileNodes = 1024;   // nodes per tile, and the element pitch of a population's rows in a buffer:
                                    // a buffer of 19 populations of 16-bit values is 38 KB, so two blocks of
                                    // two buffers fit an SM
@@ -58,19 +64,35 @@ struct TilePlan {
     uint32_t rdiv;  // ceil(2^32 / nx): the row of tile node n is umulhi(n, rdiv), exact for n, nx <= 1024
 };
 
-// Bytes of one buffer: kQ x kTileNodes stored values, then the force on the
+// D3Q27: the collision wants about 115 registers, so 256 threads per block
+// take four nodes each of a 1024-node tile (0.60 of roofline at 256^3 FP16;
+// 512 threads at 64 registers spilled 60-150 bytes and measured 0.51, 384
+// threads at 80 registers 0.59, one block of 512 threads with 4 buffers 0.52).
+template <>
+struct TmaShape<27> {
+    static constexpr int threads = 256, blocks = 2, stages = 2;
+};
+
+// Bytes of one buffer: Q x kTileNodes stored values, then the force on the
 // tile's nodes: for a field its three components (3 x kTileNodes floats),
 // for a z-profile the tile plane's three values.
-template <typename S, int FM>
+template <typename S, int FM, int Q>
 __host__ __device__ constexpr size_t stage_bytes() {
-    return (size_t)kQ * kTileNodes * sizeof(S) +
+    return (size_t)Q * kTileNodes * sizeof(S) +
            (FM == kForceField ? 3 * kTileNodes * sizeof(float) : (FM == kForceProfileZ ? 16 : 0));
 }
 
-// Shared memory of one block: the barriers, then kTmaStages buffers.
-template <typename S, int FM>
+// Shared memory of one block: the barriers, then the buffers.
+template <typename S, int FM, int Q>
 constexpr size_t tile_smem_bytes() {
-    return 128 + kTmaStages * stage_bytes<S, FM>();
+    return 128 + TmaShape<Q>::stages * stage_bytes<S, FM, Q>();
+}
+
+// Whether the resident blocks fit the 228 KB of shared memory of an SM (1 KB
+// of each block's share is reserved).
+template <typename S, int FM, int Q>
+constexpr bool tile_fits() {
+    return TmaShape<Q>::blocks * (tile_smem_bytes<S, FM, Q>() + 1024) <= 228 * 1024;
 }
 
 // Whether the staged step applies, and its plan for a grid of `grid` blocks
@@ -141,30 +163,39 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
         : "memory");
 }
 
-// e_iy + 1 and e_iz + 1 of population i in two bits each.
+// e_iy + 1 and e_iz + 1 of population i (in the order of Eq. A1 for D3Q19, of
+// Eq. 1 for D3Q27) in two bits each.
+template <int Q>
 __host__ __device__ constexpr uint64_t pack_shift(int axis) {
     uint64_t t = 0;
-    for (int i = 0; i < kQ; ++i) t |= (uint64_t)((axis == 1 ? ey19(i) : ez19(i)) + 1) << (2 * i);
+    if (Q == 19) {
+        for (int i = 0; i < kQ; ++i) t |= (uint64_t)((axis == 1 ? ey19(i) : ez19(i)) + 1) << (2 * i);
+    } else {
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                for (int c = 0; c < 3; ++c)
+                    t |= (uint64_t)((axis == 1 ? e_of(b) : e_of(c)) + 1) << (2 * q27_index(a, b, c));
+    }
     return t;
 }
-constexpr uint64_t kEyBits = pack_shift(1), kEzBits = pack_shift(2);
 
 // Arm `bar` with the tile's byte count and copy its source rows into the
 // buffer `stage`: population i's rows land at element i * kTileNodes, slot
 // row r at r * nx; after the populations, the force: for a field, component
 // c of the tile's own rows at float c * kTileNodes (bulk copies), for a
 // z-profile the plane's three values (plain shared stores). Called by all 32
-// lanes of one warp; lane i < 19 handles population i, lanes 19-21 the force
-// components.
-template <typename S, int FM, bool WALLS>
+// lanes of one warp; lane i < Q handles population i, lanes Q to Q + 2 the
+// force components.
+template <typename S, int FM, bool WALLS, int Q>
 __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, const Geom &g, const TilePlan &p,
                                            int t, unsigned char *stage, uint64_t *bar, int lane) {
     const int z = t / p.tiles_y;
     const int y0 = (t - z * p.tiles_y) * p.rows;
     const int rows = min(p.rows, g.ny - y0);
     int src_a = 0, slot_a = 0, n_a = 0, src_b = 0, slot_b = 0, n_b = 0, zs = 0;
-    if (lane < kQ) {
-        const int ey = (int)((kEyBits >> (2 * lane)) & 3u) - 1, ez = (int)((kEzBits >> (2 * lane)) & 3u) - 1;
+    if (lane < Q) {
+        constexpr uint64_t kEy = pack_shift<Q>(1), kEz = pack_shift<Q>(2);
+        const int ey = (int)((kEy >> (2 * lane)) & 3u) - 1, ez = (int)((kEz >> (2 * lane)) & 3u) - 1;
         const bool wy = WALLS && (g.walls & 2u), wz = WALLS && (g.walls & 4u);
         zs = z - ez;
         bool plane = true;
@@ -185,19 +216,19 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
             }
         }
     }
-    const bool force_lane = FM == kForceField && lane >= kQ && lane < kQ + 3;
+    const bool force_lane = FM == kForceField && lane >= Q && lane < Q + 3;
     const uint32_t row_bytes = (uint32_t)g.nx * (uint32_t)sizeof(S);
     const uint32_t bytes = force_lane ? (uint32_t)rows * (uint32_t)g.nx * 4u : (uint32_t)(n_a + n_b) * row_bytes;
     const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
-    if (FM == kForceProfileZ && lane >= kQ && lane < kQ + 3) {
+    if (FM == kForceProfileZ && lane >= Q && lane < Q + 3) {
         // the plane's force: a plain shared store, published to the waiting warps by the arrive below
-        float *fdst = reinterpret_cast<float *>(stage + (size_t)kQ * kTileNodes * sizeof(S));
-        fdst[lane - kQ] = __ldg(F.profile + (size_t)(lane - kQ) * g.nz + z);
+        float *fdst = reinterpret_cast<float *>(stage + (size_t)Q * kTileNodes * sizeof(S));
+        fdst[lane - Q] = __ldg(F.profile + (size_t)(lane - Q) * g.nz + z);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive_expect_tx(bar, total);
     __syncwarp();
-    if (lane < kQ) {
+    if (lane < Q) {
         const S *pop = src + (size_t)lane * g.stride + (size_t)zs * g.ny * g.nx;
         S *dst = reinterpret_cast<S *>(stage) + lane * kTileNodes;
         if (n_a > 0)
@@ -205,56 +236,42 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
         if (n_b > 0)
             bulk_copy_g2s(dst + slot_b * g.nx, pop + (size_t)src_b * g.nx, (uint32_t)n_b * row_bytes, bar);
     } else if (force_lane) {
-        const int c = lane - kQ;
-        float *dst = reinterpret_cast<float *>(stage + (size_t)kQ * kTileNodes * sizeof(S)) + c * kTileNodes;
+        const int c = lane - Q;
+        float *dst = reinterpret_cast<float *>(stage + (size_t)Q * kTileNodes * sizeof(S)) + c * kTileNodes;
         bulk_copy_g2s(dst, F.field + (size_t)c * F.n + ((size_t)z * g.ny + y0) * g.nx, bytes, bar);
     }
 }
 
 // Collide and store the nodes of the tile of rows y0 .. y0 + rows - 1 of
 // plane z from its staged rows.
-template <typename C, typename S, int FM, bool WALLS>
+template <typename C, typename S, int FM, bool WALLS, int Q, typename R>
 __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__restrict__ dst, const Geom &g,
-                                             const Rates &r, const ForceArgs &F, int *flag, uint32_t key,
+                                             const R &r, const ForceArgs &F, int *flag, uint32_t key,
                                              const TilePlan &p, int z, int y0, const unsigned char *buf,
                                              float tfx, float tfy, float tfz) {
     const S *stage = reinterpret_cast<const S *>(buf);
-    const float *fst = reinterpret_cast<const float *>(buf + (size_t)kQ * kTileNodes * sizeof(S));
+    const float *fst = reinterpret_cast<const float *>(buf + (size_t)Q * kTileNodes * sizeof(S));
     constexpr int TN = kTileNodes;
     const int rows = min(p.rows, g.ny - y0);
     const uint32_t nx = (uint32_t)g.nx;
     const uint32_t tile = (uint32_t)rows * nx;
     const uint32_t base = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y0) * nx;
-    for (uint32_t n = threadIdx.x; n < tile; n += kTmaThreads) {
+    for (uint32_t n = threadIdx.x; n < tile; n += TmaShape<Q>::threads) {
         const uint32_t rr = __umulhi(n, p.rdiv);
         const uint32_t x = n - rr * nx;
         const uint32_t self = base + n;
         // slots of x - 1 and x + 1 in the node's staged row, periodic in x
         const uint32_t sm = x == 0 ? n + nx - 1u : n - 1u;
         const uint32_t sp = x == nx - 1u ? n + 1u - nx : n + 1u;
-        float h[kQ];
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) {
-            const uint32_t j = ex19(i) > 0 ? sm : (ex19(i) < 0 ? sp : n);
-            h[i] = Codec<S>::load_plain(stage + i * TN + j);
-        }
+        bool xl = false, xh = false, yl = false, yh = false, zl = false, zh = false, any = false;
         if (WALLS) {
             const int y = y0 + (int)rr;
             const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
-            const bool xl = wx && x == 0, xh = wx && x == nx - 1u;
-            const bool yl = wy && y == 0, yh = wy && y == g.ny - 1;
-            const bool zl = wz && z == 0, zh = wz && z == g.nz - 1;
-            // nodes next to a wall are few: the warps without one skip this
-            if (__any_sync(__activemask(), xl || xh || yl || yh || zl || zh)) {
-                const bool bb[kQ] = {false,
-                                     xl, xh, yl, yh, zl, zh,
-                                     xl || yl, xh || yl, xl || yh, xh || yh,
-                                     xl || zl, xh || zl, xl || zh, xh || zh,
-                                     yl || zl, yh || zl, yl || zh, yh || zh};
-#pragma unroll
-                for (int i = 1; i < kQ; ++i)
-                    if (bb[i]) h[i] = Codec<S>::load(src + (size_t)opposite(i) * g.stride + self);
-            }
+            xl = wx && x == 0; xh = wx && x == nx - 1u;
+            yl = wy && y == 0; yh = wy && y == g.ny - 1;
+            zl = wz && z == 0; zh = wz && z == g.nz - 1;
+            // nodes next to a wall are few: the warps without one skip the bounce-back reads
+            any = __any_sync(__activemask(), xl || xh || yl || yh || zl || zh);
         }
         float fx = tfx, fy = tfy, fz = tfz;
         if (FM == kForceField) {  // the staged field, scaled as force_at does
@@ -266,23 +283,76 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
             fy = fst[1] * F.scale;
             fz = fst[2] * F.scale;
         }
-        const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
-        if (!(fabsf(drho) < 0.9f)) atomicOr(flag, 1);
-        store_node<S>(dst + self, g.stride, h, self, key);
+        if constexpr (Q == 19) {
+            float h[kQ];
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                const uint32_t j = ex19(i) > 0 ? sm : (ex19(i) < 0 ? sp : n);
+                h[i] = Codec<S>::load_plain(stage + i * TN + j);
+            }
+            if (WALLS && any) {
+                const bool bb[kQ] = {false,
+                                     xl, xh, yl, yh, zl, zh,
+                                     xl || yl, xh || yl, xl || yh, xh || yh,
+                                     xl || zl, xh || zl, xl || zh, xh || zh,
+                                     yl || zl, yh || zl, yl || zh, yh || zh};
+#pragma unroll
+                for (int i = 1; i < kQ; ++i)
+                    if (bb[i]) h[i] = Codec<S>::load(src + (size_t)opposite(i) * g.stride + self);
+            }
+            const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
+            if (!(fabsf(drho) < 0.9f)) atomicOr(flag, 1);
+            store_node<S>(dst + self, g.stride, h, self, key);
+        } else {  // D3Q27, the cube by velocity code (0: e = 0, 1: +1, 2: -1)
+            float h[3][3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const uint32_t j = a == 1 ? sm : (a == 2 ? sp : n);
+                        h[a][b][c] = Codec<S>::load_plain(stage + q27_index(a, b, c) * TN + j);
+                    }
+            if (WALLS && any) {
+                const bool bx[3] = {false, xl, xh}, by[3] = {false, yl, yh}, bz[3] = {false, zl, zh};
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            if (bx[a] || by[b] || bz[c]) {
+                                const int o = q27_index(a ? 3 - a : 0, b ? 3 - b : 0, c ? 3 - c : 0);
+                                h[a][b][c] = Codec<S>::load(src + (size_t)o * g.stride + self);
+                            }
+            }
+            const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
+            if (!(fabsf(drho) < 0.9f)) atomicOr(flag, 1);
+            float f[kQ27];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) f[q27_index(a, b, c)] = h[a][b][c];
+            store_node<S, kQ27>(dst + self, g.stride, f, self, key);
+        }
     }
 }
 
-template <typename C, typename S, int FM, bool WALLS>
-__global__ void __launch_bounds__(kTmaThreads, kTmaBlocksPerSM)
-    k_step_tma(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r, ForceArgs F, int *__restrict__ flag,
+template <typename C, typename S, int FM, bool WALLS, int Q, typename R>
+__global__ void __launch_bounds__(TmaShape<Q>::threads, TmaShape<Q>::blocks)
+    k_step_tma(const S *__restrict__ src, S *__restrict__ dst, Geom g, R r, ForceArgs F, int *__restrict__ flag,
                uint32_t key, TilePlan p) {
+    constexpr int kTmaStages = TmaShape<Q>::stages;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);     // [stages]: copies of the buffer's tile arrived
     int *done = reinterpret_cast<int *>(smem + 64);         // [stages]: warps finished with the buffer's tile
     int *issued = reinterpret_cast<int *>(smem + 96);       // [stages]: tiles copied into the buffer so far
     volatile int *abort = reinterpret_cast<volatile int *>(smem + 124);
     unsigned char *buf = smem + 128;
-    constexpr size_t SB = stage_bytes<S, FM>();
+    constexpr size_t SB = stage_bytes<S, FM, Q>();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     if (threadIdx.x == 0) {
@@ -299,7 +369,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaBlocksPerSM)
         for (int k = 0; k < kTmaStages; ++k) {
             const int t = blockIdx.x + k * gridDim.x;
             if (t < p.ntiles) {
-                issue_tile<S, FM, WALLS>(src, F, g, p, t, buf + k * SB, &bar[k], lane);
+                issue_tile<S, FM, WALLS, Q>(src, F, g, p, t, buf + k * SB, &bar[k], lane);
                 if (lane == 0) issued[k] = 1;
             }
         }
@@ -311,7 +381,11 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaBlocksPerSM)
     for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++k) {
         const int s = k % kTmaStages;
         float tfx = 0.0f, tfy = 0.0f, tfz = 0.0f;  // a uniform force (the others come staged)
-        if (FM == kForceUniform) force_at<FM>(F, g, z, 0u, tfx, tfy, tfz);
+        if (FM == kForceUniform) {
+            tfx = F.fx * F.scale;
+            tfy = F.fy * F.scale;
+            tfz = F.fz * F.scale;
+        }
         const bool ok = mbar_wait(&bar[s], (uint32_t)(k / kTmaStages) & 1u);
         if (!ok || *abort) {
             if (!ok && lane == 0) {
@@ -320,7 +394,8 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaBlocksPerSM)
             }
             break;
         }
-        compute_tile<C, S, FM, WALLS>(src, dst, g, r, F, flag, key, p, z, yt * p.rows, buf + s * SB, tfx, tfy, tfz);
+        compute_tile<C, S, FM, WALLS, Q>(src, dst, g, r, F, flag, key, p, z, yt * p.rows, buf + s * SB, tfx, tfy,
+                                         tfz);
         __syncwarp();
         int last = 0;
         if (lane == 0) {
@@ -332,7 +407,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaBlocksPerSM)
             const int tn = t + kTmaStages * gridDim.x;
             if (tn < p.ntiles) {
                 fence_proxy_async();  // the buffer's reads by every warp precede the copies into it
-                issue_tile<S, FM, WALLS>(src, F, g, p, tn, buf + s * SB, &bar[s], lane);
+                issue_tile<S, FM, WALLS, Q>(src, F, g, p, tn, buf + s * SB, &bar[s], lane);
                 if (lane == 0) ++issued[s];
             }
         }
@@ -352,32 +427,47 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaBlocksPerSM)
     }
 }
 
-// Launch the staged step if it applies to this geometry and buffer; returns
-// false (nothing launched) otherwise.
-template <typename C, typename S, int FM>
-bool launch_step_tma(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F, int *flag,
+// Launch the staged step (Q = 19 or 27 populations, rates R) if it applies to
+// this geometry, buffer and force; returns false (nothing launched) otherwise.
+template <int Q, typename C, typename S, int FM, typename R>
+bool launch_step_tma(const Launch &L, const void *src, void *dst, const R &r, const ForceArgs &F, int *flag,
                      uint32_t key, cudaError_t &err) {
-    TilePlan p;
-    if (!tile_plan(L.g, sizeof(S), src, 0, p)) return false;
-    if (FM == kForceField && ((((uintptr_t)F.field) & 15u) != 0 || (F.n & 3) != 0)) return false;
-    int dev = 0, sms = 0;
-    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return true;
-    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return true;
-    const size_t smem = tile_smem_bytes<S, FM>();
-    const int grid = p.ntiles < kTmaBlocksPerSM * sms ? p.ntiles : kTmaBlocksPerSM * sms;
-    tile_plan(L.g, sizeof(S), src, grid, p);
-    if (L.g.walls) {
-        auto kern = k_step_tma<C, S, FM, true>;
-        if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return true;
-        kern<<<grid, kTmaThreads, smem, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key, p);
+    if constexpr (!tile_fits<S, FM, Q>()) {
+        return false;
     } else {
-        auto kern = k_step_tma<C, S, FM, false>;
-        if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return true;
-        kern<<<grid, kTmaThreads, smem, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key, p);
+        TilePlan p;
+        if (!tile_plan(L.g, sizeof(S), src, 0, p)) return false;
+        if (FM == kForceField && ((((uintptr_t)F.field) & 15u) != 0 || (F.n & 3) != 0)) return false;
+        int dev = 0, sms = 0;
+        if ((err = cudaGetDevice(&dev)) != cudaSuccess) return true;
+        if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return true;
+        constexpr size_t smem = tile_smem_bytes<S, FM, Q>();
+        constexpr int kBlocks = TmaShape<Q>::blocks, kThreads = TmaShape<Q>::threads;
+        const int grid = p.ntiles < kBlocks * sms ? p.ntiles : kBlocks * sms;
+        tile_plan(L.g, sizeof(S), src, grid, p);
+        if (L.g.walls) {
+            auto kern = k_step_tma<C, S, FM, true, Q, R>;
+            if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+                return true;
+            kern<<<grid, kThreads, smem, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key, p);
+        } else {
+            auto kern = k_step_tma<C, S, FM, false, Q, R>;
+            if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+                return true;
+            kern<<<grid, kThreads, smem, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key, p);
+        }
+        err = cudaGetLastError();
+        return true;
     }
-    err = cudaGetLastError();
+}
+
+// Whether a step of this context would run staged (for clbm_info).
+inline bool step_staged_for(const Geom &g, size_t elem, const void *src, int q, int force_mode) {
+    TilePlan p;
+    if (!tile_plan(g, elem, src, 0, p)) return false;
+    if (q == 27 && force_mode == kForceField) return tile_fits<__half, kForceField, 27>();
     return true;
 }
 
