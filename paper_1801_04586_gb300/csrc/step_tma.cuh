@@ -13,7 +13,7 @@
 // storage stays on k_step, which already runs at the DRAM bound.
 //
 // Tile: `rows` consecutive x-rows (y0 .. y0 + rows - 1) of one z-plane, at
-// most kTileNodes nodes. Under the pull map of Eq. 8, population i of the
+// most a pitch of nodes (TmaShape). Under the pull map of Eq. 8, population i of the
 // tile's nodes comes from the same rows shifted by (-e_iy, -e_iz), each read
 // at x - e_ix. The y/z shift is applied when copying (one or two contiguous
 // runs of rows per population, two where the shift wraps around a periodic
@@ -44,16 +44,23 @@
 
 namespace clbm {
 
-// Launch shape per lattice: threads per block, resident blocks per SM
-// (registers and shared memory are sized for it) and shared buffers per block
-// (at most 7).
-template <int Q>
+// Launch shapes: threads per block, resident blocks per SM (registers and
+// shared memory are sized for them), shared buffers per block (at most 7),
+// and the tile pitch: the most nodes of a tile, and the element pitch of a
+// population's rows in a buffer.
+template <int THREADS, int BLOCKS, int STAGES, int PITCH>
 struct TmaShape {
-    static constexpr int threads = 512, blocks = 2, stages = 2;
+    static constexpr int threads = THREADS, blocks = BLOCKS, stages = STAGES, pitch = PITCH;
 };
-constexpr int kTileNodes = 1024;   // nodes per tile, and the element pitch of a population's rows in a buffer:
-                                   // a buffer of 19 populations of 16-bit values is 38 KB, so two blocks of
-                                   // two buffers fit an SM
+// D3Q19: two blocks of 512 threads take two nodes each of a 1024-node tile; a
+// buffer of 19 populations of 16-bit values is 38 KB.
+using TmaShape19 = TmaShape<512, 2, 2, 1024>;
+// D3Q19 with walls: the bounce-back reads need more than the 64 registers of
+// that shape (it spills 8-28 bytes); three blocks of 256 threads at up to 85
+// registers take three nodes each of a 768-node tile (FP16 y/z-walled 256^3:
+// 56.8k against 52.9k MLUPS). Rows above 768 nodes, and a force field, whose
+// rows do not fit three blocks' buffers, take TmaShape19.
+using TmaShape19W = TmaShape<256, 3, 2, 768>;
 constexpr long long kWaitCycles = 4000000000ll;  // bound of one barrier wait, about 2 s at 2 GHz
 
 struct TilePlan {
@@ -68,39 +75,35 @@ struct TilePlan {
 // take four nodes each of a 1024-node tile (0.60 of roofline at 256^3 FP16;
 // 512 threads at 64 registers spilled 60-150 bytes and measured 0.51, 384
 // threads at 80 registers 0.59, one block of 512 threads with 4 buffers 0.52).
-template <>
-struct TmaShape<27> {
-    static constexpr int threads = 256, blocks = 2, stages = 2;
-};
+using TmaShape27 = TmaShape<256, 2, 2, 1024>;
 
-// Bytes of one buffer: Q x kTileNodes stored values, then the force on the
-// tile's nodes: for a field its three components (3 x kTileNodes floats),
-// for a z-profile the tile plane's three values.
-template <typename S, int FM, int Q>
+// Bytes of one buffer: Q x pitch stored values, then the force on the tile's
+// nodes: for a field its three components (3 x pitch floats), for a z-profile
+// the tile plane's three values.
+template <typename S, int FM, int Q, typename SH>
 __host__ __device__ constexpr size_t stage_bytes() {
-    return (size_t)Q * kTileNodes * sizeof(S) +
-           (FM == kForceField ? 3 * kTileNodes * sizeof(float) : (FM == kForceProfileZ ? 16 : 0));
+    return (size_t)Q * SH::pitch * sizeof(S) +
+           (FM == kForceField ? 3 * SH::pitch * sizeof(float) : (FM == kForceProfileZ ? 16 : 0));
 }
 
 // Shared memory of one block: the barriers, then the buffers.
-template <typename S, int FM, int Q>
+template <typename S, int FM, int Q, typename SH>
 constexpr size_t tile_smem_bytes() {
-    return 128 + TmaShape<Q>::stages * stage_bytes<S, FM, Q>();
+    return 128 + SH::stages * stage_bytes<S, FM, Q, SH>();
 }
 
 // Whether the resident blocks fit the 228 KB of shared memory of an SM (1 KB
 // of each block's share is reserved).
-template <typename S, int FM, int Q>
+template <typename S, int FM, int Q, typename SH>
 constexpr bool tile_fits() {
-    return TmaShape<Q>::blocks * (tile_smem_bytes<S, FM, Q>() + 1024) <= 228 * 1024;
+    return SH::blocks * (tile_smem_bytes<S, FM, Q, SH>() + 1024) <= 228 * 1024;
 }
 
 // Whether the staged step applies, and its plan for a grid of `grid` blocks
-// (0: eligibility only). The copies need 16-byte aligned rows (nx x elem and
-// stride x elem multiples of 16, src 16-byte aligned) and a row must fit a
-// tile.
-inline bool tile_plan(const Geom &g, size_t elem, const void *src, int grid, TilePlan &p) {
-    const int tn = kTileNodes;
+// (0: eligibility only) and tile pitch tn. The copies need 16-byte aligned
+// rows (nx x elem and stride x elem multiples of 16, src 16-byte aligned) and
+// a row must fit a tile.
+inline bool tile_plan(const Geom &g, size_t elem, const void *src, int grid, int tn, TilePlan &p) {
     if (elem != 2) return false;  // FP32 steps stay on k_step, which already runs at the DRAM bound
     if (g.nx > tn || ((size_t)g.nx * elem) % 16 != 0 || ((size_t)g.stride * elem) % 16 != 0 ||
         ((uintptr_t)src & 15u) != 0)
@@ -180,13 +183,13 @@ __host__ __device__ constexpr uint64_t pack_shift(int axis) {
 }
 
 // Arm `bar` with the tile's byte count and copy its source rows into the
-// buffer `stage`: population i's rows land at element i * kTileNodes, slot
+// buffer `stage`: population i's rows land at element i * pitch, slot
 // row r at r * nx; after the populations, the force: for a field, component
-// c of the tile's own rows at float c * kTileNodes (bulk copies), for a
+// c of the tile's own rows at float c * pitch (bulk copies), for a
 // z-profile the plane's three values (plain shared stores). Called by all 32
 // lanes of one warp; lane i < Q handles population i, lanes Q to Q + 2 the
 // force components.
-template <typename S, int FM, bool WALLS, int Q>
+template <typename S, int FM, bool WALLS, int Q, typename SH>
 __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, const Geom &g, const TilePlan &p,
                                            int t, unsigned char *stage, uint64_t *bar, int lane) {
     const int z = t / p.tiles_y;
@@ -222,7 +225,7 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
     const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
     if (FM == kForceProfileZ && lane >= Q && lane < Q + 3) {
         // the plane's force: a plain shared store, published to the waiting warps by the arrive below
-        float *fdst = reinterpret_cast<float *>(stage + (size_t)Q * kTileNodes * sizeof(S));
+        float *fdst = reinterpret_cast<float *>(stage + (size_t)Q * SH::pitch * sizeof(S));
         fdst[lane - Q] = __ldg(F.profile + (size_t)(lane - Q) * g.nz + z);
     }
     __syncwarp();
@@ -230,33 +233,33 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
     __syncwarp();
     if (lane < Q) {
         const S *pop = src + (size_t)lane * g.stride + (size_t)zs * g.ny * g.nx;
-        S *dst = reinterpret_cast<S *>(stage) + lane * kTileNodes;
+        S *dst = reinterpret_cast<S *>(stage) + lane * SH::pitch;
         if (n_a > 0)
             bulk_copy_g2s(dst + slot_a * g.nx, pop + (size_t)src_a * g.nx, (uint32_t)n_a * row_bytes, bar);
         if (n_b > 0)
             bulk_copy_g2s(dst + slot_b * g.nx, pop + (size_t)src_b * g.nx, (uint32_t)n_b * row_bytes, bar);
     } else if (force_lane) {
         const int c = lane - Q;
-        float *dst = reinterpret_cast<float *>(stage + (size_t)Q * kTileNodes * sizeof(S)) + c * kTileNodes;
+        float *dst = reinterpret_cast<float *>(stage + (size_t)Q * SH::pitch * sizeof(S)) + c * SH::pitch;
         bulk_copy_g2s(dst, F.field + (size_t)c * F.n + ((size_t)z * g.ny + y0) * g.nx, bytes, bar);
     }
 }
 
 // Collide and store the nodes of the tile of rows y0 .. y0 + rows - 1 of
 // plane z from its staged rows.
-template <typename C, typename S, int FM, bool WALLS, int Q, typename R>
+template <typename C, typename S, int FM, bool WALLS, int Q, typename SH, typename R>
 __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__restrict__ dst, const Geom &g,
                                              const R &r, const ForceArgs &F, int *flag, uint32_t key,
                                              const TilePlan &p, int z, int y0, const unsigned char *buf,
                                              float tfx, float tfy, float tfz) {
     const S *stage = reinterpret_cast<const S *>(buf);
-    const float *fst = reinterpret_cast<const float *>(buf + (size_t)Q * kTileNodes * sizeof(S));
-    constexpr int TN = kTileNodes;
+    const float *fst = reinterpret_cast<const float *>(buf + (size_t)Q * SH::pitch * sizeof(S));
+    constexpr int TN = SH::pitch;
     const int rows = min(p.rows, g.ny - y0);
     const uint32_t nx = (uint32_t)g.nx;
     const uint32_t tile = (uint32_t)rows * nx;
     const uint32_t base = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y0) * nx;
-    for (uint32_t n = threadIdx.x; n < tile; n += TmaShape<Q>::threads) {
+    for (uint32_t n = threadIdx.x; n < tile; n += SH::threads) {
         const uint32_t rr = __umulhi(n, p.rdiv);
         const uint32_t x = n - rr * nx;
         const uint32_t self = base + n;
@@ -341,18 +344,18 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
     }
 }
 
-template <typename C, typename S, int FM, bool WALLS, int Q, typename R>
-__global__ void __launch_bounds__(TmaShape<Q>::threads, TmaShape<Q>::blocks)
+template <typename C, typename S, int FM, bool WALLS, int Q, typename SH, typename R>
+__global__ void __launch_bounds__(SH::threads, SH::blocks)
     k_step_tma(const S *__restrict__ src, S *__restrict__ dst, Geom g, R r, ForceArgs F, int *__restrict__ flag,
                uint32_t key, TilePlan p) {
-    constexpr int kTmaStages = TmaShape<Q>::stages;
+    constexpr int kTmaStages = SH::stages;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);     // [stages]: copies of the buffer's tile arrived
     int *done = reinterpret_cast<int *>(smem + 64);         // [stages]: warps finished with the buffer's tile
     int *issued = reinterpret_cast<int *>(smem + 96);       // [stages]: tiles copied into the buffer so far
     volatile int *abort = reinterpret_cast<volatile int *>(smem + 124);
     unsigned char *buf = smem + 128;
-    constexpr size_t SB = stage_bytes<S, FM, Q>();
+    constexpr size_t SB = stage_bytes<S, FM, Q, SH>();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     if (threadIdx.x == 0) {
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(TmaShape<Q>::threads, TmaShape<Q>::blocks)
         for (int k = 0; k < kTmaStages; ++k) {
             const int t = blockIdx.x + k * gridDim.x;
             if (t < p.ntiles) {
-                issue_tile<S, FM, WALLS, Q>(src, F, g, p, t, buf + k * SB, &bar[k], lane);
+                issue_tile<S, FM, WALLS, Q, SH>(src, F, g, p, t, buf + k * SB, &bar[k], lane);
                 if (lane == 0) issued[k] = 1;
             }
         }
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(TmaShape<Q>::threads, TmaShape<Q>::blocks)
             }
             break;
         }
-        compute_tile<C, S, FM, WALLS, Q>(src, dst, g, r, F, flag, key, p, z, yt * p.rows, buf + s * SB, tfx, tfy,
+        compute_tile<C, S, FM, WALLS, Q, SH>(src, dst, g, r, F, flag, key, p, z, yt * p.rows, buf + s * SB, tfx, tfy,
                                          tfz);
         __syncwarp();
         int last = 0;
@@ -407,7 +410,7 @@ __global__ void __launch_bounds__(TmaShape<Q>::threads, TmaShape<Q>::blocks)
             const int tn = t + kTmaStages * gridDim.x;
             if (tn < p.ntiles) {
                 fence_proxy_async();  // the buffer's reads by every warp precede the copies into it
-                issue_tile<S, FM, WALLS, Q>(src, F, g, p, tn, buf + s * SB, &bar[s], lane);
+                issue_tile<S, FM, WALLS, Q, SH>(src, F, g, p, tn, buf + s * SB, &bar[s], lane);
                 if (lane == 0) ++issued[s];
             }
         }
@@ -427,47 +430,53 @@ __global__ void __launch_bounds__(TmaShape<Q>::threads, TmaShape<Q>::blocks)
     }
 }
 
-// Launch the staged step (Q = 19 or 27 populations, rates R) if it applies to
-// this geometry, buffer and force; returns false (nothing launched) otherwise.
-template <int Q, typename C, typename S, int FM, typename R>
-bool launch_step_tma(const Launch &L, const void *src, void *dst, const R &r, const ForceArgs &F, int *flag,
-                     uint32_t key, cudaError_t &err) {
-    if constexpr (!tile_fits<S, FM, Q>()) {
+// Launch the staged step in shape SH if it applies to this geometry, buffer
+// and force; returns false (nothing launched) otherwise.
+template <typename SH, bool WALLS, int Q, typename C, typename S, int FM, typename R>
+bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R &r, const ForceArgs &F, int *flag,
+                           uint32_t key, cudaError_t &err) {
+    if constexpr (!tile_fits<S, FM, Q, SH>()) {
         return false;
     } else {
         TilePlan p;
-        if (!tile_plan(L.g, sizeof(S), src, 0, p)) return false;
+        if (!tile_plan(L.g, sizeof(S), src, 0, SH::pitch, p)) return false;
         if (FM == kForceField && ((((uintptr_t)F.field) & 15u) != 0 || (F.n & 3) != 0)) return false;
         int dev = 0, sms = 0;
         if ((err = cudaGetDevice(&dev)) != cudaSuccess) return true;
         if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return true;
-        constexpr size_t smem = tile_smem_bytes<S, FM, Q>();
-        constexpr int kBlocks = TmaShape<Q>::blocks, kThreads = TmaShape<Q>::threads;
-        const int grid = p.ntiles < kBlocks * sms ? p.ntiles : kBlocks * sms;
-        tile_plan(L.g, sizeof(S), src, grid, p);
-        if (L.g.walls) {
-            auto kern = k_step_tma<C, S, FM, true, Q, R>;
-            if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-                cudaSuccess)
-                return true;
-            kern<<<grid, kThreads, smem, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key, p);
-        } else {
-            auto kern = k_step_tma<C, S, FM, false, Q, R>;
-            if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-                cudaSuccess)
-                return true;
-            kern<<<grid, kThreads, smem, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key, p);
-        }
+        constexpr size_t smem = tile_smem_bytes<S, FM, Q, SH>();
+        const int grid = p.ntiles < SH::blocks * sms ? p.ntiles : SH::blocks * sms;
+        tile_plan(L.g, sizeof(S), src, grid, SH::pitch, p);
+        auto kern = k_step_tma<C, S, FM, WALLS, Q, SH, R>;
+        if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return true;
+        kern<<<grid, SH::threads, smem, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key, p);
         err = cudaGetLastError();
         return true;
+    }
+}
+
+// Launch the staged step (Q = 19 or 27 populations, rates R) if it applies;
+// returns false (nothing launched) otherwise.
+template <int Q, typename C, typename S, int FM, typename R>
+bool launch_step_tma(const Launch &L, const void *src, void *dst, const R &r, const ForceArgs &F, int *flag,
+                     uint32_t key, cudaError_t &err) {
+    if constexpr (Q == 27) {
+        return L.g.walls ? launch_step_tma_shape<TmaShape27, true, Q, C, S, FM>(L, src, dst, r, F, flag, key, err)
+                         : launch_step_tma_shape<TmaShape27, false, Q, C, S, FM>(L, src, dst, r, F, flag, key, err);
+    } else {
+        if (!L.g.walls)
+            return launch_step_tma_shape<TmaShape19, false, Q, C, S, FM>(L, src, dst, r, F, flag, key, err);
+        return launch_step_tma_shape<TmaShape19W, true, Q, C, S, FM>(L, src, dst, r, F, flag, key, err) ||
+               launch_step_tma_shape<TmaShape19, true, Q, C, S, FM>(L, src, dst, r, F, flag, key, err);
     }
 }
 
 // Whether a step of this context would run staged (for clbm_info).
 inline bool step_staged_for(const Geom &g, size_t elem, const void *src, int q, int force_mode) {
     TilePlan p;
-    if (!tile_plan(g, elem, src, 0, p)) return false;
-    if (q == 27 && force_mode == kForceField) return tile_fits<__half, kForceField, 27>();
+    if (!tile_plan(g, elem, src, 0, 1024, p)) return false;
+    if (q == 27 && force_mode == kForceField) return tile_fits<__half, kForceField, 27, TmaShape27>();
     return true;
 }
 
