@@ -1,42 +1,41 @@
-// step_tma.cuh -- the D3Q19 A/B step for 16-bit storage with the pulled rows
-// staged in shared memory by bulk asynchronous copies (cp.async.bulk: the TMA
-// unit), templated on the collision like k_step.
+// step_tma.cuh -- the A/B step for 16-bit storage (D3Q19 and D3Q27) with the
+// pulled rows staged in shared memory by bulk asynchronous copies
+// (cp.async.bulk: the TMA unit), templated on the collision like k_step.
 //
 // Why: k_step with 16-bit storage is bound by instruction issue, not DRAM:
 // a node's 19 loads each need 64-bit address arithmetic (pull offsets with
 // periodic wrap), and each load holds a register until its data arrive, so
 // the warps alternate between waiting and computing. Here the TMA unit moves
 // whole rows into shared memory a tile ahead of the threads, which read
-// their 19 values from shared memory at three addresses (x - 1, x, x + 1)
-// plus constant offsets, collide and store exactly as k_step does: the
-// results are bit-identical, with a fifth fewer instructions per node. FP32
-// storage stays on k_step, which already runs at the DRAM bound.
+// their values from shared memory at three addresses (x - 1, x, x + 1) plus
+// constant offsets, collide and store exactly as k_step does: the results
+// are bit-identical, with a fifth fewer instructions per node. FP32 storage
+// stays on k_step, which already runs at the DRAM bound.
 //
 // Tile: `rows` consecutive x-rows (y0 .. y0 + rows - 1) of one z-plane, at
-// most a pitch of nodes (TmaShape). Under the pull map of Eq. 8, population i of the
-// tile's nodes comes from the same rows shifted by (-e_iy, -e_iz), each read
-// at x - e_ix. The y/z shift is applied when copying (one or two contiguous
-// runs of rows per population, two where the shift wraps around a periodic
-// face); the x shift, with its periodic wrap, when reading shared memory.
-// Every source row of every population is copied once per step, so the DRAM
-// traffic is the algorithmic 2 x 19 values per node.
+// most a pitch of nodes (TmaShape). Under the pull map of Eq. 8, population
+// i of the tile's nodes comes from the same rows shifted by (-e_iy, -e_iz),
+// each read at x - e_ix. The y/z shift is applied when copying (one or two
+// contiguous runs of rows per population, two where the shift wraps around a
+// periodic face); the x shift, with its periodic wrap, when reading shared
+// memory. Every source row of every population is copied once per step, so
+// the DRAM traffic is the algorithmic 2 x Q values per node.
 //
 // Walls (halfway bounce-back): a source row beyond a wall face is not
 // copied; the nodes that would pull from it, and the nodes at an x wall, read
 // their own opposite population from global memory instead.
 //
 // Pipeline: a persistent grid; block b walks tiles b, b + gridDim.x, ... with
-// a few shared buffers (TmaShape) and one mbarrier each. A warp arms a buffer's
-// barrier with the tile's byte count and issues its copies (lane i:
+// a few shared buffers (TmaShape) and one mbarrier each. A warp arms a
+// buffer's barrier with the tile's byte count and issues its copies (lane i:
 // population i). Every warp waits on the barrier of its next tile, computes
 // its nodes and counts itself done with the buffer; the last warp to finish
 // refills the buffer with the tile as many tiles ahead as there are buffers.
 // There is no block barrier in the loop, so warps drift apart by up to that
-// many tiles instead
-// of waiting for the slowest. Every wait is bounded (kWaitCycles); on expiry
-// the block sets bit 1 of the flag (reported as CLBM_ERR_TIMEOUT), its warps
-// leave the loop, and one thread waits, again bounded, for the copies still
-// in flight before the block ends.
+// many tiles instead of waiting for the slowest. Every wait is bounded
+// (kWaitCycles); on expiry the block sets bit 1 of the flag (reported as
+// CLBM_ERR_TIMEOUT), its warps leave the loop, and one thread waits, again
+// bounded, for the copies still in flight before the block ends.
 #pragma once
 
 #include "d3q27.cuh"
