@@ -447,8 +447,14 @@ bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R 
         const int grid = p.ntiles < SH::blocks * sms ? p.ntiles : SH::blocks * sms;
         tile_plan(L.g, sizeof(S), src, grid, SH::pitch, p);
         auto kern = k_step_tma<C, S, FM, WALLS, Q, SH, R>;
-        if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return true;
+        // the shared-memory opt-in, once per device for this kernel (a repeated set is harmless)
+        static int opted_in[64] = {};
+        if (dev < 0 || dev >= 64 || !opted_in[dev]) {
+            if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+                return true;
+            if (dev >= 0 && dev < 64) opted_in[dev] = 1;
+        }
         kern<<<grid, SH::threads, smem, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key, p);
         err = cudaGetLastError();
         return true;
