@@ -175,6 +175,40 @@ def test_geometries_without_staging_fall_back(shape_xyz, storage):
     assert g.info()["staged"] == 0
 
 
+def test_staged_full_size_sampled_against_oracle():
+    """The FP16 256^3 Kolmogorov workload of the benchmark, in the launch
+    configuration it times: for 2048 sampled nodes x, the oracle collides the
+    node's (FP16) state; the staged step's result, read at x + e_i where
+    population i streams to, equals it rounded to FP16, within half a unit in
+    the last place plus the FP32 arithmetic's error."""
+    n = 256
+    g = Lattice(n, n, n, 0.01, storage="f16", device=dev())
+    assert g.info()["staged"] == 1
+    o = oracle.Lattice(1, 1, 1, s2=s2_of(0.01))
+    prof = synthetic.kolmogorov_profile(n, 1e-5)
+    g.set_force_profile_z(t(prof))
+    g.init_equilibrium(None, t(synthetic.divfree_velocity((n, n, n), seed=1, umax=0.02)))
+    nodes = np.random.default_rng(551).choice(n ** 3, 2048, replace=False)
+    z, y, x = nodes // (n * n), (nodes // n) % n, nodes % n
+    E = oracle.velocities(19).astype(np.int64)
+    # the state read out is post-streaming: population i of node x at t = 1 is
+    # the post-collision value of node x - e_i, so node x's result sits at x + e_i
+    dst = np.stack([(((z + E[i, 2]) % n) * n + (y + E[i, 1]) % n) * n + (x + E[i, 0]) % n + i * n ** 3
+                    for i in range(19)], axis=1)
+    h0 = g.populations(deviation=True).reshape(19, -1)[:, torch.from_numpy(nodes).to(dev())]
+    h0 = h0.double().cpu().numpy().T
+    g.step(1)
+    hg = g.populations(deviation=True).reshape(-1)[torch.from_numpy(dst.reshape(-1)).to(dev())]
+    hg = hg.double().cpu().numpy().reshape(-1, 19)
+    w = W.reshape(19)
+    ho = np.stack([oracle.collide(o, h0[k] + w, (prof[0, z[k]], prof[1, z[k]], prof[2, z[k]])) - w
+                   for k in range(len(nodes))])
+    err = np.abs(hg - ho) / ulp16(np.maximum(np.abs(hg), np.abs(ho)))
+    report("staged_f16_full_size_sampled_ulp", max_ulp=float(err.max()))
+    assert err.max() <= 0.55
+    g.close()
+
+
 def ulp16(v):
     """Spacing of FP16 numbers at |v| (subnormal spacing below 2^-14)."""
     e = np.floor(np.log2(np.maximum(np.abs(v), 2.0 ** -14)))
