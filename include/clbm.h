@@ -233,7 +233,9 @@ int clbm_reduce_pair(clbm_ctx *ctx, const float *a_dev, const float *b_dev, int6
 
 /* Read the instability flag (synchronises the stream): CLBM_OK, or
  * CLBM_ERR_UNSTABLE if any step since the last clear saw a density outside
- * (0.1, 1.9) or a non-finite one. clear != 0 resets the flag. */
+ * (0.1, 1.9) or a non-finite one, or CLBM_ERR_TIMEOUT if a staged step's
+ * wait for its bulk copies gave up (the state is then invalid). clear != 0
+ * resets the flag. */
 int clbm_check(clbm_ctx *ctx, int clear);
 
 /* Raw state: the internal population buffer (clbm_info.state_bytes bytes).
