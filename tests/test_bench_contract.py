@@ -1,0 +1,49 @@
+"""The benchmark's reference arm and the absence of a CPU fallback, on CPU.
+
+`bench.py --impl reference` times the FP64 oracle on the host cores and must
+print one JSON line with the keys every benchmark line carries, marked as the
+reference implementation, with a CPU-baseline block describing the run and
+an end-to-end block without host-device traffic. The product path, by
+contrast, runs only in the CUDA library: without a GPU the lattice refuses to
+start instead of falling back to a CPU computation.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def last_json_line(text):
+    lines = [ln for ln in text.strip().splitlines() if ln.startswith("{")]
+    assert lines, text
+    return json.loads(lines[-1])
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    d = last_json_line(r.stdout)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert key in d, key
+    assert d["impl"] == "reference"
+    assert d["unit"] == "MLUPS" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["steps"] == 1 and d["warmup"] == 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the behaviour without a GPU")
+def test_no_cpu_fallback_without_gpu():
+    from paper_1801_04586_gb300 import Lattice
+    with pytest.raises(RuntimeError, match="CUDA device is required"):
+        Lattice(8, 8, 8, 0.1)
