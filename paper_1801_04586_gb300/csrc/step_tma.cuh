@@ -182,10 +182,10 @@ __host__ __device__ constexpr uint64_t pack_shift(int axis) {
 }
 
 // Arm `bar` with the tile's byte count and copy its source rows into the
-// buffer `stage`: population i's rows land at element i * pitch, slot
-// row r at r * nx; after the populations, the force: for a field, component
-// c of the tile's own rows at float c * pitch (bulk copies), for a
-// z-profile the plane's three values (plain shared stores). Called by all 32
+// buffer `stage`: population i's rows land at element i * pitch, slot row r
+// at r * nx; after the populations, the force: for a field, component c of
+// the tile's own rows at float c * pitch (bulk copies), for a z-profile the
+// plane's three values (plain shared stores). Called by all 32
 // lanes of one warp; lane i < Q handles population i, lanes Q to Q + 2 the
 // force components.
 template <typename S, int FM, bool WALLS, int Q, typename SH>
@@ -213,7 +213,7 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
             } else if (start + rows > g.ny) {   // last slot row from row 0 (periodic) or none (wall)
                 src_a = start; slot_a = 0; n_a = g.ny - start;
                 if (!wy) { src_b = 0; slot_b = g.ny - start; n_b = rows - (g.ny - start); }
-                } else {
+            } else {
                 src_a = start; slot_a = 0; n_a = rows;
             }
         }
