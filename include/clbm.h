@@ -1,9 +1,11 @@
 /*
- * clbm.h -- C ABI of the GB300 (sm_103a) D3Q19 cascaded lattice Boltzmann
+ * clbm.h -- C ABI of the GB300 (sm_103a) cascaded lattice Boltzmann
  * library: the fused stream-and-collide step of Fei, Luo & Li,
  * "Three-dimensional cascaded lattice Boltzmann method: improved
  * implementation and consistent forcing scheme" (arXiv:1801.04586),
- * Appendix A (D3Q19) with the collision of Sec. II.A-B.
+ * on D3Q19 (Appendix A) or D3Q27 (Sec. II.A-B, Eqs. 12-16), together with
+ * the collisions the paper compares it with on the same lattices: SRT
+ * (Sec. III.A, Table I) and the non-orthogonal MRT of Appendix B.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -154,9 +156,10 @@ typedef struct clbm_info {
 
 typedef struct clbm_ctx clbm_ctx;
 
-/* Create a lattice context: validates p, allocates two population buffers
- * (A/B) of Q * N elements each on the current CUDA device, and binds the
- * context to `stream` (a cudaStream_t; NULL = legacy default stream).
+/* Create a lattice context: validates p, allocates the population buffers
+ * of Q * N elements each on the current CUDA device (two for the A/B
+ * pattern, one for the in-place pattern), and binds the context to `stream`
+ * (a cudaStream_t; NULL = legacy default stream).
  * The populations are zero deviations (f = w, rest at rho = 1) until an init
  * call. *out receives the context (owned by the caller; free with
  * clbm_destroy). Errors: CLBM_ERR_ARG, CLBM_ERR_OOM, CLBM_ERR_CUDA. */
@@ -166,7 +169,8 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out);
  * accepted. */
 int clbm_destroy(clbm_ctx *ctx);
 
-/* Fill *info. */
+/* Fill *info with the context's sizes, layout and launch choices (see
+ * clbm_info). No GPU work. Errors: CLBM_ERR_ARG for a NULL argument. */
 int clbm_get_info(const clbm_ctx *ctx, clbm_info *info);
 
 /* Body force (Sec. II.A, Eqs. 5-6 and 9; a force density). Exactly one force
