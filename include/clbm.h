@@ -267,9 +267,9 @@ int clbm_load_state(clbm_ctx *ctx, const void *host_buf, size_t bytes);
  * step's launch and copied back on a second stream of the context while
  * the following steps run. Otherwise they come from one
  * clbm_reduce_moments pass before each step, copied back asynchronously.
- * The last comes from one reduction after the final step. The call synchronises once, at the end, then returns
- * CLBM_ERR_UNSTABLE if any mass sum is non-finite or the instability flag is
- * set. Device scratch for the staging fields and partial sums is allocated
+ * The last comes from one reduction after the final step. The call
+ * synchronises once, at the end, then returns CLBM_ERR_UNSTABLE if any mass
+ * sum is non-finite or the instability flag is set. Device scratch for the staging fields and partial sums is allocated
  * on first use and kept by the context. Host buffers should be pinned for
  * full copy speed and for the copies to overlap the steps. */
 int clbm_run_host(clbm_ctx *ctx, const float *rho_host, const float *u_host, int64_t nsteps,
