@@ -73,6 +73,29 @@ def test_poiseuille_startup_series():
     assert _e2(_poiseuille(n, nu, t, s3=an.noslip_s3(s2), s2b=s2, F=F), ua) < 1e-4
 
 
+def test_poiseuille_error_linear_in_bulk_viscosity_offset():
+    """Sec. III.B, on the separate trace rate of Eq. 13: at nu = 0.1 with the
+    no-slip s3, the steady Poiseuille error E2 vanishes at xi = 2 nu / 3
+    (s2b = s2) and grows in proportion to |xi - 2 nu / 3| on both sides.
+    Re = 2 u0 L / nu = 10 (F = 1e-4, 2L = 20); xi = (2/3)(1/s2b - 1/2) c_s^2."""
+    n, nu, F = 20, 0.1, 1e-4
+    s2 = an.s2_from_nu(nu)
+    ua = an.poiseuille_steady(n, F, nu)
+    steps = int(30 * 4 * (n / 2) ** 2 / (np.pi ** 2 * nu))
+    xi0 = 2.0 * nu / 3.0
+    ratios = np.array([0.5, 0.75, 1.0, 1.5, 2.0, 3.0])  # xi / xi0
+    e2 = []
+    for r in ratios:
+        s2b = 1.0 / (r * xi0 / (2.0 / 9.0) + 0.5)
+        e2.append(_e2(_poiseuille(n, nu, steps, s3=an.noslip_s3(s2), s2b=s2b, F=F), ua))
+    e2 = np.array(e2)
+    at = ratios == 1.0
+    assert e2[at][0] < 1e-11
+    slope = e2[~at] / np.abs(ratios[~at] - 1.0)
+    assert slope.min() > 1e-7
+    np.testing.assert_allclose(slope, slope.mean(), rtol=1e-2)
+
+
 def test_square_duct_series():
     """Sec. III.C duct at nu = 0.2, Fx = 2e-4 on a 16 x 16 cross-section: the
     steady series is met within 0.15% with the no-slip s3 (16/13 at nu = 0.2),
