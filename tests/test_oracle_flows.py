@@ -73,6 +73,29 @@ def test_poiseuille_startup_series():
     assert _e2(_poiseuille(n, nu, t, s3=an.noslip_s3(s2), s2b=s2, F=F), ua) < 1e-4
 
 
+@pytest.mark.parametrize("q,nu", [(19, 0.05), (19, 0.1), (19, 0.2), (27, 0.1)])
+def test_poiseuille_slip_closed_form(q, nu):
+    """Sec. III.B's no-slip rule s3 = (16 - 8 s2)/(8 - s2) is the case
+    Lambda = (1/s2 - 1/2)(1/s3 - 1/2) = 3/16 of the bounce-back analysis it
+    cites (Ginzburg & d'Humieres, Phys. Rev. E 68, 066614, 2003): for any
+    s3, the steady profile between halfway bounce-back walls is the exact
+    parabola plus a uniform slip F (16 Lambda - 3) / (24 nu). On D3Q27 the
+    rate s3b of the k111 group (Eq. 13) does not enter."""
+    n, F = 20, 1e-6
+    s2 = an.s2_from_nu(nu)
+    ua = an.poiseuille_steady(n, F, nu)
+    steps = int(40 * 4 * (n / 2) ** 2 / (np.pi ** 2 * nu))
+    Ff = np.zeros((3, n, 1, 1))
+    Ff[0] = F
+    for s3 in (0.6, 0.9, 1.2, 1.5):
+        lam = (1.0 / s2 - 0.5) * (1.0 / s3 - 0.5)
+        lat = o.Lattice(1, 1, n, walls=4, s2=s2, s2b=s2, s3=s3, q=q, s3b=1.7 if q == 27 else 1.0)
+        f = o.step(lat, o.init(lat, None, None, Ff), Ff, steps)
+        d = o.macros(lat, f, Ff)[1][0, :, 0, 0] - ua
+        assert d.max() - d.min() < 1e-13
+        assert d.mean() == pytest.approx(F * (16.0 * lam - 3.0) / (24.0 * nu), rel=1e-6, abs=1e-14)
+
+
 def test_poiseuille_error_linear_in_bulk_viscosity_offset():
     """Sec. III.B, on the separate trace rate of Eq. 13: at nu = 0.1 with the
     no-slip s3, the steady Poiseuille error E2 vanishes at xi = 2 nu / 3
