@@ -38,6 +38,8 @@
 // bounded, for the copies still in flight before the block ends.
 #pragma once
 
+#include <atomic>
+
 #include "d3q27.cuh"
 #include "kernels.cuh"
 
@@ -447,13 +449,14 @@ bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R 
         const int grid = p.ntiles < SH::blocks * sms ? p.ntiles : SH::blocks * sms;
         tile_plan(L.g, sizeof(S), src, grid, SH::pitch, p);
         auto kern = k_step_tma<C, S, FM, WALLS, Q, SH, R>;
-        // the shared-memory opt-in, once per device for this kernel (a repeated set is harmless)
-        static int opted_in[64] = {};
-        if (dev < 0 || dev >= 64 || !opted_in[dev]) {
+        // the shared-memory opt-in, once per device for this kernel; host threads
+        // may race to set it, which repeats a harmless call
+        static std::atomic<int> opted_in[64] = {};
+        if (dev < 0 || dev >= 64 || !opted_in[dev].load(std::memory_order_relaxed)) {
             if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
                 cudaSuccess)
                 return true;
-            if (dev >= 0 && dev < 64) opted_in[dev] = 1;
+            if (dev >= 0 && dev < 64) opted_in[dev].store(1, std::memory_order_relaxed);
         }
         kern<<<grid, SH::threads, smem, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key, p);
         err = cudaGetLastError();
