@@ -47,3 +47,13 @@ def test_no_cpu_fallback_without_gpu():
     from paper_1801_04586_gb300 import Lattice
     with pytest.raises(RuntimeError, match="CUDA device is required"):
         Lattice(8, 8, 8, 0.1)
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun with N > 1 only rank 0 times the oracle and prints; the
+    other ranks exit 0 without work or output."""
+    env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
