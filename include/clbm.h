@@ -326,10 +326,18 @@ int clbm_adjoint_step(clbm_ctx *ctx, const void *state_dev, const float *lam_nex
  * It allocates nothing and needs no context: the per-block partial sums live
  * in a fixed 384 KiB __device__ array that every GPU loading the library holds
  * until exit. n may not exceed 134,217,728 (CLBM_ERR_ARG, with a message).
- * The first call on each device looks up that array's device address; make it
- * before any stream capture. All calls on a device share the array: calls that
- * overlap on the GPU race and must be serialised by the caller. The sums may
- * differ from clbm_reduce_pair's in the last bits (different block count). */
+ * The first call on each device is its set-up: it looks up that array's
+ * device address and caches it for the process. Under CUDA's lazy module
+ * loading (the default since CUDA 12.2) that first call may also load the
+ * library's device code, which allocates the array and the code and may
+ * synchronise; make it once at set-up, before any stream capture. Later calls
+ * allocate nothing. The cached address belongs to the device's primary
+ * context: after cudaDeviceReset (or anything else that destroys that
+ * context) later calls would use a stale address and must not be made.
+ * All calls on a device share the array: calls that overlap on the GPU
+ * (different streams, or other host threads) race and must be serialised by
+ * the caller. The sums may differ from clbm_reduce_pair's in the last bits
+ * (different block count). */
 int clbm_reduce_pair_noalloc(const float *a_dev, const float *b_dev, int64_t n, double *out_dev, void *stream);
 
 /* ---- many independent lattices in one launch per step ----

@@ -18,7 +18,12 @@
 //   - every call on a device shares it: each call's blocks overwrite exactly
 //     the slots its final pass reads, so nothing needs clearing between
 //     calls, but calls that overlap on the GPU (different streams, or another
-//     host thread) race on it and must be serialised by the caller.
+//     host thread) race on it and must be serialised by the caller;
+//   - the array's device address is looked up once per device and cached for
+//     the process: it belongs to the device's primary context, so a
+//     cudaDeviceReset leaves it stale (callers must not call after a reset);
+//   - under lazy module loading the first call on a device may load the
+//     module (allocating the array and the code): it is the set-up call.
 #include <cuda_runtime.h>
 
 #include <mutex>

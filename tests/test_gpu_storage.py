@@ -94,11 +94,12 @@ def test_duct_copy_against_oracle():
         errs[storage] = _e2(_duct_profile(g, nz, ny), uo)
         g.close()
     report("duct_128x32x32_vs_oracle", **errs)
-    # FP32: rounding of 20000 FP32 steps; f16sr: the stated 1e-3. Round-to-
-    # nearest FP16/BF16 stall once the per-step force increment falls below
-    # half a unit in the last place: reported, not asserted.
+    # FP32: rounding of 20000 FP32 steps; f16sr and bf16sr: the stated 1e-3.
+    # Round-to-nearest FP16/BF16 stall once the per-step force increment falls
+    # below half a unit in the last place: reported, not asserted.
     assert errs["f32"] < 1e-4
     assert errs["f16sr"] < 1e-3
+    assert errs["bf16sr"] < 1e-3
 
 
 def test_duct_512x128x128_against_series():
@@ -126,3 +127,4 @@ def test_duct_512x128x128_against_series():
     report("duct_512x128x128_vs_series", **errs, **rates)
     assert errs["f32"] < 1e-3
     assert errs["f16sr"] < 1e-3
+    assert errs["bf16sr"] < 1e-3
