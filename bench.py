@@ -8,9 +8,12 @@ lattice time step: one launch of the fused stream-and-collide kernel over all
 16,777,216 nodes. The two population buffers (1.27 GB each) are ten times the
 129 MB L2, so every step streams from HBM.
 
-Prints one JSON line (rank 0). Under torchrun (N > 1) every rank runs its own
-independent 256^3 box (weak scaling, no collective on the data path); the
-timed region is bracketed by barriers and the slowest rank's time is used.
+Prints one JSON line (rank 0). Under torchrun (N > 1) the ranks hold the z-slabs
+of one 256 x 256 x (256 N) periodic Kolmogorov box, 256^3 nodes each (weak
+scaling), and exchange the 5 populations that cross each slab face after every
+step with NCCL point-to-point transfers that overlap the slab interior's update
+(--decomp replicas runs N independent boxes instead); the timed region is
+bracketed by barriers and the slowest rank's time is used.
 
 --impl reference times the FP64 CPU oracle, as it stands, on the host cores on
 a bounded slab of the same workload.
@@ -76,6 +79,11 @@ def parse():
                     help="collision of the timed lattice (the benchmark line is cascaded; others for profiling)")
     ap.add_argument("--pattern", default="ab", choices=["ab", "aa"],
                     help="storage pattern of the timed lattice (the benchmark line is ab; aa for profiling)")
+    ap.add_argument("--decomp", default="slab", choices=["slab", "replicas"],
+                    help="N > 1: z-slabs of one lattice with face exchange (default) or independent boxes")
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="N > 1: nccl (faces between GPUs) or gloo (faces through host memory; several ranks may "
+                         "share one GPU, for testing the decomposition)")
     return ap.parse_args()
 
 
@@ -276,6 +284,53 @@ def bench_storage(storage, K, warmup, dev, side, prof, u0, peak, variant=0, latt
             "buffers": info["buffers"], "state_gb": info["buffers"] * info["state_bytes"] / 1e9}
 
 
+def bench_duct(storage, K, warmup, dev, peak):
+    """The mixed-precision square duct: 512 (periodic, x) x 128 x 128 with walls
+    on y and z, uniform F_x = 2e-6, nu = 0.05, from rest."""
+    import torch
+
+    from paper_1801_04586_gb300 import Lattice
+    lat = Lattice(512, 128, 128, 0.05, walls=6, storage=storage, device=dev)
+    lat.set_force_uniform(2e-6)
+    lat.init_equilibrium()
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record(lat.stream)
+    for _ in range(K):
+        lat.step(1)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    lat.check()
+    ms = e0.elapsed_time(e1)
+    n = lat.n
+    lat.close()
+    bpn = (4 if storage == "f32" else 2) * 2 * 19
+    achieved = bpn * n / (ms / K * 1e-3) / 1e9
+    return {"value": n * K / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / K, "bytes_per_node": bpn,
+            "achieved_gbs": achieved, "frac": achieved / peak}
+
+
+def compact(variants):
+    """The variant lines in short form for the benchmark line: [MLUPS, fraction
+    of the measured copy roofline] for throughput lines, the ratios for the
+    adjoint and the batch. The full figures go to stderr."""
+    out = {}
+    for name, v in variants.items():
+        if "value" in v:
+            out[name] = [round(v["value"]), round(v["frac"], 3)]
+        elif name.startswith("adjoint_kernel"):
+            out[name] = {"ratio": round(v["ratio"], 3), "frac": round(v["adjoint_frac"], 3)}
+        elif name.startswith("adjoint_unroll"):
+            out[name] = {"ratio": round(v["ratio"], 3)}
+        elif name.startswith("batched"):
+            out[name] = {"graph": round(v["graph_mlups"]), "per_domain": round(v["per_domain_mlups"]),
+                         "frac": round(v["graph_frac"], 3)}
+        else:
+            out[name] = v
+    return out
+
+
 def bench_adjoint(dev, side, K, peak):
     """Adjoint step kernel versus forward step kernel on the same lattice with a
     force field (F ~ N(0, 1e-5^2), seed 3): per-launch times."""
@@ -394,14 +449,19 @@ def run_gb300(args):
     import numpy as np
     import torch
 
-    from paper_1801_04586_gb300 import Lattice, synthetic
+    from paper_1801_04586_gb300 import Lattice, slabs, synthetic
+    from paper_1801_04586_gb300._capi import SLAB_FACES, SLAB_INTERIOR
     from paper_1801_04586_gb300.builder import build
 
     ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if args.dist_backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            torch.cuda.set_device(local % torch.cuda.device_count())
+            dist.init_process_group("gloo")
     else:
         dist = None
         torch.cuda.set_device(0)
@@ -413,8 +473,14 @@ def run_gb300(args):
     bx, by = (int(v) for v in args.block.split(","))
     side = args.size
     shape = (side, side, side)
+    slab = ws > 1 and args.decomp == "slab"
+    host_faces = slab and args.dist_backend == "gloo"
+    # a z-slab of the 256 x 256 x (256 N) box: the force profile and u0 repeat
+    # every 256 planes, so each slab takes the single box's
+    skw = dict(slab=3, z0=rank * side) if slab else {}
+    variant = 1 if slab and args.variant == 0 else args.variant
     lat = Lattice(side, side, side, NU, walls=0, storage=args.storage, block=(bx, by), device=dev,
-                  variant=args.variant, lattice=args.lattice, pattern=args.pattern, model=args.model)
+                  variant=variant, lattice=args.lattice, pattern=args.pattern, model=args.model, **skw)
     prof = torch.from_numpy(synthetic.kolmogorov_profile(side, F0)).to(dev)
     u0_np = synthetic.divfree_velocity(shape, seed=1, umax=UMAX)
     u0 = torch.from_numpy(u0_np).to(dev)
@@ -423,8 +489,21 @@ def run_gb300(args):
     stream = lat.stream
     sampler = ClockSampler(dev.index) if rank == 0 else None
 
+    def one_step(L):
+        if not slab:
+            L.step(1)
+            return
+        # faces first; their transfer overlaps the interior planes' update
+        L.slab_step(SLAB_FACES)
+        reqs = slabs.exchange_faces(L, rank, ws, dist, host=host_faces, wait=False)
+        L.slab_step(SLAB_INTERIOR)
+        for r in reqs:
+            r.wait()
+
     # warm-up
-    lat.step(args.warmup)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step(lat)
     torch.cuda.synchronize()
     lat.check()
 
@@ -438,7 +517,7 @@ def run_gb300(args):
     with torch.cuda.stream(stream):
         for k in range(K):
             starts[k].record(stream)
-            lat.step(1)
+            one_step(lat)
             ends[k].record(stream)
     torch.cuda.synchronize()
     if dist is not None:
@@ -448,9 +527,9 @@ def run_gb300(args):
     per_launch = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     lat.check()
     if dist is not None:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+        tt = torch.tensor([elapsed_ms], device=dev if args.dist_backend == "nccl" else "cpu")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
     clocks = sampler.stop(t_host0, t_host1) if sampler else None
 
     nodes = lat.n
@@ -460,75 +539,94 @@ def run_gb300(args):
     bytes_per_node = (2 if args.storage != "f32" else 4) * 2 * args.lattice
     achieved = bytes_per_node * nodes / mean_launch_s / 1e9
     default_case = (args.storage, args.lattice, args.pattern, args.variant, args.model) == (
-        "f32", 19, "ab", 0, "cascaded")
+        "f32", 19, "ab", 0, "cascaded") and not slab
     traffic = profiled_traffic() if default_case and side == N_SIDE else None
 
     e2e = None
     if not args.no_e2e:
-        lat_e = Lattice(side, side, side, NU, walls=0, storage="f32", block=(bx, by), device=dev)
-        lat_e.set_force_profile_z(prof)
         rho_h = torch.ones(shape, dtype=torch.float32).pin_memory()
         u_h = torch.from_numpy(u0_np).pin_memory()
         rho_o = torch.empty(shape, dtype=torch.float32).pin_memory()
         u_o = torch.empty((3,) + shape, dtype=torch.float32).pin_memory()
         mom = torch.empty(4 * (K + 1), dtype=torch.float64).pin_memory()
-        wk = max(1, min(args.warmup, 3))
-        lat_e.run_host(rho_h, u_h, wk, rho_o, u_o, mom[: 4 * (wk + 1)])
+        if not slab:
+            lat_e = Lattice(side, side, side, NU, walls=0, storage="f32", block=(bx, by), device=dev)
+            lat_e.set_force_profile_z(prof)
+            wk = max(1, min(args.warmup, 3))
+            lat_e.run_host(rho_h, u_h, wk, rho_o, u_o, mom[: 4 * (wk + 1)])
+            what = ("clbm_run_host: pinned host rho,u -> init -> K steps, each step's FP64 mass/momentum "
+                    "sums (formed in the step kernel) copied back, final rho,u read back")
+        else:
+            lat_e = Lattice(side, side, side, NU, walls=0, storage="f32", block=(bx, by), device=dev, variant=1,
+                            **skw)
+            lat_e.set_force_profile_z(prof)
+            what = ("z-slabs: pinned host rho,u -> init -> K steps with face exchange, each step's FP64 "
+                    "mass/momentum sums copied back, final rho,u read back")
+        d_rho = torch.empty(shape, dtype=torch.float32, device=dev)
+        d_u = torch.empty((3,) + shape, dtype=torch.float32, device=dev)
+        d_mom = torch.empty(4 * (K + 1), dtype=torch.float64, device=dev)
+
+        def slab_job():
+            with torch.cuda.stream(lat_e.stream):
+                d_rho.copy_(rho_h, non_blocking=True)
+                d_u.copy_(u_h, non_blocking=True)
+                lat_e.init_equilibrium(d_rho, d_u)
+                for k in range(K):
+                    lat_e.reduce_moments(d_mom[4 * k: 4 * k + 4])
+                    one_step(lat_e)
+                lat_e.reduce_moments(d_mom[4 * K:])
+                lat_e.macros(d_rho, d_u)
+                rho_o.copy_(d_rho, non_blocking=True)
+                u_o.copy_(d_u, non_blocking=True)
+                mom.copy_(d_mom, non_blocking=True)
+            torch.cuda.synchronize()
+
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lat_e.run_host(rho_h, u_h, K, rho_o, u_o, mom)
+        if slab:
+            slab_job()
+        else:
+            lat_e.run_host(rho_h, u_h, K, rho_o, u_o, mom)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         if dist is not None:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+            tt = torch.tensor([dt], device=dev if args.dist_backend == "nccl" else "cpu")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
         h2d = (rho_h.numel() + u_h.numel()) * 4
         d2h = (rho_o.numel() + u_o.numel()) * 4 + mom.numel() * 8
-        # the same field copies alone, outside the timed region: how much of the
-        # e2e time is the one-off host traffic
-        d_u = torch.empty((3,) + shape, dtype=torch.float32, device=dev)
-        c0, c1 = _events()
-        c2 = torch.cuda.Event(enable_timing=True)
-        c0.record()
-        d_u.copy_(u_h, non_blocking=True)
-        c1.record()
-        u_o.copy_(d_u, non_blocking=True)
-        c2.record()
-        torch.cuda.synchronize()
-        ub = u_h.numel() * 4
         e2e = {"value": ws * nodes * K / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / K,
-               "d2h_bytes_per_step": d2h / K,
-               "what": "clbm_run_host: pinned host rho,u -> init -> K steps, each step's FP64 mass/momentum "
-                       "sums (formed in the step kernel) copied back, final rho,u read back",
-               "h2d_gbs": ub / (c0.elapsed_time(c1) * 1e-3) / 1e9, "d2h_gbs": ub / (c1.elapsed_time(c2) * 1e-3) / 1e9,
-               "ms_total": dt * 1e3}
-        del d_u
+               "d2h_bytes_per_step": d2h / K, "steps": K, "what": what, "ms_total": dt * 1e3}
+        del d_rho, d_u, d_mom
         lat_e.close()
 
     variants = None
-    if not args.no_variants:
+    if not args.no_variants and not slab:
         S = lambda storage, **kw: (lambda: bench_storage(storage, K, args.warmup, dev, side, prof, u0, peak,  # noqa
                                                           **kw))
+        D = lambda storage: (lambda: bench_duct(storage, K, args.warmup, dev, peak))  # noqa
         lines = {
-            "f32_two_nodes_per_thread": S("f32", variant=2),
-            "f16_storage": S("f16"),
-            "bf16_storage": S("bf16"),
-            "f16_storage_one_node_per_thread": S("f16", variant=1),
-            "f16_stochastic_storage": S("f16sr"),
-            "bf16_stochastic_storage": S("bf16sr"),
-            "aa_in_place_f32": S("f32", pattern="aa"),
-            "aa_in_place_f16": S("f16", pattern="aa"),
+            "f16sr": S("f16sr"),
+            "bf16sr": S("bf16sr"),
+            "f16": S("f16"),
+            "bf16": S("bf16"),
+            "duct_f32": D("f32"),
+            "duct_f16sr": D("f16sr"),
+            "duct_bf16sr": D("bf16sr"),
+            "f16_1node": S("f16", variant=1),
+            "f32_2node": S("f32", variant=2),
+            "aa_f32": S("f32", pattern="aa"),
+            "aa_f16": S("f16", pattern="aa"),
             "walls_yz_f32": S("f32", walls=6),
             "srt_f32": S("f32", model="srt"),
             "mrt_f32": S("f32", model="mrt"),
-            "d3q27_f32": S("f32", lattice=27),
-            "d3q27_srt_f32": S("f32", lattice=27, model="srt"),
-            "d3q27_mrt_f32": S("f32", lattice=27, model="mrt"),
-            "d3q27_aa_in_place_f32": S("f32", lattice=27, pattern="aa"),
-            "d3q27_f16_storage": S("f16", lattice=27),
+            "q27_f32": S("f32", lattice=27),
+            "q27_srt_f32": S("f32", lattice=27, model="srt"),
+            "q27_mrt_f32": S("f32", lattice=27, model="mrt"),
+            "q27_aa_f32": S("f32", lattice=27, pattern="aa"),
+            "q27_f16": S("f16", lattice=27),
             "adjoint_kernel_256": lambda: bench_adjoint(dev, side, max(10, min(K, 100)), peak),
             "adjoint_unroll_64": lambda: bench_unroll(dev),
             "batched_64_domains": lambda: bench_batch(dev, args.batch_steps, peak),
@@ -546,32 +644,41 @@ def run_gb300(args):
 
     if rank == 0:
         info = lat.info()
+        if slab:
+            parallelism = (f"{ws} z-slabs of one {side}x{side}x{side * ws} box, {side}^3 each, face exchange "
+                           f"over {args.dist_backend} overlapped with the interior update")
+            workload = workload_name(side, args).replace(f"periodic {side}^3", f"periodic {side}x{side}x{side * ws}")
+        else:
+            parallelism = f"{ws} independent replica(s), one per GPU"
+            workload = workload_name(side, args)
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.storage == "f32" else f"f32 arithmetic, {args.storage} storage",
             "data": "synthetic",
-            "config": {"workload": workload_name(side, args),
+            "config": {"workload": workload,
                        "nx": side, "ny": side, "nz": side, "nu": NU, "F0": F0,
                        "storage": f"{args.storage} {args.pattern.upper()} "
                                   + ("staged in shared memory" if info["staged"] else "one node per thread"),
                        "block": [info["block_x"], info["block_y"]],
                        "l2": f"inputs larger than L2: {info['buffers']} population buffer(s) of "
                              f"{info['state_bytes'] / 1e9:.2f} GB vs 129 MB L2, no flush",
-                       "parallelism": f"{ws} independent replica(s), one per GPU"},
+                       "parallelism": parallelism},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
+                         "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "algorithmic_bytes_per_launch": bytes_per_node * nodes,
                          "kernel": "k_step<Cascaded,float,1,false>" if default_case
                          else f"step kernel, {args.model} collision, {args.storage} storage, D3Q{args.lattice}, "
-                              f"{args.pattern} pattern"},
+                              f"{args.pattern} pattern" + (", z-slab (faces + interior launches)" if slab else "")},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "variants": variants,
-            "gpu_launches": K,
+            "gpu_launches": K * (2 if slab else 1),
             "clocks": clocks,
+            "variants": compact(variants) if variants else None,
         }
+        if variants:
+            print(json.dumps({"variants_full": variants}), file=sys.stderr, flush=True)
         print(json.dumps(line), flush=True)
     lat.close()
     if dist is not None:

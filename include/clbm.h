@@ -46,7 +46,8 @@ extern "C" {
 #define CLBM_ERR_CUDA     -3  /* a CUDA runtime call or kernel launch failed */
 #define CLBM_ERR_UNSTABLE -4  /* a node's density left (0.1, 1.9) or became non-finite */
 #define CLBM_ERR_STATE    -5  /* call not valid in the context's current state */
-#define CLBM_ERR_TIMEOUT  -6  /* a step kernel's wait for its staged copies gave up (about 2 s); the state is invalid */
+#define CLBM_ERR_TIMEOUT  -6  /* a step kernel's wait for its staged copies gave up (clbm_params.wait_cycles); the state is invalid */
+#define CLBM_ERR_BOUNDS   -7  /* bounds-checked build only: a kernel derived an out-of-range index (see clbm_check) */
 
 /* ---- storage formats of the populations (deviations f - w_i) ---- */
 #define CLBM_STORAGE_F32     0
@@ -122,7 +123,27 @@ extern "C" {
  *      threads); the recomputation/adjoint entry points and batches are D3Q19
  *      only. Population arrays then hold 27 x N floats in the order of Eq. 1.
  * s3b, s4b, s5, s6: the further D3Q27 rates of Eq. 13 (k~111; k~211, k~121,
- *      k~112; k~122, k~212, k~221; k~222); 0 selects 1. Ignored for D3Q19. */
+ *      k~112; k~122, k~212, k~221; k~222); 0 selects 1. Ignored for D3Q19.
+ * slab, z0: the context holds the z-slab z0 .. z0 + nz - 1 of a larger lattice
+ *      that is split along z across contexts (the decomposition of the
+ *      streaming step, Eq. 8, across the z faces; see clbm_slab_step). slab
+ *      bit 0 (CLBM_SLAB_LO): across the z- face the populations with e_z = +1
+ *      (Eq. A1: 5, 11, 12, 15, 16) come from the neighbour below; bit 1
+ *      (CLBM_SLAB_HI): across the z+ face the populations with e_z = -1 (6, 13,
+ *      14, 17, 18) come from the neighbour above. Such a halo face is neither
+ *      periodic nor a wall; a z face without its bit follows `walls` (periodic
+ *      within the slab, or a wall with CLBM_WALL_Z). z0 is the global index of
+ *      the slab's first plane: it only feeds the dither of stochastic
+ *      rounding, so that the slabs store exactly what one undivided lattice
+ *      would. slab = 0 (the default) is an ordinary lattice. Slabs: D3Q19,
+ *      cascaded model, A/B pattern, one node per thread (variant 0 or 1).
+ * wait_cycles: bound, in SM clock cycles, of each wait of the staged step
+ *      (variant 0, 16-bit storage) for the bulk copies of its next tile; 0
+ *      selects 4e9 (about 2 s). A wait that runs out makes the kernel give up
+ *      the step and return: every block first waits (bounded by 4e9 cycles)
+ *      for the copies it has in flight, then sets the flag that clbm_check
+ *      reports as CLBM_ERR_TIMEOUT; the state is then invalid. Tests make a
+ *      wait run out on purpose with inject = CLBM_INJECT_DROP_COPY. */
 typedef struct clbm_params {
     int32_t nx, ny, nz;
     uint32_t walls;
@@ -135,8 +156,23 @@ typedef struct clbm_params {
     int32_t pattern;          /* CLBM_PATTERN_AB (0) or CLBM_PATTERN_AA */
     double s3b, s4b, s5, s6;
     int32_t model;            /* CLBM_MODEL_CASCADED (0), CLBM_MODEL_SRT or CLBM_MODEL_MRT */
+    int32_t slab;             /* 0, or CLBM_SLAB_LO | CLBM_SLAB_HI halo faces of a z-slab */
+    int32_t z0;               /* global index of a z-slab's first plane (0 otherwise) */
     int32_t reserved;         /* must be 0 */
+    int64_t wait_cycles;      /* staged step's wait bound in SM clock cycles (0: the default, about 2 s) */
+    int32_t inject;           /* failure injection for tests: 0, or CLBM_INJECT_DROP_COPY */
+    int32_t reserved2;        /* must be 0 */
 } clbm_params;
+
+/* Failure injection (clbm_params.inject), decided on the host: the staged
+ * step arms the barrier of its first tile with the tile's byte count but
+ * issues none of that tile's copies, so the waits on it run out after
+ * wait_cycles and the step ends with CLBM_ERR_TIMEOUT. Nothing faults: no copy
+ * is lost in flight, every wait is bounded. For failure-detection tests. */
+#define CLBM_INJECT_DROP_COPY 1
+
+#define CLBM_SLAB_LO 1
+#define CLBM_SLAB_HI 2
 
 typedef struct clbm_info {
     int64_t n_nodes;          /* N */
@@ -152,6 +188,8 @@ typedef struct clbm_info {
     int32_t buffers;          /* population buffers held: 2 (A/B) or 1 (AA) */
     int32_t model;            /* CLBM_MODEL_* */
     int32_t staged;           /* 1: steps stage the pulled rows in shared memory (variant 0, see clbm_params) */
+    int32_t slab;             /* halo faces of a z-slab (clbm_params.slab) */
+    int64_t face_bytes;       /* z-slab: bytes of one face's 5 populations (5 x nx x ny values), else 0 */
 } clbm_info;
 
 typedef struct clbm_ctx clbm_ctx;
@@ -238,8 +276,13 @@ int clbm_reduce_pair(clbm_ctx *ctx, const float *a_dev, const float *b_dev, int6
 /* Read the instability flag (synchronises the stream): CLBM_OK, or
  * CLBM_ERR_UNSTABLE if any step since the last clear saw a density outside
  * (0.1, 1.9) or a non-finite one, or CLBM_ERR_TIMEOUT if a staged step's
- * wait for its bulk copies gave up (the state is then invalid). clear != 0
- * resets the flag. */
+ * wait for its bulk copies gave up (the state is then invalid). In the
+ * bounds-checked debug build (libclbm_bc.so, compiled with
+ * -DCLBM_BOUNDS_CHECK) every index a step or state kernel derives from the
+ * streaming maps or a staged tile is checked against its buffer; a violation
+ * is redirected in bounds and recorded, and this call then returns
+ * CLBM_ERR_BOUNDS with the count and the first offending index in its
+ * message. clear != 0 resets the flag and the record. */
 int clbm_check(clbm_ctx *ctx, int clear);
 
 /* Raw state: the internal population buffer (clbm_info.state_bytes bytes).
@@ -313,6 +356,56 @@ int clbm_adjoint_segment(clbm_ctx *ctx, const void *ckpt_dev, void *tape_dev, in
 int clbm_adjoint_seed(clbm_ctx *ctx, const void *state_dev, const float *gu_dev, float *lam_dev, float *gF_dev);
 int clbm_adjoint_step(clbm_ctx *ctx, const void *state_dev, const float *lam_next_dev, float *lam_dev,
                       float *gF_dev);
+
+/* ---- z-slab decomposition (clbm_params.slab) ----
+ *
+ * One lattice split along z into slabs, one context each (for example one
+ * per GPU). The pull of Eq. 8 at a slab's first plane needs, for the 5
+ * populations with e_z = +1, the post-collision values of the last plane of
+ * the slab below; at its last plane, for the 5 with e_z = -1, those of the
+ * first plane of the slab above. A slab context keeps these in halo planes
+ * of its state and writes its own outgoing values to send planes, so one
+ * time step of the whole lattice is: every slab steps, then every pair of
+ * neighbours exchanges one face each way (5 x nx x ny values). The interior
+ * update is the same kernel arithmetic as clbm_step; the slabs together give
+ * bit for bit the state of one undivided lattice.
+ *
+ * Initialisation (clbm_init_equilibrium, clbm_set_populations) needs no
+ * exchange: it fills the slab's halo planes from its own state. After every
+ * step, before the next step or any read-out (clbm_get_macros,
+ * clbm_get_populations, clbm_reduce_moments), the caller must move each
+ * face: the first half of this slab's send planes (its first plane's e_z = -1
+ * populations) into the second half of the lower neighbour's receive planes,
+ * and the second half of the send planes (its last plane's e_z = +1
+ * populations) into the first half of the upper neighbour's receive planes.
+ * A slab with both halo faces may be its own neighbour (a periodic z axis on
+ * one context). clbm_step on a slab context takes at most one step per call.
+ * Slab contexts refuse clbm_run_host and the recomputation/adjoint calls
+ * (CLBM_ERR_STATE). */
+#define CLBM_SLAB_ALL      0  /* the whole step, then the state advances */
+#define CLBM_SLAB_FACES    1  /* only the first and last planes (the send planes are then complete) */
+#define CLBM_SLAB_INTERIOR 2  /* the other planes, then the state advances (after CLBM_SLAB_FACES) */
+
+/* Enqueue one time step, or a part of it, on the context's stream. Splitting
+ * the step lets the face exchange overlap the interior update: after
+ * CLBM_SLAB_FACES the send planes are complete (once that work has run) and
+ * the receive planes of the new state may be written while
+ * CLBM_SLAB_INTERIOR runs. Errors: CLBM_ERR_ARG (not a slab context, unknown
+ * part), CLBM_ERR_STATE (CLBM_SLAB_INTERIOR without CLBM_SLAB_FACES before
+ * it, or another part while a split step is pending). */
+int clbm_slab_step(clbm_ctx *ctx, int part);
+
+/* Device addresses of the newest state's send and receive planes (the
+ * state the latest step writes, even before CLBM_SLAB_INTERIOR finishes it).
+ * Each is 10 planes of nx x ny values in the storage format (x fastest),
+ * 2 * face_bytes bytes: send_dev first holds the slab's first plane's e_z = -1
+ * populations (6, 13, 14, 17, 18) for the lower neighbour, then its last
+ * plane's e_z = +1 populations (5, 11, 12, 15, 16) for the upper neighbour;
+ * recv_dev first takes the lower neighbour's e_z = +1 face, then the upper
+ * neighbour's e_z = -1 face. The addresses belong to the context and change
+ * from step to step (the A/B buffers alternate): query them after each step.
+ * Any output pointer may be NULL. Errors: CLBM_ERR_ARG (not a slab context). */
+int clbm_slab_faces(clbm_ctx *ctx, void **send_dev, void **recv_dev, int64_t *face_bytes);
 
 /* ---- FP64 pair reduction without a context or allocation ----
  *

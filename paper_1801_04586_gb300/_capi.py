@@ -10,6 +10,8 @@ import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libclbm.so")
+# The bounds-checked debug build of the same library (builder.build(bounds_check=True)).
+LIB_BC_PATH = os.path.join(PKG, "libclbm_bc.so")
 
 CLBM_OK = 0
 CLBM_ERR_ARG = -1
@@ -18,11 +20,15 @@ CLBM_ERR_CUDA = -3
 CLBM_ERR_UNSTABLE = -4
 CLBM_ERR_STATE = -5
 CLBM_ERR_TIMEOUT = -6
+CLBM_ERR_BOUNDS = -7
 
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "f16sr": 3, "bf16sr": 4}
 PATTERN = {"ab": 0, "aa": 1}
 MODEL = {"cascaded": 0, "srt": 1, "mrt": 2}
 WALL_X, WALL_Y, WALL_Z = 1, 2, 4
+SLAB_LO, SLAB_HI = 1, 2
+SLAB_ALL, SLAB_FACES, SLAB_INTERIOR = 0, 1, 2
+INJECT_DROP_COPY = 1
 
 
 class Params(ctypes.Structure):
@@ -32,7 +38,9 @@ class Params(ctypes.Structure):
                 ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("lattice", ctypes.c_int32), ("pattern", ctypes.c_int32), ("s3b", ctypes.c_double),
                 ("s4b", ctypes.c_double), ("s5", ctypes.c_double), ("s6", ctypes.c_double),
-                ("model", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("model", ctypes.c_int32), ("slab", ctypes.c_int32), ("z0", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("wait_cycles", ctypes.c_int64), ("inject", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
 
 
 class Domain(ctypes.Structure):
@@ -56,7 +64,8 @@ class Info(ctypes.Structure):
                 ("steps_done", ctypes.c_int64), ("storage", ctypes.c_int32), ("block_x", ctypes.c_int32),
                 ("block_y", ctypes.c_int32), ("s2", ctypes.c_double), ("nodes_per_thread", ctypes.c_int32),
                 ("q", ctypes.c_int32), ("pattern", ctypes.c_int32), ("buffers", ctypes.c_int32),
-                ("model", ctypes.c_int32), ("staged", ctypes.c_int32)]
+                ("model", ctypes.c_int32), ("staged", ctypes.c_int32), ("slab", ctypes.c_int32),
+                ("face_bytes", ctypes.c_int64)]
 
 
 P = ctypes.c_void_p
@@ -91,6 +100,8 @@ SIGNATURES = {
     "clbm_adjoint_step": [P, P, P, P, P],
     "clbm_adjoint_segment": [P, P, P, I64, P, P, P],
     "clbm_reduce_pair_noalloc": [P, P, I64, P, P],
+    "clbm_slab_step": [P, I32],
+    "clbm_slab_faces": [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64)],
     "clbm_batch_create": [P, I32, I32, P, ctypes.POINTER(P)],
     "clbm_batch_destroy": [P],
     "clbm_batch_get_info": [P, P],
@@ -111,13 +122,16 @@ _lib = None
 
 
 def lib():
-    """Load libclbm.so (built by __graft_entry__.build() or build.py)."""
+    """Load libclbm.so (built by __graft_entry__.build() or builder.build()),
+    or, when the environment variable CLBM_LIBRARY=bounds_check is set, its
+    bounds-checked debug build libclbm_bc.so."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1801_04586_gb300.build.build() "
+        path = LIB_BC_PATH if os.environ.get("CLBM_LIBRARY") == "bounds_check" else LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1801_04586_gb300.builder.build() "
                                "(nvcc, sm_103a); there is no fallback implementation")
-        L = ctypes.CDLL(LIB_PATH)
+        L = ctypes.CDLL(path)
         for name, args in SIGNATURES.items():
             fn = getattr(L, name)
             fn.argtypes = args

@@ -30,11 +30,14 @@ __device__ __forceinline__ bool node_of(const Geom &g, int &x, int &y, int &z) {
 // Slots of the post-streaming populations of node (x,y,z) in a state buffer.
 // map 0: A/B pattern, the pull map; 1: in-place (AA) pattern after an even
 // number of steps, natural order at the node; 2: AA after an odd number of
-// steps, the swapped pull map of the odd step (step.cu).
+// steps, the swapped pull map of the odd step (step.cu); 3: the pull map of a
+// z-slab, through its halo planes across halo faces.
 template <bool WALLS>
 __device__ __forceinline__ void state_slots(const Geom &g, int x, int y, int z, int map, uint32_t (&off)[kQ],
                                             int (&pop)[kQ]) {
-    if (map == 1) {
+    if (map == 3) {
+        pull_sources<WALLS, false, true>(g, x, y, z, off, pop);
+    } else if (map == 1) {
         const uint32_t self = ((uint32_t)z * g.ny + y) * g.nx + x;
 #pragma unroll
         for (int i = 0; i < kQ; ++i) { off[i] = self; pop[i] = i; }
@@ -54,7 +57,7 @@ __device__ __forceinline__ void scatter_node(S *dst, const Geom &g, int x, int y
     int pop[kQ];
     state_slots<WALLS>(g, x, y, z, map, off, pop);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) dst[(size_t)pop[i] * g.stride + off[i]] = Codec<S>::from_f(h[i]);
+    for (int i = 0; i < kQ; ++i) dst[CLBM_IDX(g, (size_t)pop[i] * g.stride + off[i])] = Codec<S>::from_f(h[i]);
 }
 
 template <typename S, bool WALLS>
@@ -64,7 +67,7 @@ __device__ __forceinline__ uint32_t pull_node(const S *src, const Geom &g, int x
     int pop[kQ];
     state_slots<WALLS>(g, x, y, z, map, off, pop);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load_plain(src + (size_t)pop[i] * g.stride + off[i]);
+    for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load_plain(src + CLBM_IDX(g, (size_t)pop[i] * g.stride + off[i]));
     return ((uint32_t)z * g.ny + y) * g.nx + x;
 }
 

@@ -90,9 +90,20 @@ struct clbm_ctx {
     dim3 block;
     cudaStream_t cap_stream;   // private stream for graph capture (first use)
     cudaGraphExec_t graph;     // kGraphSteps steps from phase 0; null until built, dropped when the force changes
+    bool slab_pending;         // z-slab: CLBM_SLAB_FACES done, CLBM_SLAB_INTERIOR not yet
 };
 
 namespace {
+
+// Elements of one state buffer: the Q population arrays, then for a z-slab
+// its halo planes (kSlabPlanes of nx * ny values, see d3q19.cuh).
+size_t state_elems(const clbm_ctx *c) {
+    size_t e = (size_t)c->q * c->g.stride;
+    if (c->g.slab) e += (size_t)kSlabPlanes * c->g.nx * c->g.ny;
+    return e;
+}
+
+size_t state_bytes(const clbm_ctx *c) { return state_elems(c) * c->elem; }
 
 // The force in use at the context's current time step.
 ForceArgs force_at_zero(const clbm_ctx *c) {
@@ -136,9 +147,12 @@ Launch launch_of(const clbm_ctx *c) {
     L.stream = c->stream;
     L.packed = false;
     L.staged = c->staged;
-    // A/B: the pull map; AA: natural slots after an even number of steps, the
-    // odd step's swapped pull map after an odd number.
-    L.map = c->aa ? ((c->steps_done & 1) ? 2 : 1) : 0;
+    // A/B: the pull map (through the halo planes for a z-slab); AA: natural
+    // slots after an even number of steps, the odd step's swapped pull map
+    // after an odd number.
+    L.map = c->aa ? ((c->steps_done & 1) ? 2 : 1) : (c->g.slab ? 3 : 0);
+    L.wait_cycles = c->p.wait_cycles;
+    L.drop_first_tile = c->p.inject == CLBM_INJECT_DROP_COPY;
     return L;
 }
 
@@ -198,6 +212,9 @@ cudaError_t one_step(const clbm_ctx *c, const Launch &L, int cur, int64_t step) 
         const bool odd = (step & 1) != 0;
         return c->q == 27 ? step27_aa(c, L, c->buf[0], F, key, odd) : step19_aa(c, L, c->buf[0], F, key, odd);
     }
+    if (c->g.slab)
+        return launch_step_slab(c->p.storage, L, c->buf[cur], c->buf[cur ^ 1], c->rates, F, c->d_flag, key, 0, 1,
+                                c->g.nz);
     return c->q == 27 ? step27(c, L, c->buf[cur], c->buf[cur ^ 1], F, key)
                       : step19(c, L, c->buf[cur], c->buf[cur ^ 1], F, key);
 }
@@ -244,6 +261,7 @@ const char *clbm_status_string(int status) {
         case CLBM_ERR_UNSTABLE: return "unstable: density out of range or non-finite";
         case CLBM_ERR_STATE: return "invalid state";
         case CLBM_ERR_TIMEOUT: return "timeout: a staged copy did not complete";
+        case CLBM_ERR_BOUNDS: return "bounds: a kernel derived an out-of-range index";
         default: return "unknown status";
     }
 }
@@ -278,8 +296,21 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
         return fail(CLBM_ERR_ARG, "clbm_create: pattern must be CLBM_PATTERN_AB or CLBM_PATTERN_AA");
     if (p->pattern == CLBM_PATTERN_AA && p->variant == 2)
         return fail(CLBM_ERR_ARG, "clbm_create: the in-place pattern runs one node per thread (variant 0 or 1)");
-    if (p->model < CLBM_MODEL_CASCADED || p->model > CLBM_MODEL_MRT || p->reserved != 0)
+    if (p->model < CLBM_MODEL_CASCADED || p->model > CLBM_MODEL_MRT || p->reserved != 0 || p->reserved2 != 0)
         return fail(CLBM_ERR_ARG, "clbm_create: model must be CLBM_MODEL_CASCADED, _SRT or _MRT (reserved 0)");
+    if (p->slab & ~(CLBM_SLAB_LO | CLBM_SLAB_HI)) return fail(CLBM_ERR_ARG, "clbm_create: unknown slab bits");
+    if (p->wait_cycles < 0) return fail(CLBM_ERR_ARG, "clbm_create: wait_cycles must be >= 0");
+    if (p->inject != 0 && p->inject != CLBM_INJECT_DROP_COPY)
+        return fail(CLBM_ERR_ARG, "clbm_create: inject must be 0 or CLBM_INJECT_DROP_COPY");
+    if (p->slab && (q != 19 || p->model != CLBM_MODEL_CASCADED || p->pattern != CLBM_PATTERN_AB || p->variant == 2))
+        return fail(CLBM_ERR_ARG,
+                    "clbm_create: z-slabs are D3Q19, cascaded, A/B pattern, one node per thread (variant 0 or 1)");
+    if (p->z0 < 0 || (!p->slab && p->z0 != 0))
+        return fail(CLBM_ERR_ARG, "clbm_create: z0 must be >= 0, and 0 unless slab is set");
+    if (p->slab && ((int64_t)p->z0 + p->nz) * p->nx * p->ny > ((int64_t)1 << 31) - 1)
+        return fail(CLBM_ERR_ARG, "clbm_create: the slab's global node indices exceed 2^31-1");
+    if (p->slab && (int64_t)kSlabPlanes * p->nx * p->ny > ((int64_t)1 << 31) - 1)
+        return fail(CLBM_ERR_ARG, "clbm_create: the slab's halo planes exceed 2^31-1 values");
     if (p->model != CLBM_MODEL_CASCADED && p->variant == 2)
         return fail(CLBM_ERR_ARG, "clbm_create: the SRT and MRT models run one node per thread");
     int bx = p->block_x, by = p->block_y;
@@ -298,6 +329,8 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     c->g.nx = p->nx; c->g.ny = p->ny; c->g.nz = p->nz;
     c->g.walls = p->walls;
     c->g.stride = (n + 63) / 64 * 64;  // every population array starts 256-byte aligned (f32)
+    c->g.slab = (uint32_t)p->slab;
+    c->g.node0 = (uint32_t)((int64_t)p->z0 * p->nx * p->ny);
     c->stream = (cudaStream_t)stream;
     c->s2 = s2;
     c->rates.om2 = (float)(1.0 - s2);
@@ -314,7 +347,7 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     c->gamma = 0.0;
     c->q = q;
     c->packed = q == 19 && p->variant == 2;
-    c->staged = p->variant == 0 && p->pattern != CLBM_PATTERN_AA;
+    c->staged = p->variant == 0 && p->pattern != CLBM_PATTERN_AA && !p->slab;
     c->aa = p->pattern == CLBM_PATTERN_AA;
     c->model = p->model;
     c->rates27.om2 = c->rates.om2;
@@ -330,7 +363,7 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     c->block = dim3(bx, by, 1);
     c->cur = 0;
     c->steps_done = 0;
-    const size_t bytes = (size_t)c->q * c->g.stride * c->elem;
+    const size_t bytes = (state_bytes(c) + 255) / 256 * 256;  // both buffers 256-byte aligned
     const size_t nbuf = c->aa ? 1 : 2;
     cudaError_t e = cudaMalloc(&c->buf[0], nbuf * bytes);
     if (e != cudaSuccess) {
@@ -347,9 +380,13 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
         return fail(CLBM_ERR_OOM, std::string("clbm_create: cudaMalloc: ") + cudaGetErrorString(e));
     }
     c->d_partials = (double *)((char *)c->d_flag + 256);
+#ifdef CLBM_BOUNDS_CHECK
+    c->g.bc = (BoundsRecord *)((char *)c->d_flag + 64);  // the flag block's bytes 64-79
+    c->g.bc_limit = state_elems(c);
+#endif
     // rest state: zero deviations in every buffer (zero bits are zero in all formats)
     if ((e = cudaMemsetAsync(c->buf[0], 0, nbuf * bytes, c->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream)) != cudaSuccess) {
+        (e = cudaMemsetAsync(c->d_flag, 0, 128, c->stream)) != cudaSuccess) {
         cudaFree(c->d_flag);
         cudaFree(c->buf[0]);
         delete c;
@@ -381,7 +418,7 @@ int clbm_get_info(const clbm_ctx *c, clbm_info *info) {
     if (!c || !info) return fail(CLBM_ERR_ARG, "clbm_get_info: null pointer");
     info->n_nodes = c->n;
     info->pop_stride = c->g.stride;
-    info->state_bytes = (int64_t)c->q * c->g.stride * (int64_t)c->elem;
+    info->state_bytes = (int64_t)state_bytes(c);
     info->steps_done = c->steps_done;
     info->storage = c->p.storage;
     info->block_x = (int32_t)c->block.x;
@@ -393,6 +430,8 @@ int clbm_get_info(const clbm_ctx *c, clbm_info *info) {
     info->buffers = c->aa ? 1 : 2;
     info->model = c->model;
     info->staged = c->staged && step_staged(c->g, c->elem, c->buf[0], c->q, c->force.mode) ? 1 : 0;
+    info->slab = (int32_t)c->g.slab;
+    info->face_bytes = c->g.slab ? (int64_t)5 * c->g.nx * c->g.ny * (int64_t)c->elem : 0;
     return CLBM_OK;
 }
 
@@ -432,6 +471,7 @@ int clbm_set_force_decay(clbm_ctx *c, double gamma) {
 
 int clbm_init_equilibrium(clbm_ctx *c, const float *rho, const float *u) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_init_equilibrium: null context");
+    if (c->slab_pending) return fail(CLBM_ERR_STATE, "clbm_init_equilibrium: a split slab step is pending");
     c->steps_done = 0;  // before launch_of: the in-place pattern starts in natural order
     cudaError_t e = c->q == 27
         ? launch_init27(c->p.storage, launch_of(c), c->buf[c->cur], rho, u, c->n, force_at_zero(c))
@@ -443,6 +483,8 @@ int clbm_init_equilibrium(clbm_ctx *c, const float *rho, const float *u) {
 int clbm_step(clbm_ctx *c, int64_t nsteps) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_step: null context");
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_step: nsteps < 0");
+    if (c->g.slab && (nsteps > 1 || c->slab_pending))
+        return fail(CLBM_ERR_STATE, "clbm_step: a z-slab takes one step per call (faces are exchanged between steps)");
     Range range("clbm_step");
     const Launch L = step_launch_of(c);
     auto advance = [&]() -> int {
@@ -456,7 +498,7 @@ int clbm_step(clbm_ctx *c, int64_t nsteps) {
     // Long runs with static launch arguments replay a captured graph of
     // kGraphSteps steps: one launch call per 16 steps instead of 16.
     const bool stochastic = c->p.storage == CLBM_STORAGE_F16_SR || c->p.storage == CLBM_STORAGE_BF16_SR;
-    if (!stochastic && c->gamma == 0.0 && nsteps >= 2 * kGraphSteps) {
+    if (!stochastic && c->gamma == 0.0 && nsteps >= 2 * kGraphSteps && !c->g.slab) {
         const int phase = c->aa ? (int)(c->steps_done & 1) : c->cur;
         if (phase != 0) {
             int rc = advance();
@@ -497,6 +539,7 @@ int clbm_get_populations(clbm_ctx *c, float *f, int deviation) {
 
 int clbm_set_populations(clbm_ctx *c, const float *f, int deviation) {
     if (!c || !f) return fail(CLBM_ERR_ARG, "clbm_set_populations: null pointer");
+    if (c->slab_pending) return fail(CLBM_ERR_STATE, "clbm_set_populations: a split slab step is pending");
     c->steps_done = 0;  // before launch_of: the in-place pattern restarts in natural order
     cudaError_t e = c->q == 27 ? launch_scatter27(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation)
                                : launch_scatter(c->p.storage, launch_of(c), c->buf[c->cur], f, c->n, deviation);
@@ -525,12 +568,24 @@ int clbm_check(clbm_ctx *c, int clear) {
     if (!c) return fail(CLBM_ERR_ARG, "clbm_check: null context");
     int h = 0;
     cudaError_t e = cudaMemcpyAsync(&h, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+#ifdef CLBM_BOUNDS_CHECK
+    BoundsRecord rec = {0ull, 0ull};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rec, c->g.bc, sizeof(rec), cudaMemcpyDeviceToHost, c->stream);
+#endif
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_check");
     if (clear) {
-        e = cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
+        e = cudaMemsetAsync(c->d_flag, 0, 128, c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "clbm_check");
     }
+#ifdef CLBM_BOUNDS_CHECK
+    if (rec.count) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "clbm_check: %llu out-of-range indices; the first: kind %llu, index %llu",
+                      rec.count, rec.first >> 56, rec.first & 0x00ffffffffffffffull);
+        return fail(CLBM_ERR_BOUNDS, msg);
+    }
+#endif
     if (h & 2)
         return fail(CLBM_ERR_TIMEOUT, "clbm_check: a staged step's bulk copy did not complete; the state is invalid");
     if (h) return fail(CLBM_ERR_UNSTABLE, "clbm_check: a node's density left (0.1, 1.9) or became non-finite");
@@ -539,7 +594,7 @@ int clbm_check(clbm_ctx *c, int clear) {
 
 int clbm_export_state(clbm_ctx *c, void *dst) {
     if (!c || !dst) return fail(CLBM_ERR_ARG, "clbm_export_state: null pointer");
-    const size_t bytes = (size_t)c->q * c->g.stride * c->elem;
+    const size_t bytes = state_bytes(c);
     cudaError_t e = cudaMemcpyAsync(dst, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_export_state");
     return CLBM_OK;
@@ -547,7 +602,8 @@ int clbm_export_state(clbm_ctx *c, void *dst) {
 
 int clbm_import_state(clbm_ctx *c, const void *src, int64_t set_steps) {
     if (!c || !src) return fail(CLBM_ERR_ARG, "clbm_import_state: null pointer");
-    const size_t bytes = (size_t)c->q * c->g.stride * c->elem;
+    if (c->slab_pending) return fail(CLBM_ERR_STATE, "clbm_import_state: a split slab step is pending");
+    const size_t bytes = state_bytes(c);
     cudaError_t e = cudaMemcpyAsync(c->buf[c->cur], src, bytes, cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "clbm_import_state");
     if (set_steps >= 0) c->steps_done = set_steps;
@@ -556,7 +612,7 @@ int clbm_import_state(clbm_ctx *c, const void *src, int64_t set_steps) {
 
 int clbm_save_state(clbm_ctx *c, void *host, size_t *bytes) {
     if (!c || !bytes) return fail(CLBM_ERR_ARG, "clbm_save_state: null pointer");
-    const size_t raw = (size_t)c->q * c->g.stride * c->elem;
+    const size_t raw = state_bytes(c);
     const size_t need = sizeof(StateHeader) + raw;
     if (!host) {
         *bytes = need;
@@ -586,9 +642,10 @@ int clbm_save_state(clbm_ctx *c, void *host, size_t *bytes) {
 int clbm_load_state(clbm_ctx *c, const void *host, size_t bytes) {
     if (!c || !host) return fail(CLBM_ERR_ARG, "clbm_load_state: null pointer");
     if (bytes < sizeof(StateHeader)) return fail(CLBM_ERR_ARG, "clbm_load_state: buffer too small");
+    if (c->slab_pending) return fail(CLBM_ERR_STATE, "clbm_load_state: a split slab step is pending");
     StateHeader h;
     std::memcpy(&h, host, sizeof(h));
-    const size_t raw = (size_t)c->q * c->g.stride * c->elem;
+    const size_t raw = state_bytes(c);
     if (std::memcmp(h.magic, "CLBMLBM", 8) != 0 || h.version != 2)
         return fail(CLBM_ERR_ARG, "clbm_load_state: not a state buffer");
     if (h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz || h.walls != (int32_t)c->g.walls ||
@@ -607,6 +664,7 @@ int clbm_load_state(clbm_ctx *c, const void *host, size_t bytes) {
 int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
     if (!c || !src || !dst) return fail(CLBM_ERR_ARG, "clbm_step_raw: null pointer");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_step_raw: D3Q19 only");
+    if (c->g.slab) return fail(CLBM_ERR_STATE, "clbm_step_raw: not for z-slabs");
     if (c->aa) return fail(CLBM_ERR_ARG, "clbm_step_raw: A/B pattern only");
     if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_step_raw: cascaded model only");
     if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_step_raw: needs a static force (decay 0)");
@@ -621,6 +679,7 @@ int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
 int clbm_adjoint_seed(clbm_ctx *c, const void *state, const float *gu, float *lam, float *gF) {
     if (!c || !gu || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: null pointer");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: D3Q19 only");
+    if (c->g.slab) return fail(CLBM_ERR_STATE, "clbm_adjoint_seed: not for z-slabs");
     if (c->aa) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: A/B pattern only");
     if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: cascaded model only");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: FP32 storage only");
@@ -634,6 +693,7 @@ int clbm_adjoint_seed(clbm_ctx *c, const void *state, const float *gu, float *la
 int clbm_adjoint_step(clbm_ctx *c, const void *state, const float *lam_next, float *lam, float *gF) {
     if (!c || !state || !lam_next || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: null pointer");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: D3Q19 only");
+    if (c->g.slab) return fail(CLBM_ERR_STATE, "clbm_adjoint_step: not for z-slabs");
     if (c->aa) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: A/B pattern only");
     if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: cascaded model only");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: FP32 storage only");
@@ -650,6 +710,7 @@ int clbm_adjoint_segment(clbm_ctx *c, const void *ckpt, void *tape, int64_t k, f
     if (!c || !ckpt || !lam || !lam_tmp || !gF || k < 1 || (k > 1 && !tape) || lam == lam_tmp)
         return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: bad argument");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: D3Q19 only");
+    if (c->g.slab) return fail(CLBM_ERR_STATE, "clbm_adjoint_segment: not for z-slabs");
     if (c->aa) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: A/B pattern only");
     if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: cascaded model only");
     Range range("clbm_adjoint_segment");
@@ -678,6 +739,7 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     if (!c) return fail(CLBM_ERR_ARG, "clbm_run_host: null context");
     Range range("clbm_run_host");
     if (nsteps < 0) return fail(CLBM_ERR_ARG, "clbm_run_host: nsteps < 0");
+    if (c->g.slab) return fail(CLBM_ERR_STATE, "clbm_run_host: not for z-slabs (faces are exchanged between steps)");
     const Launch L = launch_of(c);
     cudaError_t e;
     if (!c->d_io) {
@@ -795,6 +857,52 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         for (int64_t t = 0; t <= nsteps; ++t)
             if (!std::isfinite(moments_h[4 * t])) return fail(CLBM_ERR_UNSTABLE, "clbm_run_host: non-finite mass");
     return clbm_check(c, 0);
+}
+
+int clbm_slab_step(clbm_ctx *c, int part) {
+    if (!c) return fail(CLBM_ERR_ARG, "clbm_slab_step: null context");
+    if (!c->g.slab) return fail(CLBM_ERR_ARG, "clbm_slab_step: not a z-slab context");
+    if (part != CLBM_SLAB_ALL && part != CLBM_SLAB_FACES && part != CLBM_SLAB_INTERIOR)
+        return fail(CLBM_ERR_ARG, "clbm_slab_step: unknown part");
+    if ((part == CLBM_SLAB_INTERIOR) != c->slab_pending)
+        return fail(CLBM_ERR_STATE, part == CLBM_SLAB_INTERIOR
+                                        ? "clbm_slab_step: CLBM_SLAB_INTERIOR needs CLBM_SLAB_FACES first"
+                                        : "clbm_slab_step: a split step is pending (CLBM_SLAB_INTERIOR)");
+    Range range("clbm_slab_step");
+    const Launch L = launch_of(c);
+    const ForceArgs F = force_now(c);
+    const uint32_t key = step_key(c->steps_done);
+    const int nz = c->g.nz;
+    const void *src = c->buf[c->cur];
+    void *dst = c->buf[c->cur ^ 1];
+    cudaError_t e = cudaSuccess;
+    if (part == CLBM_SLAB_ALL)
+        e = launch_step_slab(c->p.storage, L, src, dst, c->rates, F, c->d_flag, key, 0, 1, nz);
+    else if (part == CLBM_SLAB_FACES)  // planes 0 and nz - 1 (one plane if nz == 1)
+        e = launch_step_slab(c->p.storage, L, src, dst, c->rates, F, c->d_flag, key, 0, nz > 1 ? nz - 1 : 1,
+                             nz > 1 ? 2 : 1);
+    else
+        e = launch_step_slab(c->p.storage, L, src, dst, c->rates, F, c->d_flag, key, 1, 1, nz - 2);
+    if (e != cudaSuccess) return cuda_fail(e, "clbm_slab_step");
+    if (part == CLBM_SLAB_FACES) {
+        c->slab_pending = true;
+    } else {
+        c->slab_pending = false;
+        c->cur ^= 1;
+        ++c->steps_done;
+    }
+    return CLBM_OK;
+}
+
+int clbm_slab_faces(clbm_ctx *c, void **send, void **recv, int64_t *face_bytes) {
+    if (!c) return fail(CLBM_ERR_ARG, "clbm_slab_faces: null context");
+    if (!c->g.slab) return fail(CLBM_ERR_ARG, "clbm_slab_faces: not a z-slab context");
+    const size_t plane = (size_t)c->g.nx * c->g.ny;
+    char *halo = (char *)c->buf[c->cur ^ (c->slab_pending ? 1 : 0)] + (size_t)c->q * c->g.stride * c->elem;
+    if (recv) *recv = halo;
+    if (send) *send = halo + 10 * plane * c->elem;
+    if (face_bytes) *face_bytes = (int64_t)(5 * plane * c->elem);
+    return CLBM_OK;
 }
 
 }  // extern "C"

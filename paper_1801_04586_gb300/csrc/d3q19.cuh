@@ -31,6 +31,10 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+#include "bounds.cuh"
+
 namespace clbm {
 
 constexpr int kQ = 19;
@@ -91,12 +95,29 @@ template <> struct Codec<float> {
     static __device__ __forceinline__ float from_f(float v) { return v; }
     static __device__ __forceinline__ float from_f_sr(float v, uint32_t) { return v; }
 };
+// 16-bit formats also convert a pair of FP32 values (hi, lo) in one
+// instruction, the results in the upper and lower half of a word (pair_rn /
+// pair_sr below), and widen a stored pair read as one word (unpack2: .x the
+// lower half, the value at the lower address).
+__device__ __forceinline__ uint32_t rn_pair_f16(float hi, float lo);
+__device__ __forceinline__ uint32_t rn_pair_bf16(float hi, float lo);
+__device__ __forceinline__ float2 unpack2_f16(uint32_t w) {
+    __half2_raw raw;
+    raw.x = (unsigned short)(w & 0xffffu);
+    raw.y = (unsigned short)(w >> 16);
+    return __half22float2(__half2(raw));
+}
+__device__ __forceinline__ float2 unpack2_bf16(uint32_t w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
 template <> struct Codec<__half> {
     static constexpr bool kStochastic = false;
     static __device__ __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ float load_plain(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ __half from_f(float v) { return __float2half_rn(v); }
     static __device__ __forceinline__ __half from_f_sr(float v, uint32_t) { return __float2half_rn(v); }
+    static __device__ __forceinline__ uint32_t pair_rn(float hi, float lo) { return rn_pair_f16(hi, lo); }
+    static __device__ __forceinline__ float2 unpack2(uint32_t w) { return unpack2_f16(w); }
 };
 template <> struct Codec<__nv_bfloat16> {
     static constexpr bool kStochastic = false;
@@ -104,55 +125,98 @@ template <> struct Codec<__nv_bfloat16> {
     static __device__ __forceinline__ float load_plain(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ __nv_bfloat16 from_f(float v) { return __float2bfloat16_rn(v); }
     static __device__ __forceinline__ __nv_bfloat16 from_f_sr(float v, uint32_t) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ uint32_t pair_rn(float hi, float lo) { return rn_pair_bf16(hi, lo); }
+    static __device__ __forceinline__ float2 unpack2(uint32_t w) { return unpack2_bf16(w); }
 };
-// Stochastic rounding: add a uniform random integer below one unit in the last
-// place of the target to the FP32 bit pattern (sign-magnitude, so this acts on
-// |v|) and truncate; |v| rounds up with probability equal to the dropped
-// fraction, so the stored value is unbiased. FP16 drops 13 mantissa bits in
-// its normal range; below 2^-14 (subnormal FP16, spacing 6e-8) it rounds to
-// nearest.
+// Stochastic rounding by the conversion instruction of sm_100-class GPUs,
+// cvt.rs.{f16x2,bf16x2}.f32 d, a, b, rbits: it adds a random integer below one
+// unit in the last place of the target to |x| (FP32 sign-magnitude bits) and
+// truncates, so |x| rounds up with probability equal to the dropped fraction
+// and the stored value is unbiased (also in the FP16 subnormal range). Of the
+// 32 random bits, the lower half serves b (stored in the lower 16 bits of d),
+// the upper half serves a (upper 16 bits); FP16 takes the low 13 bits of its
+// half (the 13 bits it drops in its normal range), BF16 all 16.
+// sr_pair(hi, lo, r): both values in one instruction; the 16-bit results in
+// the upper and lower half of the returned word.
+__device__ __forceinline__ uint32_t sr_pair_f16(float hi, float lo, uint32_t r) {
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    return d;
+}
+__device__ __forceinline__ uint32_t sr_pair_bf16(float hi, float lo, uint32_t r) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    return d;
+}
+// Round-to-nearest-even pair conversions (cvt.rn.{f16x2,bf16x2}.f32).
+__device__ __forceinline__ uint32_t rn_pair_f16(float hi, float lo) {
+    uint32_t d;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ uint32_t rn_pair_bf16(float hi, float lo) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+// One value with the random half of r that its node's parity selects (odd:
+// upper half, even: lower half), bit for bit what the pair conversion gives
+// that node.
 template <> struct Codec<HalfSR> {
     static constexpr bool kStochastic = true;
     static __device__ __forceinline__ float load(const HalfSR *p) { return __half2float(__ldg(&p->v)); }
     static __device__ __forceinline__ float load_plain(const HalfSR *p) { return __half2float(p->v); }
     static __device__ __forceinline__ HalfSR from_f(float v) { return HalfSR{__float2half_rn(v)}; }
-    static __device__ __forceinline__ HalfSR from_f_sr(float v, uint32_t r) {
-        if (fabsf(v) < 6.103515625e-05f) return HalfSR{__float2half_rn(v)};
-        return HalfSR{__float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1fffu)))};
+    static __device__ __forceinline__ HalfSR from_f_sr(float v, uint32_t r, bool odd) {
+        const uint32_t d = odd ? sr_pair_f16(v, 0.0f, r) >> 16 : sr_pair_f16(0.0f, v, r) & 0xffffu;
+        __half_raw raw;
+        raw.x = (unsigned short)d;
+        return HalfSR{__half(raw)};
     }
+    static __device__ __forceinline__ uint32_t pair_sr(float hi, float lo, uint32_t r) { return sr_pair_f16(hi, lo, r); }
+    static __device__ __forceinline__ float2 unpack2(uint32_t w) { return unpack2_f16(w); }
 };
 template <> struct Codec<BF16SR> {
     static constexpr bool kStochastic = true;
     static __device__ __forceinline__ float load(const BF16SR *p) { return __bfloat162float(__ldg(&p->v)); }
     static __device__ __forceinline__ float load_plain(const BF16SR *p) { return __bfloat162float(p->v); }
     static __device__ __forceinline__ BF16SR from_f(float v) { return BF16SR{__float2bfloat16_rn(v)}; }
-    static __device__ __forceinline__ BF16SR from_f_sr(float v, uint32_t r) {
+    static __device__ __forceinline__ BF16SR from_f_sr(float v, uint32_t r, bool odd) {
+        const uint32_t d = odd ? sr_pair_bf16(v, 0.0f, r) >> 16 : sr_pair_bf16(0.0f, v, r) & 0xffffu;
         __nv_bfloat16_raw raw;
-        raw.x = (unsigned short)((__float_as_uint(v) + (r & 0xffffu)) >> 16);
+        raw.x = (unsigned short)d;
         return BF16SR{__nv_bfloat16(raw)};
     }
+    static __device__ __forceinline__ uint32_t pair_sr(float hi, float lo, uint32_t r) {
+        return sr_pair_bf16(hi, lo, r);
+    }
+    static __device__ __forceinline__ float2 unpack2(uint32_t w) { return unpack2_bf16(w); }
 };
 
+// Random bits of stochastic rounding for population i of the node pair
+// p = node >> 1 (nodes 2p and 2p + 1, adjacent in x): 32 bits, the lower half
+// for the even node and the upper half for the odd one, as the pair
+// conversion takes them. The pair's hash is the full lowbias32 mix of (p,
+// key); each population then takes one xorshift-multiply round of it offset
+// by a Weyl step (the first round of the same mixer): a bijection of a
+// uniform word, so every dither stays uniform. The bits depend on (key, node,
+// i) alone, so every storage pattern and staging path stores the same values.
+__device__ __forceinline__ uint32_t pair_hash(uint32_t pair, uint32_t key) { return lowbias32(pair ^ key); }
+__device__ __forceinline__ uint32_t pop_bits(uint32_t base, int i) {
+    uint32_t r = base + (uint32_t)i * 0x9e3779b9u;
+    r ^= r >> 16;
+    return r * 0x7feb352du;
+}
+
 // Encode the NQ post-collision deviations h (population order) of one node
-// in the storage format. key: per-step random key (stochastic formats only);
-// the dither of population i depends on (key, node, i) alone, so every
-// storage pattern and staging path stores the same values. The node's hash
-// is the full lowbias32 mix of (node, key); each pair of populations then
-// takes one xorshift-multiply round of it offset by a Weyl step (the first
-// round of the same mixer): a bijection of a uniform word, so every dither
-// stays uniform, at a third of the cost of a full mix per pair.
+// in the storage format. key: per-step random key (stochastic formats only).
 template <typename S, int NQ>
 __device__ __forceinline__ void encode_each(const float (&h)[NQ], uint32_t node, uint32_t key, S (&e)[NQ]) {
     if constexpr (Codec<S>::kStochastic) {
-        const uint32_t base = lowbias32(node ^ key);
+        const uint32_t base = pair_hash(node >> 1, key);
+        const bool odd = node & 1u;
 #pragma unroll
-        for (int i = 0; i < NQ; i += 2) {
-            uint32_t r = base + (uint32_t)i * 0x9e3779b9u;
-            r ^= r >> 16;
-            r *= 0x7feb352du;
-            e[i] = Codec<S>::from_f_sr(h[i], r);
-            if (i + 1 < NQ) e[i + 1] = Codec<S>::from_f_sr(h[i + 1], r >> 16);
-        }
+        for (int i = 0; i < NQ; ++i) e[i] = Codec<S>::from_f_sr(h[i], pop_bits(base, i), odd);
     } else {
 #pragma unroll
         for (int i = 0; i < NQ; ++i) e[i] = Codec<S>::from_f(h[i]);
@@ -184,7 +248,33 @@ struct Geom {
     int nx, ny, nz;
     uint32_t walls;     // bit 0: x walls, bit 1: y walls, bit 2: z walls
     int64_t stride;     // elements between population arrays
+    // z-slab of a larger lattice: bit 0, the z- face takes the populations
+    // crossing it from a halo plane set (the neighbour below); bit 1, the z+
+    // face (the neighbour above). A halo face is neither periodic nor a wall.
+    uint32_t slab = 0;
+    uint32_t node0 = 0; // global linear index of the slab's first node (dither of stochastic rounding)
+#ifdef CLBM_BOUNDS_CHECK
+    BoundsRecord *bc = nullptr;  // violation record (bounds.cuh)
+    uint64_t bc_limit = 0;       // elements of one state buffer
+#endif
 };
+
+// Halo region of a z-slab's state buffer, after the Q population arrays (at
+// element Q * stride), in planes of nx * ny values indexed y * nx + x:
+//   planes 0-4:   received, e_z = +1 populations (Eq. A1 order 5, 11, 12, 15,
+//                 16) of the plane below the slab, pulled across the z- face;
+//   planes 5-9:   received, e_z = -1 populations (6, 13, 14, 17, 18) of the
+//                 plane above, pulled across the z+ face;
+//   planes 10-14: sent, the slab's own e_z = -1 populations of plane 0 (the
+//                 lower neighbour's planes 5-9);
+//   planes 15-19: sent, the slab's own e_z = +1 populations of plane nz - 1
+//                 (the upper neighbour's planes 0-4).
+constexpr int kSlabPlanes = 20;
+__host__ __device__ constexpr int zface_index(int i) {
+    return (i == 5 || i == 6) ? 0 : (i == 11 || i == 13) ? 1 : (i == 12 || i == 14) ? 2 : (i == 15 || i == 17) ? 3 : 4;
+}
+__host__ __device__ constexpr int zplus_pop(int k) { return k == 0 ? 5 : k == 1 ? 11 : k == 2 ? 12 : k == 3 ? 15 : 16; }
+__host__ __device__ constexpr int zminus_pop(int k) { return k == 0 ? 6 : k == 1 ? 13 : k == 2 ? 14 : k == 3 ? 17 : 18; }
 
 // Pull sources of the 19 populations arriving at node (x, y, z) (Eq. 8 read
 // backwards): population i comes from (i, x - e_i) with periodic wrap, or,
@@ -195,7 +285,12 @@ struct Geom {
 // SWAP = true gives the same offsets with the opposite array index, (ibar,
 // x - e_i) or (i, x): the slots of the in-place (AA) pattern's odd step, which
 // reads population i there and writes post-collision population ibar there.
-template <bool WALLS, bool SWAP = false>
+//
+// SLAB = true: the z faces flagged in g.slab are halo faces. A population whose
+// source lies across one (and is not bounced back at an x or y wall) is read
+// from the halo region (pop = kQ, off = plane offset within it, see
+// kSlabPlanes); z walls apply only to the faces that are not halo faces.
+template <bool WALLS, bool SWAP = false, bool SLAB = false>
 __device__ __forceinline__ void pull_sources(const Geom &g, int x, int y, int z,
                                              uint32_t (&off)[kQ], int (&pop)[kQ]) {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -218,11 +313,14 @@ __device__ __forceinline__ void pull_sources(const Geom &g, int x, int y, int z,
     off[15] = rmm + x;  off[16] = rpm + x;  off[17] = rmp + x;  off[18] = rpp + x;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) pop[i] = SWAP ? opposite(i) : i;
+    bool bbx[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) bbx[i] = false;
     if (WALLS) {
         const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
         const bool xl = wx && x == 0, xh = wx && x == nx - 1;  // ex = +1 / -1 bounce
         const bool yl = wy && y == 0, yh = wy && y == ny - 1;
-        const bool zl = wz && z == 0, zh = wz && z == nz - 1;
+        const bool zl = wz && z == 0 && !(SLAB && (g.slab & 1u)), zh = wz && z == nz - 1 && !(SLAB && (g.slab & 2u));
         // ex, ey, ez of each direction decide which faces it can cross.
         const bool bb[kQ] = {false,
                              xl, xh, yl, yh, zl, zh,
@@ -232,6 +330,27 @@ __device__ __forceinline__ void pull_sources(const Geom &g, int x, int y, int z,
 #pragma unroll
         for (int i = 1; i < kQ; ++i) {
             if (bb[i]) { pop[i] = SWAP ? i : opposite(i); off[i] = self; }
+            bbx[i] = bb[i];
+        }
+    }
+    if (SLAB) {
+        // across a halo face: the neighbour's post-collision value, from the halo planes
+        const uint32_t plane = unx * uny;
+        if ((g.slab & 1u) && z == 0) {
+#pragma unroll
+            for (int i = 1; i < kQ; ++i)
+                if (ez19(i) > 0 && !bbx[i]) {
+                    pop[i] = kQ;
+                    off[i] = (uint32_t)zface_index(i) * plane + (off[i] - (uint32_t)zm * plane);
+                }
+        }
+        if ((g.slab & 2u) && z == nz - 1) {
+#pragma unroll
+            for (int i = 1; i < kQ; ++i)
+                if (ez19(i) < 0 && !bbx[i]) {
+                    pop[i] = kQ;
+                    off[i] = (uint32_t)(5 + zface_index(i)) * plane + (off[i] - (uint32_t)zp * plane);
+                }
         }
     }
 }
@@ -290,6 +409,28 @@ struct Rates {
     float om4;  // 1 - s4
 };
 
+// One node's value with operators that round every operation on its own
+// (__fadd_rn, __fsub_rn and __fmul_rn are never merged into fused
+// multiply-adds; fused ones are written as fmaf). The collision of the 16-bit
+// storage formats runs on it, so that it rounds exactly like the f2 form
+// below, lane by lane: a step that collides two nodes at once with the FP32x2
+// instructions then stores the same bits as one node per thread.
+struct f1 {
+    float v;
+};
+__device__ __forceinline__ f1 mk1(float a) { return f1{a}; }
+__device__ __forceinline__ f1 operator+(f1 a, f1 b) { return f1{__fadd_rn(a.v, b.v)}; }
+__device__ __forceinline__ f1 operator-(f1 a, f1 b) { return f1{__fsub_rn(a.v, b.v)}; }
+__device__ __forceinline__ f1 operator-(f1 a) { return f1{-a.v}; }
+__device__ __forceinline__ f1 operator*(f1 a, f1 b) { return f1{__fmul_rn(a.v, b.v)}; }
+__device__ __forceinline__ f1 operator*(float s, f1 b) { return f1{__fmul_rn(s, b.v)}; }
+__device__ __forceinline__ f1 operator*(f1 b, float s) { return f1{__fmul_rn(b.v, s)}; }
+__device__ __forceinline__ f1 operator+(float s, f1 b) { return f1{__fadd_rn(s, b.v)}; }
+__device__ __forceinline__ f1 operator+(f1 b, float s) { return f1{__fadd_rn(b.v, s)}; }
+__device__ __forceinline__ f1 &operator*=(f1 &a, float s) { return a = a * s; }
+__device__ __forceinline__ f1 fmaf(f1 a, f1 b, f1 c) { return f1{::fmaf(a.v, b.v, c.v)}; }
+__device__ __forceinline__ f1 fmaf(float a, f1 b, f1 c) { return f1{::fmaf(a, b.v, c.v)}; }
+
 // Two nodes' values packed for the FP32x2 instructions of sm_100-class GPUs
 // (__fadd2_rn / __fmul2_rn / __ffma2_rn round each lane exactly like the
 // scalar operation). The collision templates below run on float or on f2.
@@ -323,6 +464,7 @@ __device__ __forceinline__ float recip_nr(float x) {
     return fmaf(r, e, r);
 }
 __device__ __forceinline__ f2 recip_nr(f2 x) { return mk2(recip_nr(x.v.x), recip_nr(x.v.y)); }
+__device__ __forceinline__ f1 recip_nr(f1 x) { return f1{recip_nr(x.v)}; }
 
 // The collision's 1/rho: recip_nr when FR (16-bit storage, whose steps are
 // bound by instruction issue: 3 to 6 % faster), the IEEE division otherwise
@@ -441,8 +583,8 @@ __device__ __forceinline__ void inverse_moments(const MomentsT<T> &q, T (&h)[kQ]
 // One collision (Steps 1-3 of Sec. II.B) on deviations h, in place.
 // Returns drho = rho - 1 of the pre-collision state (Eq. 9); if j_out is not
 // null it receives rho*u of Eq. 9 (momentum including F/2).
-template <bool FR = false, typename T>
-__device__ __forceinline__ T collide(T (&h)[kQ], T Fx, T Fy, T Fz, const Rates &r, float3 *j_out = nullptr) {
+template <bool FR, typename T>
+__device__ __forceinline__ T collide_t(T (&h)[kQ], T Fx, T Fy, T Fz, const Rates &r, float3 *j_out) {
     MomentsT<T> k;
     raw_moments(h, k);
     const T drho = k.m000;
@@ -450,8 +592,10 @@ __device__ __forceinline__ T collide(T (&h)[kQ], T Fx, T Fy, T Fz, const Rates &
     const T inv = recip_of<FR>(rho);
     const T jx = fmaf(0.5f, Fx, k.m100), jy = fmaf(0.5f, Fy, k.m010), jz = fmaf(0.5f, Fz, k.m001);
     const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
-    if constexpr (sizeof(T) == sizeof(float)) {
+    if constexpr (std::is_same<T, float>::value) {
         if (j_out) *j_out = make_float3(jx, jy, jz);
+    } else if constexpr (std::is_same<T, f1>::value) {
+        if (j_out) *j_out = make_float3(jx.v, jy.v, jz.v);
     }
     EqDevT<T> e;
     eq_dev(drho, rho, jx, jy, jz, ux, uy, uz, e);
@@ -528,6 +672,25 @@ __device__ __forceinline__ T collide(T (&h)[kQ], T Fx, T Fy, T Fz, const Rates &
     q.m220 = r220 + e.d220; q.m202 = r202 + e.d202; q.m022 = r022 + e.d022;
     inverse_moments(q, h);
     return drho;
+}
+
+// The collision of one node (float) or two (f2). With FR (16-bit storage) a
+// float node runs on f1, rounding every operation on its own, so that it
+// matches the f2 form bit for bit; FP32 storage keeps the compiler's fused
+// multiply-adds.
+template <bool FR = false, typename T>
+__device__ __forceinline__ T collide(T (&h)[kQ], T Fx, T Fy, T Fz, const Rates &r, float3 *j_out = nullptr) {
+    if constexpr (FR && std::is_same<T, float>::value) {
+        f1 g[kQ];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) g[i].v = h[i];
+        const f1 drho = collide_t<FR>(g, f1{Fx}, f1{Fy}, f1{Fz}, r, j_out);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) h[i] = g[i].v;
+        return drho.v;
+    } else {
+        return collide_t<FR>(h, Fx, Fy, Fz, r, j_out);
+    }
 }
 
 // Deviations of the generalized local equilibrium at (rho, u):

@@ -28,13 +28,20 @@ struct Launch {
     bool staged;       // launch_step (A/B, one node per thread): rows staged by bulk copies where they apply
                        // (step_tma.cuh)
     int map;           // state kernels: slots of the post-streaming state (0 A/B pull map,
-                       // 1 in-place pattern after even steps, 2 after odd steps)
+                       // 1 in-place pattern after even steps, 2 after odd steps, 3 the A/B pull
+                       // map of a z-slab with halo faces)
+    long long wait_cycles = 0;  // staged step: bound of a wait for a tile's copies (0: kWaitCycles)
+    bool drop_first_tile = false;  // staged step, failure injection: tile 0's copies are not issued
 };
 
 // storage: 0 = f32, 1 = f16, 2 = bf16, 3 = f16 stochastic, 4 = bf16 stochastic
 // (CLBM_STORAGE_*). key: per-step dither key (stochastic formats).
 cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
                         const ForceArgs &F, int *flag, uint32_t key);
+// The cascaded step on a z-slab (Geom::slab halo faces): the planes z0,
+// z0 + zs, ... (nplanes of them) from src into dst (step.cu).
+cudaError_t launch_step_slab(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
+                             const ForceArgs &F, int *flag, uint32_t key, int z0, int zs, int nplanes);
 // Whether an A/B step of a q-population lattice from a state buffer at src
 // (elem bytes per value) with force mode force_mode runs the shared-memory
 // staged kernel (step_tma.cuh) when the launch asks for it.

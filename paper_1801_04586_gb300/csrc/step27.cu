@@ -61,7 +61,7 @@ __device__ __forceinline__ uint32_t state_load27(const S *src, const Geom &g, in
         for (int b = 0; b < 3; ++b)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                h[a][b][c] = Codec<S>::load_plain(src + (size_t)pop[a][b][c] * g.stride + off[a][b][c]);
+                h[a][b][c] = Codec<S>::load_plain(src + CLBM_IDX(g, (size_t)pop[a][b][c] * g.stride + off[a][b][c]));
     return ((uint32_t)z * g.ny + y) * g.nx + x;
 }
 
@@ -77,7 +77,7 @@ __device__ __forceinline__ void scatter27(S *dst, const Geom &g, int x, int y, i
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dst[(size_t)pop[a][b][c] * g.stride + off[a][b][c]] = Codec<S>::from_f(h[a][b][c]);
+            for (int c = 0; c < 3; ++c) dst[CLBM_IDX(g, (size_t)pop[a][b][c] * g.stride + off[a][b][c])] = Codec<S>::from_f(h[a][b][c]);
 }
 
 template <typename S, int FM, bool WALLS>

@@ -45,7 +45,7 @@ __device__ __forceinline__ uint32_t pull27(const S *src, const Geom &g, int x, i
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) h[a][b][c] = Codec<S>::load(src + (size_t)pop[a][b][c] * g.stride + off[a][b][c]);
+            for (int c = 0; c < 3; ++c) h[a][b][c] = Codec<S>::load(src + CLBM_IDX(g, (size_t)pop[a][b][c] * g.stride + off[a][b][c]));
     return ((uint32_t)z * g.ny + y) * g.nx + x;
 }
 
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256, 4) k_step27(const S *__restrict__ src, S 
     if (!(fabsf(drho) < 0.9f)) *flag = 1;
     float f[kQ27];
     flatten27(h, f);
-    store_node<S, kQ27>(dst + self, g.stride, f, self, key);
+    store_node<S, kQ27>(dst + CLBM_SLOTS(g, self, (kQ27 - 1) * g.stride), g.stride, f, self, key);
 }
 
 // In-place (AA) pattern, as k_step_aa in step_kernels.cuh: the even kind
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_step27_aa(S *f, Geom g, Rates27 r, Forc
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) h[a][b][c] = Codec<S>::load(f + (size_t)pop[a][b][c] * g.stride + off[a][b][c]);
+            for (int c = 0; c < 3; ++c) h[a][b][c] = Codec<S>::load(f + CLBM_IDX(g, (size_t)pop[a][b][c] * g.stride + off[a][b][c]));
     float fx, fy, fz;
     force27<FM>(F, g, z, self, fx, fy, fz);
     const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_step27_aa(S *f, Geom g, Rates27 r, Forc
                 doff[p] = off[oa][ob][oc];
                 dpop[p] = pop[oa][ob][oc];
             }
-    store_each<S, kQ27>(v, self, key, [&](int p) { return f + (size_t)dpop[p] * g.stride + doff[p]; });
+    store_each<S, kQ27>(v, self, key, [&](int p) { return f + CLBM_IDX(g, (size_t)dpop[p] * g.stride + doff[p]); });
 }
 
 // ---- dispatch: storage x force mode x walls

@@ -59,12 +59,54 @@ __global__ void __launch_bounds__(512) k_step(const S *__restrict__ src, S *__re
     pull_sources<WALLS>(g, x, y, z, off, pop);
     float h[kQ];
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + (size_t)pop[i] * g.stride + off[i]);
+    for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + CLBM_IDX(g, (size_t)pop[i] * g.stride + off[i]));
     float fx, fy, fz;
     force_at<FM>(F, g, z, off[0], fx, fy, fz);
     const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
     if (!(fabsf(drho) < 0.9f)) *flag = 1;
-    store_node<S>(dst + off[0], g.stride, h, off[0], key);
+    // the node's slots off[0] + i * stride, i < kQ, lie below the last one's bound
+    store_node<S>(dst + CLBM_SLOTS(g, off[0], (kQ - 1) * g.stride), g.stride, h, off[0], key);
+}
+
+// The step on a z-slab of a larger lattice (Eq. 8 across the slab's halo
+// faces, see Geom::slab): the same update as k_step for the planes
+// z = z0, z0 + zs, ... (blockIdx.z counts them), pulling the populations that
+// cross a halo face from the halo planes of src, and also writing the node's
+// outgoing populations across a halo face into the send planes of dst for the
+// neighbour. The dither of stochastic rounding takes the global node index
+// (node0 + local index), so a slab stores exactly what the undivided lattice
+// stores.
+template <typename C, typename S, int FM, bool WALLS>
+__global__ void __launch_bounds__(512) k_step_slab(const S *__restrict__ src, S *__restrict__ dst, Geom g, Rates r,
+                                                   ForceArgs F, int *__restrict__ flag, uint32_t key, int z0, int zs) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = z0 + (int)blockIdx.z * zs;
+    if (x >= g.nx || y >= g.ny) return;
+    uint32_t off[kQ];
+    int pop[kQ];
+    pull_sources<WALLS, false, true>(g, x, y, z, off, pop);
+    float h[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(src + CLBM_IDX(g, (size_t)pop[i] * g.stride + off[i]));
+    const uint32_t plane = (uint32_t)g.nx * (uint32_t)g.ny;
+    const uint32_t ps = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
+    const uint32_t self = (uint32_t)z * plane + ps;
+    float fx, fy, fz;
+    force_at<FM>(F, g, z, self, fx, fy, fz);
+    const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
+    if (!(fabsf(drho) < 0.9f)) *flag = 1;
+    S e[kQ];
+    encode_each<S, kQ>(h, self + g.node0, key, e);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) dst[CLBM_IDX(g, (size_t)i * g.stride + self)] = e[i];
+    const size_t send = (size_t)kQ * g.stride;
+    if ((g.slab & 1u) && z == 0)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) dst[CLBM_IDX(g, send + (size_t)(10 + k) * plane + ps)] = e[zminus_pop(k)];
+    if ((g.slab & 2u) && z == g.nz - 1)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) dst[CLBM_IDX(g, send + (size_t)(15 + k) * plane + ps)] = e[zplus_pop(k)];
 }
 
 // In-place (AA) pattern: one population array set, two step kinds that
@@ -94,7 +136,7 @@ __global__ void __launch_bounds__(512, sizeof(S) == 2 ? 2 : 0) k_step_aa(S *f, G
         int pop[kQ];
         pull_sources<WALLS, true>(g, x, y, z, off, pop);
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(f + (size_t)pop[i] * g.stride + off[i]);
+        for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(f + CLBM_IDX(g, (size_t)pop[i] * g.stride + off[i]));
         float fx, fy, fz;
         force_at<FM>(F, g, z, self, fx, fy, fz);
         const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
@@ -106,15 +148,15 @@ __global__ void __launch_bounds__(512, sizeof(S) == 2 ? 2 : 0) k_step_aa(S *f, G
         int xs = x, ys = y, zs = z;
         asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs) : "f"(h[0]), "f"(h[kQ - 1]));
         push_targets<WALLS>(g, xs, ys, zs, off, pop);
-        store_each<S, kQ>(h, self, key, [&](int i) { return f + (size_t)pop[i] * g.stride + off[i]; });
+        store_each<S, kQ>(h, self, key, [&](int i) { return f + CLBM_IDX(g, (size_t)pop[i] * g.stride + off[i]); });
     } else {
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(f + (size_t)i * g.stride + self);
+        for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(f + CLBM_IDX(g, (size_t)i * g.stride + self));
         float fx, fy, fz;
         force_at<FM>(F, g, z, self, fx, fy, fz);
         const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
         if (!(fabsf(drho) < 0.9f)) *flag = 1;
-        store_each<S, kQ>(h, self, key, [&](int i) { return f + (size_t)opposite(i) * g.stride + self; });
+        store_each<S, kQ>(h, self, key, [&](int i) { return f + CLBM_IDX(g, (size_t)opposite(i) * g.stride + self); });
     }
 }
 
@@ -174,6 +216,43 @@ static cudaError_t step_aa_force_t(const Launch &L, void *f, const Rates &r, con
         case kForceUniform: return step_aa_walls_t<C, S, kForceUniform>(L, f, r, F, flag, key, odd);
         case kForceProfileZ: return step_aa_walls_t<C, S, kForceProfileZ>(L, f, r, F, flag, key, odd);
         default: return step_aa_walls_t<C, S, kForceField>(L, f, r, F, flag, key, odd);
+    }
+}
+
+template <typename C, typename S, int FM>
+static cudaError_t step_slab_walls_t(const Launch &L, const void *src, void *dst, const Rates &r,
+                                     const ForceArgs &F, int *flag, uint32_t key, int z0, int zs, int nplanes) {
+    if (nplanes <= 0) return cudaSuccess;
+    dim3 grid = L.grid;
+    grid.z = (unsigned)nplanes;
+    if (L.g.walls)
+        k_step_slab<C, S, FM, true><<<grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key,
+                                                                    z0, zs);
+    else
+        k_step_slab<C, S, FM, false><<<grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, key,
+                                                                     z0, zs);
+    return cudaGetLastError();
+}
+
+// One z-slab step (or a part of it: the planes z0, z0 + zs, ..., nplanes of
+// them) with collision C, any storage format.
+template <typename C>
+cudaError_t launch_step_slab_with(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
+                                  const ForceArgs &F, int *flag, uint32_t key, int z0, int zs, int nplanes) {
+    auto by_force = [&](auto tag) -> cudaError_t {
+        using S = decltype(tag);
+        switch (F.mode) {
+            case kForceUniform: return step_slab_walls_t<C, S, kForceUniform>(L, src, dst, r, F, flag, key, z0, zs, nplanes);
+            case kForceProfileZ: return step_slab_walls_t<C, S, kForceProfileZ>(L, src, dst, r, F, flag, key, z0, zs, nplanes);
+            default: return step_slab_walls_t<C, S, kForceField>(L, src, dst, r, F, flag, key, z0, zs, nplanes);
+        }
+    };
+    switch (storage) {
+        case 0: return by_force(float{});
+        case 1: return by_force(__half{});
+        case 2: return by_force(__nv_bfloat16{});
+        case 3: return by_force(HalfSR{});
+        default: return by_force(BF16SR{});
     }
 }
 

@@ -7,6 +7,7 @@
 namespace clbm {
 
 struct Mrt {
+    static constexpr bool kPairs = false;  // one node at a time (float only)
     template <bool FR = false>
     static __device__ __forceinline__ float run(float (&h)[kQ], float Fx, float Fy, float Fz, const Rates &r) {
         return collide_mrt<FR>(h, Fx, Fy, Fz, r);

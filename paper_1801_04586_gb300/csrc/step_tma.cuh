@@ -32,10 +32,11 @@
 // its nodes and counts itself done with the buffer; the last warp to finish
 // refills the buffer with the tile as many tiles ahead as there are buffers.
 // There is no block barrier in the loop, so warps drift apart by up to that
-// many tiles instead of waiting for the slowest. Every wait is bounded
-// (kWaitCycles); on expiry the block sets bit 1 of the flag (reported as
-// CLBM_ERR_TIMEOUT), its warps leave the loop, and one thread waits, again
-// bounded, for the copies still in flight before the block ends.
+// many tiles instead of waiting for the slowest. Every wait is bounded (the
+// context's bound, kWaitCycles by default); on expiry the block sets bit 1 of
+// the flag (reported as CLBM_ERR_TIMEOUT), its warps leave the loop, and one
+// thread waits, bounded by kWaitCycles, for the copies still in flight before
+// the block ends, so no copy lands in shared memory the block no longer owns.
 #pragma once
 
 #include <atomic>
@@ -49,9 +50,10 @@ namespace clbm {
 // shared memory are sized for them), shared buffers per block (at most 7),
 // and the tile pitch: the most nodes of a tile, and the element pitch of a
 // population's rows in a buffer.
-template <int THREADS, int BLOCKS, int STAGES, int PITCH>
+template <int THREADS, int BLOCKS, int STAGES, int PITCH, bool PAIRS = false>
 struct TmaShape {
     static constexpr int threads = THREADS, blocks = BLOCKS, stages = STAGES, pitch = PITCH;
+    static constexpr bool pairs = PAIRS;  // each thread collides two adjacent nodes at once (FP32x2)
 };
 // D3Q19: two blocks of 512 threads take two nodes each of a 1024-node tile; a
 // buffer of 19 populations of 16-bit values is 38 KB.
@@ -62,7 +64,12 @@ using TmaShape19 = TmaShape<512, 2, 2, 1024>;
 // 56.8k against 52.9k MLUPS). Rows above 768 nodes, and a force field, whose
 // rows do not fit three blocks' buffers, take TmaShape19.
 using TmaShape19W = TmaShape<256, 3, 2, 768>;
-constexpr long long kWaitCycles = 4000000000ll;  // bound of one barrier wait, about 2 s at 2 GHz
+// D3Q19, two adjacent nodes per thread collided together on the FP32x2
+// instructions (collisions that provide the f2 form): twice the live values,
+// so two blocks of 256 threads (up to 128 registers) take two pairs each of a
+// 1024-node tile.
+using TmaShape19P = TmaShape<256, 2, 2, 1024, true>;
+constexpr long long kWaitCycles = 4000000000ll;  // default bound of one barrier wait, about 2 s at 2 GHz
 
 struct TilePlan {
     int rows;       // x-rows per tile
@@ -70,6 +77,8 @@ struct TilePlan {
     int ntiles;     // tiles_y * nz
     int dz, dy;     // a block's step of gridDim.x tiles as (planes, tiles) : gridDim.x = dz tiles_y + dy
     uint32_t rdiv;  // ceil(2^32 / nx): the row of tile node n is umulhi(n, rdiv), exact for n, nx <= 1024
+    long long wait; // bound of a thread's wait for a tile's copies, in SM clock cycles
+    int drop_tile;  // failure injection: this tile's barrier is armed but its copies are not issued (-1: none)
 };
 
 // D3Q27: the collision wants about 115 registers, so 256 threads per block
@@ -117,6 +126,8 @@ inline bool tile_plan(const Geom &g, size_t elem, const void *src, int grid, int
     p.dz = grid / p.tiles_y;
     p.dy = grid - p.dz * p.tiles_y;
     p.rdiv = 0xffffffffu / (uint32_t)g.nx + 1u;
+    p.wait = kWaitCycles;
+    p.drop_tile = -1;
     return true;
 }
 
@@ -150,12 +161,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return done != 0;
 }
 
-// Wait for the phase of `parity` to complete; false after about kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for the phase of `parity` to complete; false after about `bound` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long bound) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > bound) return false;
     return true;
 }
 
@@ -190,9 +201,11 @@ __host__ __device__ constexpr uint64_t pack_shift(int axis) {
 // plane's three values (plain shared stores). Called by all 32
 // lanes of one warp; lane i < Q handles population i, lanes Q to Q + 2 the
 // force components.
+// With drop (failure injection, from the host) the barrier is armed with the
+// tile's byte count but no copy is issued, so no wait on it can complete.
 template <typename S, int FM, bool WALLS, int Q, typename SH>
 __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, const Geom &g, const TilePlan &p,
-                                           int t, unsigned char *stage, uint64_t *bar, int lane) {
+                                           int t, unsigned char *stage, uint64_t *bar, int lane, bool drop = false) {
     const int z = t / p.tiles_y;
     const int y0 = (t - z * p.tiles_y) * p.rows;
     const int rows = min(p.rows, g.ny - y0);
@@ -232,17 +245,30 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
     __syncwarp();
     if (lane == 0) mbar_arrive_expect_tx(bar, total);
     __syncwarp();
+    if (drop) return;
     if (lane < Q) {
-        const S *pop = src + (size_t)lane * g.stride + (size_t)zs * g.ny * g.nx;
+        const size_t pop = (size_t)lane * g.stride + (size_t)zs * g.ny * g.nx;
         S *dst = reinterpret_cast<S *>(stage) + lane * SH::pitch;
-        if (n_a > 0)
-            bulk_copy_g2s(dst + slot_a * g.nx, pop + (size_t)src_a * g.nx, (uint32_t)n_a * row_bytes, bar);
-        if (n_b > 0)
-            bulk_copy_g2s(dst + slot_b * g.nx, pop + (size_t)src_b * g.nx, (uint32_t)n_b * row_bytes, bar);
+        if (n_a > 0) {
+            size_t from = pop + (size_t)src_a * g.nx, to = (size_t)slot_a * g.nx;
+            if (!CLBM_RANGE_OK(g, from, (size_t)n_a * g.nx, g.bc_limit) ||
+                !CLBM_RANGE_OK(g, to, (size_t)n_a * g.nx, SH::pitch))
+                from = to = 0;  // bounds-checked build: recorded, the copy redirected in bounds
+            bulk_copy_g2s(dst + to, src + from, (uint32_t)n_a * row_bytes, bar);
+        }
+        if (n_b > 0) {
+            size_t from = pop + (size_t)src_b * g.nx, to = (size_t)slot_b * g.nx;
+            if (!CLBM_RANGE_OK(g, from, (size_t)n_b * g.nx, g.bc_limit) ||
+                !CLBM_RANGE_OK(g, to, (size_t)n_b * g.nx, SH::pitch))
+                from = to = 0;
+            bulk_copy_g2s(dst + to, src + from, (uint32_t)n_b * row_bytes, bar);
+        }
     } else if (force_lane) {
         const int c = lane - Q;
         float *dst = reinterpret_cast<float *>(stage + (size_t)Q * SH::pitch * sizeof(S)) + c * SH::pitch;
-        bulk_copy_g2s(dst, F.field + (size_t)c * F.n + ((size_t)z * g.ny + y0) * g.nx, bytes, bar);
+        size_t from = (size_t)c * F.n + ((size_t)z * g.ny + y0) * g.nx;
+        if (!CLBM_RANGE_OK(g, from, (size_t)rows * g.nx, 3 * (size_t)F.n)) from = 0;
+        bulk_copy_g2s(dst, F.field + from, bytes, bar);
     }
 }
 
@@ -292,7 +318,7 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
                 const uint32_t j = ex19(i) > 0 ? sm : (ex19(i) < 0 ? sp : n);
-                h[i] = Codec<S>::load_plain(stage + i * TN + j);
+                h[i] = Codec<S>::load_plain(stage + i * TN + CLBM_SIDX(g, j, tile));
             }
             if (WALLS && any) {
                 const bool bb[kQ] = {false,
@@ -302,11 +328,11 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
                                      yl || zl, yh || zl, yl || zh, yh || zh};
 #pragma unroll
                 for (int i = 1; i < kQ; ++i)
-                    if (bb[i]) h[i] = Codec<S>::load(src + (size_t)opposite(i) * g.stride + self);
+                    if (bb[i]) h[i] = Codec<S>::load(src + CLBM_IDX(g, (size_t)opposite(i) * g.stride + self));
             }
             const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
             if (!(fabsf(drho) < 0.9f)) atomicOr(flag, 1);
-            store_node<S>(dst + self, g.stride, h, self, key);
+            store_node<S>(dst + CLBM_SLOTS(g, self, (kQ - 1) * g.stride), g.stride, h, self, key);
         } else {  // D3Q27, the cube by velocity code (0: e = 0, 1: +1, 2: -1)
             float h[3][3][3];
 #pragma unroll
@@ -316,7 +342,7 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const uint32_t j = a == 1 ? sm : (a == 2 ? sp : n);
-                        h[a][b][c] = Codec<S>::load_plain(stage + q27_index(a, b, c) * TN + j);
+                        h[a][b][c] = Codec<S>::load_plain(stage + q27_index(a, b, c) * TN + CLBM_SIDX(g, j, tile));
                     }
             if (WALLS && any) {
                 const bool bx[3] = {false, xl, xh}, by[3] = {false, yl, yh}, bz[3] = {false, zl, zh};
@@ -328,7 +354,7 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
                         for (int c = 0; c < 3; ++c)
                             if (bx[a] || by[b] || bz[c]) {
                                 const int o = q27_index(a ? 3 - a : 0, b ? 3 - b : 0, c ? 3 - c : 0);
-                                h[a][b][c] = Codec<S>::load(src + (size_t)o * g.stride + self);
+                                h[a][b][c] = Codec<S>::load(src + CLBM_IDX(g, (size_t)o * g.stride + self));
                             }
             }
             const float drho = C::template run<sizeof(S) == 2>(h, fx, fy, fz, r);
@@ -340,7 +366,106 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
                 for (int b = 0; b < 3; ++b)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) f[q27_index(a, b, c)] = h[a][b][c];
-            store_node<S, kQ27>(dst + self, g.stride, f, self, key);
+            store_node<S, kQ27>(dst + CLBM_SLOTS(g, self, (kQ27 - 1) * g.stride), g.stride, f, self, key);
+        }
+    }
+}
+
+// The D3Q19 tile two adjacent nodes at a time: nodes n and n + 1 (n even, so
+// both in the same row: nx is even) are collided together in f2 lanes .x and
+// .y. Populations with e_x = 0 take both staged values with one 32-bit shared
+// load; each population's two results are converted by one pair conversion
+// (the even node in the lower half) and stored with one 32-bit store. The
+// collision of f2 rounds like the scalar 16-bit collision (f1), and the pair
+// conversions like the single ones, so the stored bits equal compute_tile's.
+template <typename C, typename S, int FM, bool WALLS, typename SH, typename R>
+__device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S *__restrict__ dst, const Geom &g,
+                                                   const R &r, const ForceArgs &F, int *flag, uint32_t key,
+                                                   const TilePlan &p, int z, int y0, const unsigned char *buf,
+                                                   float tfx, float tfy, float tfz) {
+    const S *stage = reinterpret_cast<const S *>(buf);
+    const float *fst = reinterpret_cast<const float *>(buf + (size_t)kQ * SH::pitch * sizeof(S));
+    constexpr int TN = SH::pitch;
+    const int rows = min(p.rows, g.ny - y0);
+    const uint32_t nx = (uint32_t)g.nx;
+    const uint32_t tile = (uint32_t)rows * nx;
+    const uint32_t base = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y0) * nx;
+    for (uint32_t n = 2u * threadIdx.x; n < tile; n += 2u * SH::threads) {
+        const uint32_t rr = __umulhi(n, p.rdiv);
+        const uint32_t x = n - rr * nx;  // even
+        const uint32_t self = base + n;   // even: the pair's index is self / 2
+        // staged slots of x - 1 for node n and of x + 2 for node n + 1, periodic in x
+        const uint32_t sm0 = x == 0 ? n + nx - 1u : n - 1u;
+        const uint32_t sp1 = x + 2u == nx ? n + 2u - nx : n + 2u;
+        f2 h[kQ];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const S *row = stage + i * TN;
+            if (ex19(i) == 0) {
+                // both slots n and n + 1 below tile: n below tile - 1
+                const float2 v =
+                    Codec<S>::unpack2(*reinterpret_cast<const uint32_t *>(row + CLBM_SIDX(g, n, tile - 1u)));
+                h[i] = f2{v};
+            } else if (ex19(i) > 0) {  // from x - 1
+                h[i] = mk2(Codec<S>::load_plain(row + CLBM_SIDX(g, sm0, tile)),
+                           Codec<S>::load_plain(row + CLBM_SIDX(g, n, tile)));
+            } else {                   // from x + 1
+                h[i] = mk2(Codec<S>::load_plain(row + CLBM_SIDX(g, n + 1u, tile)),
+                           Codec<S>::load_plain(row + CLBM_SIDX(g, sp1, tile)));
+            }
+        }
+        if (WALLS) {
+            const int y = y0 + (int)rr;
+            const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
+            const bool yl = wy && y == 0, yh = wy && y == g.ny - 1;
+            const bool zl = wz && z == 0, zh = wz && z == g.nz - 1;
+            const bool xl0 = wx && x == 0, xh1 = wx && x + 2u == nx;  // x wall of node n / node n + 1
+            const bool any = __any_sync(__activemask(), xl0 || xh1 || yl || yh || zl || zh);
+            if (any) {
+                // node n (lane .x): no x+ wall unless nx == 1, impossible here (nx even)
+                const bool bb0[kQ] = {false,
+                                      xl0, false, yl, yh, zl, zh,
+                                      xl0 || yl, yl, xl0 || yh, yh,
+                                      xl0 || zl, zl, xl0 || zh, zh,
+                                      yl || zl, yh || zl, yl || zh, yh || zh};
+                // node n + 1 (lane .y): its x- neighbour is node n
+                const bool bb1[kQ] = {false,
+                                      false, xh1, yl, yh, zl, zh,
+                                      yl, xh1 || yl, yh, xh1 || yh,
+                                      zl, xh1 || zl, zh, xh1 || zh,
+                                      yl || zl, yh || zl, yl || zh, yh || zh};
+#pragma unroll
+                for (int i = 1; i < kQ; ++i) {
+                    if (bb0[i]) h[i].v.x = Codec<S>::load(src + CLBM_IDX(g, (size_t)opposite(i) * g.stride + self));
+                    if (bb1[i])
+                        h[i].v.y = Codec<S>::load(src + CLBM_IDX(g, (size_t)opposite(i) * g.stride + self + 1u));
+                }
+            }
+        }
+        f2 fx = mk2(tfx), fy = mk2(tfy), fz = mk2(tfz);
+        if (FM == kForceField) {  // the staged field, scaled as force_at does
+            const float2 a = *reinterpret_cast<const float2 *>(fst + n);
+            const float2 b = *reinterpret_cast<const float2 *>(fst + TN + n);
+            const float2 c = *reinterpret_cast<const float2 *>(fst + 2 * TN + n);
+            fx = mk2(a.x * F.scale, a.y * F.scale);
+            fy = mk2(b.x * F.scale, b.y * F.scale);
+            fz = mk2(c.x * F.scale, c.y * F.scale);
+        } else if (FM == kForceProfileZ) {
+            fx = mk2(fst[0] * F.scale);
+            fy = mk2(fst[1] * F.scale);
+            fz = mk2(fst[2] * F.scale);
+        }
+        const f2 drho = C::template run<true>(h, fx, fy, fz, r);
+        if (!(fabsf(drho.v.x) < 0.9f) || !(fabsf(drho.v.y) < 0.9f)) atomicOr(flag, 1);
+        uint32_t *out = reinterpret_cast<uint32_t *>(dst + CLBM_SLOTS(g, self, (kQ - 1) * g.stride + 1u));
+        if constexpr (Codec<S>::kStochastic) {
+            const uint32_t hb = pair_hash(self >> 1, key);
+#pragma unroll
+            for (int i = 0; i < kQ; ++i)
+                out[(size_t)i * (g.stride >> 1)] = Codec<S>::pair_sr(h[i].v.y, h[i].v.x, pop_bits(hb, i));
+        } else {
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) out[(size_t)i * (g.stride >> 1)] = Codec<S>::pair_rn(h[i].v.y, h[i].v.x);
         }
     }
 }
@@ -373,8 +498,9 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
         for (int k = 0; k < kTmaStages; ++k) {
             const int t = blockIdx.x + k * gridDim.x;
             if (t < p.ntiles) {
-                issue_tile<S, FM, WALLS, Q, SH>(src, F, g, p, t, buf + k * SB, &bar[k], lane);
-                if (lane == 0) issued[k] = 1;
+                const bool drop = t == p.drop_tile;
+                issue_tile<S, FM, WALLS, Q, SH>(src, F, g, p, t, buf + k * SB, &bar[k], lane, drop);
+                if (lane == 0 && !drop) issued[k] = 1;  // the drain waits only for copies actually issued
             }
         }
     // No block barrier inside the loop: each warp takes the tiles in order,
@@ -390,7 +516,7 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
             tfy = F.fy * F.scale;
             tfz = F.fz * F.scale;
         }
-        const bool ok = mbar_wait(&bar[s], (uint32_t)(k / kTmaStages) & 1u);
+        const bool ok = mbar_wait(&bar[s], (uint32_t)(k / kTmaStages) & 1u, p.wait);
         if (!ok || *abort) {
             if (!ok && lane == 0) {
                 *abort = 1;
@@ -398,8 +524,12 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
             }
             break;
         }
-        compute_tile<C, S, FM, WALLS, Q, SH>(src, dst, g, r, F, flag, key, p, z, yt * p.rows, buf + s * SB, tfx, tfy,
-                                         tfz);
+        if constexpr (SH::pairs)
+            compute_tile_pairs<C, S, FM, WALLS, SH>(src, dst, g, r, F, flag, key, p, z, yt * p.rows, buf + s * SB,
+                                                    tfx, tfy, tfz);
+        else
+            compute_tile<C, S, FM, WALLS, Q, SH>(src, dst, g, r, F, flag, key, p, z, yt * p.rows, buf + s * SB, tfx,
+                                                 tfy, tfz);
         __syncwarp();
         int last = 0;
         if (lane == 0) {
@@ -427,7 +557,7 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
         // a copy did not arrive in time: before the block's shared memory is
         // released, wait (bounded) for the last copy issued into each buffer
         for (int s = 0; s < kTmaStages; ++s)
-            if (issued[s] > 0) mbar_wait(&bar[s], (uint32_t)(issued[s] - 1) & 1u);
+            if (issued[s] > 0) mbar_wait(&bar[s], (uint32_t)(issued[s] - 1) & 1u, kWaitCycles);
     }
 }
 
@@ -448,6 +578,8 @@ bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R 
         constexpr size_t smem = tile_smem_bytes<S, FM, Q, SH>();
         const int grid = p.ntiles < SH::blocks * sms ? p.ntiles : SH::blocks * sms;
         tile_plan(L.g, sizeof(S), src, grid, SH::pitch, p);
+        if (L.wait_cycles > 0) p.wait = L.wait_cycles;
+        if (L.drop_first_tile) p.drop_tile = 0;
         auto kern = k_step_tma<C, S, FM, WALLS, Q, SH, R>;
         // the shared-memory opt-in, once per device for this kernel; host threads
         // may race to set it, which repeats a harmless call
@@ -472,6 +604,9 @@ bool launch_step_tma(const Launch &L, const void *src, void *dst, const R &r, co
     if constexpr (Q == 27) {
         return L.g.walls ? launch_step_tma_shape<TmaShape27, true, Q, C, S, FM>(L, src, dst, r, F, flag, key, err)
                          : launch_step_tma_shape<TmaShape27, false, Q, C, S, FM>(L, src, dst, r, F, flag, key, err);
+    } else if constexpr (C::kPairs) {
+        return L.g.walls ? launch_step_tma_shape<TmaShape19P, true, Q, C, S, FM>(L, src, dst, r, F, flag, key, err)
+                         : launch_step_tma_shape<TmaShape19P, false, Q, C, S, FM>(L, src, dst, r, F, flag, key, err);
     } else {
         if (!L.g.walls)
             return launch_step_tma_shape<TmaShape19, false, Q, C, S, FM>(L, src, dst, r, F, flag, key, err);

@@ -21,6 +21,20 @@ def _ptr(t: Optional[torch.Tensor]):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+class _DeviceSpan:
+    """A span of device memory owned by the library, exposed to PyTorch through
+    the CUDA array interface (no copy)."""
+
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), False),
+                                         "version": 3, "strides": None, "stream": None}
+
+
+def _device_bytes(ptr: int, nbytes: int, device) -> torch.Tensor:
+    with torch.cuda.device(device):
+        return torch.as_tensor(_DeviceSpan(ptr, nbytes), device=device)
+
+
 class Lattice:
     """CLBM lattice (Fei, Luo & Li, arXiv:1801.04586): D3Q19 of Appendix A
     (lattice=19) or D3Q27 of Sec. II (lattice=27).
@@ -33,13 +47,19 @@ class Lattice:
     buffers, pull) or 'aa' (one buffer updated in place); model is
     'cascaded' (the paper's collision), or one of the comparison models
     'srt' (SRT-LBM at s2) and 'mrt' (non-orthogonal MRT of Appendix B).
+    slab (SLAB_LO | SLAB_HI bits) and z0 make the lattice the z-slab
+    z0 .. z0 + nz - 1 of a larger one whose z faces take their crossing
+    populations from halo planes (see slab_step, faces and slabs.py).
+    wait_cycles bounds the staged step's waits for its copies (0: about 2 s);
+    inject = INJECT_DROP_COPY withholds the first tile's copies (failure-
+    detection tests: the step then ends with CLBM_ERR_TIMEOUT).
     """
 
     def __init__(self, nx: int, ny: int, nz: int, nu: float, walls: int = 0, s2b: float = 1.0,
                  s3: float = 1.0, s4: float = 1.0, storage: str = "f32", block: Tuple[int, int] = (0, 0),
                  device=None, stream: Optional[torch.cuda.Stream] = None, variant: int = 0, lattice: int = 19,
                  s3b: float = 1.0, s4b: float = 1.0, s5: float = 1.0, s6: float = 1.0, pattern: str = "ab",
-                 model: str = "cascaded"):
+                 model: str = "cascaded", slab: int = 0, z0: int = 0, wait_cycles: int = 0, inject: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required: the lattice runs only in libclbm.so's kernels")
         self.lib = _capi.lib()
@@ -53,12 +73,15 @@ class Lattice:
         self.pattern = pattern
         self.model = model
         self.q = 27 if int(lattice) == 27 else 19
+        self.slab = int(slab)
+        self.z0 = int(z0)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             p = _capi.Params(self.nx, self.ny, self.nz, self.walls, float(nu), float(s2b), float(s3), float(s4),
                              _capi.STORAGE[storage], int(block[0]), int(block[1]), int(variant), int(lattice),
                              _capi.PATTERN[pattern],
-                             float(s3b), float(s4b), float(s5), float(s6), _capi.MODEL[model], 0)
+                             float(s3b), float(s4b), float(s5), float(s6), _capi.MODEL[model], self.slab,
+                             self.z0, 0, int(wait_cycles), int(inject), 0)
             h = ctypes.c_void_p()
             check(self.lib.clbm_create(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
                   "clbm_create")
@@ -199,6 +222,23 @@ class Lattice:
     @property
     def steps_done(self) -> int:
         return int(self.info()["steps_done"])
+
+    # ---- z-slab decomposition
+    def slab_step(self, part: int = _capi.SLAB_ALL):
+        """One step of a z-slab (or its faces / interior part, SLAB_FACES then
+        SLAB_INTERIOR); exchange faces (slabs.exchange_faces) before the next."""
+        check(self.lib.clbm_slab_step(self.h, int(part)), "clbm_slab_step")
+
+    def faces(self) -> Tuple[torch.Tensor, torch.Tensor]:
+        """(send, recv): byte views of the newest state's send and receive
+        planes, each 2 x face_bytes (first half: the lower neighbour's share,
+        second half: the upper's). They alias library memory and are valid
+        until the next step."""
+        send, recv, nb = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+        check(self.lib.clbm_slab_faces(self.h, ctypes.byref(send), ctypes.byref(recv), ctypes.byref(nb)),
+              "clbm_slab_faces")
+        return (_device_bytes(send.value, 2 * nb.value, self.device),
+                _device_bytes(recv.value, 2 * nb.value, self.device))
 
     # ---- recomputation and adjoint (FP32 storage)
     def step_raw(self, src: torch.Tensor, dst: torch.Tensor):

@@ -1,18 +1,28 @@
-"""Host-side bookkeeping of a z-slab decomposition of one lattice across ranks.
+"""Host-side driver of a z-slab decomposition of one lattice across ranks.
 
 Each rank owns a contiguous range of z planes. One time step needs, from each
-neighbour, the populations that cross the shared face: with the pull scheme of
-the GPU kernel these are the 5 post-collision populations with e_z = +1
-(Z_PLUS, Eq. A1 order) of the plane below the face and the 5 with e_z = -1
-(Z_MINUS) of the plane above it. A solver that stores the post-streaming state
-(as the FP64 oracle does) exchanges whole boundary planes instead and steps a
-slab extended by one ghost plane on each side. Holds no method arithmetic.
+neighbour, the populations that cross the shared face (Eq. 8): with the pull
+scheme of the GPU kernel these are the 5 post-collision populations with
+e_z = +1 (Z_PLUS, Eq. A1 order) of the plane below the face and the 5 with
+e_z = -1 (Z_MINUS) of the plane above it. A slab lattice of the library
+(Lattice(..., slab=..., z0=...)) writes its outgoing faces into send planes
+and pulls the incoming ones from receive planes; exchange_faces moves them
+between ranks after every step, over torch.distributed point-to-point calls
+(NCCL on device memory, or staged through host memory for gloo), or within
+one rank for a single slab that is its own neighbour.
+
+A solver that stores the post-streaming state (as the FP64 oracle does)
+exchanges whole boundary planes instead and steps a slab extended by one
+ghost plane on each side (exchange_planes). Holds no method arithmetic.
 """
 from __future__ import annotations
 
 from typing import List, Tuple
 
 import torch
+
+SLAB_LO, SLAB_HI = 1, 2
+TAG_UP, TAG_DOWN = 11, 12  # faces travelling to the upper / lower neighbour
 
 Z_PLUS = (5, 11, 12, 15, 16)
 Z_MINUS = (6, 13, 14, 17, 18)
@@ -51,3 +61,78 @@ def exchange_planes(local: torch.Tensor, rank: int, world: int, dist) -> Tuple[t
     for r in reqs:
         r.wait()
     return ghost_below, ghost_above
+
+
+def slab_of(nz: int, rank: int, world: int, periodic_z: bool = True) -> Tuple[int, int, int]:
+    """(z0, nz_local, slab bits) of rank's slab of an nz-plane lattice. A
+    periodic z axis gives every slab both halo faces (one rank: its own
+    neighbour); with z walls the first slab's z- face and the last slab's z+
+    face are walls instead."""
+    z0, z1 = partition(nz, world)[rank]
+    if periodic_z:
+        bits = SLAB_LO | SLAB_HI
+    else:
+        bits = (SLAB_LO if rank > 0 else 0) | (SLAB_HI if rank < world - 1 else 0)
+    return z0, z1 - z0, bits
+
+
+def exchange_faces(lat, rank: int, world: int, dist=None, host: bool = False, wait: bool = True) -> list:
+    """After a step (or after its SLAB_FACES part): send this slab's outgoing
+    faces to its z neighbours and receive theirs into the newest state's
+    receive planes. The first half of `send` (the first plane's e_z = -1
+    populations) goes down, into the lower neighbour's second receive half;
+    the second half (the last plane's e_z = +1 populations) goes up, into the
+    upper neighbour's first receive half. Messages going up are issued before
+    those going down, so that with NCCL (which matches a pair's messages in
+    order) two ranks that are each other's upper and lower neighbour pair
+    them correctly. host=True stages the faces through host memory (gloo).
+    With wait=False (device path) the point-to-point requests are returned
+    unwaited, so that the caller can enqueue the interior part of the step
+    before waiting: their wait() makes the current stream wait for the
+    transfers."""
+    send, recv = lat.faces()
+    half = send.numel() // 2
+    has_lo, has_hi = bool(lat.slab & SLAB_LO), bool(lat.slab & SLAB_HI)
+    with torch.cuda.stream(lat.stream):
+        if world == 1 or dist is None:
+            # its own neighbour on both sides (a periodic z axis on one slab)
+            if has_hi:
+                recv[:half].copy_(send[half:])
+            if has_lo:
+                recv[half:].copy_(send[:half])
+            return []
+        lo, hi = neighbours(rank, world)
+        if host:
+            send_h = send.cpu()
+            recv_h = torch.empty(recv.numel(), dtype=torch.uint8)
+            s_up, s_dn, r_lo, r_hi = send_h[half:], send_h[:half], recv_h[:half], recv_h[half:]
+        else:
+            s_up, s_dn, r_lo, r_hi = send[half:], send[:half], recv[:half], recv[half:]
+        ops = []
+        if has_hi:
+            ops.append(("send", s_up, hi, TAG_UP))
+        if has_lo:
+            ops.append(("recv", r_lo, lo, TAG_UP))
+        if has_lo:
+            ops.append(("send", s_dn, lo, TAG_DOWN))
+        if has_hi:
+            ops.append(("recv", r_hi, hi, TAG_DOWN))
+        if host:
+            reqs = [dist.isend(t, p, tag=tag) if kind == "send" else dist.irecv(t, p, tag=tag)
+                    for kind, t, p, tag in ops]
+            for r in reqs:
+                r.wait()
+            if has_lo:
+                recv[:half].copy_(recv_h[:half])
+            if has_hi:
+                recv[half:].copy_(recv_h[half:])
+            return []
+        if not ops:
+            return []
+        p2p = [dist.P2POp(dist.isend if kind == "send" else dist.irecv, t, p, tag=tag) for kind, t, p, tag in ops]
+        reqs = dist.batch_isend_irecv(p2p)
+        if wait:
+            for r in reqs:
+                r.wait()
+            return []
+        return reqs

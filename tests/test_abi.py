@@ -49,7 +49,7 @@ def _params(**kw):
     from paper_1801_04586_gb300 import _capi
     base = dict(nx=8, ny=8, nz=8, walls=0, nu=0.1, s2b=1.0, s3=1.0, s4=1.0, storage=0, block_x=0, block_y=0,
                 variant=0, lattice=0, pattern=0, s3b=0.0, s4b=0.0, s5=0.0, s6=0.0, model=0,
-                reserved=0)
+                slab=0, z0=0, reserved=0, wait_cycles=0, inject=0, reserved2=0)
     base.update(kw)
     return _capi.Params(**base)
 
@@ -61,7 +61,11 @@ def _params(**kw):
                                 dict(lattice=21), dict(lattice=27, s5=2.5), dict(lattice=27, variant=2),
                                 dict(lattice=27, block_x=512, block_y=1), dict(pattern=2),
                                 dict(pattern=-1), dict(pattern=1, variant=2), dict(model=3), dict(model=-1),
-                                dict(reserved=1), dict(model=2, variant=2)])
+                                dict(reserved=1), dict(model=2, variant=2), dict(slab=4), dict(slab=1, lattice=27),
+                                dict(slab=2, model=1), dict(slab=3, pattern=1), dict(slab=1, variant=2),
+                                dict(z0=5), dict(slab=1, z0=-1),
+                                dict(slab=3, nx=1024, ny=1024, nz=8, z0=2100), dict(wait_cycles=-1),
+                                dict(inject=2), dict(reserved2=1)])
 def test_create_rejects_bad_parameters(lib, kw):
     from paper_1801_04586_gb300 import _capi
     h = ctypes.c_void_p()
@@ -78,5 +82,7 @@ def test_null_pointers_rejected(lib):
     assert lib.clbm_step(None, 1) == _capi.CLBM_ERR_ARG
     assert lib.clbm_get_macros(None, None, None) == _capi.CLBM_ERR_ARG
     assert lib.clbm_destroy(None) == _capi.CLBM_OK
+    assert lib.clbm_slab_step(None, 0) == _capi.CLBM_ERR_ARG
+    assert lib.clbm_slab_faces(None, None, None, None) == _capi.CLBM_ERR_ARG
     assert lib.clbm_status_string(_capi.CLBM_ERR_UNSTABLE).decode().startswith("unstable")
     assert lib.clbm_status_string(_capi.CLBM_ERR_TIMEOUT).decode().startswith("timeout")

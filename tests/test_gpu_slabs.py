@@ -1,0 +1,197 @@
+"""The z-slab decomposition of the library's step (Eq. 8 across the slab
+faces) against one undivided lattice, through the C ABI: slabs that exchange
+their faces after every step reproduce the undivided state bit for bit, for
+periodic and walled z axes, x/y walls, every storage format (stochastic
+rounding included: its dither takes the global node index), a one-plane
+slab, the split step (faces, then interior, with the exchange between), and
+two ranks in separate processes on the one GPU exchanging through host
+memory (gloo). Plus the calls a slab context refuses."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from gpu_common import dev, t
+from paper_1801_04586_gb300 import Lattice, _capi, slabs, synthetic
+
+pytestmark = pytest.mark.gpu
+
+RATES = dict(s2b=1.2, s3=1.1, s4=0.9)
+
+
+def _inputs(shape, seed):
+    u0 = synthetic.divfree_velocity(shape, seed=seed, umax=0.03)
+    F = synthetic.gaussian_force(shape, 1e-4, seed=seed + 1)
+    return u0, F
+
+
+def _undivided(nx, ny, nz, walls, storage, u0, F, steps, nu=0.04):
+    g = Lattice(nx, ny, nz, nu, walls=walls, storage=storage, device=dev(), **RATES)
+    g.set_force_field(t(F))
+    g.init_equilibrium(None, t(u0))
+    for _ in range(steps):
+        g.step(1)
+    out = g.populations(deviation=True).cpu()
+    g.close()
+    return out
+
+
+def _make_slabs(nx, ny, nz, walls, storage, u0, F, ranges, periodic, nu=0.04):
+    lats, keep = [], []
+    world = len(ranges)
+    for r, (z0, z1) in enumerate(ranges):
+        if periodic:
+            bits = 3
+        else:
+            bits = (1 if r > 0 else 0) | (2 if r < world - 1 else 0)
+        lat = Lattice(nx, ny, z1 - z0, nu, walls=walls, storage=storage, device=dev(), slab=bits, z0=z0, **RATES)
+        Fs = t(np.ascontiguousarray(F[:, z0:z1]))
+        lat.set_force_field(Fs)
+        lat.init_equilibrium(None, t(np.ascontiguousarray(u0[:, z0:z1])))
+        lats.append(lat)
+        keep.append(Fs)
+    return lats, keep
+
+
+def _exchange_all(lats):
+    """Every face to its neighbour (one process; the lattices share a stream)."""
+    world = len(lats)
+    faces = [lat.faces() for lat in lats]
+    for r, lat in enumerate(lats):
+        send = faces[r][0]
+        half = send.numel() // 2
+        lo, hi = (r - 1) % world, (r + 1) % world
+        if lat.slab & 2:
+            faces[hi][1][:half].copy_(send[half:])
+        if lat.slab & 1:
+            faces[lo][1][half:].copy_(send[:half])
+
+
+def _gather(lats):
+    return torch.cat([lat.populations(deviation=True).cpu() for lat in lats], dim=1)
+
+
+CASES = [
+    # (nx, ny, nz, walls, storage, ranges, periodic)
+    (24, 20, 16, 0, "f32", [(0, 8), (8, 16)], True),
+    (24, 20, 16, 4, "f32", [(0, 8), (8, 16)], False),
+    (33, 17, 12, 7, "f32", [(0, 5), (5, 6), (6, 12)], False),
+    (24, 20, 15, 3, "f32", [(0, 4), (4, 5), (5, 15)], True),
+    (32, 16, 16, 6, "f16", [(0, 7), (7, 16)], False),
+    (32, 16, 16, 0, "bf16", [(0, 9), (9, 16)], True),
+    (32, 16, 16, 4, "f16sr", [(0, 8), (8, 16)], False),
+    (32, 16, 16, 0, "bf16sr", [(0, 3), (3, 11), (11, 16)], True),
+    (40, 12, 10, 0, "f32", [(0, 10)], True),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}w{c[3]}{c[4]}s{len(c[5])}")
+def test_slabs_reproduce_the_undivided_lattice(case):
+    nx, ny, nz, walls, storage, ranges, periodic = case
+    if not periodic:
+        walls |= 4
+    shape = (nz, ny, nx)
+    u0, F = _inputs(shape, 5)
+    steps = 40
+    ref = _undivided(nx, ny, nz, walls, storage, u0, F, steps)
+    lats, keep = _make_slabs(nx, ny, nz, walls, storage, u0, F, ranges, periodic)
+    assert torch.equal(_gather(lats), _undivided(nx, ny, nz, walls, storage, u0, F, 0))
+    for _ in range(steps):
+        for lat in lats:
+            lat.slab_step()
+        _exchange_all(lats)
+    got = _gather(lats)
+    assert torch.equal(got, ref)
+    mom = sum(lat.reduce_moments().cpu().numpy() for lat in lats)
+    g = Lattice(nx, ny, nz, 0.04, walls=walls, storage=storage, device=dev(), **RATES)
+    g.set_force_field(t(F))
+    g.set_populations(ref.to(dev()), deviation=True)
+    np.testing.assert_allclose(mom, g.reduce_moments().cpu().numpy(), rtol=1e-13, atol=1e-13)
+    g.close()
+    for lat in lats:
+        lat.check()
+        lat.close()
+
+
+def test_split_step_with_overlapped_exchange_equals_whole_step():
+    """SLAB_FACES, the exchange, then SLAB_INTERIOR: the receive planes of the
+    new state are written while the interior part is still to run."""
+    nx, ny, nz = 48, 24, 20
+    shape = (nz, ny, nx)
+    u0, F = _inputs(shape, 9)
+    ref = _undivided(nx, ny, nz, 0, "f32", u0, F, 30)
+    lats, keep = _make_slabs(nx, ny, nz, 0, "f32", u0, F, [(0, 10), (10, 20)], True)
+    for _ in range(30):
+        for lat in lats:
+            lat.slab_step(_capi.SLAB_FACES)
+        _exchange_all(lats)
+        for lat in lats:
+            lat.slab_step(_capi.SLAB_INTERIOR)
+    assert torch.equal(_gather(lats), ref)
+    for lat in lats:
+        lat.close()
+
+
+def test_slab_context_refuses_what_needs_no_exchange():
+    lat = Lattice(16, 8, 6, 0.05, device=dev(), slab=3, z0=4)
+    info = lat.info()
+    assert info["slab"] == 3 and info["face_bytes"] == 5 * 16 * 8 * 4
+    assert info["state_bytes"] == (19 * info["pop_stride"] + 20 * 16 * 8) * 4
+    lib = lat.lib
+    assert lib.clbm_step(lat.h, 2) == _capi.CLBM_ERR_STATE
+    assert lib.clbm_slab_step(lat.h, _capi.SLAB_INTERIOR) == _capi.CLBM_ERR_STATE
+    assert lib.clbm_slab_step(lat.h, 7) == _capi.CLBM_ERR_ARG
+    assert lib.clbm_slab_step(lat.h, _capi.SLAB_FACES) == _capi.CLBM_OK
+    assert lib.clbm_slab_step(lat.h, _capi.SLAB_FACES) == _capi.CLBM_ERR_STATE
+    assert lib.clbm_slab_step(lat.h, _capi.SLAB_INTERIOR) == _capi.CLBM_OK
+    assert lib.clbm_run_host(lat.h, None, None, 1, None, None, None) == _capi.CLBM_ERR_STATE
+    assert lib.clbm_step_raw(lat.h, lat.export_state().data_ptr(), lat.export_state().data_ptr()) \
+        == _capi.CLBM_ERR_STATE
+    plain = Lattice(16, 8, 6, 0.05, device=dev())
+    assert plain.lib.clbm_slab_step(plain.h, 0) == _capi.CLBM_ERR_ARG
+    lat.close()
+    plain.close()
+
+
+# ---- two ranks in separate processes on the one GPU (gloo, faces through host memory)
+NX, NY, NZ, STEPS = 40, 24, 18, 25
+
+
+def _rank_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    shape = (NZ, NY, NX)
+    u0, F = _inputs(shape, 13)
+    z0, nzl, bits = slabs.slab_of(NZ, rank, world, periodic_z=True)
+    lat = Lattice(NX, NY, nzl, 0.04, walls=2, storage="f32", device=dev(), slab=bits, z0=z0, **RATES)
+    Fs = t(np.ascontiguousarray(F[:, z0:z0 + nzl]))
+    lat.set_force_field(Fs)
+    lat.init_equilibrium(None, t(np.ascontiguousarray(u0[:, z0:z0 + nzl])))
+    for _ in range(STEPS):
+        lat.slab_step()
+        slabs.exchange_faces(lat, rank, world, dist, host=True)
+    torch.save(lat.populations(deviation=True).cpu(), f"{out_path}.{rank}")
+    lat.check()
+    lat.close()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_two_rank_processes_match_the_undivided_lattice(tmp_path):
+    out = str(tmp_path / "slab")
+    mp.start_processes(_rank_worker, args=(2, _free_port(), out), nprocs=2, start_method="spawn", join=True)
+    got = torch.cat([torch.load(f"{out}.{r}") for r in range(2)], dim=1)
+    u0, F = _inputs((NZ, NY, NX), 13)
+    assert torch.equal(got, _undivided(NX, NY, NZ, 2, "f32", u0, F, STEPS))

@@ -3,8 +3,10 @@ against the one-node-per-thread step (k_step), and against the FP64 oracle.
 
 The staged kernel copies the pulled rows into shared memory with bulk
 asynchronous copies and reads them back shifted along x; it performs the same
-collision on the same values, so its populations must equal k_step's bit for
-bit, for every 16-bit format, collision model, wall set and tile shape: tiles
+collision on the same values (the cascaded collision on two adjacent nodes at
+once, with FP32x2 instructions that round like the one-node form, and pair
+conversions), so its populations must equal k_step's bit for bit, for every
+16-bit format, collision model, wall set and tile shape: tiles
 of several rows with a partial last tile, one row per tile (nx = 1024), a
 single row (ny = 1), a single plane (nz = 1), and x walls, whose nodes read
 their bounce-back partners from global memory.
@@ -34,6 +36,9 @@ CASES = [
     ((24, 50, 1), 4, "f16", "cascaded"),     # nz = 1 between two z walls
     ((48, 16, 16), 1, "f16sr", "srt"),       # x walls
     ((32, 32, 32), 0, "bf16", "mrt"),
+    ((48, 16, 16), 1, "bf16sr", "cascaded"),  # x walls, node pairs (both lanes bounce at the two x faces)
+    ((16, 9, 5), 5, "f16", "cascaded"),       # x and z walls, node pairs
+    ((8, 3, 2), 7, "f16sr", "cascaded"),      # a single node pair between x walls
 ]
 
 

@@ -1,7 +1,10 @@
-"""A z-slab decomposition of one periodic-in-z lattice over 2 CPU ranks (gloo):
-each rank steps its slab extended by ghost planes received from its
-neighbours, with the FP64 oracle as the local solver; the gathered result must
-equal the undivided oracle run bit for bit."""
+"""The z-slab decomposition's host side on CPU ranks (gloo): the partition and
+neighbour bookkeeping; the face exchange that the library's slab lattices use
+(slabs.exchange_faces) routing every face to the right neighbour and slot, for
+2 and 3 ranks, periodic and walled z, over host-staged and batched
+point-to-point calls; and one periodic-in-z lattice stepped on 2 ranks, each
+its slab extended by ghost planes from its neighbours, with the FP64 oracle
+as the local solver, equal to the undivided oracle run bit for bit."""
 import os
 import socket
 
@@ -77,3 +80,68 @@ def test_two_rank_slabs_match_single_domain(tmp_path):
     lat = _lattice(NZ)
     ref = oracle.step(lat, oracle.init(lat, rho, u, F), F, STEPS)
     np.testing.assert_array_equal(np.load(out), ref)
+
+
+class _FakeSlab:
+    """Stands in for a library slab lattice: send planes filled with a
+    pattern naming (rank, half, byte), receive planes zeroed."""
+
+    def __init__(self, rank, bits, half):
+        self.slab = bits
+        self.stream = None
+        i = torch.arange(half, dtype=torch.int64)
+        self.send = torch.cat([(rank * 40 + 7 + i * 3) % 251, (rank * 40 + 19 + i * 5) % 251]).to(torch.uint8)
+        self.recv = torch.zeros(2 * half, dtype=torch.uint8)
+
+    def faces(self):
+        return self.send, self.recv
+
+
+def _exchange_worker(rank, world, port, periodic, host, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    half = 37
+    _, _, bits = slabs.slab_of(3 * world, rank, world, periodic_z=periodic)
+    lat = _FakeSlab(rank, bits, half)
+    slabs.exchange_faces(lat, rank, world, dist, host=host)
+    torch.save({"send": lat.send, "recv": lat.recv, "bits": bits}, f"{out_path}.{rank}")
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,periodic,host", [(2, True, True), (3, True, True), (3, False, True),
+                                                 (2, True, False), (3, False, False)])
+def test_face_exchange_routes_every_face(tmp_path, world, periodic, host):
+    """After exchange_faces, each rank's first receive half holds its lower
+    neighbour's upper send half and its second receive half its upper
+    neighbour's lower send half; receive halves at wall faces stay untouched."""
+    out = str(tmp_path / "faces")
+    mp.start_processes(_exchange_worker, args=(world, _free_port(), periodic, host, out), nprocs=world,
+                       start_method="spawn", join=True)
+    got = [torch.load(f"{out}.{r}") for r in range(world)]
+    for r in range(world):
+        lo, hi = slabs.neighbours(r, world)
+        half = got[r]["send"].numel() // 2
+        bits = got[r]["bits"]
+        if bits & slabs.SLAB_LO:
+            assert torch.equal(got[r]["recv"][:half], got[lo]["send"][half:])
+        else:
+            assert not periodic and r == 0 and torch.count_nonzero(got[r]["recv"][:half]) == 0
+        if bits & slabs.SLAB_HI:
+            assert torch.equal(got[r]["recv"][half:], got[hi]["send"][:half])
+        else:
+            assert not periodic and r == world - 1 and torch.count_nonzero(got[r]["recv"][half:]) == 0
+
+
+def test_single_slab_is_its_own_neighbour():
+    lat = _FakeSlab(0, slabs.SLAB_LO | slabs.SLAB_HI, 5)
+    slabs.exchange_faces(lat, 0, 1)
+    assert torch.equal(lat.recv[:5], lat.send[5:]) and torch.equal(lat.recv[5:], lat.send[:5])
+
+
+def test_slab_of_partitions_and_flags_faces():
+    assert slabs.slab_of(10, 0, 3) == (0, 4, 3)
+    assert slabs.slab_of(10, 1, 3, periodic_z=False) == (4, 3, 3)
+    assert slabs.slab_of(10, 2, 3, periodic_z=False) == (7, 3, 1)
+    assert slabs.slab_of(10, 0, 3, periodic_z=False) == (0, 4, 2)
+    assert slabs.slab_of(5, 0, 1, periodic_z=False) == (0, 5, 0)
