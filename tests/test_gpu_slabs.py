@@ -136,6 +136,44 @@ def test_split_step_with_overlapped_exchange_equals_whole_step():
         lat.close()
 
 
+def test_kolmogorov_slabs_with_profile_force_and_split_steps():
+    """The configuration the benchmark runs on several GPUs, on one: z-slabs of
+    a periodic Kolmogorov box (z-profile force F_x = F0 sin(2 pi z/nz), each
+    slab given its own planes of the profile), FP32 and stochastic FP16,
+    stepped in faces and interior parts with the exchange between them."""
+    nx, ny, nz, F0 = 32, 24, 24, 1e-4
+    shape = (nz, ny, nx)
+    prof = synthetic.kolmogorov_profile(nz, F0)
+    u0 = synthetic.divfree_velocity(shape, seed=1, umax=0.02)
+    for storage in ("f32", "f16sr"):
+        g = Lattice(nx, ny, nz, 0.01, storage=storage, device=dev())
+        gp = t(prof)
+        g.set_force_profile_z(gp)
+        g.init_equilibrium(None, t(u0))
+        for _ in range(25):
+            g.step(1)
+        ref = g.populations(deviation=True).cpu()
+        g.close()
+        lats, keep = [], []
+        for z0, z1 in [(0, 8), (8, 16), (16, 24)]:
+            lat = Lattice(nx, ny, z1 - z0, 0.01, storage=storage, device=dev(), slab=3, z0=z0)
+            p = t(np.ascontiguousarray(prof[:, z0:z1]))
+            lat.set_force_profile_z(p)
+            lat.init_equilibrium(None, t(np.ascontiguousarray(u0[:, z0:z1])))
+            lats.append(lat)
+            keep.append(p)
+        for _ in range(25):
+            for lat in lats:
+                lat.slab_step(_capi.SLAB_FACES)
+            _exchange_all(lats)
+            for lat in lats:
+                lat.slab_step(_capi.SLAB_INTERIOR)
+        assert torch.equal(_gather(lats), ref), storage
+        for lat in lats:
+            lat.check()
+            lat.close()
+
+
 def test_slab_context_refuses_what_needs_no_exchange():
     lat = Lattice(16, 8, 6, 0.05, device=dev(), slab=3, z0=4)
     info = lat.info()
