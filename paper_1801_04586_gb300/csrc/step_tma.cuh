@@ -524,12 +524,26 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
             }
             break;
         }
-        if constexpr (SH::pairs)
-            compute_tile_pairs<C, S, FM, WALLS, SH>(src, dst, g, r, F, flag, key, p, z, yt * p.rows, buf + s * SB,
-                                                    tfx, tfy, tfz);
-        else
-            compute_tile<C, S, FM, WALLS, Q, SH>(src, dst, g, r, F, flag, key, p, z, yt * p.rows, buf + s * SB, tfx,
-                                                 tfy, tfz);
+        // Only tiles with a node next to a wall take the wall code; the others run the periodic loop, which
+        // the wall handling would otherwise slow on every tile (12-21 % for the node-pair loop).
+        const int y0 = yt * p.rows;
+        const bool wall_tile = WALLS && ((g.walls & 1u) || ((g.walls & 4u) && (z == 0 || z == g.nz - 1)) ||
+                                         ((g.walls & 2u) && (y0 == 0 || y0 + p.rows >= g.ny)));
+        if constexpr (SH::pairs) {
+            if (wall_tile)
+                compute_tile_pairs<C, S, FM, true, SH>(src, dst, g, r, F, flag, key, p, z, y0, buf + s * SB, tfx,
+                                                       tfy, tfz);
+            else
+                compute_tile_pairs<C, S, FM, false, SH>(src, dst, g, r, F, flag, key, p, z, y0, buf + s * SB, tfx,
+                                                        tfy, tfz);
+        } else {
+            if (wall_tile)
+                compute_tile<C, S, FM, true, Q, SH>(src, dst, g, r, F, flag, key, p, z, y0, buf + s * SB, tfx, tfy,
+                                                    tfz);
+            else
+                compute_tile<C, S, FM, false, Q, SH>(src, dst, g, r, F, flag, key, p, z, y0, buf + s * SB, tfx, tfy,
+                                                     tfz);
+        }
         __syncwarp();
         int last = 0;
         if (lane == 0) {
