@@ -233,3 +233,26 @@ def test_two_rank_processes_match_the_undivided_lattice(tmp_path):
     got = torch.cat([torch.load(f"{out}.{r}") for r in range(2)], dim=1)
     u0, F = _inputs((NZ, NY, NX), 13)
     assert torch.equal(got, _undivided(NX, NY, NZ, 2, "f32", u0, F, STEPS))
+
+
+def test_benchmark_slab_mode_runs_two_ranks_on_one_gpu():
+    """bench.py --gpus 2 under torchrun, its z-slab mode: two ranks sharing the
+    one GPU (gloo, faces through host memory; the NCCL exchange needs one GPU
+    per rank) print one contract line for the 256 x 256 x 512 box with two
+    launches per step."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--gpus", "2", "--steps", "4",
+           "--warmup", "2", "--dist-backend", "gloo", "--no-variants", "--no-cpu-baseline"]
+    r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["steps"] == 4 and d["scaling"] == "weak" and d["value"] > 0
+    assert d["gpu_launches"] == 8
+    assert "z-slabs" in d["config"]["parallelism"] and "256x256x512" in d["config"]["workload"]
+    assert d["e2e"]["value"] > 0
