@@ -299,15 +299,20 @@ __device__ __forceinline__ void force_adj(const ForceArgs &F, const Geom &g, int
 
 // One adjoint step. state: raw buffer whose pull gives f^t; lam_next: adjoint
 // of f^{t+1} (19 x n, post-streaming layout); lam: adjoint of f^t (19 x n);
-// gF: dL/dF accumulated (3 x n).
+// gF: dL/dF accumulated (3 x n). The node's three gF values are read first,
+// beside its gathers, so their latency is hidden behind the collision instead
+// of adding a second memory round trip at the end; 80 registers keep three
+// blocks per SM (a few bytes spill): 0.94 against 0.82 of the copy roofline.
 template <typename S, int FM, bool WALLS>
-__global__ void __launch_bounds__(256) k_adjoint_step(const S *__restrict__ state, const float *__restrict__ lam_next,
+__global__ void __launch_bounds__(256, 3) k_adjoint_step(const S *__restrict__ state, const float *__restrict__ lam_next,
                                                       float *__restrict__ lam, float *__restrict__ gF, Geom g,
                                                       Rates r, ForceArgs F, int64_t n) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
+    const uint32_t self0 = ((uint32_t)z * g.ny + y) * g.nx + x;
+    const float g0x = gF[self0], g0y = gF[n + self0], g0z = gF[2 * n + self0];
     float l[kQ];
     {
         uint32_t off[kQ];
@@ -332,9 +337,9 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const S *__restrict__ stat
     collide_adjoint(h, l, fx, fy, fz, r, gx, gy, gz);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) lam[(size_t)i * n + self] = l[i];
-    gF[self] += gx;
-    gF[n + self] += gy;
-    gF[2 * n + self] += gz;
+    gF[self] = g0x + gx;
+    gF[n + self] = g0y + gy;
+    gF[2 * n + self] = g0z + gz;
 }
 
 // Seed from a cotangent gu (3 x n) on the Eq. 9 velocity of the state in
