@@ -12,8 +12,9 @@ Prints one JSON line (rank 0). Under torchrun (N > 1) the ranks hold the z-slabs
 of one 256 x 256 x (256 N) periodic Kolmogorov box, 256^3 nodes each (weak
 scaling), and exchange the 5 populations that cross each slab face after every
 step with NCCL point-to-point transfers that overlap the slab interior's update
-(--decomp replicas runs N independent boxes instead); the timed region is
-bracketed by barriers and the slowest rank's time is used.
+(--decomp replicas runs N independent boxes instead; --scaling strong splits
+one 512^3 box into N slabs); the timed region is bracketed by barriers and the
+slowest rank's time is used.
 
 --impl reference times the FP64 CPU oracle, as it stands, on the host cores on
 a bounded slab of the same workload.
@@ -81,6 +82,10 @@ def parse():
                     help="storage pattern of the timed lattice (the benchmark line is ab; aa for profiling)")
     ap.add_argument("--decomp", default="slab", choices=["slab", "replicas"],
                     help="N > 1: z-slabs of one lattice with face exchange (default) or independent boxes")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="N > 1: weak (256^3 per GPU, the default) or strong (one --strong-side^3 box split into N "
+                         "z-slabs)")
+    ap.add_argument("--strong-side", type=int, default=512, help="side of the box of --scaling strong")
     ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
                     help="N > 1: nccl (faces between GPUs) or gloo (faces through host memory; several ranks may "
                          "share one GPU, for testing the decomposition)")
@@ -508,17 +513,34 @@ def run_gb300(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     bx, by = (int(v) for v in args.block.split(","))
     side = args.size
-    shape = (side, side, side)
+    strong = args.scaling == "strong"
+    if strong and args.decomp != "slab":
+        raise SystemExit("--scaling strong splits one box into z-slabs (--decomp slab)")
+    gside = args.strong_side if strong else side
+    if strong and gside % side:
+        raise SystemExit("--strong-side must be a multiple of --size (the period of the initial field)")
     slab = ws > 1 and args.decomp == "slab"
     host_faces = slab and args.dist_backend == "gloo"
-    # a z-slab of the 256 x 256 x (256 N) box: the force profile and u0 repeat
-    # every 256 planes, so each slab takes the single box's
-    skw = dict(slab=3, z0=rank * side) if slab else {}
+    # The box of the run: weak scaling, 256 x 256 x (256 N) (one 256^3 slab per
+    # rank); strong scaling, one gside^3 box split into N z-slabs. The force
+    # profile and u0 repeat every `side` nodes along each axis, so every slab
+    # takes its planes of the single side^3 box's fields.
+    if strong:
+        nxy = gside
+        z0, z1 = slabs.partition(gside, ws)[rank]
+    else:
+        nxy = side
+        z0, z1 = (rank * side, (rank + 1) * side) if slab else (0, side)
+    nzl = z1 - z0
+    shape = (nzl, nxy, nxy)
+    skw = dict(slab=3, z0=z0) if slab else {}
     variant = 1 if slab and args.variant == 0 else args.variant
-    lat = Lattice(side, side, side, NU, walls=0, storage=args.storage, block=(bx, by), device=dev,
+    lat = Lattice(nxy, nxy, nzl, NU, walls=0, storage=args.storage, block=(bx, by), device=dev,
                   variant=variant, lattice=args.lattice, pattern=args.pattern, model=args.model, **skw)
-    prof = torch.from_numpy(synthetic.kolmogorov_profile(side, F0)).to(dev)
-    u0_np = synthetic.divfree_velocity(shape, seed=1, umax=UMAX)
+    zi, xi = np.arange(z0, z1) % side, np.arange(nxy) % side
+    prof = torch.from_numpy(np.ascontiguousarray(synthetic.kolmogorov_profile(side, F0)[:, zi])).to(dev)
+    u_base = synthetic.divfree_velocity((side, side, side), seed=1, umax=UMAX)
+    u0_np = np.ascontiguousarray(u_base[:, zi][:, :, xi][:, :, :, xi])
     u0 = torch.from_numpy(u0_np).to(dev)
     lat.set_force_profile_z(prof)
     lat.init_equilibrium(None, u0)
@@ -569,13 +591,14 @@ def run_gb300(args):
     clocks = sampler.stop(t_host0, t_host1) if sampler else None
 
     nodes = lat.n
-    value = ws * nodes * K / (elapsed_ms * 1e-3) / 1e6
+    job_nodes = gside ** 3 if strong else ws * nodes
+    value = job_nodes * K / (elapsed_ms * 1e-3) / 1e6
     mean_launch_s = statistics.mean(per_launch) * 1e-3
     peak, peak_kind = measured_peaks()
     bytes_per_node = (2 if args.storage != "f32" else 4) * 2 * args.lattice
     achieved = bytes_per_node * nodes / mean_launch_s / 1e9
     default_case = (args.storage, args.lattice, args.pattern, args.variant, args.model) == (
-        "f32", 19, "ab", 0, "cascaded") and not slab
+        "f32", 19, "ab", 0, "cascaded") and not slab and not strong
     traffic = profiled_traffic() if default_case and side == N_SIDE else None
 
     e2e = None
@@ -586,14 +609,14 @@ def run_gb300(args):
         u_o = torch.empty((3,) + shape, dtype=torch.float32).pin_memory()
         mom = torch.empty(4 * (K + 1), dtype=torch.float64).pin_memory()
         if not slab:
-            lat_e = Lattice(side, side, side, NU, walls=0, storage="f32", block=(bx, by), device=dev)
+            lat_e = Lattice(nxy, nxy, nzl, NU, walls=0, storage="f32", block=(bx, by), device=dev)
             lat_e.set_force_profile_z(prof)
             wk = max(1, min(args.warmup, 3))
             lat_e.run_host(rho_h, u_h, wk, rho_o, u_o, mom[: 4 * (wk + 1)])
             what = ("clbm_run_host: pinned host rho,u -> init -> K steps, each step's FP64 mass/momentum "
                     "sums (formed in the step kernel) copied back, final rho,u read back")
         else:
-            lat_e = Lattice(side, side, side, NU, walls=0, storage="f32", block=(bx, by), device=dev, variant=1,
+            lat_e = Lattice(nxy, nxy, nzl, NU, walls=0, storage="f32", block=(bx, by), device=dev, variant=1,
                             **skw)
             lat_e.set_force_profile_z(prof)
             what = ("z-slabs: pinned host rho,u -> init -> K steps with face exchange, each step's FP64 "
@@ -633,13 +656,13 @@ def run_gb300(args):
             dt = float(tt.item())
         h2d = (rho_h.numel() + u_h.numel()) * 4
         d2h = (rho_o.numel() + u_o.numel()) * 4 + mom.numel() * 8
-        e2e = {"value": ws * nodes * K / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / K,
+        e2e = {"value": job_nodes * K / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / K,
                "d2h_bytes_per_step": d2h / K, "steps": K, "what": what, "ms_total": dt * 1e3}
         del d_rho, d_u, d_mom
         lat_e.close()
 
     variants = None
-    if not args.no_variants and not slab:
+    if not args.no_variants and not slab and not strong:
         S = lambda storage, **kw: (lambda: bench_storage(storage, K, args.warmup, dev, side, prof, u0, peak,  # noqa
                                                           **kw))
         D = lambda storage: (lambda: bench_duct(storage, K, args.warmup, dev, peak))  # noqa
@@ -681,7 +704,16 @@ def run_gb300(args):
 
     if rank == 0:
         info = lat.info()
-        if slab:
+        if strong and ws == 1:
+            parallelism = f"the whole {gside}^3 box on one GPU"
+            workload = (workload_name(side, args).replace(f"periodic {side}^3", f"periodic {gside}^3")
+                        + f" (force and initial field of period {side})")
+        elif strong:
+            parallelism = (f"{ws} z-slabs of one {gside}^3 box, {gside}x{gside}x{nzl} on rank 0, face exchange "
+                           f"over {args.dist_backend} overlapped with the interior update")
+            workload = (workload_name(side, args).replace(f"periodic {side}^3", f"periodic {gside}^3")
+                        + f" (force and initial field of period {side})")
+        elif slab:
             parallelism = (f"{ws} z-slabs of one {side}x{side}x{side * ws} box, {side}^3 each, face exchange "
                            f"over {args.dist_backend} overlapped with the interior update")
             workload = workload_name(side, args).replace(f"periodic {side}^3", f"periodic {side}x{side}x{side * ws}")
@@ -690,11 +722,12 @@ def run_gb300(args):
             workload = workload_name(side, args)
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": args.warmup,
-            "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "strong" if strong else "weak",
+            "vs_baseline": None,
             "dtype": "f32" if args.storage == "f32" else f"f32 arithmetic, {args.storage} storage",
             "data": "synthetic",
             "config": {"workload": workload,
-                       "nx": side, "ny": side, "nz": side, "nu": NU, "F0": F0,
+                       "nx": nxy, "ny": nxy, "nz": gside if strong else nzl * (ws if slab else 1), "nu": NU, "F0": F0,
                        "storage": f"{args.storage} {args.pattern.upper()} "
                                   + ("staged in shared memory" if info["staged"] else "one node per thread"),
                        "block": [info["block_x"], info["block_y"]],

@@ -174,6 +174,38 @@ def test_kolmogorov_slabs_with_profile_force_and_split_steps():
             lat.close()
 
 
+def test_slab_checkpoint_round_trip_continues_bit_identically():
+    """A slab's saved state holds its halo planes: restoring it into fresh
+    contexts, after the exchange that followed the last step, continues the
+    decomposed run exactly as the uninterrupted one."""
+    nx, ny, nz = 24, 16, 12
+    shape = (nz, ny, nx)
+    u0, F = _inputs(shape, 31)
+    ranges = [(0, 5), (5, 12)]
+    lats, keep = _make_slabs(nx, ny, nz, 2, "f16sr", u0, F, ranges, True)
+    for _ in range(7):
+        for lat in lats:
+            lat.slab_step()
+        _exchange_all(lats)
+    saved = [lat.save_state() for lat in lats]
+    for _ in range(9):
+        for lat in lats:
+            lat.slab_step()
+        _exchange_all(lats)
+    ref = _gather(lats)
+    fresh, keep2 = _make_slabs(nx, ny, nz, 2, "f16sr", u0, F, ranges, True)
+    for lat, data in zip(fresh, saved):
+        lat.load_state(data)
+        assert lat.steps_done == 7
+    for _ in range(9):
+        for lat in fresh:
+            lat.slab_step()
+        _exchange_all(fresh)
+    assert torch.equal(_gather(fresh), ref)
+    for lat in lats + fresh:
+        lat.close()
+
+
 def test_slab_context_refuses_what_needs_no_exchange():
     lat = Lattice(16, 8, 6, 0.05, device=dev(), slab=3, z0=4)
     info = lat.info()
@@ -235,11 +267,13 @@ def test_two_rank_processes_match_the_undivided_lattice(tmp_path):
     assert torch.equal(got, _undivided(NX, NY, NZ, 2, "f32", u0, F, STEPS))
 
 
-def test_benchmark_slab_mode_runs_two_ranks_on_one_gpu():
+@pytest.mark.parametrize("scaling", ["weak", "strong"])
+def test_benchmark_slab_mode_runs_two_ranks_on_one_gpu(scaling):
     """bench.py --gpus 2 under torchrun, its z-slab mode: two ranks sharing the
     one GPU (gloo, faces through host memory; the NCCL exchange needs one GPU
-    per rank) print one contract line for the 256 x 256 x 512 box with two
-    launches per step."""
+    per rank) print one contract line with two launches per step, for the
+    256 x 256 x 512 box (weak scaling) or one 128^3 box split in two (strong
+    scaling, a small copy of the 512^3 mode)."""
     import json
     import subprocess
     import sys
@@ -247,12 +281,18 @@ def test_benchmark_slab_mode_runs_two_ranks_on_one_gpu():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--gpus", "2", "--steps", "4",
            "--warmup", "2", "--dist-backend", "gloo", "--no-variants", "--no-cpu-baseline"]
+    if scaling == "strong":
+        cmd += ["--scaling", "strong", "--size", "64", "--strong-side", "128"]
     r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1, r.stdout[-2000:]
     d = json.loads(lines[0])
-    assert d["n_gpus"] == 2 and d["steps"] == 4 and d["scaling"] == "weak" and d["value"] > 0
+    assert d["n_gpus"] == 2 and d["steps"] == 4 and d["scaling"] == scaling and d["value"] > 0
     assert d["gpu_launches"] == 8
-    assert "z-slabs" in d["config"]["parallelism"] and "256x256x512" in d["config"]["workload"]
+    assert "z-slab" in d["config"]["parallelism"]
+    if scaling == "weak":
+        assert "256x256x512" in d["config"]["workload"]
+    else:
+        assert "128^3" in d["config"]["workload"] and d["config"]["nz"] == 128
     assert d["e2e"]["value"] > 0
