@@ -316,7 +316,7 @@ def bench_duct(storage, K, warmup, dev, peak):
             "achieved_gbs": achieved, "frac": achieved / peak}
 
 
-def bench_slab_self(K, warmup, dev, side, prof, u0, peak):
+def bench_slab_self(K, warmup, dev, side, prof, u0, peak, storage="f32"):
     """One side^3 z-slab that is its own neighbour on both faces (a periodic z
     axis on one GPU), stepped as faces then interior with the face exchange
     (device copies) between: the per-GPU cost of the slab decomposition."""
@@ -324,7 +324,7 @@ def bench_slab_self(K, warmup, dev, side, prof, u0, peak):
 
     from paper_1801_04586_gb300 import Lattice, slabs
     from paper_1801_04586_gb300._capi import SLAB_FACES, SLAB_INTERIOR
-    lat = Lattice(side, side, side, NU, device=dev, slab=3, z0=0)
+    lat = Lattice(side, side, side, NU, storage=storage, device=dev, slab=3, z0=0)
     lat.set_force_profile_z(prof)
     lat.init_equilibrium(None, u0)
 
@@ -347,9 +347,10 @@ def bench_slab_self(K, warmup, dev, side, prof, u0, peak):
     ms = e0.elapsed_time(e1)
     n = lat.n
     lat.close()
-    achieved = BYTES_PER_NODE * n / (ms / K * 1e-3) / 1e9
+    bpn = (4 if storage == "f32" else 2) * 2 * 19
+    achieved = bpn * n / (ms / K * 1e-3) / 1e9
     return {"value": n * K / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / K,
-            "bytes_per_node": BYTES_PER_NODE, "achieved_gbs": achieved, "frac": achieved / peak}
+            "bytes_per_node": bpn, "achieved_gbs": achieved, "frac": achieved / peak}
 
 
 def compact(variants):
@@ -687,6 +688,7 @@ def run_gb300(args):
             "q27_aa_f32": S("f32", lattice=27, pattern="aa"),
             "q27_f16": S("f16", lattice=27),
             "slab_self_f32": lambda: bench_slab_self(K, args.warmup, dev, side, prof, u0, peak),
+            "slab_self_f16sr": lambda: bench_slab_self(K, args.warmup, dev, side, prof, u0, peak, "f16sr"),
             "adjoint_kernel_256": lambda: bench_adjoint(dev, side, max(10, min(K, 100)), peak),
             "adjoint_unroll_64": lambda: bench_unroll(dev),
             "batched_64_domains": lambda: bench_batch(dev, args.batch_steps, peak),

@@ -136,7 +136,8 @@ extern "C" {
  *      the slab's first plane: it only feeds the dither of stochastic
  *      rounding, so that the slabs store exactly what one undivided lattice
  *      would. slab = 0 (the default) is an ordinary lattice. Slabs: D3Q19,
- *      cascaded model, A/B pattern, one node per thread (variant 0 or 1).
+ *      cascaded model, A/B pattern, variant 0 (16-bit storage staged where it
+ *      applies) or 1.
  * wait_cycles: bound, in SM clock cycles, of each wait of the staged step
  *      (variant 0, 16-bit storage) for the bulk copies of its next tile; 0
  *      selects 4e9 (about 2 s). A wait that runs out makes the kernel give up

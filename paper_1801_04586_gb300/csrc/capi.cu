@@ -347,7 +347,7 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     c->gamma = 0.0;
     c->q = q;
     c->packed = q == 19 && p->variant == 2;
-    c->staged = p->variant == 0 && p->pattern != CLBM_PATTERN_AA && !p->slab;
+    c->staged = p->variant == 0 && p->pattern != CLBM_PATTERN_AA;
     c->aa = p->pattern == CLBM_PATTERN_AA;
     c->model = p->model;
     c->rates27.om2 = c->rates.om2;

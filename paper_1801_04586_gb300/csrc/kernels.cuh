@@ -32,6 +32,7 @@ struct Launch {
                        // map of a z-slab with halo faces)
     long long wait_cycles = 0;  // staged step: bound of a wait for a tile's copies (0: kWaitCycles)
     bool drop_first_tile = false;  // staged step, failure injection: tile 0's copies are not issued
+    int z0 = 0, zs = 1, nplanes = -1;  // staged step: the planes z0, z0 + zs, ... (nplanes of them; -1: all)
 };
 
 // storage: 0 = f32, 1 = f16, 2 = bf16, 3 = f16 stochastic, 4 = bf16 stochastic

@@ -235,12 +235,30 @@ static cudaError_t step_slab_walls_t(const Launch &L, const void *src, void *dst
 }
 
 // One z-slab step (or a part of it: the planes z0, z0 + zs, ..., nplanes of
-// them) with collision C, any storage format.
+// them) with collision C, any storage format. 16-bit storage takes the staged
+// step where it applies (its copies read the halo planes across halo faces
+// and it writes the send planes), one node per thread otherwise.
 template <typename C>
 cudaError_t launch_step_slab_with(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
                                   const ForceArgs &F, int *flag, uint32_t key, int z0, int zs, int nplanes) {
     auto by_force = [&](auto tag) -> cudaError_t {
         using S = decltype(tag);
+        if constexpr (sizeof(S) == 2) {  // 16-bit storage: the staged step, its z-face rows from the halo planes
+            if (L.staged && nplanes > 0) {
+                Launch Ls = L;
+                Ls.z0 = z0;
+                Ls.zs = zs;
+                Ls.nplanes = nplanes;
+                cudaError_t e = cudaSuccess;
+                bool done = false;
+                switch (F.mode) {
+                    case kForceUniform: done = launch_step_tma<19, C, S, kForceUniform>(Ls, src, dst, r, F, flag, key, e); break;
+                    case kForceProfileZ: done = launch_step_tma<19, C, S, kForceProfileZ>(Ls, src, dst, r, F, flag, key, e); break;
+                    default: done = launch_step_tma<19, C, S, kForceField>(Ls, src, dst, r, F, flag, key, e); break;
+                }
+                if (done) return e;
+            }
+        }
         switch (F.mode) {
             case kForceUniform: return step_slab_walls_t<C, S, kForceUniform>(L, src, dst, r, F, flag, key, z0, zs, nplanes);
             case kForceProfileZ: return step_slab_walls_t<C, S, kForceProfileZ>(L, src, dst, r, F, flag, key, z0, zs, nplanes);

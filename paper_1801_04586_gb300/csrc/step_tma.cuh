@@ -74,7 +74,8 @@ constexpr long long kWaitCycles = 4000000000ll;  // default bound of one barrier
 struct TilePlan {
     int rows;       // x-rows per tile
     int tiles_y;    // tiles per z-plane
-    int ntiles;     // tiles_y * nz
+    int ntiles;     // tiles_y * the number of planes stepped
+    int z0, zs;     // the planes stepped: z0, z0 + zs, ... (all planes: 0, 1)
     int dz, dy;     // a block's step of gridDim.x tiles as (planes, tiles) : gridDim.x = dz tiles_y + dy
     uint32_t rdiv;  // ceil(2^32 / nx): the row of tile node n is umulhi(n, rdiv), exact for n, nx <= 1024
     long long wait; // bound of a thread's wait for a tile's copies, in SM clock cycles
@@ -113,7 +114,8 @@ constexpr bool tile_fits() {
 // (0: eligibility only) and tile pitch tn. The copies need 16-byte aligned
 // rows (nx x elem and stride x elem multiples of 16, src 16-byte aligned) and
 // a row must fit a tile.
-inline bool tile_plan(const Geom &g, size_t elem, const void *src, int grid, int tn, TilePlan &p) {
+inline bool tile_plan(const Geom &g, size_t elem, const void *src, int grid, int tn, TilePlan &p, int z0 = 0,
+                      int zs = 1, int nplanes = -1) {
     if (elem != 2) return false;  // FP32 steps stay on k_step, which already runs at the DRAM bound
     if (g.nx > tn || ((size_t)g.nx * elem) % 16 != 0 || ((size_t)g.stride * elem) % 16 != 0 ||
         ((uintptr_t)src & 15u) != 0)
@@ -122,7 +124,9 @@ inline bool tile_plan(const Geom &g, size_t elem, const void *src, int grid, int
     if (n >= (int64_t(1) << 31)) return false;
     p.rows = g.ny < tn / g.nx ? g.ny : tn / g.nx;
     p.tiles_y = (g.ny + p.rows - 1) / p.rows;
-    p.ntiles = p.tiles_y * g.nz;
+    p.ntiles = p.tiles_y * (nplanes < 0 ? g.nz : nplanes);
+    p.z0 = z0;
+    p.zs = zs;
     p.dz = grid / p.tiles_y;
     p.dy = grid - p.dz * p.tiles_y;
     p.rdiv = 0xffffffffu / (uint32_t)g.nx + 1u;
@@ -206,10 +210,12 @@ __host__ __device__ constexpr uint64_t pack_shift(int axis) {
 template <typename S, int FM, bool WALLS, int Q, typename SH>
 __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, const Geom &g, const TilePlan &p,
                                            int t, unsigned char *stage, uint64_t *bar, int lane, bool drop = false) {
-    const int z = t / p.tiles_y;
-    const int y0 = (t - z * p.tiles_y) * p.rows;
+    const int zi = t / p.tiles_y;
+    const int z = p.z0 + zi * p.zs;
+    const int y0 = (t - zi * p.tiles_y) * p.rows;
     const int rows = min(p.rows, g.ny - y0);
     int src_a = 0, slot_a = 0, n_a = 0, src_b = 0, slot_b = 0, n_b = 0, zs = 0;
+    int halo = -1;  // z-slab: the halo plane the rows come from (across a halo face), else -1
     if (lane < Q) {
         constexpr uint64_t kEy = pack_shift<Q>(1), kEz = pack_shift<Q>(2);
         const int ey = (int)((kEy >> (2 * lane)) & 3u) - 1, ez = (int)((kEz >> (2 * lane)) & 3u) - 1;
@@ -217,7 +223,9 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
         zs = z - ez;
         bool plane = true;
         if (zs < 0 || zs >= g.nz) {
-            if (wz) plane = false;              // beyond a z wall: bounce-back, read from global
+            if (zs < 0 && (g.slab & 1u)) halo = zface_index(lane);          // the lower neighbour's face
+            else if (zs >= g.nz && (g.slab & 2u)) halo = 5 + zface_index(lane);  // the upper neighbour's face
+            else if (wz) plane = false;         // beyond a z wall: bounce-back, read from global
             else zs = zs < 0 ? zs + g.nz : zs - g.nz;
         }
         if (plane) {
@@ -247,7 +255,8 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
     __syncwarp();
     if (drop) return;
     if (lane < Q) {
-        const size_t pop = (size_t)lane * g.stride + (size_t)zs * g.ny * g.nx;
+        const size_t pop = halo >= 0 ? (size_t)kQ * g.stride + (size_t)halo * g.ny * g.nx
+                                     : (size_t)lane * g.stride + (size_t)zs * g.ny * g.nx;
         S *dst = reinterpret_cast<S *>(stage) + lane * SH::pitch;
         if (n_a > 0) {
             size_t from = pop + (size_t)src_a * g.nx, to = (size_t)slot_a * g.nx;
@@ -299,7 +308,7 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
             const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
             xl = wx && x == 0; xh = wx && x == nx - 1u;
             yl = wy && y == 0; yh = wy && y == g.ny - 1;
-            zl = wz && z == 0; zh = wz && z == g.nz - 1;
+            zl = wz && z == 0 && !(g.slab & 1u); zh = wz && z == g.nz - 1 && !(g.slab & 2u);
             // nodes next to a wall are few: the warps without one skip the bounce-back reads
             any = __any_sync(__activemask(), xl || xh || yl || yh || zl || zh);
         }
@@ -418,7 +427,7 @@ __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S 
             const int y = y0 + (int)rr;
             const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
             const bool yl = wy && y == 0, yh = wy && y == g.ny - 1;
-            const bool zl = wz && z == 0, zh = wz && z == g.nz - 1;
+            const bool zl = wz && z == 0 && !(g.slab & 1u), zh = wz && z == g.nz - 1 && !(g.slab & 2u);
             const bool xl0 = wx && x == 0, xh1 = wx && x + 2u == nx;  // x wall of node n / node n + 1
             const bool any = __any_sync(__activemask(), xl0 || xh1 || yl || yh || zl || zh);
             if (any) {
@@ -458,14 +467,23 @@ __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S 
         const f2 drho = C::template run<true>(h, fx, fy, fz, r);
         if (!(fabsf(drho.v.x) < 0.9f) || !(fabsf(drho.v.y) < 0.9f)) atomicOr(flag, 1);
         uint32_t *out = reinterpret_cast<uint32_t *>(dst + CLBM_SLOTS(g, self, (kQ - 1) * g.stride + 1u));
-        if constexpr (Codec<S>::kStochastic) {
-            const uint32_t hb = pair_hash(self >> 1, key);
+        // a z-slab's first / last plane also sends its outgoing face (send planes, see kSlabPlanes)
+        const uint32_t plane = nx * (uint32_t)g.ny, ps = self - (uint32_t)z * plane;
+        const bool send_lo = (g.slab & 1u) && z == 0, send_hi = (g.slab & 2u) && z == g.nz - 1;
+        const size_t send = (size_t)kQ * g.stride + ps;  // element offset of the node in send plane 0 (even)
+        const uint32_t hb = Codec<S>::kStochastic ? pair_hash((self + g.node0) >> 1, key) : 0u;
 #pragma unroll
-            for (int i = 0; i < kQ; ++i)
-                out[(size_t)i * (g.stride >> 1)] = Codec<S>::pair_sr(h[i].v.y, h[i].v.x, pop_bits(hb, i));
-        } else {
-#pragma unroll
-            for (int i = 0; i < kQ; ++i) out[(size_t)i * (g.stride >> 1)] = Codec<S>::pair_rn(h[i].v.y, h[i].v.x);
+        for (int i = 0; i < kQ; ++i) {
+            uint32_t w;
+            if constexpr (Codec<S>::kStochastic)
+                w = Codec<S>::pair_sr(h[i].v.y, h[i].v.x, pop_bits(hb, i));
+            else
+                w = Codec<S>::pair_rn(h[i].v.y, h[i].v.x);
+            out[(size_t)i * (g.stride >> 1)] = w;
+            if (ez19(i) < 0 && send_lo)
+                *reinterpret_cast<uint32_t *>(dst + CLBM_IDX(g, send + (size_t)(10 + zface_index(i)) * plane)) = w;
+            if (ez19(i) > 0 && send_hi)
+                *reinterpret_cast<uint32_t *>(dst + CLBM_IDX(g, send + (size_t)(15 + zface_index(i)) * plane)) = w;
         }
     }
 }
@@ -527,21 +545,24 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
         // Only tiles with a node next to a wall take the wall code; the others run the periodic loop, which
         // the wall handling would otherwise slow on every tile (12-21 % for the node-pair loop).
         const int y0 = yt * p.rows;
-        const bool wall_tile = WALLS && ((g.walls & 1u) || ((g.walls & 4u) && (z == 0 || z == g.nz - 1)) ||
-                                         ((g.walls & 2u) && (y0 == 0 || y0 + p.rows >= g.ny)));
+        const int zp = p.z0 + z * p.zs;  // the tile's plane (z counts the planes stepped)
+        const bool wall_tile =
+            WALLS && ((g.walls & 1u) ||
+                      ((g.walls & 4u) && ((zp == 0 && !(g.slab & 1u)) || (zp == g.nz - 1 && !(g.slab & 2u)))) ||
+                      ((g.walls & 2u) && (y0 == 0 || y0 + p.rows >= g.ny)));
         if constexpr (SH::pairs) {
             if (wall_tile)
-                compute_tile_pairs<C, S, FM, true, SH>(src, dst, g, r, F, flag, key, p, z, y0, buf + s * SB, tfx,
+                compute_tile_pairs<C, S, FM, true, SH>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB, tfx,
                                                        tfy, tfz);
             else
-                compute_tile_pairs<C, S, FM, false, SH>(src, dst, g, r, F, flag, key, p, z, y0, buf + s * SB, tfx,
+                compute_tile_pairs<C, S, FM, false, SH>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB, tfx,
                                                         tfy, tfz);
         } else {
             if (wall_tile)
-                compute_tile<C, S, FM, true, Q, SH>(src, dst, g, r, F, flag, key, p, z, y0, buf + s * SB, tfx, tfy,
+                compute_tile<C, S, FM, true, Q, SH>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB, tfx, tfy,
                                                     tfz);
             else
-                compute_tile<C, S, FM, false, Q, SH>(src, dst, g, r, F, flag, key, p, z, y0, buf + s * SB, tfx, tfy,
+                compute_tile<C, S, FM, false, Q, SH>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB, tfx, tfy,
                                                      tfz);
         }
         __syncwarp();
@@ -584,14 +605,14 @@ bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R 
         return false;
     } else {
         TilePlan p;
-        if (!tile_plan(L.g, sizeof(S), src, 0, SH::pitch, p)) return false;
+        if (!tile_plan(L.g, sizeof(S), src, 0, SH::pitch, p, L.z0, L.zs, L.nplanes)) return false;
         if (FM == kForceField && ((((uintptr_t)F.field) & 15u) != 0 || (F.n & 3) != 0)) return false;
         int dev = 0, sms = 0;
         if ((err = cudaGetDevice(&dev)) != cudaSuccess) return true;
         if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return true;
         constexpr size_t smem = tile_smem_bytes<S, FM, Q, SH>();
         const int grid = p.ntiles < SH::blocks * sms ? p.ntiles : SH::blocks * sms;
-        tile_plan(L.g, sizeof(S), src, grid, SH::pitch, p);
+        tile_plan(L.g, sizeof(S), src, grid, SH::pitch, p, L.z0, L.zs, L.nplanes);
         if (L.wait_cycles > 0) p.wait = L.wait_cycles;
         if (L.drop_first_tile) p.drop_tile = 0;
         auto kern = k_step_tma<C, S, FM, WALLS, Q, SH, R>;

@@ -79,14 +79,14 @@ def in_place(shape_xyz, walls, storage, lattice=19):
     return {}
 
 
-def slabs_case():
+def slabs_case(storage="f32"):
     nx, ny, nz = 24, 10, 9
     shape = (nz, ny, nx)
     u0 = synthetic.divfree_velocity(shape, seed=5, umax=0.03)
     ranges = [(0, 1), (1, 5), (5, 9)]
     lats = []
     for z0, z1 in ranges:
-        lat = Lattice(nx, ny, z1 - z0, 0.04, walls=2, device=dev(), slab=3, z0=z0, **RATES)
+        lat = Lattice(nx, ny, z1 - z0, 0.04, walls=2, storage=storage, device=dev(), slab=3, z0=z0, **RATES)
         lat.init_equilibrium(None, t(np.ascontiguousarray(u0[:, z0:z1])))
         lats.append(lat)
     for _ in range(6):
@@ -119,6 +119,7 @@ CASES = [("degenerate", degenerate, c) for c in DEGENERATE] + [
     ("in_place", in_place, ((16, 9, 4), 0, "f16sr")),
     ("in_place", in_place, ((9, 6, 5), 3, "f32", 27)),
     ("slabs", slabs_case, ()),
+    ("slabs", slabs_case, ("f16sr",)),
 ]
 
 

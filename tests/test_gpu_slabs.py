@@ -86,6 +86,8 @@ CASES = [
     (32, 16, 16, 4, "f16sr", [(0, 8), (8, 16)], False),
     (32, 16, 16, 0, "bf16sr", [(0, 3), (3, 11), (11, 16)], True),
     (40, 12, 10, 0, "f32", [(0, 10)], True),
+    (32, 16, 10, 2, "f16", [(0, 4), (4, 5), (5, 10)], True),   # staged 16-bit, a one-plane slab
+    (40, 12, 9, 5, "f16sr", [(0, 3), (3, 9)], False),          # staged, x walls and z walls at the ends
 ]
 
 
@@ -99,6 +101,8 @@ def test_slabs_reproduce_the_undivided_lattice(case):
     steps = 40
     ref = _undivided(nx, ny, nz, walls, storage, u0, F, steps)
     lats, keep = _make_slabs(nx, ny, nz, walls, storage, u0, F, ranges, periodic)
+    if storage != "f32":  # 16-bit slabs run the staged step, reading the halo planes in its copies
+        assert all(lat.info()["staged"] == 1 for lat in lats)
     assert torch.equal(_gather(lats), _undivided(nx, ny, nz, walls, storage, u0, F, 0))
     for _ in range(steps):
         for lat in lats:
