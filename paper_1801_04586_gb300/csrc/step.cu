@@ -1,18 +1,10 @@
 // step.cu -- the cascaded collision's step kernels (Eqs. 5, 7, 9 with A3, A5,
 // A6; collision in d3q19.cuh, kernels in step_kernels.cuh), plus the form
 // with two nodes per thread on the FP32x2 instructions.
+#include "cascaded.cuh"
 #include "step_kernels.cuh"
 
 namespace clbm {
-
-// The paper's cascaded collision with the consistent forcing scheme.
-struct Cascaded {
-    static constexpr bool kPairs = true;  // also runs on f2 (two nodes at once): the staged step pairs nodes
-    template <bool FR = false, typename T>
-    static __device__ __forceinline__ T run(T (&h)[kQ], T Fx, T Fy, T Fz, const Rates &r) {
-        return collide<FR>(h, Fx, Fy, Fz, r);
-    }
-};
 
 // Two nodes per thread: x and x + blockDim.x of a 2 * blockDim.x segment of a
 // row, collided together with the FP32x2 instructions (f2 in d3q19.cuh), which
@@ -83,11 +75,6 @@ cudaError_t launch_step(int storage, const Launch &L, const void *src, void *dst
         case 3: return step2_force<HalfSR>(L, src, dst, r, F, flag, key);
         default: return step2_force<BF16SR>(L, src, dst, r, F, flag, key);
     }
-}
-
-cudaError_t launch_step_slab(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
-                             const ForceArgs &F, int *flag, uint32_t key, int z0, int zs, int nplanes) {
-    return launch_step_slab_with<Cascaded>(storage, L, src, dst, r, F, flag, key, z0, zs, nplanes);
 }
 
 bool step_staged(const Geom &g, size_t elem, const void *src, int q, int force_mode) {

@@ -252,9 +252,15 @@ cudaError_t launch_step_slab_with(int storage, const Launch &L, const void *src,
                 cudaError_t e = cudaSuccess;
                 bool done = false;
                 switch (F.mode) {
-                    case kForceUniform: done = launch_step_tma<19, C, S, kForceUniform>(Ls, src, dst, r, F, flag, key, e); break;
-                    case kForceProfileZ: done = launch_step_tma<19, C, S, kForceProfileZ>(Ls, src, dst, r, F, flag, key, e); break;
-                    default: done = launch_step_tma<19, C, S, kForceField>(Ls, src, dst, r, F, flag, key, e); break;
+                    case kForceUniform:
+                        done = launch_step_tma<19, C, S, kForceUniform, true>(Ls, src, dst, r, F, flag, key, e);
+                        break;
+                    case kForceProfileZ:
+                        done = launch_step_tma<19, C, S, kForceProfileZ, true>(Ls, src, dst, r, F, flag, key, e);
+                        break;
+                    default:
+                        done = launch_step_tma<19, C, S, kForceField, true>(Ls, src, dst, r, F, flag, key, e);
+                        break;
                 }
                 if (done) return e;
             }

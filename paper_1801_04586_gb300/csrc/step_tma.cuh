@@ -207,11 +207,13 @@ __host__ __device__ constexpr uint64_t pack_shift(int axis) {
 // force components.
 // With drop (failure injection, from the host) the barrier is armed with the
 // tile's byte count but no copy is issued, so no wait on it can complete.
-template <typename S, int FM, bool WALLS, int Q, typename SH>
+// SLAB: the tiles cover the planes z0, z0 + zs, ... of a z-slab, and rows
+// across a halo face come from that face's receive plane.
+template <typename S, int FM, bool WALLS, int Q, typename SH, bool SLAB>
 __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, const Geom &g, const TilePlan &p,
                                            int t, unsigned char *stage, uint64_t *bar, int lane, bool drop = false) {
     const int zi = t / p.tiles_y;
-    const int z = p.z0 + zi * p.zs;
+    const int z = SLAB ? p.z0 + zi * p.zs : zi;
     const int y0 = (t - zi * p.tiles_y) * p.rows;
     const int rows = min(p.rows, g.ny - y0);
     int src_a = 0, slot_a = 0, n_a = 0, src_b = 0, slot_b = 0, n_b = 0, zs = 0;
@@ -223,8 +225,8 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
         zs = z - ez;
         bool plane = true;
         if (zs < 0 || zs >= g.nz) {
-            if (zs < 0 && (g.slab & 1u)) halo = zface_index(lane);          // the lower neighbour's face
-            else if (zs >= g.nz && (g.slab & 2u)) halo = 5 + zface_index(lane);  // the upper neighbour's face
+            if (SLAB && zs < 0 && (g.slab & 1u)) halo = zface_index(lane);          // the lower neighbour's face
+            else if (SLAB && zs >= g.nz && (g.slab & 2u)) halo = 5 + zface_index(lane);  // the upper one's
             else if (wz) plane = false;         // beyond a z wall: bounce-back, read from global
             else zs = zs < 0 ? zs + g.nz : zs - g.nz;
         }
@@ -255,8 +257,8 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
     __syncwarp();
     if (drop) return;
     if (lane < Q) {
-        const size_t pop = halo >= 0 ? (size_t)kQ * g.stride + (size_t)halo * g.ny * g.nx
-                                     : (size_t)lane * g.stride + (size_t)zs * g.ny * g.nx;
+        const size_t pop = SLAB && halo >= 0 ? (size_t)kQ * g.stride + (size_t)halo * g.ny * g.nx
+                                             : (size_t)lane * g.stride + (size_t)zs * g.ny * g.nx;
         S *dst = reinterpret_cast<S *>(stage) + lane * SH::pitch;
         if (n_a > 0) {
             size_t from = pop + (size_t)src_a * g.nx, to = (size_t)slot_a * g.nx;
@@ -308,7 +310,7 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
             const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
             xl = wx && x == 0; xh = wx && x == nx - 1u;
             yl = wy && y == 0; yh = wy && y == g.ny - 1;
-            zl = wz && z == 0 && !(g.slab & 1u); zh = wz && z == g.nz - 1 && !(g.slab & 2u);
+            zl = wz && z == 0; zh = wz && z == g.nz - 1;
             // nodes next to a wall are few: the warps without one skip the bounce-back reads
             any = __any_sync(__activemask(), xl || xh || yl || yh || zl || zh);
         }
@@ -387,7 +389,10 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
 // (the even node in the lower half) and stored with one 32-bit store. The
 // collision of f2 rounds like the scalar 16-bit collision (f1), and the pair
 // conversions like the single ones, so the stored bits equal compute_tile's.
-template <typename C, typename S, int FM, bool WALLS, typename SH, typename R>
+// SLAB: z walls only at faces that are not halo faces, the first / last plane
+// also store their outgoing pair words into the send planes, and the dither
+// hashes global pair indices.
+template <typename C, typename S, int FM, bool WALLS, typename SH, bool SLAB, typename R>
 __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S *__restrict__ dst, const Geom &g,
                                                    const R &r, const ForceArgs &F, int *flag, uint32_t key,
                                                    const TilePlan &p, int z, int y0, const unsigned char *buf,
@@ -427,7 +432,8 @@ __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S 
             const int y = y0 + (int)rr;
             const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
             const bool yl = wy && y == 0, yh = wy && y == g.ny - 1;
-            const bool zl = wz && z == 0 && !(g.slab & 1u), zh = wz && z == g.nz - 1 && !(g.slab & 2u);
+            const bool zl = wz && z == 0 && !(SLAB && (g.slab & 1u));
+            const bool zh = wz && z == g.nz - 1 && !(SLAB && (g.slab & 2u));
             const bool xl0 = wx && x == 0, xh1 = wx && x + 2u == nx;  // x wall of node n / node n + 1
             const bool any = __any_sync(__activemask(), xl0 || xh1 || yl || yh || zl || zh);
             if (any) {
@@ -467,31 +473,44 @@ __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S 
         const f2 drho = C::template run<true>(h, fx, fy, fz, r);
         if (!(fabsf(drho.v.x) < 0.9f) || !(fabsf(drho.v.y) < 0.9f)) atomicOr(flag, 1);
         uint32_t *out = reinterpret_cast<uint32_t *>(dst + CLBM_SLOTS(g, self, (kQ - 1) * g.stride + 1u));
-        // a z-slab's first / last plane also sends its outgoing face (send planes, see kSlabPlanes)
-        const uint32_t plane = nx * (uint32_t)g.ny, ps = self - (uint32_t)z * plane;
-        const bool send_lo = (g.slab & 1u) && z == 0, send_hi = (g.slab & 2u) && z == g.nz - 1;
-        const size_t send = (size_t)kQ * g.stride + ps;  // element offset of the node in send plane 0 (even)
-        const uint32_t hb = Codec<S>::kStochastic ? pair_hash((self + g.node0) >> 1, key) : 0u;
+        if constexpr (!SLAB) {
+            if constexpr (Codec<S>::kStochastic) {
+                const uint32_t hb = pair_hash(self >> 1, key);
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) {
-            uint32_t w;
-            if constexpr (Codec<S>::kStochastic)
-                w = Codec<S>::pair_sr(h[i].v.y, h[i].v.x, pop_bits(hb, i));
-            else
-                w = Codec<S>::pair_rn(h[i].v.y, h[i].v.x);
-            out[(size_t)i * (g.stride >> 1)] = w;
-            if (ez19(i) < 0 && send_lo)
-                *reinterpret_cast<uint32_t *>(dst + CLBM_IDX(g, send + (size_t)(10 + zface_index(i)) * plane)) = w;
-            if (ez19(i) > 0 && send_hi)
-                *reinterpret_cast<uint32_t *>(dst + CLBM_IDX(g, send + (size_t)(15 + zface_index(i)) * plane)) = w;
+                for (int i = 0; i < kQ; ++i)
+                    out[(size_t)i * (g.stride >> 1)] = Codec<S>::pair_sr(h[i].v.y, h[i].v.x, pop_bits(hb, i));
+            } else {
+#pragma unroll
+                for (int i = 0; i < kQ; ++i) out[(size_t)i * (g.stride >> 1)] = Codec<S>::pair_rn(h[i].v.y, h[i].v.x);
+            }
+        } else {
+            // the first / last plane also sends its outgoing face (send planes, see kSlabPlanes)
+            const uint32_t plane = nx * (uint32_t)g.ny, ps = self - (uint32_t)z * plane;
+            const bool send_lo = (g.slab & 1u) && z == 0, send_hi = (g.slab & 2u) && z == g.nz - 1;
+            const size_t send = (size_t)kQ * g.stride + ps;  // element offset of the node in send plane 0 (even)
+            const uint32_t hb = Codec<S>::kStochastic ? pair_hash((self + g.node0) >> 1, key) : 0u;
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                uint32_t w;
+                if constexpr (Codec<S>::kStochastic)
+                    w = Codec<S>::pair_sr(h[i].v.y, h[i].v.x, pop_bits(hb, i));
+                else
+                    w = Codec<S>::pair_rn(h[i].v.y, h[i].v.x);
+                out[(size_t)i * (g.stride >> 1)] = w;
+                if (ez19(i) < 0 && send_lo)
+                    *reinterpret_cast<uint32_t *>(dst + CLBM_IDX(g, send + (size_t)(10 + zface_index(i)) * plane)) = w;
+                if (ez19(i) > 0 && send_hi)
+                    *reinterpret_cast<uint32_t *>(dst + CLBM_IDX(g, send + (size_t)(15 + zface_index(i)) * plane)) = w;
+            }
         }
     }
 }
 
-template <typename C, typename S, int FM, bool WALLS, int Q, typename SH, typename R>
+template <typename C, typename S, int FM, bool WALLS, int Q, typename SH, bool SLAB, typename R>
 __global__ void __launch_bounds__(SH::threads, SH::blocks)
     k_step_tma(const S *__restrict__ src, S *__restrict__ dst, Geom g, R r, ForceArgs F, int *__restrict__ flag,
                uint32_t key, TilePlan p) {
+    static_assert(!SLAB || SH::pairs, "z-slabs take the node-pair tile");
     constexpr int kTmaStages = SH::stages;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);     // [stages]: copies of the buffer's tile arrived
@@ -517,7 +536,7 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
             const int t = blockIdx.x + k * gridDim.x;
             if (t < p.ntiles) {
                 const bool drop = t == p.drop_tile;
-                issue_tile<S, FM, WALLS, Q, SH>(src, F, g, p, t, buf + k * SB, &bar[k], lane, drop);
+                issue_tile<S, FM, WALLS, Q, SH, SLAB>(src, F, g, p, t, buf + k * SB, &bar[k], lane, drop);
                 if (lane == 0 && !drop) issued[k] = 1;  // the drain waits only for copies actually issued
             }
         }
@@ -545,18 +564,17 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
         // Only tiles with a node next to a wall take the wall code; the others run the periodic loop, which
         // the wall handling would otherwise slow on every tile (12-21 % for the node-pair loop).
         const int y0 = yt * p.rows;
-        const int zp = p.z0 + z * p.zs;  // the tile's plane (z counts the planes stepped)
-        const bool wall_tile =
-            WALLS && ((g.walls & 1u) ||
-                      ((g.walls & 4u) && ((zp == 0 && !(g.slab & 1u)) || (zp == g.nz - 1 && !(g.slab & 2u)))) ||
-                      ((g.walls & 2u) && (y0 == 0 || y0 + p.rows >= g.ny)));
+        const int zp = SLAB ? p.z0 + z * p.zs : z;  // the tile's plane (z counts the planes stepped)
+        const bool zlo = zp == 0 && !(SLAB && (g.slab & 1u)), zhi = zp == g.nz - 1 && !(SLAB && (g.slab & 2u));
+        const bool wall_tile = WALLS && ((g.walls & 1u) || ((g.walls & 4u) && (zlo || zhi)) ||
+                                         ((g.walls & 2u) && (y0 == 0 || y0 + p.rows >= g.ny)));
         if constexpr (SH::pairs) {
             if (wall_tile)
-                compute_tile_pairs<C, S, FM, true, SH>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB, tfx,
-                                                       tfy, tfz);
+                compute_tile_pairs<C, S, FM, true, SH, SLAB>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB,
+                                                             tfx, tfy, tfz);
             else
-                compute_tile_pairs<C, S, FM, false, SH>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB, tfx,
-                                                        tfy, tfz);
+                compute_tile_pairs<C, S, FM, false, SH, SLAB>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB,
+                                                              tfx, tfy, tfz);
         } else {
             if (wall_tile)
                 compute_tile<C, S, FM, true, Q, SH>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB, tfx, tfy,
@@ -576,7 +594,7 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
             const int tn = t + kTmaStages * gridDim.x;
             if (tn < p.ntiles) {
                 fence_proxy_async();  // the buffer's reads by every warp precede the copies into it
-                issue_tile<S, FM, WALLS, Q, SH>(src, F, g, p, tn, buf + s * SB, &bar[s], lane);
+                issue_tile<S, FM, WALLS, Q, SH, SLAB>(src, F, g, p, tn, buf + s * SB, &bar[s], lane);
                 if (lane == 0) ++issued[s];
             }
         }
@@ -597,25 +615,28 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
 }
 
 // Launch the staged step in shape SH if it applies to this geometry, buffer
-// and force; returns false (nothing launched) otherwise.
-template <typename SH, bool WALLS, int Q, typename C, typename S, int FM, typename R>
+// and force; returns false (nothing launched) otherwise. SLAB: the planes
+// L.z0, L.z0 + L.zs, ... (L.nplanes of them) of a z-slab.
+template <typename SH, bool WALLS, int Q, typename C, typename S, int FM, bool SLAB, typename R>
 bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R &r, const ForceArgs &F, int *flag,
                            uint32_t key, cudaError_t &err) {
     if constexpr (!tile_fits<S, FM, Q, SH>()) {
         return false;
     } else {
         TilePlan p;
-        if (!tile_plan(L.g, sizeof(S), src, 0, SH::pitch, p, L.z0, L.zs, L.nplanes)) return false;
+        if (!tile_plan(L.g, sizeof(S), src, 0, SH::pitch, p, SLAB ? L.z0 : 0, SLAB ? L.zs : 1,
+                       SLAB ? L.nplanes : -1))
+            return false;
         if (FM == kForceField && ((((uintptr_t)F.field) & 15u) != 0 || (F.n & 3) != 0)) return false;
         int dev = 0, sms = 0;
         if ((err = cudaGetDevice(&dev)) != cudaSuccess) return true;
         if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return true;
         constexpr size_t smem = tile_smem_bytes<S, FM, Q, SH>();
         const int grid = p.ntiles < SH::blocks * sms ? p.ntiles : SH::blocks * sms;
-        tile_plan(L.g, sizeof(S), src, grid, SH::pitch, p, L.z0, L.zs, L.nplanes);
+        tile_plan(L.g, sizeof(S), src, grid, SH::pitch, p, SLAB ? L.z0 : 0, SLAB ? L.zs : 1, SLAB ? L.nplanes : -1);
         if (L.wait_cycles > 0) p.wait = L.wait_cycles;
         if (L.drop_first_tile) p.drop_tile = 0;
-        auto kern = k_step_tma<C, S, FM, WALLS, Q, SH, R>;
+        auto kern = k_step_tma<C, S, FM, WALLS, Q, SH, SLAB, R>;
         // the shared-memory opt-in, once per device for this kernel; host threads
         // may race to set it, which repeats a harmless call
         static std::atomic<int> opted_in[64] = {};
@@ -632,21 +653,26 @@ bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R 
 }
 
 // Launch the staged step (Q = 19 or 27 populations, rates R) if it applies;
-// returns false (nothing launched) otherwise.
-template <int Q, typename C, typename S, int FM, typename R>
+// returns false (nothing launched) otherwise. SLAB: a z-slab's planes
+// (D3Q19, collisions with the node-pair form).
+template <int Q, typename C, typename S, int FM, bool SLAB = false, typename R>
 bool launch_step_tma(const Launch &L, const void *src, void *dst, const R &r, const ForceArgs &F, int *flag,
                      uint32_t key, cudaError_t &err) {
     if constexpr (Q == 27) {
-        return L.g.walls ? launch_step_tma_shape<TmaShape27, true, Q, C, S, FM>(L, src, dst, r, F, flag, key, err)
-                         : launch_step_tma_shape<TmaShape27, false, Q, C, S, FM>(L, src, dst, r, F, flag, key, err);
+        static_assert(!SLAB, "z-slabs: D3Q19 with the node-pair collision");
+        return L.g.walls
+                   ? launch_step_tma_shape<TmaShape27, true, Q, C, S, FM, false>(L, src, dst, r, F, flag, key, err)
+                   : launch_step_tma_shape<TmaShape27, false, Q, C, S, FM, false>(L, src, dst, r, F, flag, key, err);
     } else if constexpr (C::kPairs) {
-        return L.g.walls ? launch_step_tma_shape<TmaShape19P, true, Q, C, S, FM>(L, src, dst, r, F, flag, key, err)
-                         : launch_step_tma_shape<TmaShape19P, false, Q, C, S, FM>(L, src, dst, r, F, flag, key, err);
+        return L.g.walls
+                   ? launch_step_tma_shape<TmaShape19P, true, Q, C, S, FM, SLAB>(L, src, dst, r, F, flag, key, err)
+                   : launch_step_tma_shape<TmaShape19P, false, Q, C, S, FM, SLAB>(L, src, dst, r, F, flag, key, err);
     } else {
+        static_assert(!SLAB, "z-slabs: D3Q19 with the node-pair collision");
         if (!L.g.walls)
-            return launch_step_tma_shape<TmaShape19, false, Q, C, S, FM>(L, src, dst, r, F, flag, key, err);
-        return launch_step_tma_shape<TmaShape19W, true, Q, C, S, FM>(L, src, dst, r, F, flag, key, err) ||
-               launch_step_tma_shape<TmaShape19, true, Q, C, S, FM>(L, src, dst, r, F, flag, key, err);
+            return launch_step_tma_shape<TmaShape19, false, Q, C, S, FM, false>(L, src, dst, r, F, flag, key, err);
+        return launch_step_tma_shape<TmaShape19W, true, Q, C, S, FM, false>(L, src, dst, r, F, flag, key, err) ||
+               launch_step_tma_shape<TmaShape19, true, Q, C, S, FM, false>(L, src, dst, r, F, flag, key, err);
     }
 }
 

@@ -232,18 +232,22 @@ def test_slab_context_refuses_what_needs_no_exchange():
 
 
 # ---- two ranks in separate processes on the one GPU (gloo, faces through host memory)
-NX, NY, NZ, STEPS = 40, 24, 18, 25
+NX, NY, NZ, STEPS = 40, 24, 18, 100
+RANK_CASES = [  # (walls, storage, periodic z)
+    (2, "f32", True),
+    (2 | 4, "f16sr", False),  # z walls at the box ends, the staged 16-bit step
+]
 
 
-def _rank_worker(rank, world, port, out_path):
+def _rank_worker(rank, world, port, out_path, walls, storage, periodic):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     torch.cuda.set_device(0)
     shape = (NZ, NY, NX)
     u0, F = _inputs(shape, 13)
-    z0, nzl, bits = slabs.slab_of(NZ, rank, world, periodic_z=True)
-    lat = Lattice(NX, NY, nzl, 0.04, walls=2, storage="f32", device=dev(), slab=bits, z0=z0, **RATES)
+    z0, nzl, bits = slabs.slab_of(NZ, rank, world, periodic_z=periodic)
+    lat = Lattice(NX, NY, nzl, 0.04, walls=walls, storage=storage, device=dev(), slab=bits, z0=z0, **RATES)
     Fs = t(np.ascontiguousarray(F[:, z0:z0 + nzl]))
     lat.set_force_field(Fs)
     lat.init_equilibrium(None, t(np.ascontiguousarray(u0[:, z0:z0 + nzl])))
@@ -263,12 +267,15 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def test_two_rank_processes_match_the_undivided_lattice(tmp_path):
+@pytest.mark.parametrize("case", RANK_CASES, ids=lambda c: f"w{c[0]}{c[1]}{'p' if c[2] else ''}")
+def test_two_rank_processes_match_the_undivided_lattice(tmp_path, case):
+    walls, storage, periodic = case
     out = str(tmp_path / "slab")
-    mp.start_processes(_rank_worker, args=(2, _free_port(), out), nprocs=2, start_method="spawn", join=True)
+    mp.start_processes(_rank_worker, args=(2, _free_port(), out, walls, storage, periodic), nprocs=2,
+                       start_method="spawn", join=True)
     got = torch.cat([torch.load(f"{out}.{r}") for r in range(2)], dim=1)
     u0, F = _inputs((NZ, NY, NX), 13)
-    assert torch.equal(got, _undivided(NX, NY, NZ, 2, "f32", u0, F, STEPS))
+    assert torch.equal(got, _undivided(NX, NY, NZ, walls, storage, u0, F, STEPS))
 
 
 @pytest.mark.parametrize("scaling", ["weak", "strong"])
