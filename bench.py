@@ -318,8 +318,9 @@ def bench_duct(storage, K, warmup, dev, peak):
 
 def bench_slab_self(K, warmup, dev, side, prof, u0, peak, storage="f32"):
     """One side^3 z-slab that is its own neighbour on both faces (a periodic z
-    axis on one GPU), stepped as faces then interior with the face exchange
-    (device copies) between: the per-GPU cost of the slab decomposition."""
+    axis on one GPU), stepped as faces then interior, the face exchange
+    (device copies on a side stream) overlapping the interior: the per-GPU
+    cost of the slab decomposition."""
     import torch
 
     from paper_1801_04586_gb300 import Lattice, slabs
@@ -328,10 +329,12 @@ def bench_slab_self(K, warmup, dev, side, prof, u0, peak, storage="f32"):
     lat.set_force_profile_z(prof)
     lat.init_equilibrium(None, u0)
 
-    def one():
+    def one():  # as the ranks of a multi-GPU run: the face copies overlap the interior part
         lat.slab_step(SLAB_FACES)
-        slabs.exchange_faces(lat, 0, 1)
+        reqs = slabs.exchange_faces(lat, 0, 1, wait=False)
         lat.slab_step(SLAB_INTERIOR)
+        for r in reqs:
+            r.wait()
 
     with torch.cuda.stream(lat.stream):
         for _ in range(warmup):

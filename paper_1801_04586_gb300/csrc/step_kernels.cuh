@@ -18,6 +18,8 @@
 // MRT comparison models (models.cuh; step_srt.cu, step_mrt.cu).
 #pragma once
 
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace clbm {
@@ -236,40 +238,63 @@ static cudaError_t step_slab_walls_t(const Launch &L, const void *src, void *dst
 
 // One z-slab step (or a part of it: the planes z0, z0 + zs, ..., nplanes of
 // them) with collision C, any storage format. 16-bit storage takes the staged
-// step where it applies (its copies read the halo planes across halo faces
-// and it writes the send planes), one node per thread otherwise.
+// step where it applies: its copies read the halo planes across halo faces,
+// and its launches over the first and last planes (SEND) also write the send
+// planes. A whole-slab step is those two planes, then the rest, so that the
+// interior runs the kernel without the send stores. Otherwise one node per
+// thread.
 template <typename C>
 cudaError_t launch_step_slab_with(int storage, const Launch &L, const void *src, void *dst, const Rates &r,
                                   const ForceArgs &F, int *flag, uint32_t key, int z0, int zs, int nplanes) {
     auto by_force = [&](auto tag) -> cudaError_t {
         using S = decltype(tag);
-        if constexpr (sizeof(S) == 2) {  // 16-bit storage: the staged step, its z-face rows from the halo planes
+        auto one_node = [&](int a, int b, int n) -> cudaError_t {
+            switch (F.mode) {
+                case kForceUniform:
+                    return step_slab_walls_t<C, S, kForceUniform>(L, src, dst, r, F, flag, key, a, b, n);
+                case kForceProfileZ:
+                    return step_slab_walls_t<C, S, kForceProfileZ>(L, src, dst, r, F, flag, key, a, b, n);
+                default:
+                    return step_slab_walls_t<C, S, kForceField>(L, src, dst, r, F, flag, key, a, b, n);
+            }
+        };
+        if constexpr (sizeof(S) == 2) {
             if (L.staged && nplanes > 0) {
-                Launch Ls = L;
-                Ls.z0 = z0;
-                Ls.zs = zs;
-                Ls.nplanes = nplanes;
+                // the planes a, a + b, ... (n of them) staged; false: not launched (the staged step does not apply)
+                auto staged = [&](auto send, int a, int b, int n, cudaError_t &e) -> bool {
+                    constexpr bool SD = decltype(send)::value;
+                    Launch Ls = L;
+                    Ls.z0 = a;
+                    Ls.zs = b;
+                    Ls.nplanes = n;
+                    switch (F.mode) {
+                        case kForceUniform:
+                            return launch_step_tma<19, C, S, kForceUniform, true, SD>(Ls, src, dst, r, F, flag, key, e);
+                        case kForceProfileZ:
+                            return launch_step_tma<19, C, S, kForceProfileZ, true, SD>(Ls, src, dst, r, F, flag, key,
+                                                                                        e);
+                        default:
+                            return launch_step_tma<19, C, S, kForceField, true, SD>(Ls, src, dst, r, F, flag, key, e);
+                    }
+                };
+                const int nz = L.g.nz;
                 cudaError_t e = cudaSuccess;
-                bool done = false;
-                switch (F.mode) {
-                    case kForceUniform:
-                        done = launch_step_tma<19, C, S, kForceUniform, true>(Ls, src, dst, r, F, flag, key, e);
-                        break;
-                    case kForceProfileZ:
-                        done = launch_step_tma<19, C, S, kForceProfileZ, true>(Ls, src, dst, r, F, flag, key, e);
-                        break;
-                    default:
-                        done = launch_step_tma<19, C, S, kForceField, true>(Ls, src, dst, r, F, flag, key, e);
-                        break;
+                if (z0 == 0 && zs == 1 && nplanes == nz && nz > 2) {
+                    if (staged(std::true_type{}, 0, nz - 1, 2, e)) {
+                        if (e != cudaSuccess) return e;
+                        if (staged(std::false_type{}, 1, 1, nz - 2, e)) return e;
+                        return one_node(1, 1, nz - 2);
+                    }
+                } else {
+                    bool ends = false;  // whether the set holds the first or last plane
+                    for (int k = 0; k < nplanes; ++k) ends = ends || z0 + k * zs == 0 || z0 + k * zs == nz - 1;
+                    if (ends ? staged(std::true_type{}, z0, zs, nplanes, e)
+                             : staged(std::false_type{}, z0, zs, nplanes, e))
+                        return e;
                 }
-                if (done) return e;
             }
         }
-        switch (F.mode) {
-            case kForceUniform: return step_slab_walls_t<C, S, kForceUniform>(L, src, dst, r, F, flag, key, z0, zs, nplanes);
-            case kForceProfileZ: return step_slab_walls_t<C, S, kForceProfileZ>(L, src, dst, r, F, flag, key, z0, zs, nplanes);
-            default: return step_slab_walls_t<C, S, kForceField>(L, src, dst, r, F, flag, key, z0, zs, nplanes);
-        }
+        return one_node(z0, zs, nplanes);
     };
     switch (storage) {
         case 0: return by_force(float{});

@@ -389,10 +389,10 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
 // (the even node in the lower half) and stored with one 32-bit store. The
 // collision of f2 rounds like the scalar 16-bit collision (f1), and the pair
 // conversions like the single ones, so the stored bits equal compute_tile's.
-// SLAB: z walls only at faces that are not halo faces, the first / last plane
-// also store their outgoing pair words into the send planes, and the dither
-// hashes global pair indices.
-template <typename C, typename S, int FM, bool WALLS, typename SH, bool SLAB, typename R>
+// SLAB: z walls only at faces that are not halo faces, and the dither hashes
+// global pair indices. SEND (a halo face's plane): the outgoing pair words
+// also go to the send planes.
+template <typename C, typename S, int FM, bool WALLS, typename SH, bool SLAB, bool SEND, typename R>
 __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S *__restrict__ dst, const Geom &g,
                                                    const R &r, const ForceArgs &F, int *flag, uint32_t key,
                                                    const TilePlan &p, int z, int y0, const unsigned char *buf,
@@ -473,9 +473,9 @@ __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S 
         const f2 drho = C::template run<true>(h, fx, fy, fz, r);
         if (!(fabsf(drho.v.x) < 0.9f) || !(fabsf(drho.v.y) < 0.9f)) atomicOr(flag, 1);
         uint32_t *out = reinterpret_cast<uint32_t *>(dst + CLBM_SLOTS(g, self, (kQ - 1) * g.stride + 1u));
-        if constexpr (!SLAB) {
+        if constexpr (!SEND) {
             if constexpr (Codec<S>::kStochastic) {
-                const uint32_t hb = pair_hash(self >> 1, key);
+                const uint32_t hb = pair_hash((SLAB ? self + g.node0 : self) >> 1, key);
 #pragma unroll
                 for (int i = 0; i < kQ; ++i)
                     out[(size_t)i * (g.stride >> 1)] = Codec<S>::pair_sr(h[i].v.y, h[i].v.x, pop_bits(hb, i));
@@ -506,11 +506,14 @@ __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S 
     }
 }
 
-template <typename C, typename S, int FM, bool WALLS, int Q, typename SH, bool SLAB, typename R>
+// SLAB: the tiles of a z-slab's planes z0, z0 + zs, ...; SEND: those planes
+// are its first and/or last, whose outgoing words also go to the send planes.
+template <typename C, typename S, int FM, bool WALLS, int Q, typename SH, bool SLAB, bool SEND, typename R>
 __global__ void __launch_bounds__(SH::threads, SH::blocks)
     k_step_tma(const S *__restrict__ src, S *__restrict__ dst, Geom g, R r, ForceArgs F, int *__restrict__ flag,
                uint32_t key, TilePlan p) {
     static_assert(!SLAB || SH::pairs, "z-slabs take the node-pair tile");
+    static_assert(SLAB || !SEND, "only a z-slab sends faces");
     constexpr int kTmaStages = SH::stages;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);     // [stages]: copies of the buffer's tile arrived
@@ -569,12 +572,13 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
         const bool wall_tile = WALLS && ((g.walls & 1u) || ((g.walls & 4u) && (zlo || zhi)) ||
                                          ((g.walls & 2u) && (y0 == 0 || y0 + p.rows >= g.ny)));
         if constexpr (SH::pairs) {
+            const unsigned char *b = buf + s * SB;
             if (wall_tile)
-                compute_tile_pairs<C, S, FM, true, SH, SLAB>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB,
-                                                             tfx, tfy, tfz);
+                compute_tile_pairs<C, S, FM, true, SH, SLAB, SEND>(src, dst, g, r, F, flag, key, p, zp, y0, b, tfx,
+                                                                   tfy, tfz);
             else
-                compute_tile_pairs<C, S, FM, false, SH, SLAB>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB,
-                                                              tfx, tfy, tfz);
+                compute_tile_pairs<C, S, FM, false, SH, SLAB, SEND>(src, dst, g, r, F, flag, key, p, zp, y0, b, tfx,
+                                                                    tfy, tfz);
         } else {
             if (wall_tile)
                 compute_tile<C, S, FM, true, Q, SH>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB, tfx, tfy,
@@ -616,8 +620,9 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
 
 // Launch the staged step in shape SH if it applies to this geometry, buffer
 // and force; returns false (nothing launched) otherwise. SLAB: the planes
-// L.z0, L.z0 + L.zs, ... (L.nplanes of them) of a z-slab.
-template <typename SH, bool WALLS, int Q, typename C, typename S, int FM, bool SLAB, typename R>
+// L.z0, L.z0 + L.zs, ... (L.nplanes of them) of a z-slab; SEND: they are its
+// first and/or last plane, and send their outgoing faces.
+template <typename SH, bool WALLS, int Q, typename C, typename S, int FM, bool SLAB, bool SEND, typename R>
 bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R &r, const ForceArgs &F, int *flag,
                            uint32_t key, cudaError_t &err) {
     if constexpr (!tile_fits<S, FM, Q, SH>()) {
@@ -636,7 +641,7 @@ bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R 
         tile_plan(L.g, sizeof(S), src, grid, SH::pitch, p, SLAB ? L.z0 : 0, SLAB ? L.zs : 1, SLAB ? L.nplanes : -1);
         if (L.wait_cycles > 0) p.wait = L.wait_cycles;
         if (L.drop_first_tile) p.drop_tile = 0;
-        auto kern = k_step_tma<C, S, FM, WALLS, Q, SH, SLAB, R>;
+        auto kern = k_step_tma<C, S, FM, WALLS, Q, SH, SLAB, SEND, R>;
         // the shared-memory opt-in, once per device for this kernel; host threads
         // may race to set it, which repeats a harmless call
         static std::atomic<int> opted_in[64] = {};
@@ -654,25 +659,31 @@ bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R 
 
 // Launch the staged step (Q = 19 or 27 populations, rates R) if it applies;
 // returns false (nothing launched) otherwise. SLAB: a z-slab's planes
-// (D3Q19, collisions with the node-pair form).
-template <int Q, typename C, typename S, int FM, bool SLAB = false, typename R>
+// (D3Q19, collisions with the node-pair form); SEND: as launch_step_tma_shape.
+template <int Q, typename C, typename S, int FM, bool SLAB = false, bool SEND = false, typename R>
 bool launch_step_tma(const Launch &L, const void *src, void *dst, const R &r, const ForceArgs &F, int *flag,
                      uint32_t key, cudaError_t &err) {
     if constexpr (Q == 27) {
         static_assert(!SLAB, "z-slabs: D3Q19 with the node-pair collision");
         return L.g.walls
-                   ? launch_step_tma_shape<TmaShape27, true, Q, C, S, FM, false>(L, src, dst, r, F, flag, key, err)
-                   : launch_step_tma_shape<TmaShape27, false, Q, C, S, FM, false>(L, src, dst, r, F, flag, key, err);
+                   ? launch_step_tma_shape<TmaShape27, true, Q, C, S, FM, false, false>(L, src, dst, r, F, flag, key,
+                                                                                       err)
+                   : launch_step_tma_shape<TmaShape27, false, Q, C, S, FM, false, false>(L, src, dst, r, F, flag, key,
+                                                                                        err);
     } else if constexpr (C::kPairs) {
         return L.g.walls
-                   ? launch_step_tma_shape<TmaShape19P, true, Q, C, S, FM, SLAB>(L, src, dst, r, F, flag, key, err)
-                   : launch_step_tma_shape<TmaShape19P, false, Q, C, S, FM, SLAB>(L, src, dst, r, F, flag, key, err);
+                   ? launch_step_tma_shape<TmaShape19P, true, Q, C, S, FM, SLAB, SEND>(L, src, dst, r, F, flag, key,
+                                                                                      err)
+                   : launch_step_tma_shape<TmaShape19P, false, Q, C, S, FM, SLAB, SEND>(L, src, dst, r, F, flag, key,
+                                                                                       err);
     } else {
         static_assert(!SLAB, "z-slabs: D3Q19 with the node-pair collision");
         if (!L.g.walls)
-            return launch_step_tma_shape<TmaShape19, false, Q, C, S, FM, false>(L, src, dst, r, F, flag, key, err);
-        return launch_step_tma_shape<TmaShape19W, true, Q, C, S, FM, false>(L, src, dst, r, F, flag, key, err) ||
-               launch_step_tma_shape<TmaShape19, true, Q, C, S, FM, false>(L, src, dst, r, F, flag, key, err);
+            return launch_step_tma_shape<TmaShape19, false, Q, C, S, FM, false, false>(L, src, dst, r, F, flag, key,
+                                                                                      err);
+        return launch_step_tma_shape<TmaShape19W, true, Q, C, S, FM, false, false>(L, src, dst, r, F, flag, key,
+                                                                                  err) ||
+               launch_step_tma_shape<TmaShape19, true, Q, C, S, FM, false, false>(L, src, dst, r, F, flag, key, err);
     }
 }
 

@@ -76,6 +76,35 @@ def slab_of(nz: int, rank: int, world: int, periodic_z: bool = True) -> Tuple[in
     return z0, z1 - z0, bits
 
 
+_SIDE_STREAMS = {}
+
+
+def _side_stream(device) -> torch.cuda.Stream:
+    """One stream per device for the face copies of self-neighbouring slabs."""
+    key = torch.device(device).index
+    if key not in _SIDE_STREAMS:
+        _SIDE_STREAMS[key] = torch.cuda.Stream(device=device)
+    return _SIDE_STREAMS[key]
+
+
+def _self_copies(send, recv, half, has_lo, has_hi):
+    """A slab's own outgoing faces into its receive planes (on the current stream)."""
+    if has_hi:
+        recv[:half].copy_(send[half:])
+    if has_lo:
+        recv[half:].copy_(send[:half])
+
+
+class _StreamJoin:
+    """An unwaited transfer on another stream: wait() makes the current stream wait for it."""
+
+    def __init__(self, done: torch.cuda.Event):
+        self.done = done
+
+    def wait(self):
+        torch.cuda.current_stream().wait_event(self.done)
+
+
 def exchange_faces(lat, rank: int, world: int, dist=None, host: bool = False, wait: bool = True) -> list:
     """After a step (or after its SLAB_FACES part): send this slab's outgoing
     faces to its z neighbours and receive theirs into the newest state's
@@ -86,21 +115,29 @@ def exchange_faces(lat, rank: int, world: int, dist=None, host: bool = False, wa
     those going down, so that with NCCL (which matches a pair's messages in
     order) two ranks that are each other's upper and lower neighbour pair
     them correctly. host=True stages the faces through host memory (gloo).
-    With wait=False (device path) the point-to-point requests are returned
-    unwaited, so that the caller can enqueue the interior part of the step
-    before waiting: their wait() makes the current stream wait for the
-    transfers."""
+    With wait=False (device path) the transfers are returned unwaited, so
+    that the caller can enqueue the interior part of the step before waiting:
+    their wait() makes the current stream wait for them. For a slab that is
+    its own neighbour they are device copies on a side stream, which start
+    once the lattice's stream has passed the faces part."""
     send, recv = lat.faces()
     half = send.numel() // 2
     has_lo, has_hi = bool(lat.slab & SLAB_LO), bool(lat.slab & SLAB_HI)
     with torch.cuda.stream(lat.stream):
         if world == 1 or dist is None:
             # its own neighbour on both sides (a periodic z axis on one slab)
-            if has_hi:
-                recv[:half].copy_(send[half:])
-            if has_lo:
-                recv[half:].copy_(send[:half])
-            return []
+            if wait:
+                _self_copies(send, recv, half, has_lo, has_hi)
+                return []
+            ready = torch.cuda.Event()
+            ready.record(lat.stream)
+            side = _side_stream(lat.device)
+            side.wait_event(ready)
+            with torch.cuda.stream(side):
+                _self_copies(send, recv, half, has_lo, has_hi)
+            done = torch.cuda.Event()
+            done.record(side)
+            return [_StreamJoin(done)]
         lo, hi = neighbours(rank, world)
         if host:
             send_h = send.cpu()

@@ -140,6 +140,30 @@ def test_split_step_with_overlapped_exchange_equals_whole_step():
         lat.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16sr"])
+def test_self_neighbour_with_unwaited_side_stream_exchange(storage):
+    """One periodic slab that is its own neighbour, its face copies left
+    unwaited on the side stream while the interior part runs (the benchmark's
+    single-GPU slab line): equal to the undivided lattice after 60 steps."""
+    nx, ny, nz = 32, 16, 14
+    u0, F = _inputs((nz, ny, nx), 21)
+    ref = _undivided(nx, ny, nz, 0, storage, u0, F, 60)
+    lats, keep = _make_slabs(nx, ny, nz, 0, storage, u0, F, [(0, nz)], True)
+    lat = lats[0]
+    with torch.cuda.stream(lat.stream):
+        for _ in range(60):
+            lat.slab_step(_capi.SLAB_FACES)
+            reqs = slabs.exchange_faces(lat, 0, 1, wait=False)
+            assert len(reqs) == 1
+            lat.slab_step(_capi.SLAB_INTERIOR)
+            for r in reqs:
+                r.wait()
+    torch.cuda.synchronize()
+    assert torch.equal(_gather(lats), ref)
+    lat.check()
+    lat.close()
+
+
 def test_kolmogorov_slabs_with_profile_force_and_split_steps():
     """The configuration the benchmark runs on several GPUs, on one: z-slabs of
     a periodic Kolmogorov box (z-profile force F_x = F0 sin(2 pi z/nz), each
