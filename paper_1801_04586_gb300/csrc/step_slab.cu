@@ -1,9 +1,9 @@
 // step_slab.cu -- the cascaded step on a z-slab with halo faces (Eq. 8
 // across the slab faces): the staged node-pair step for 16-bit storage, the
-// one-node kernel otherwise (step_kernels.cuh, step_tma.cuh). Its own
+// one-node kernel otherwise (step_slab_kernels.cuh, step_tma.cuh). Its own
 // translation unit, so that the slab instantiations build beside step.cu.
 #include "cascaded.cuh"
-#include "step_kernels.cuh"
+#include "step_slab_kernels.cuh"
 
 namespace clbm {
 
