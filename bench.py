@@ -683,6 +683,7 @@ def run_gb300(args):
             "f32_2node": S("f32", variant=2),
             "aa_f32": S("f32", pattern="aa"),
             "aa_f16": S("f16", pattern="aa"),
+            "aa_f16sr": S("f16sr", pattern="aa"),
             "walls_yz_f32": S("f32", walls=6),
             "srt_f32": S("f32", model="srt"),
             "mrt_f32": S("f32", model="mrt"),

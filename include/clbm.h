@@ -108,8 +108,9 @@ extern "C" {
  * walls: CLBM_WALL_* bits; an axis without a bit is periodic.
  * block_x, block_y: CUDA block shape of the step kernel (block_x a multiple
  *      of 32, block_x*block_y <= 512); 0 selects the built-in default.
- * variant: step kernel form. 0 (the default): A/B steps with 16-bit storage
- *      stage the pulled rows in shared memory with bulk asynchronous copies
+ * variant: step kernel form. 0 (the default): A/B steps with 16-bit storage,
+ *      and the cascaded D3Q19 in-place (AA) steps with 16-bit storage, stage
+ *      the rows they read in shared memory with bulk asynchronous copies
  *      where the geometry allows (nx <= 1024, nx a multiple of 8; D3Q27 not
  *      with a force field), one node per thread otherwise; 1: always one node per thread,
  *      plain loads (block_x, block_y apply); 2: two nodes per thread (x and

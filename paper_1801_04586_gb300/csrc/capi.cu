@@ -82,7 +82,7 @@ struct clbm_ctx {
     int64_t steps_done;
     double gamma;         // force decay rate (clbm_set_force_decay)
     bool packed;          // step kernel with two nodes per thread (FP32x2 arithmetic)
-    bool staged;          // A/B D3Q19 step with rows staged in shared memory by bulk copies (variant 0)
+    bool staged;          // steps with rows staged in shared memory by bulk copies (variant 0; see clbm_create)
     int q;                // 19 (Appendix A) or 27 (Sec. II)
     bool aa;              // in-place (AA) pattern: one population buffer, step kind by parity
     int model;            // CLBM_MODEL_*
@@ -347,7 +347,9 @@ int clbm_create(const clbm_params *p, void *stream, clbm_ctx **out) {
     c->gamma = 0.0;
     c->q = q;
     c->packed = q == 19 && p->variant == 2;
-    c->staged = p->variant == 0 && p->pattern != CLBM_PATTERN_AA;
+    // staged: A/B steps, and the cascaded D3Q19 in-place step (node pairs)
+    c->staged = p->variant == 0 &&
+                (p->pattern != CLBM_PATTERN_AA || (q == 19 && p->model == CLBM_MODEL_CASCADED));
     c->aa = p->pattern == CLBM_PATTERN_AA;
     c->model = p->model;
     c->rates27.om2 = c->rates.om2;

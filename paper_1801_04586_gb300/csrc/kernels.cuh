@@ -25,8 +25,8 @@ struct Launch {
     dim3 block, grid;  // grid of the one-node-per-thread kernels
     cudaStream_t stream;
     bool packed;       // launch_step: two nodes per thread (grid.x halved)
-    bool staged;       // launch_step (A/B, one node per thread): rows staged by bulk copies where they apply
-                       // (step_tma.cuh)
+    bool staged;       // launch_step (A/B) and launch_step_aa (16-bit, cascaded): rows staged by bulk copies
+                       // where they apply (step_tma.cuh)
     int map;           // state kernels: slots of the post-streaming state (0 A/B pull map,
                        // 1 in-place pattern after even steps, 2 after odd steps, 3 the A/B pull
                        // map of a z-slab with halo faces)
@@ -51,6 +51,10 @@ bool step_staged(const Geom &g, size_t elem, const void *src, int q, int force_m
 // selects the odd step kind (step.cu).
 cudaError_t launch_step_aa(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,
                            uint32_t key, bool odd);
+// The cascaded in-place step with 16-bit storage staged in node pairs, if it
+// applies (step_aa.cu); false: nothing launched.
+bool launch_step_aa_staged(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,
+                           uint32_t key, bool odd, cudaError_t &err);
 // The comparison collision models (models.cuh): SRT-LBM and non-orthogonal
 // MRT, A/B and in-place forms (step_srt.cu, step_mrt.cu).
 cudaError_t launch_step_srt(int storage, const Launch &L, const void *src, void *dst, const Rates &r,

@@ -83,6 +83,8 @@ bool step_staged(const Geom &g, size_t elem, const void *src, int q, int force_m
 
 cudaError_t launch_step_aa(int storage, const Launch &L, void *f, const Rates &r, const ForceArgs &F, int *flag,
                            uint32_t key, bool odd) {
+    cudaError_t e = cudaSuccess;
+    if (L.staged && launch_step_aa_staged(storage, L, f, r, F, flag, key, odd, e)) return e;
     return launch_step_aa_with<Cascaded>(storage, L, f, r, F, flag, key, odd);
 }
 

@@ -92,19 +92,19 @@ cudaError_t launch_step_slab_with(int storage, const Launch &L, const void *src,
             if (L.staged && nplanes > 0) {
                 // the planes a, a + b, ... (n of them) staged; false: not launched (the staged step does not apply)
                 auto staged = [&](auto send, int a, int b, int n, cudaError_t &e) -> bool {
-                    constexpr bool SD = decltype(send)::value;
+                    constexpr int SD = decltype(send)::value ? kTileSlabSend : kTileSlab;
                     Launch Ls = L;
                     Ls.z0 = a;
                     Ls.zs = b;
                     Ls.nplanes = n;
                     switch (F.mode) {
                         case kForceUniform:
-                            return launch_step_tma<19, C, S, kForceUniform, true, SD>(Ls, src, dst, r, F, flag, key, e);
+                            return launch_step_tma<19, C, S, kForceUniform, SD>(Ls, src, dst, r, F, flag, key, e);
                         case kForceProfileZ:
-                            return launch_step_tma<19, C, S, kForceProfileZ, true, SD>(Ls, src, dst, r, F, flag, key,
+                            return launch_step_tma<19, C, S, kForceProfileZ, SD>(Ls, src, dst, r, F, flag, key,
                                                                                         e);
                         default:
-                            return launch_step_tma<19, C, S, kForceField, true, SD>(Ls, src, dst, r, F, flag, key, e);
+                            return launch_step_tma<19, C, S, kForceField, SD>(Ls, src, dst, r, F, flag, key, e);
                     }
                 };
                 const int nz = L.g.nz;

@@ -71,6 +71,17 @@ using TmaShape19W = TmaShape<256, 3, 2, 768>;
 using TmaShape19P = TmaShape<256, 2, 2, 1024, true>;
 constexpr long long kWaitCycles = 4000000000ll;  // default bound of one barrier wait, about 2 s at 2 GHz
 
+// What a staged launch computes (a compile-time mode).
+enum TileMode : int {
+    kTilePull = 0,      // A/B step: population i's rows shifted by e_i (the pull of Eq. 8), results to slot i
+    kTileSlab = 1,      // the same on a z-slab: rows across a halo face come from its receive planes
+    kTileSlabSend = 2,  // ... over a slab's first / last plane, which also writes the send planes
+    kTileAAEven = 3,    // in-place even step: the node's own slots, results to the opposite slots
+    kTileAAOdd = 4,     // in-place odd step: the opposite slots' rows shifted by e_i, results pushed by e_i
+};
+template <int M>
+constexpr bool tile_slab() { return M == kTileSlab || M == kTileSlabSend; }
+
 struct TilePlan {
     int rows;       // x-rows per tile
     int tiles_y;    // tiles per z-plane
@@ -207,11 +218,15 @@ __host__ __device__ constexpr uint64_t pack_shift(int axis) {
 // force components.
 // With drop (failure injection, from the host) the barrier is armed with the
 // tile's byte count but no copy is issued, so no wait on it can complete.
-// SLAB: the tiles cover the planes z0, z0 + zs, ... of a z-slab, and rows
-// across a halo face come from that face's receive plane.
-template <typename S, int FM, bool WALLS, int Q, typename SH, bool SLAB>
+// Slab modes: the tiles cover the planes z0, z0 + zs, ... of a z-slab, and
+// rows across a halo face come from that face's receive plane. In-place
+// modes: the even step copies the tile's own rows of population i, the odd
+// step the rows of the opposite population, shifted as the pull.
+template <typename S, int FM, bool WALLS, int Q, typename SH, int MODE>
 __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, const Geom &g, const TilePlan &p,
                                            int t, unsigned char *stage, uint64_t *bar, int lane, bool drop = false) {
+    constexpr bool SLAB = tile_slab<MODE>();
+    static_assert(MODE < kTileAAEven || Q == kQ, "in-place modes: D3Q19");
     const int zi = t / p.tiles_y;
     const int z = SLAB ? p.z0 + zi * p.zs : zi;
     const int y0 = (t - zi * p.tiles_y) * p.rows;
@@ -220,7 +235,8 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
     int halo = -1;  // z-slab: the halo plane the rows come from (across a halo face), else -1
     if (lane < Q) {
         constexpr uint64_t kEy = pack_shift<Q>(1), kEz = pack_shift<Q>(2);
-        const int ey = (int)((kEy >> (2 * lane)) & 3u) - 1, ez = (int)((kEz >> (2 * lane)) & 3u) - 1;
+        const int ey = MODE == kTileAAEven ? 0 : (int)((kEy >> (2 * lane)) & 3u) - 1;
+        const int ez = MODE == kTileAAEven ? 0 : (int)((kEz >> (2 * lane)) & 3u) - 1;
         const bool wy = WALLS && (g.walls & 2u), wz = WALLS && (g.walls & 4u);
         zs = z - ez;
         bool plane = true;
@@ -257,8 +273,9 @@ __device__ __forceinline__ void issue_tile(const S *src, const ForceArgs &F, con
     __syncwarp();
     if (drop) return;
     if (lane < Q) {
+        const int slot = MODE == kTileAAOdd ? opposite(lane) : lane;  // the population array the rows come from
         const size_t pop = SLAB && halo >= 0 ? (size_t)kQ * g.stride + (size_t)halo * g.ny * g.nx
-                                             : (size_t)lane * g.stride + (size_t)zs * g.ny * g.nx;
+                                             : (size_t)slot * g.stride + (size_t)zs * g.ny * g.nx;
         S *dst = reinterpret_cast<S *>(stage) + lane * SH::pitch;
         if (n_a > 0) {
             size_t from = pop + (size_t)src_a * g.nx, to = (size_t)slot_a * g.nx;
@@ -382,6 +399,57 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
     }
 }
 
+// Stores of the in-place odd step for the node pair x, x + 1 (x even) of row
+// y, plane z: population i of a node goes where the next even step reads it,
+// (i, node + e_i) with periodic wrap, or (ibar, node) when node + e_i lies
+// beyond a wall (Eq. 8 with halfway bounce-back). word(i) holds population i
+// of both nodes, node x in the lower half. With e_x = 0 both targets are one
+// aligned pair; otherwise they straddle a pair boundary and take two 16-bit
+// stores.
+template <typename S, bool WALLS, typename W>
+__device__ __forceinline__ void push_pairs(S *f, const Geom &g, uint32_t x, uint32_t y, uint32_t z, uint32_t self,
+                                           W word) {
+    const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny, nz = (uint32_t)g.nz, plane = nx * ny;
+    // steps to the next / previous row and plane, periodic
+    const int32_t yp = y + 1u == ny ? -(int32_t)((ny - 1u) * nx) : (int32_t)nx;
+    const int32_t ym = y == 0u ? (int32_t)((ny - 1u) * nx) : -(int32_t)nx;
+    const int32_t zp = z + 1u == nz ? -(int32_t)((nz - 1u) * plane) : (int32_t)plane;
+    const int32_t zm = z == 0u ? (int32_t)((nz - 1u) * plane) : -(int32_t)plane;
+    const int32_t xm0 = x == 0u ? (int32_t)(nx - 1u) : -1;       // node x to x - 1
+    const int32_t xp1 = x + 2u == nx ? -(int32_t)(nx - 1u) : 1;  // node x + 1 to x + 2
+    bool xl0 = false, xh1 = false, yl = false, yh = false, zl = false, zh = false;
+    if (WALLS) {  // leaving through a wall face: node x through x-, node x + 1 through x+
+        const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
+        xl0 = wx && x == 0u;
+        xh1 = wx && x + 2u == nx;
+        yl = wy && y == 0u;
+        yh = wy && y + 1u == ny;
+        zl = wz && z == 0u;
+        zh = wz && z + 1u == nz;
+    }
+    unsigned short *f16 = reinterpret_cast<unsigned short *>(f);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const int ex = ex19(i), ey = ey19(i), ez = ez19(i);
+        const uint32_t w = word(i);
+        const int32_t dyz = (ey > 0 ? yp : ey < 0 ? ym : 0) + (ez > 0 ? zp : ez < 0 ? zm : 0);
+        const bool byz = (ey > 0 && yh) || (ey < 0 && yl) || (ez > 0 && zh) || (ez < 0 && zl);
+        const size_t si = (size_t)i * g.stride, sb = (size_t)opposite(i) * g.stride;
+        if (ex == 0) {
+            const size_t t = byz ? sb + self : si + (uint32_t)((int32_t)self + dyz);
+            *reinterpret_cast<uint32_t *>(f + CLBM_IDX(g, t)) = w;
+        } else {
+            // targets relative to node x: e_x = +1: x + 1 and x + 2; e_x = -1: x - 1 and x
+            const bool b0 = ex > 0 ? byz : (byz || xl0), b1 = ex > 0 ? (byz || xh1) : byz;
+            const int32_t d0 = ex > 0 ? 1 : xm0, d1 = ex > 0 ? 1 + xp1 : 0;
+            const size_t t0 = b0 ? sb + self : si + (uint32_t)((int32_t)self + dyz + d0);
+            const size_t t1 = b1 ? sb + self + 1u : si + (uint32_t)((int32_t)self + dyz + d1);
+            f16[CLBM_IDX(g, t0)] = (unsigned short)(w & 0xffffu);
+            f16[CLBM_IDX(g, t1)] = (unsigned short)(w >> 16);
+        }
+    }
+}
+
 // The D3Q19 tile two adjacent nodes at a time: nodes n and n + 1 (n even, so
 // both in the same row: nx is even) are collided together in f2 lanes .x and
 // .y. Populations with e_x = 0 take both staged values with one 32-bit shared
@@ -389,14 +457,19 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
 // (the even node in the lower half) and stored with one 32-bit store. The
 // collision of f2 rounds like the scalar 16-bit collision (f1), and the pair
 // conversions like the single ones, so the stored bits equal compute_tile's.
-// SLAB: z walls only at faces that are not halo faces, and the dither hashes
-// global pair indices. SEND (a halo face's plane): the outgoing pair words
-// also go to the send planes.
-template <typename C, typename S, int FM, bool WALLS, typename SH, bool SLAB, bool SEND, typename R>
-__device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S *__restrict__ dst, const Geom &g,
-                                                   const R &r, const ForceArgs &F, int *flag, uint32_t key,
-                                                   const TilePlan &p, int z, int y0, const unsigned char *buf,
-                                                   float tfx, float tfy, float tfz) {
+// Slab modes: z walls only at faces that are not halo faces, and the dither
+// hashes global pair indices; kTileSlabSend (a halo face's plane) also
+// stores the outgoing pair words into the send planes. In-place modes (src
+// and dst the one array): the even step reads the node's own slots and
+// stores population i into slot ibar; the odd step bounces back from slot i
+// and pushes population i to (i, x + e_i), or to (ibar, x) beyond a wall, as
+// pair words where the two targets are adjacent (e_x = 0) and as two 16-bit
+// stores otherwise.
+template <typename C, typename S, int FM, bool WALLS, typename SH, int MODE, typename R>
+__device__ __forceinline__ void compute_tile_pairs(const S *src, S *dst, const Geom &g, const R &r, const ForceArgs &F,
+                                                   int *flag, uint32_t key, const TilePlan &p, int z, int y0,
+                                                   const unsigned char *buf, float tfx, float tfy, float tfz) {
+    constexpr bool SLAB = tile_slab<MODE>(), SEND = MODE == kTileSlabSend;
     const S *stage = reinterpret_cast<const S *>(buf);
     const float *fst = reinterpret_cast<const float *>(buf + (size_t)kQ * SH::pitch * sizeof(S));
     constexpr int TN = SH::pitch;
@@ -415,7 +488,7 @@ __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S 
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
             const S *row = stage + i * TN;
-            if (ex19(i) == 0) {
+            if (ex19(i) == 0 || MODE == kTileAAEven) {
                 // both slots n and n + 1 below tile: n below tile - 1
                 const float2 v =
                     Codec<S>::unpack2(*reinterpret_cast<const uint32_t *>(row + CLBM_SIDX(g, n, tile - 1u)));
@@ -428,7 +501,7 @@ __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S 
                            Codec<S>::load_plain(row + CLBM_SIDX(g, sp1, tile)));
             }
         }
-        if (WALLS) {
+        if (WALLS && MODE != kTileAAEven) {  // (the in-place even step reads only its own slots)
             const int y = y0 + (int)rr;
             const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
             const bool yl = wy && y == 0, yh = wy && y == g.ny - 1;
@@ -451,9 +524,10 @@ __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S 
                                       yl || zl, yh || zl, yl || zh, yh || zh};
 #pragma unroll
                 for (int i = 1; i < kQ; ++i) {
-                    if (bb0[i]) h[i].v.x = Codec<S>::load(src + CLBM_IDX(g, (size_t)opposite(i) * g.stride + self));
-                    if (bb1[i])
-                        h[i].v.y = Codec<S>::load(src + CLBM_IDX(g, (size_t)opposite(i) * g.stride + self + 1u));
+                    // bounce-back: slot ibar of the node (A/B), slot i (in-place odd step)
+                    const size_t b = (size_t)(MODE == kTileAAOdd ? i : opposite(i)) * g.stride + self;
+                    if (bb0[i]) h[i].v.x = Codec<S>::load(src + CLBM_IDX(g, b));
+                    if (bb1[i]) h[i].v.y = Codec<S>::load(src + CLBM_IDX(g, b + 1u));
                 }
             }
         }
@@ -472,30 +546,32 @@ __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S 
         }
         const f2 drho = C::template run<true>(h, fx, fy, fz, r);
         if (!(fabsf(drho.v.x) < 0.9f) || !(fabsf(drho.v.y) < 0.9f)) atomicOr(flag, 1);
-        uint32_t *out = reinterpret_cast<uint32_t *>(dst + CLBM_SLOTS(g, self, (kQ - 1) * g.stride + 1u));
-        if constexpr (!SEND) {
-            if constexpr (Codec<S>::kStochastic) {
-                const uint32_t hb = pair_hash((SLAB ? self + g.node0 : self) >> 1, key);
+        const uint32_t hb = Codec<S>::kStochastic ? pair_hash((SLAB ? self + g.node0 : self) >> 1, key) : 0u;
+        auto word = [&](int i) -> uint32_t {  // population i of both nodes, the even node in the lower half
+            if constexpr (Codec<S>::kStochastic)
+                return Codec<S>::pair_sr(h[i].v.y, h[i].v.x, pop_bits(hb, i));
+            else
+                return Codec<S>::pair_rn(h[i].v.y, h[i].v.x);
+        };
+        if constexpr (MODE == kTileAAOdd) {
+            push_pairs<S, WALLS>(dst, g, x, (uint32_t)(y0 + (int)rr), (uint32_t)z, self, word);
+        } else if constexpr (MODE == kTileAAEven) {
+            uint32_t *out = reinterpret_cast<uint32_t *>(dst + CLBM_SLOTS(g, self, (kQ - 1) * g.stride + 1u));
 #pragma unroll
-                for (int i = 0; i < kQ; ++i)
-                    out[(size_t)i * (g.stride >> 1)] = Codec<S>::pair_sr(h[i].v.y, h[i].v.x, pop_bits(hb, i));
-            } else {
+            for (int i = 0; i < kQ; ++i) out[(size_t)opposite(i) * (g.stride >> 1)] = word(i);
+        } else if constexpr (!SEND) {
+            uint32_t *out = reinterpret_cast<uint32_t *>(dst + CLBM_SLOTS(g, self, (kQ - 1) * g.stride + 1u));
 #pragma unroll
-                for (int i = 0; i < kQ; ++i) out[(size_t)i * (g.stride >> 1)] = Codec<S>::pair_rn(h[i].v.y, h[i].v.x);
-            }
+            for (int i = 0; i < kQ; ++i) out[(size_t)i * (g.stride >> 1)] = word(i);
         } else {
             // the first / last plane also sends its outgoing face (send planes, see kSlabPlanes)
+            uint32_t *out = reinterpret_cast<uint32_t *>(dst + CLBM_SLOTS(g, self, (kQ - 1) * g.stride + 1u));
             const uint32_t plane = nx * (uint32_t)g.ny, ps = self - (uint32_t)z * plane;
             const bool send_lo = (g.slab & 1u) && z == 0, send_hi = (g.slab & 2u) && z == g.nz - 1;
             const size_t send = (size_t)kQ * g.stride + ps;  // element offset of the node in send plane 0 (even)
-            const uint32_t hb = Codec<S>::kStochastic ? pair_hash((self + g.node0) >> 1, key) : 0u;
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
-                uint32_t w;
-                if constexpr (Codec<S>::kStochastic)
-                    w = Codec<S>::pair_sr(h[i].v.y, h[i].v.x, pop_bits(hb, i));
-                else
-                    w = Codec<S>::pair_rn(h[i].v.y, h[i].v.x);
+                const uint32_t w = word(i);
                 out[(size_t)i * (g.stride >> 1)] = w;
                 if (ez19(i) < 0 && send_lo)
                     *reinterpret_cast<uint32_t *>(dst + CLBM_IDX(g, send + (size_t)(10 + zface_index(i)) * plane)) = w;
@@ -506,14 +582,16 @@ __device__ __forceinline__ void compute_tile_pairs(const S *__restrict__ src, S 
     }
 }
 
-// SLAB: the tiles of a z-slab's planes z0, z0 + zs, ...; SEND: those planes
-// are its first and/or last, whose outgoing words also go to the send planes.
-template <typename C, typename S, int FM, bool WALLS, int Q, typename SH, bool SLAB, bool SEND, typename R>
+// MODE (TileMode): the A/B pull step, on a whole lattice or on a z-slab's
+// planes z0, z0 + zs, ... (those two with the send-plane stores over its
+// first and/or last plane), or one of the two in-place kinds (src == dst:
+// every tile's copies and stores touch only its own nodes' slots).
+template <typename C, typename S, int FM, bool WALLS, int Q, typename SH, int MODE, typename R>
 __global__ void __launch_bounds__(SH::threads, SH::blocks)
     k_step_tma(const S *__restrict__ src, S *__restrict__ dst, Geom g, R r, ForceArgs F, int *__restrict__ flag,
                uint32_t key, TilePlan p) {
-    static_assert(!SLAB || SH::pairs, "z-slabs take the node-pair tile");
-    static_assert(SLAB || !SEND, "only a z-slab sends faces");
+    constexpr bool SLAB = tile_slab<MODE>();
+    static_assert(MODE == kTilePull || SH::pairs, "z-slabs and the in-place kinds take the node-pair tile");
     constexpr int kTmaStages = SH::stages;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);     // [stages]: copies of the buffer's tile arrived
@@ -539,7 +617,7 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
             const int t = blockIdx.x + k * gridDim.x;
             if (t < p.ntiles) {
                 const bool drop = t == p.drop_tile;
-                issue_tile<S, FM, WALLS, Q, SH, SLAB>(src, F, g, p, t, buf + k * SB, &bar[k], lane, drop);
+                issue_tile<S, FM, WALLS, Q, SH, MODE>(src, F, g, p, t, buf + k * SB, &bar[k], lane, drop);
                 if (lane == 0 && !drop) issued[k] = 1;  // the drain waits only for copies actually issued
             }
         }
@@ -574,11 +652,11 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
         if constexpr (SH::pairs) {
             const unsigned char *b = buf + s * SB;
             if (wall_tile)
-                compute_tile_pairs<C, S, FM, true, SH, SLAB, SEND>(src, dst, g, r, F, flag, key, p, zp, y0, b, tfx,
-                                                                   tfy, tfz);
+                compute_tile_pairs<C, S, FM, true, SH, MODE>(src, dst, g, r, F, flag, key, p, zp, y0, b, tfx, tfy,
+                                                             tfz);
             else
-                compute_tile_pairs<C, S, FM, false, SH, SLAB, SEND>(src, dst, g, r, F, flag, key, p, zp, y0, b, tfx,
-                                                                    tfy, tfz);
+                compute_tile_pairs<C, S, FM, false, SH, MODE>(src, dst, g, r, F, flag, key, p, zp, y0, b, tfx, tfy,
+                                                              tfz);
         } else {
             if (wall_tile)
                 compute_tile<C, S, FM, true, Q, SH>(src, dst, g, r, F, flag, key, p, zp, y0, buf + s * SB, tfx, tfy,
@@ -598,7 +676,7 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
             const int tn = t + kTmaStages * gridDim.x;
             if (tn < p.ntiles) {
                 fence_proxy_async();  // the buffer's reads by every warp precede the copies into it
-                issue_tile<S, FM, WALLS, Q, SH, SLAB>(src, F, g, p, tn, buf + s * SB, &bar[s], lane);
+                issue_tile<S, FM, WALLS, Q, SH, MODE>(src, F, g, p, tn, buf + s * SB, &bar[s], lane);
                 if (lane == 0) ++issued[s];
             }
         }
@@ -619,15 +697,16 @@ __global__ void __launch_bounds__(SH::threads, SH::blocks)
 }
 
 // Launch the staged step in shape SH if it applies to this geometry, buffer
-// and force; returns false (nothing launched) otherwise. SLAB: the planes
-// L.z0, L.z0 + L.zs, ... (L.nplanes of them) of a z-slab; SEND: they are its
-// first and/or last plane, and send their outgoing faces.
-template <typename SH, bool WALLS, int Q, typename C, typename S, int FM, bool SLAB, bool SEND, typename R>
+// and force; returns false (nothing launched) otherwise. MODE (TileMode):
+// the slab modes step the planes L.z0, L.z0 + L.zs, ... (L.nplanes of them);
+// the in-place modes take src == dst.
+template <typename SH, bool WALLS, int Q, typename C, typename S, int FM, int MODE, typename R>
 bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R &r, const ForceArgs &F, int *flag,
                            uint32_t key, cudaError_t &err) {
     if constexpr (!tile_fits<S, FM, Q, SH>()) {
         return false;
     } else {
+        constexpr bool SLAB = tile_slab<MODE>();
         TilePlan p;
         if (!tile_plan(L.g, sizeof(S), src, 0, SH::pitch, p, SLAB ? L.z0 : 0, SLAB ? L.zs : 1,
                        SLAB ? L.nplanes : -1))
@@ -641,7 +720,7 @@ bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R 
         tile_plan(L.g, sizeof(S), src, grid, SH::pitch, p, SLAB ? L.z0 : 0, SLAB ? L.zs : 1, SLAB ? L.nplanes : -1);
         if (L.wait_cycles > 0) p.wait = L.wait_cycles;
         if (L.drop_first_tile) p.drop_tile = 0;
-        auto kern = k_step_tma<C, S, FM, WALLS, Q, SH, SLAB, SEND, R>;
+        auto kern = k_step_tma<C, S, FM, WALLS, Q, SH, MODE, R>;
         // the shared-memory opt-in, once per device for this kernel; host threads
         // may race to set it, which repeats a harmless call
         static std::atomic<int> opted_in[64] = {};
@@ -658,32 +737,30 @@ bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R 
 }
 
 // Launch the staged step (Q = 19 or 27 populations, rates R) if it applies;
-// returns false (nothing launched) otherwise. SLAB: a z-slab's planes
-// (D3Q19, collisions with the node-pair form); SEND: as launch_step_tma_shape.
-template <int Q, typename C, typename S, int FM, bool SLAB = false, bool SEND = false, typename R>
+// returns false (nothing launched) otherwise. Modes other than kTilePull:
+// D3Q19 with a collision that has the node-pair form.
+template <int Q, typename C, typename S, int FM, int MODE = kTilePull, typename R>
 bool launch_step_tma(const Launch &L, const void *src, void *dst, const R &r, const ForceArgs &F, int *flag,
                      uint32_t key, cudaError_t &err) {
     if constexpr (Q == 27) {
-        static_assert(!SLAB, "z-slabs: D3Q19 with the node-pair collision");
-        return L.g.walls
-                   ? launch_step_tma_shape<TmaShape27, true, Q, C, S, FM, false, false>(L, src, dst, r, F, flag, key,
-                                                                                       err)
-                   : launch_step_tma_shape<TmaShape27, false, Q, C, S, FM, false, false>(L, src, dst, r, F, flag, key,
-                                                                                        err);
-    } else if constexpr (C::kPairs) {
-        return L.g.walls
-                   ? launch_step_tma_shape<TmaShape19P, true, Q, C, S, FM, SLAB, SEND>(L, src, dst, r, F, flag, key,
-                                                                                      err)
-                   : launch_step_tma_shape<TmaShape19P, false, Q, C, S, FM, SLAB, SEND>(L, src, dst, r, F, flag, key,
-                                                                                       err);
-    } else {
-        static_assert(!SLAB, "z-slabs: D3Q19 with the node-pair collision");
-        if (!L.g.walls)
-            return launch_step_tma_shape<TmaShape19, false, Q, C, S, FM, false, false>(L, src, dst, r, F, flag, key,
+        static_assert(MODE == kTilePull, "D3Q27: the A/B pull step");
+        return L.g.walls ? launch_step_tma_shape<TmaShape27, true, Q, C, S, FM, MODE>(L, src, dst, r, F, flag, key, err)
+                         : launch_step_tma_shape<TmaShape27, false, Q, C, S, FM, MODE>(L, src, dst, r, F, flag, key,
                                                                                       err);
-        return launch_step_tma_shape<TmaShape19W, true, Q, C, S, FM, false, false>(L, src, dst, r, F, flag, key,
-                                                                                  err) ||
-               launch_step_tma_shape<TmaShape19, true, Q, C, S, FM, false, false>(L, src, dst, r, F, flag, key, err);
+    } else if constexpr (C::kPairs) {
+        if constexpr (MODE == kTileAAEven)  // reads only its own slots: no wall code
+            return launch_step_tma_shape<TmaShape19P, false, Q, C, S, FM, MODE>(L, src, dst, r, F, flag, key, err);
+        else
+            return L.g.walls
+                       ? launch_step_tma_shape<TmaShape19P, true, Q, C, S, FM, MODE>(L, src, dst, r, F, flag, key, err)
+                       : launch_step_tma_shape<TmaShape19P, false, Q, C, S, FM, MODE>(L, src, dst, r, F, flag, key,
+                                                                                     err);
+    } else {
+        static_assert(MODE == kTilePull, "slabs and the in-place kinds: collisions with the node-pair form");
+        if (!L.g.walls)
+            return launch_step_tma_shape<TmaShape19, false, Q, C, S, FM, MODE>(L, src, dst, r, F, flag, key, err);
+        return launch_step_tma_shape<TmaShape19W, true, Q, C, S, FM, MODE>(L, src, dst, r, F, flag, key, err) ||
+               launch_step_tma_shape<TmaShape19, true, Q, C, S, FM, MODE>(L, src, dst, r, F, flag, key, err);
     }
 }
 

@@ -62,13 +62,17 @@ def staged(shape_xyz, walls, storage, lattice=19):
     return {}
 
 
-def in_place(shape_xyz, walls, storage, lattice=19):
+def in_place(shape_xyz, walls, storage, lattice=19, variant=1):
+    """The in-place pattern (variant 0: staged in node pairs for 16-bit D3Q19)
+    against the one-node A/B step."""
     nx, ny, nz = shape_xyz
     shape = (nz, ny, nx)
     outs = []
     for pattern in ("aa", "ab"):
-        g = Lattice(nx, ny, nz, 0.03, walls=walls, storage=storage, pattern=pattern, lattice=lattice, variant=1,
-                    device=dev(), **RATES)
+        g = Lattice(nx, ny, nz, 0.03, walls=walls, storage=storage, pattern=pattern, lattice=lattice,
+                    variant=variant if pattern == "aa" else 1, device=dev(), **RATES)
+        if pattern == "aa":
+            assert g.info()["staged"] == (1 if variant == 0 else 0)
         g.set_force_field(t(synthetic.gaussian_force(shape, 1e-4, seed=61)))
         g.init_equilibrium(None, t(synthetic.divfree_velocity(shape, seed=62, umax=0.03)))
         g.step(7)
@@ -118,6 +122,8 @@ CASES = [("degenerate", degenerate, c) for c in DEGENERATE] + [
     ("in_place", in_place, ((13, 7, 5), 7, "f32")),
     ("in_place", in_place, ((16, 9, 4), 0, "f16sr")),
     ("in_place", in_place, ((9, 6, 5), 3, "f32", 27)),
+    ("in_place", in_place, ((48, 30, 10), 7, "f16sr", 19, 0)),
+    ("in_place", in_place, ((8, 130, 3), 0, "bf16", 19, 0)),
     ("slabs", slabs_case, ()),
     ("slabs", slabs_case, ("f16sr",)),
 ]

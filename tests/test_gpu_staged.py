@@ -241,3 +241,54 @@ def test_staged_step_against_oracle():
     err = np.abs(hg - ho) / ulp16(np.maximum(np.abs(hg), np.abs(ho)))
     report("staged_f16_one_step_ulp", shape=str(shape), walls=walls, max_ulp=float(err.max()))
     assert err.max() <= 0.55
+
+
+# ---- the in-place (AA) pattern, staged in node pairs
+AA_CASES = [
+    # (nx, ny, nz), walls, storage, force
+    ((48, 30, 10), 7, "f16", "field"),       # walls on every axis, 21 rows per tile, ragged second tile
+    ((48, 30, 10), 7, "bf16sr", "field"),
+    ((64, 40, 6), 2, "f16sr", "profile"),    # y walls only: pushes across the y faces bounce
+    ((32, 20, 12), 1, "bf16", "uniform"),    # x walls only: both lanes of a pair at the two x faces
+    ((256, 8, 5), 4, "f16sr", "field"),      # 4 rows per tile, z walls
+    ((8, 130, 3), 0, "bf16sr", "uniform"),   # nx = 8: pushes wrap in x inside one pair row, two tiles per plane
+    ((40, 12, 9), 0, "f16", "profile"),      # periodic: every push wraps somewhere
+    ((16, 9, 1), 3, "f16sr", "field"),       # nz = 1, periodic z: z pushes land in the same plane
+]
+
+
+@pytest.mark.parametrize("shape_xyz,walls,storage,force", AA_CASES)
+def test_staged_in_place_equals_one_node_in_place_and_ab(shape_xyz, walls, storage, force):
+    """The staged node-pair in-place step (even kind: own rows, stores to the
+    opposite slots; odd kind: opposite rows shifted as the pull, pushes with
+    16-bit stores where a pair's targets straddle) stores the same bits as the
+    one-node in-place kernel and as the A/B step, after odd and even step
+    counts."""
+    nx, ny, nz = shape_xyz
+    shape = (nz, ny, nx)
+    mk = lambda **kw: Lattice(nx, ny, nz, 0.03, walls=walls, storage=storage, device=dev(), **RATES, **kw)
+    staged, plain, ab = mk(pattern="aa"), mk(pattern="aa", variant=1), mk()
+    assert staged.info()["staged"] == 1 and plain.info()["staged"] == 0
+    rho = synthetic.density_perturbation(shape, 0.01, seed=41)
+    u = synthetic.divfree_velocity(shape, seed=42, umax=0.04)
+    F = t(synthetic.gaussian_force(shape, 1e-4, seed=43))
+    prof = t(synthetic.kolmogorov_profile(nz, 1e-4))
+    for g in (staged, plain, ab):
+        if force == "field":
+            g.set_force_field(F)
+        elif force == "profile":
+            g.set_force_profile_z(prof)
+        else:
+            g.set_force_uniform(2e-5, -1e-5, 3e-5)
+        g.init_equilibrium(t(rho), t(u))
+    done = 0
+    for n in (1, 1, 5, 9):  # compared after 1, 2, 7 and 16 steps
+        for g in (staged, plain, ab):
+            g.step(n)
+        done += n
+        ps = staged.populations(deviation=True)
+        assert torch.equal(ps, plain.populations(deviation=True)), f"staged vs one-node in place after {done}"
+        assert torch.equal(ps, ab.populations(deviation=True)), f"staged in place vs A/B after {done}"
+    for g in (staged, plain, ab):
+        g.check()
+        g.close()
