@@ -399,6 +399,16 @@ __device__ __forceinline__ void compute_tile(const S *__restrict__ src, S *__res
     }
 }
 
+// Element o of population array `slot` of the 16-bit state f: the array's
+// base first, then a 32-bit offset (bounds-checked builds check the index).
+__device__ __forceinline__ unsigned short *pop_elem(unsigned short *f, const Geom &g, int slot, uint32_t o) {
+#ifdef CLBM_BOUNDS_CHECK
+    return f + CLBM_IDX(g, (size_t)slot * g.stride + o);
+#else
+    return (f + (size_t)slot * g.stride) + o;
+#endif
+}
+
 // Stores of the in-place odd step for the node pair x, x + 1 (x even) of row
 // y, plane z: population i of a node goes where the next even step reads it,
 // (i, node + e_i) with periodic wrap, or (ibar, node) when node + e_i lies
@@ -434,18 +444,15 @@ __device__ __forceinline__ void push_pairs(S *f, const Geom &g, uint32_t x, uint
         const uint32_t w = word(i);
         const int32_t dyz = (ey > 0 ? yp : ey < 0 ? ym : 0) + (ez > 0 ? zp : ez < 0 ? zm : 0);
         const bool byz = (ey > 0 && yh) || (ey < 0 && yl) || (ez > 0 && zh) || (ez < 0 && zl);
-        const size_t si = (size_t)i * g.stride, sb = (size_t)opposite(i) * g.stride;
+        const uint32_t o = (uint32_t)((int32_t)self + dyz);  // the pair's target in the shifted row
         if (ex == 0) {
-            const size_t t = byz ? sb + self : si + (uint32_t)((int32_t)self + dyz);
-            *reinterpret_cast<uint32_t *>(f + CLBM_IDX(g, t)) = w;
+            *reinterpret_cast<uint32_t *>(byz ? pop_elem(f16, g, opposite(i), self) : pop_elem(f16, g, i, o)) = w;
         } else {
             // targets relative to node x: e_x = +1: x + 1 and x + 2; e_x = -1: x - 1 and x
             const bool b0 = ex > 0 ? byz : (byz || xl0), b1 = ex > 0 ? (byz || xh1) : byz;
-            const int32_t d0 = ex > 0 ? 1 : xm0, d1 = ex > 0 ? 1 + xp1 : 0;
-            const size_t t0 = b0 ? sb + self : si + (uint32_t)((int32_t)self + dyz + d0);
-            const size_t t1 = b1 ? sb + self + 1u : si + (uint32_t)((int32_t)self + dyz + d1);
-            f16[CLBM_IDX(g, t0)] = (unsigned short)(w & 0xffffu);
-            f16[CLBM_IDX(g, t1)] = (unsigned short)(w >> 16);
+            const uint32_t o0 = o + (uint32_t)(ex > 0 ? 1 : xm0), o1 = o + (uint32_t)(ex > 0 ? 1 + xp1 : 0);
+            *(b0 ? pop_elem(f16, g, opposite(i), self) : pop_elem(f16, g, i, o0)) = (unsigned short)(w & 0xffffu);
+            *(b1 ? pop_elem(f16, g, opposite(i), self + 1u) : pop_elem(f16, g, i, o1)) = (unsigned short)(w >> 16);
         }
     }
 }
