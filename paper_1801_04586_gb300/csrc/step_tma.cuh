@@ -40,6 +40,7 @@
 #pragma once
 
 #include <atomic>
+#include <numeric>
 
 #include "d3q27.cuh"
 #include "kernels.cuh"
@@ -723,7 +724,12 @@ bool launch_step_tma_shape(const Launch &L, const void *src, void *dst, const R 
         if ((err = cudaGetDevice(&dev)) != cudaSuccess) return true;
         if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return true;
         constexpr size_t smem = tile_smem_bytes<S, FM, Q, SH>();
-        const int grid = p.ntiles < SH::blocks * sms ? p.ntiles : SH::blocks * sms;
+        int grid = p.ntiles < SH::blocks * sms ? p.ntiles : SH::blocks * sms;
+        // Block b takes the tiles b, b + grid, ...; with a grid sharing a factor with the tiles per plane a
+        // block meets only some row positions, and the few blocks whose positions hold the y-wall rows take
+        // all the slower wall tiles. A grid coprime to it spreads them evenly.
+        if (WALLS && grid < p.ntiles)
+            while (grid > 1 && std::gcd(grid, p.tiles_y) != 1) --grid;
         tile_plan(L.g, sizeof(S), src, grid, SH::pitch, p, SLAB ? L.z0 : 0, SLAB ? L.zs : 1, SLAB ? L.nplanes : -1);
         if (L.wait_cycles > 0) p.wait = L.wait_cycles;
         if (L.drop_first_tile) p.drop_tile = 0;
