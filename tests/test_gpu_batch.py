@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from gpu_common import F32_REL_TOL, W, dev, make_pair, rel_err
-from paper_1801_04586_gb300 import Batch
+from paper_1801_04586_gb300 import Batch, synthetic
 
 pytestmark = pytest.mark.gpu
 
@@ -99,4 +99,38 @@ def test_batch_16bit_storage_matches_single_lattices(storage):
     b.check()
     for k, d in enumerate(DOMAINS):
         assert torch.equal(b.populations(k, deviation=True).cpu(), _single(d, 21, storage)), f"domain {k}"
+    b.close()
+
+
+def test_batch_64_domains_full_size_sampled():
+    """The benchmark's batch at full size (64 channels/ducts, sides U{32..128},
+    seed 6: 32.4M nodes), autotuned as the benchmark does, one step through
+    the graph-mode call: in six domains (the largest, the smallest, the first
+    duct and channel, two more), 512 sampled nodes against the FP64 oracle's
+    first step, and the whole domain bit-identical to the lattice stepped
+    alone."""
+    doms = synthetic.batch_domains(64, seed=6)
+    b = Batch(doms, device=dev())
+    b.init_equilibrium()
+    b.autotune(trial_steps=3)
+    b.step(1, Batch.GRAPH)
+    b.check()
+    sizes = [d["nx"] * d["ny"] * d["nz"] for d in doms]
+    pick = [int(np.argmax(sizes)), int(np.argmin(sizes)), next(k for k, d in enumerate(doms) if d["walls"] == 6),
+            next(k for k, d in enumerate(doms) if d["walls"] == 4), 17, 42]
+    rng = np.random.default_rng(11)
+    for k in dict.fromkeys(pick):
+        d = doms[k]
+        shape = (d["nz"], d["ny"], d["nx"])
+        n = sizes[k]
+        fg = b.populations(k, deviation=True)
+        assert torch.equal(fg.cpu(), _single(d, 1)), f"domain {k}"
+        o = oracle.Lattice(d["nx"], d["ny"], d["nz"], walls=d["walls"], s2=1.0 / (3 * d["nu"] + 0.5))
+        F = np.zeros((3,) + shape)
+        F[0] = np.float32(d["fx"])
+        nodes = rng.choice(n, min(512, n), replace=False)
+        fo = oracle.first_step_nodes(o, nodes, None, None, F)
+        hg = fg.reshape(19, -1)[:, torch.from_numpy(nodes).to(dev())].double().cpu().numpy().T
+        err = np.max(np.abs(hg + W.reshape(1, 19) - fo) / np.abs(fo))
+        assert err < 1e-6, (k, err)
     b.close()
