@@ -331,3 +331,44 @@ def test_benchmark_slab_mode_runs_two_ranks_on_one_gpu(scaling):
     else:
         assert "128^3" in d["config"]["workload"] and d["config"]["nz"] == 128
     assert d["e2e"]["value"] > 0
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16sr"])
+def test_full_size_slab_rank_sampled_first_step(storage):
+    """A rank of the multi-GPU benchmark at full size: one 256^3 z-slab of the
+    periodic Kolmogorov box (F_x = 1e-5 sin(2 pi z/256), nu = 0.01, u0 of max
+    |u| = 0.02), its own neighbour, stepped as the benchmark does (faces part,
+    face copies on the side stream, interior part). Bit-identical to the
+    unsplit lattice, and (FP32) within 1e-6 of the oracle's first step at 2048
+    sampled nodes."""
+    import oracle
+    from gpu_common import W as W19
+    n, nu = 256, 0.01
+    shape = (n, n, n)
+    prof = synthetic.kolmogorov_profile(n, 1e-5)
+    u0 = synthetic.divfree_velocity(shape, seed=1, umax=0.02)
+    lat = Lattice(n, n, n, nu, storage=storage, device=dev(), slab=3, z0=0)
+    lat.set_force_profile_z(t(prof))
+    lat.init_equilibrium(None, t(u0))
+    with torch.cuda.stream(lat.stream):
+        lat.slab_step(_capi.SLAB_FACES)
+        reqs = slabs.exchange_faces(lat, 0, 1, wait=False)
+        lat.slab_step(_capi.SLAB_INTERIOR)
+        for r in reqs:
+            r.wait()
+    torch.cuda.synchronize()
+    lat.check()
+    fs = lat.populations(deviation=True)
+    lat.close()
+    g = Lattice(n, n, n, nu, storage=storage, device=dev())
+    g.set_force_profile_z(t(prof))
+    g.init_equilibrium(None, t(u0))
+    g.step(1)
+    assert torch.equal(fs, g.populations(deviation=True))
+    g.close()
+    if storage == "f32":
+        o = oracle.Lattice(n, n, n, s2=1.0 / (3 * nu + 0.5))
+        nodes = np.random.default_rng(9).choice(n ** 3, 2048, replace=False)
+        hg = fs.reshape(19, -1)[:, torch.from_numpy(nodes).to(dev())].double().cpu().numpy().T
+        fo = oracle.first_step_nodes(o, nodes, None, u0, synthetic.profile_to_field(prof, shape))
+        assert np.max(np.abs(hg + W19.reshape(1, 19) - fo) / np.abs(fo)) < 1e-6
