@@ -339,7 +339,9 @@ int clbm_run_host(clbm_ctx *ctx, const float *rho_host, const float *u_host, int
  * clbm_adjoint_step: adjoint of the step f^{t+1} = P C(f^t, F) (Eqs. 5, 7, 8,
  * 9), with f^t the pull of state_dev: lam_dev = J_f^T lam*, where lam* is
  * lam_next_dev read at the slot each population streams into (periodic wrap,
- * or its opposite at its own node across a wall face), and gF_dev +=
+ * or its opposite at its own node across a wall face; on a z-slab, across a
+ * halo face, from lam_next_dev's receive planes, see the z-slab section),
+ * and gF_dev +=
  * J_F^T lam* (dL/dF of a force field, accumulated). lam_dev must not alias
  * lam_next_dev. The force in use is the context's (any mode; for a uniform or
  * profile force gF is still per node). */
@@ -382,8 +384,28 @@ int clbm_adjoint_step(clbm_ctx *ctx, const void *state_dev, const float *lam_nex
  * populations) into the first half of the upper neighbour's receive planes.
  * A slab with both halo faces may be its own neighbour (a periodic z axis on
  * one context). clbm_step on a slab context takes at most one step per call.
- * Slab contexts refuse clbm_run_host and the recomputation/adjoint calls
- * (CLBM_ERR_STATE). */
+ * Slab contexts refuse clbm_run_host and clbm_adjoint_segment, whose inner
+ * steps would need exchanges (CLBM_ERR_STATE).
+ *
+ * Recomputation and adjoint on slabs (the reverse-direction halo):
+ * clbm_step_raw steps every plane of a raw state through the halo map and
+ * writes dst's send planes; the caller moves dst's faces as above (the halo
+ * planes of a raw state follow its q x pop_stride values: 10 receive, then 10
+ * send planes of nx x ny values). The adjoint gathers lambda from the node
+ * each population streams into, so at the slab's last plane the e_z = +1
+ * populations need the upper neighbour's first-plane lambda, and at its first
+ * plane the e_z = -1 populations the lower neighbour's last-plane lambda. The
+ * adjoint arrays of a slab (lam_dev, lam_next_dev) therefore hold 19 x N
+ * floats, then 10 receive planes (0-4 from the lower neighbour, populations
+ * 6, 13, 14, 17, 18; 5-9 from the upper neighbour, populations 5, 11, 12,
+ * 15, 16), then 10 send planes that clbm_adjoint_seed and clbm_adjoint_step
+ * write (10-14: this slab's first-plane lambda of 5, 11, 12, 15, 16; 15-19:
+ * its last-plane lambda of 6, 13, 14, 17, 18); each plane is nx x ny floats.
+ * Before the next adjoint step the caller moves them like the population
+ * faces: the first half of the send planes into the second half of the lower
+ * neighbour's receive planes, the second half into the first half of the
+ * upper neighbour's. The slabs' lambda and dL/dF then equal those of one
+ * undivided lattice bit for bit. */
 #define CLBM_SLAB_ALL      0  /* the whole step, then the state advances */
 #define CLBM_SLAB_FACES    1  /* only the first and last planes (the send planes are then complete) */
 #define CLBM_SLAB_INTERIOR 2  /* the other planes, then the state advances (after CLBM_SLAB_FACES) */

@@ -297,13 +297,90 @@ __device__ __forceinline__ void force_adj(const ForceArgs &F, const Geom &g, int
     fz *= F.scale;
 }
 
+// push_targets on a z-slab (Geom::slab): z walls only at faces that are not
+// halo faces, and a population leaving across a halo face (not bounced back at
+// an x or y wall) has its target in the neighbour's first or last plane. The
+// adjoint of that target comes from the receive planes appended to the lambda
+// array (pop = kQ, off within them): planes 0-4 the lower neighbour's last
+// plane (e_z = -1 at z = 0), planes 5-9 the upper neighbour's first plane
+// (e_z = +1 at z = nz - 1), in the order of zface_index.
+template <bool WALLS>
+__device__ __forceinline__ void push_targets_slab(const Geom &g, int x, int y, int z, uint32_t (&off)[kQ],
+                                                  int (&pop)[kQ]) {
+    push_targets<false>(g, x, y, z, off, pop);  // periodic targets
+    const uint32_t plane = (uint32_t)g.nx * (uint32_t)g.ny;
+    const uint32_t self = (uint32_t)z * plane + (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
+    bool bb[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) bb[i] = false;
+    if (WALLS) {
+        const bool wx = g.walls & 1u, wy = g.walls & 2u, wz = g.walls & 4u;
+        const bool xl = wx && x == 0, xh = wx && x == g.nx - 1;  // leaving through x- (ex = -1) / x+ (ex = +1)
+        const bool yl = wy && y == 0, yh = wy && y == g.ny - 1;
+        const bool zl = wz && z == 0 && !(g.slab & 1u), zh = wz && z == g.nz - 1 && !(g.slab & 2u);
+        const bool w[kQ] = {false,
+                            xh, xl, yh, yl, zh, zl,
+                            xh || yh, xl || yh, xh || yl, xl || yl,
+                            xh || zh, xl || zh, xh || zl, xl || zl,
+                            yh || zh, yl || zh, yh || zl, yl || zl};
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) {
+            bb[i] = w[i];
+            if (w[i]) {
+                pop[i] = opposite(i);
+                off[i] = self;
+            }
+        }
+    }
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+    if ((g.slab & 1u) && z == 0) {
+#pragma unroll
+        for (int i = 1; i < kQ; ++i)
+            if (ez19(i) < 0 && !bb[i]) {
+                pop[i] = kQ;
+                off[i] = (uint32_t)zface_index(i) * plane + (off[i] - (uint32_t)zm * plane);
+            }
+    }
+    if ((g.slab & 2u) && z == g.nz - 1) {
+#pragma unroll
+        for (int i = 1; i < kQ; ++i)
+            if (ez19(i) > 0 && !bb[i]) {
+                pop[i] = kQ;
+                off[i] = (uint32_t)(5 + zface_index(i)) * plane + (off[i] - (uint32_t)zp * plane);
+            }
+    }
+}
+
+// A z-slab's outgoing adjoint faces, after the 10 receive planes of the lambda
+// array: its first plane's lambda of the e_z = +1 populations (send planes
+// 10-14, for the lower neighbour, whose last plane pushes them into this one)
+// and its last plane's lambda of the e_z = -1 populations (15-19, for the upper
+// neighbour).
+__device__ __forceinline__ void send_adjoint_faces(float *lam, const Geom &g, int64_t n, int z, uint32_t self,
+                                                   const float (&l)[kQ]) {
+    const uint32_t plane = (uint32_t)g.nx * (uint32_t)g.ny, ps = self - (uint32_t)z * plane;
+    float *send = lam + (size_t)kQ * n + (size_t)10 * plane + ps;
+    if ((g.slab & 1u) && z == 0) {
+#pragma unroll
+        for (int i = 1; i < kQ; ++i)
+            if (ez19(i) > 0) send[(size_t)zface_index(i) * plane] = l[i];
+    }
+    if ((g.slab & 2u) && z == g.nz - 1) {
+#pragma unroll
+        for (int i = 1; i < kQ; ++i)
+            if (ez19(i) < 0) send[(size_t)(5 + zface_index(i)) * plane] = l[i];
+    }
+}
+
 // One adjoint step. state: raw buffer whose pull gives f^t; lam_next: adjoint
 // of f^{t+1} (19 x n, post-streaming layout); lam: adjoint of f^t (19 x n);
 // gF: dL/dF accumulated (3 x n). The node's three gF values are read first,
 // beside its gathers, so their latency is hidden behind the collision instead
 // of adding a second memory round trip at the end; 80 registers keep three
 // blocks per SM (a few bytes spill): 0.94 against 0.82 of the copy roofline.
-template <typename S, int FM, bool WALLS>
+// SLAB: a z-slab (pull through the halo map, gathers across halo faces from
+// lam_next's receive planes, send planes of lam written).
+template <typename S, int FM, bool WALLS, bool SLAB>
 __global__ void __launch_bounds__(256, 3) k_adjoint_step(const S *__restrict__ state, const float *__restrict__ lam_next,
                                                       float *__restrict__ lam, float *__restrict__ gF, Geom g,
                                                       Rates r, ForceArgs F, int64_t n) {
@@ -317,7 +394,10 @@ __global__ void __launch_bounds__(256, 3) k_adjoint_step(const S *__restrict__ s
     {
         uint32_t off[kQ];
         int pop[kQ];
-        push_targets<WALLS>(g, x, y, z, off, pop);
+        if (SLAB)
+            push_targets_slab<WALLS>(g, x, y, z, off, pop);
+        else
+            push_targets<WALLS>(g, x, y, z, off, pop);
 #pragma unroll
         for (int i = 0; i < kQ; ++i) l[i] = __ldg(lam_next + (size_t)pop[i] * n + off[i]);
     }
@@ -326,7 +406,7 @@ __global__ void __launch_bounds__(256, 3) k_adjoint_step(const S *__restrict__ s
     {
         uint32_t off[kQ];
         int pop[kQ];
-        pull_sources<WALLS>(g, x, y, z, off, pop);
+        pull_sources<WALLS, false, SLAB>(g, x, y, z, off, pop);
 #pragma unroll
         for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(state + (size_t)pop[i] * g.stride + off[i]);
         self = off[0];
@@ -337,6 +417,7 @@ __global__ void __launch_bounds__(256, 3) k_adjoint_step(const S *__restrict__ s
     collide_adjoint(h, l, fx, fy, fz, r, gx, gy, gz);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) lam[(size_t)i * n + self] = l[i];
+    if (SLAB) send_adjoint_faces(lam, g, n, z, self, l);
     gF[self] = g0x + gx;
     gF[n + self] = g0y + gy;
     gF[2 * n + self] = g0z + gz;
@@ -344,7 +425,7 @@ __global__ void __launch_bounds__(256, 3) k_adjoint_step(const S *__restrict__ s
 
 // Seed from a cotangent gu (3 x n) on the Eq. 9 velocity of the state in
 // `state`: lam_i = sum_a gu_a (e_ia - u_a)/rho, gF = gu/(2 rho) (written).
-template <typename S, int FM, bool WALLS>
+template <typename S, int FM, bool WALLS, bool SLAB>
 __global__ void k_adjoint_seed(const S *__restrict__ state, const float *__restrict__ gu, float *__restrict__ lam,
                                float *__restrict__ gF, Geom g, ForceArgs F, int64_t n) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -353,7 +434,7 @@ __global__ void k_adjoint_seed(const S *__restrict__ state, const float *__restr
     if (x >= g.nx || y >= g.ny) return;
     uint32_t off[kQ];
     int pop[kQ];
-    pull_sources<WALLS>(g, x, y, z, off, pop);
+    pull_sources<WALLS, false, SLAB>(g, x, y, z, off, pop);
     float h[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(state + (size_t)pop[i] * g.stride + off[i]);
@@ -366,50 +447,52 @@ __global__ void k_adjoint_seed(const S *__restrict__ state, const float *__restr
     const float ax = gu[self] * inv, ay = gu[n + self] * inv, az = gu[2 * n + self] * inv;
     const float base = -(ax * ux + ay * uy + az * uz);
     // lam_i = base + ax e_ix + ay e_iy + az e_iz
-    lam[self] = base;
-    lam[(size_t)1 * n + self] = base + ax;  lam[(size_t)2 * n + self] = base - ax;
-    lam[(size_t)3 * n + self] = base + ay;  lam[(size_t)4 * n + self] = base - ay;
-    lam[(size_t)5 * n + self] = base + az;  lam[(size_t)6 * n + self] = base - az;
-    lam[(size_t)7 * n + self] = base + ax + ay;   lam[(size_t)8 * n + self] = base - ax + ay;
-    lam[(size_t)9 * n + self] = base + ax - ay;   lam[(size_t)10 * n + self] = base - ax - ay;
-    lam[(size_t)11 * n + self] = base + ax + az;  lam[(size_t)12 * n + self] = base - ax + az;
-    lam[(size_t)13 * n + self] = base + ax - az;  lam[(size_t)14 * n + self] = base - ax - az;
-    lam[(size_t)15 * n + self] = base + ay + az;  lam[(size_t)16 * n + self] = base - ay + az;
-    lam[(size_t)17 * n + self] = base + ay - az;  lam[(size_t)18 * n + self] = base - ay - az;
+    const float l[kQ] = {base,
+                         base + ax, base - ax, base + ay, base - ay, base + az, base - az,
+                         base + ax + ay, base - ax + ay, base + ax - ay, base - ax - ay,
+                         base + ax + az, base - ax + az, base + ax - az, base - ax - az,
+                         base + ay + az, base - ay + az, base + ay - az, base - ay - az};
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) lam[(size_t)i * n + self] = l[i];
+    if (SLAB) send_adjoint_faces(lam, g, n, z, self, l);
     gF[self] = 0.5f * ax;
     gF[n + self] = 0.5f * ay;
     gF[2 * n + self] = 0.5f * az;
 }
 
-#define CLBM_ADJ_DISPATCH(storage, fmode, walls, KERNEL, ...)                                                \
+#define CLBM_ADJ_LAUNCH(FMODE, walls, slab, KERNEL, ...)                                                     \
+    do {                                                                                                    \
+        if (slab) {                                                                                         \
+            if (walls) KERNEL<S, FMODE, true, true><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);         \
+            else KERNEL<S, FMODE, false, true><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);              \
+        } else {                                                                                            \
+            if (walls) KERNEL<S, FMODE, true, false><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);        \
+            else KERNEL<S, FMODE, false, false><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);             \
+        }                                                                                                   \
+    } while (0)
+
+#define CLBM_ADJ_DISPATCH(storage, fmode, walls, slab, KERNEL, ...)                                          \
     do {                                                                                                    \
         if ((storage) != 0) return cudaErrorInvalidValue;                                                   \
         using S = float;                                                                                    \
         switch (fmode) {                                                                                    \
-            case kForceUniform:                                                                             \
-                if (walls) KERNEL<S, kForceUniform, true><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);   \
-                else KERNEL<S, kForceUniform, false><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);        \
-                break;                                                                                      \
-            case kForceProfileZ:                                                                            \
-                if (walls) KERNEL<S, kForceProfileZ, true><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);  \
-                else KERNEL<S, kForceProfileZ, false><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);       \
-                break;                                                                                      \
-            default:                                                                                        \
-                if (walls) KERNEL<S, kForceField, true><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);     \
-                else KERNEL<S, kForceField, false><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);          \
-                break;                                                                                      \
+            case kForceUniform: CLBM_ADJ_LAUNCH(kForceUniform, walls, slab, KERNEL, __VA_ARGS__); break;     \
+            case kForceProfileZ: CLBM_ADJ_LAUNCH(kForceProfileZ, walls, slab, KERNEL, __VA_ARGS__); break;   \
+            default: CLBM_ADJ_LAUNCH(kForceField, walls, slab, KERNEL, __VA_ARGS__); break;                  \
         }                                                                                                   \
     } while (0)
 
 cudaError_t launch_adjoint_step(int storage, const Launch &L, const void *state, const float *lam_next, float *lam,
                                 float *gF, const Rates &r, const ForceArgs &F, int64_t n) {
-    CLBM_ADJ_DISPATCH(storage, F.mode, L.g.walls, k_adjoint_step, (const S *)state, lam_next, lam, gF, L.g, r, F, n);
+    CLBM_ADJ_DISPATCH(storage, F.mode, L.g.walls, L.g.slab, k_adjoint_step, (const S *)state, lam_next, lam, gF, L.g,
+                      r, F, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_seed(int storage, const Launch &L, const void *state, const float *gu, float *lam,
                                 float *gF, const ForceArgs &F, int64_t n) {
-    CLBM_ADJ_DISPATCH(storage, F.mode, L.g.walls, k_adjoint_seed, (const S *)state, gu, lam, gF, L.g, F, n);
+    CLBM_ADJ_DISPATCH(storage, F.mode, L.g.walls, L.g.slab, k_adjoint_seed, (const S *)state, gu, lam, gF, L.g, F,
+                      n);
     return cudaGetLastError();
 }
 

@@ -666,14 +666,17 @@ int clbm_load_state(clbm_ctx *c, const void *host, size_t bytes) {
 int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
     if (!c || !src || !dst) return fail(CLBM_ERR_ARG, "clbm_step_raw: null pointer");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_step_raw: D3Q19 only");
-    if (c->g.slab) return fail(CLBM_ERR_STATE, "clbm_step_raw: not for z-slabs");
     if (c->aa) return fail(CLBM_ERR_ARG, "clbm_step_raw: A/B pattern only");
     if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_step_raw: cascaded model only");
     if (c->gamma != 0.0) return fail(CLBM_ERR_STATE, "clbm_step_raw: needs a static force (decay 0)");
-    const size_t bytes = (size_t)c->q * c->g.stride * c->elem;
+    const size_t bytes = state_bytes(c);
     if ((const char *)src < (const char *)dst + bytes && (const char *)dst < (const char *)src + bytes)
         return fail(CLBM_ERR_ARG, "clbm_step_raw: src and dst overlap");
-    cudaError_t e = launch_step(c->p.storage, step_launch_of(c), src, dst, c->rates, c->force, c->d_flag, step_key(0));
+    // a z-slab: every plane through the halo map, dst's send planes written (the caller exchanges them)
+    cudaError_t e = c->g.slab ? launch_step_slab(c->p.storage, launch_of(c), src, dst, c->rates, c->force, c->d_flag,
+                                                 step_key(0), 0, 1, c->g.nz)
+                              : launch_step(c->p.storage, step_launch_of(c), src, dst, c->rates, c->force, c->d_flag,
+                                            step_key(0));
     if (e != cudaSuccess) return cuda_fail(e, "clbm_step_raw");
     return CLBM_OK;
 }
@@ -681,7 +684,6 @@ int clbm_step_raw(clbm_ctx *c, const void *src, void *dst) {
 int clbm_adjoint_seed(clbm_ctx *c, const void *state, const float *gu, float *lam, float *gF) {
     if (!c || !gu || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: null pointer");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: D3Q19 only");
-    if (c->g.slab) return fail(CLBM_ERR_STATE, "clbm_adjoint_seed: not for z-slabs");
     if (c->aa) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: A/B pattern only");
     if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: cascaded model only");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_seed: FP32 storage only");
@@ -695,7 +697,6 @@ int clbm_adjoint_seed(clbm_ctx *c, const void *state, const float *gu, float *la
 int clbm_adjoint_step(clbm_ctx *c, const void *state, const float *lam_next, float *lam, float *gF) {
     if (!c || !state || !lam_next || !lam || !gF) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: null pointer");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: D3Q19 only");
-    if (c->g.slab) return fail(CLBM_ERR_STATE, "clbm_adjoint_step: not for z-slabs");
     if (c->aa) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: A/B pattern only");
     if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: cascaded model only");
     if (c->p.storage != CLBM_STORAGE_F32) return fail(CLBM_ERR_ARG, "clbm_adjoint_step: FP32 storage only");
@@ -712,7 +713,8 @@ int clbm_adjoint_segment(clbm_ctx *c, const void *ckpt, void *tape, int64_t k, f
     if (!c || !ckpt || !lam || !lam_tmp || !gF || k < 1 || (k > 1 && !tape) || lam == lam_tmp)
         return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: bad argument");
     if (c->q != 19) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: D3Q19 only");
-    if (c->g.slab) return fail(CLBM_ERR_STATE, "clbm_adjoint_segment: not for z-slabs");
+    if (c->g.slab)
+        return fail(CLBM_ERR_STATE, "clbm_adjoint_segment: not for z-slabs (its recomputed steps need face exchanges)");
     if (c->aa) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: A/B pattern only");
     if (c->model != CLBM_MODEL_CASCADED) return fail(CLBM_ERR_ARG, "clbm_adjoint_segment: cascaded model only");
     Range range("clbm_adjoint_segment");

@@ -249,16 +249,33 @@ class Lattice:
                 raise ValueError(f"{name}: expected a contiguous device buffer of >= {nb} bytes")
         check(self.lib.clbm_step_raw(self.h, _ptr(src), _ptr(dst)), "clbm_step_raw")
 
+    def lam_numel(self) -> int:
+        """Floats of an adjoint array: 19 x N in the post-streaming layout; a
+        z-slab appends 20 planes (10 receive, 10 send; slabs.lam_faces)."""
+        return 19 * self.nz * self.ny * self.nx + (20 * self.ny * self.nx if self.slab else 0)
+
+    def empty_lam(self) -> torch.Tensor:
+        return torch.zeros(self.lam_numel(), dtype=torch.float32, device=self.device)
+
+    def _lam(self, t: torch.Tensor, name: str):
+        if not self.slab:
+            return self._dev(t, (19,) + self.shape, name)
+        if t.device != self.device or t.dtype != torch.float32 or not t.is_contiguous() or \
+                t.numel() < self.lam_numel():
+            raise ValueError(f"{name}: expected a contiguous float32 tensor of >= {self.lam_numel()} elements "
+                             f"on {self.device} (a z-slab's adjoint array with its halo planes)")
+        return t
+
     def adjoint_seed(self, gu: torch.Tensor, lam: torch.Tensor, gF: torch.Tensor,
                      state: Optional[torch.Tensor] = None):
         self._dev(gu, (3,) + self.shape, "gu")
-        self._dev(lam, (19,) + self.shape, "lam")
+        self._lam(lam, "lam")
         self._dev(gF, (3,) + self.shape, "gF")
         check(self.lib.clbm_adjoint_seed(self.h, _ptr(state), _ptr(gu), _ptr(lam), _ptr(gF)), "clbm_adjoint_seed")
 
     def adjoint_step(self, state: torch.Tensor, lam_next: torch.Tensor, lam: torch.Tensor, gF: torch.Tensor):
-        self._dev(lam_next, (19,) + self.shape, "lam_next")
-        self._dev(lam, (19,) + self.shape, "lam")
+        self._lam(lam_next, "lam_next")
+        self._lam(lam, "lam")
         self._dev(gF, (3,) + self.shape, "gF")
         if state.numel() * state.element_size() < self.state_bytes():
             raise ValueError("state: buffer too small")

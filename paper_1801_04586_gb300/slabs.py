@@ -121,17 +121,69 @@ def exchange_faces(lat, rank: int, world: int, dist=None, host: bool = False, wa
     its own neighbour they are device copies on a side stream, which start
     once the lattice's stream has passed the faces part."""
     send, recv = lat.faces()
+    return exchange_views(send, recv, lat.slab, lat.stream, getattr(lat, "device", None), rank, world, dist, host,
+                          wait)
+
+
+def state_faces(lat, state: torch.Tensor) -> Tuple[torch.Tensor, torch.Tensor]:
+    """(send, recv) byte views of the halo planes of a raw state buffer of
+    `lat` (clbm_export_state layout: the population arrays, then 10 receive
+    planes, then 10 send planes), as faces() gives them for the context's own
+    state. For the recomputation of states by step_raw."""
+    info = lat.info()
+    elem = 4 if info["storage"] == 0 else 2
+    plane = lat.nx * lat.ny
+    base = info["q"] * info["pop_stride"] * elem
+    b = state.view(torch.uint8)
+    return b[base + 10 * plane * elem: base + 20 * plane * elem], b[base: base + 10 * plane * elem]
+
+
+def lam_faces(lat, lam: torch.Tensor) -> Tuple[torch.Tensor, torch.Tensor]:
+    """(send, recv) byte views of the halo planes of an adjoint array of a
+    z-slab (Lattice.lam_numel floats: 19 x N, 10 receive planes, 10 send
+    planes). The adjoint gathers lambda from the node each population streams
+    into, so across a halo face it needs the upper neighbour's first plane
+    (e_z = +1) and the lower neighbour's last plane (e_z = -1); adjoint_seed and
+    adjoint_step write this slab's matching faces into the send planes."""
+    plane = lat.nx * lat.ny
+    base = 19 * lat.nz * plane * 4
+    b = lam.view(torch.uint8)
+    return b[base + 10 * plane * 4: base + 20 * plane * 4], b[base: base + 10 * plane * 4]
+
+
+def exchange_adjoint_faces(lat, lam: torch.Tensor, rank: int, world: int, dist=None, host: bool = False,
+                           wait: bool = True) -> list:
+    """After adjoint_seed or adjoint_step wrote lam: its faces to the z
+    neighbours and theirs into lam's receive planes, as exchange_faces does
+    for the populations (the reverse-direction halo of the adjoint)."""
+    send, recv = lam_faces(lat, lam)
+    return exchange_views(send, recv, lat.slab, lat.stream, lat.device, rank, world, dist, host, wait)
+
+
+def exchange_state_faces(lat, state: torch.Tensor, rank: int, world: int, dist=None, host: bool = False,
+                         wait: bool = True) -> list:
+    """After step_raw wrote the raw state `state`: its faces to the z
+    neighbours and theirs into its receive planes."""
+    send, recv = state_faces(lat, state)
+    return exchange_views(send, recv, lat.slab, lat.stream, lat.device, rank, world, dist, host, wait)
+
+
+def exchange_views(send: torch.Tensor, recv: torch.Tensor, slab: int, stream, device, rank: int, world: int,
+                   dist=None, host: bool = False, wait: bool = True) -> list:
+    """The exchange behind exchange_faces, on byte views: the first half of
+    `send` goes down into the lower neighbour's second receive half, the
+    second half up into the upper neighbour's first (see exchange_faces)."""
     half = send.numel() // 2
-    has_lo, has_hi = bool(lat.slab & SLAB_LO), bool(lat.slab & SLAB_HI)
-    with torch.cuda.stream(lat.stream):
+    has_lo, has_hi = bool(slab & SLAB_LO), bool(slab & SLAB_HI)
+    with torch.cuda.stream(stream):
         if world == 1 or dist is None:
             # its own neighbour on both sides (a periodic z axis on one slab)
             if wait:
                 _self_copies(send, recv, half, has_lo, has_hi)
                 return []
             ready = torch.cuda.Event()
-            ready.record(lat.stream)
-            side = _side_stream(lat.device)
+            ready.record(stream)
+            side = _side_stream(device)
             side.wait_event(ready)
             with torch.cuda.stream(side):
                 _self_copies(send, recv, half, has_lo, has_hi)

@@ -57,10 +57,11 @@ def _make_slabs(nx, ny, nz, walls, storage, u0, F, ranges, periodic, nu=0.04):
     return lats, keep
 
 
-def _exchange_all(lats):
-    """Every face to its neighbour (one process; the lattices share a stream)."""
+def _exchange_all(lats, faces=None):
+    """Every face to its neighbour (one process; the lattices share a stream).
+    faces: (send, recv) views per slab (default: the newest states')."""
     world = len(lats)
-    faces = [lat.faces() for lat in lats]
+    faces = [lat.faces() for lat in lats] if faces is None else faces
     for r, lat in enumerate(lats):
         send = faces[r][0]
         half = send.numel() // 2
@@ -247,8 +248,12 @@ def test_slab_context_refuses_what_needs_no_exchange():
     assert lib.clbm_slab_step(lat.h, _capi.SLAB_FACES) == _capi.CLBM_ERR_STATE
     assert lib.clbm_slab_step(lat.h, _capi.SLAB_INTERIOR) == _capi.CLBM_OK
     assert lib.clbm_run_host(lat.h, None, None, 1, None, None, None) == _capi.CLBM_ERR_STATE
-    assert lib.clbm_step_raw(lat.h, lat.export_state().data_ptr(), lat.export_state().data_ptr()) \
-        == _capi.CLBM_ERR_STATE
+    st = lat.export_state()
+    la, lb = lat.empty_lam(), lat.empty_lam()
+    assert la.numel() == 19 * 16 * 8 * 6 + 20 * 16 * 8
+    gf = torch.zeros(3 * 16 * 8 * 6, device=dev())
+    assert lib.clbm_adjoint_segment(lat.h, st.data_ptr(), None, 1, la.data_ptr(), lb.data_ptr(),
+                                    gf.data_ptr()) == _capi.CLBM_ERR_STATE
     plain = Lattice(16, 8, 6, 0.05, device=dev())
     assert plain.lib.clbm_slab_step(plain.h, 0) == _capi.CLBM_ERR_ARG
     lat.close()
@@ -372,3 +377,81 @@ def test_full_size_slab_rank_sampled_first_step(storage):
         hg = fs.reshape(19, -1)[:, torch.from_numpy(nodes).to(dev())].double().cpu().numpy().T
         fo = oracle.first_step_nodes(o, nodes, None, u0, synthetic.profile_to_field(prof, shape))
         assert np.max(np.abs(hg + W19.reshape(1, 19) - fo) / np.abs(fo)) < 1e-6
+
+
+ADJ_CASES = [
+    # (nx, ny, nz, walls, ranges, periodic z)
+    (24, 16, 12, 0, [(0, 5), (5, 6), (6, 12)], True),  # a one-plane slab
+    (20, 12, 10, 3, [(0, 4), (4, 10)], False),         # x and y walls, z walls at the ends
+]
+
+
+@pytest.mark.parametrize("case", ADJ_CASES, ids=lambda c: f"w{c[3]}s{len(c[4])}{'p' if c[5] else ''}")
+def test_slab_adjoint_equals_undivided(case):
+    """The adjoint across slabs (the reverse-direction halo): slabs stepped
+    forward with face exchanges, then seeded from a cotangent on the final
+    velocity and stepped back with the adjoint faces exchanged after every
+    adjoint step, give bit for bit the undivided lattice's lambda^0 and dL/dF.
+    The same holds with the slab states recomputed from state 0 by step_raw
+    and the state-face exchange."""
+    nx, ny, nz, walls, ranges, periodic = case
+    if not periodic:
+        walls |= 4
+    shape = (nz, ny, nx)
+    u0, F = _inputs(shape, 31)
+    gu = synthetic.gaussian_force(shape, 1e-2, seed=33)
+    K = 6
+    g = Lattice(nx, ny, nz, 0.04, walls=walls, device=dev(), **RATES)
+    g.set_force_field(t(F))
+    g.init_equilibrium(None, t(u0))
+    states = [g.export_state().clone()]
+    for _ in range(K):
+        g.step(1)
+        states.append(g.export_state().clone())
+    lam, lam2 = g.empty_lam(), g.empty_lam()
+    gF = torch.zeros((3,) + shape, device=dev())
+    g.adjoint_seed(t(gu), lam, gF, state=states[K])
+    for k in range(K - 1, -1, -1):
+        g.adjoint_step(states[k], lam, lam2, gF)
+        lam, lam2 = lam2, lam
+    ref_lam, ref_gF = lam.view(19, nz, ny, nx).cpu(), gF.cpu()
+    g.close()
+
+    lats, keep = _make_slabs(nx, ny, nz, walls, "f32", u0, F, ranges, periodic)
+    saved = [[lat.export_state().clone()] for lat in lats]
+    for _ in range(K):
+        for lat in lats:
+            lat.slab_step()
+        _exchange_all(lats)
+        for r, lat in enumerate(lats):
+            saved[r].append(lat.export_state().clone())
+    # the same states recomputed from state 0
+    recomputed = [[st[0]] for st in saved]
+    for _ in range(K):
+        outs = [torch.empty_like(st[0]) for st in saved]
+        for r, lat in enumerate(lats):
+            lat.step_raw(recomputed[r][-1], outs[r])
+        _exchange_all(lats, [slabs.state_faces(lat, o) for lat, o in zip(lats, outs)])
+        for r in range(len(lats)):
+            recomputed[r].append(outs[r])
+
+    for tape in (saved, recomputed):
+        lam_s = [lat.empty_lam() for lat in lats]
+        lam2_s = [lat.empty_lam() for lat in lats]
+        gF_s = [torch.zeros((3, z1 - z0, ny, nx), device=dev()) for z0, z1 in ranges]
+        for r, (lat, (z0, z1)) in enumerate(zip(lats, ranges)):
+            lat.adjoint_seed(t(np.ascontiguousarray(gu[:, z0:z1])), lam_s[r], gF_s[r], state=tape[r][K])
+        _exchange_all(lats, [slabs.lam_faces(lat, a) for lat, a in zip(lats, lam_s)])
+        for k in range(K - 1, -1, -1):
+            for r, lat in enumerate(lats):
+                lat.adjoint_step(tape[r][k], lam_s[r], lam2_s[r], gF_s[r])
+            _exchange_all(lats, [slabs.lam_faces(lat, a) for lat, a in zip(lats, lam2_s)])
+            lam_s, lam2_s = lam2_s, lam_s
+        got_lam = torch.cat([a[:19 * (z1 - z0) * ny * nx].view(19, z1 - z0, ny, nx).cpu()
+                             for a, (z0, z1) in zip(lam_s, ranges)], dim=1)
+        got_gF = torch.cat([a.cpu() for a in gF_s], dim=1)
+        assert torch.equal(got_lam, ref_lam)
+        assert torch.equal(got_gF, ref_gF)
+    for lat in lats:
+        lat.check()
+        lat.close()
