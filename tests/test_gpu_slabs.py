@@ -455,3 +455,69 @@ def test_slab_adjoint_equals_undivided(case):
     for lat in lats:
         lat.check()
         lat.close()
+
+
+def _adjoint_rank_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    nx, ny, nz, K = 20, 12, 10, 5
+    shape = (nz, ny, nx)
+    u0, F = _inputs(shape, 41)
+    gu = synthetic.gaussian_force(shape, 1e-2, seed=43)
+    z0, nzl, bits = slabs.slab_of(nz, rank, world, periodic_z=True)
+    lat = Lattice(nx, ny, nzl, 0.04, walls=2, device=dev(), slab=bits, z0=z0, **RATES)
+    Fs = t(np.ascontiguousarray(F[:, z0:z0 + nzl]))
+    lat.set_force_field(Fs)
+    lat.init_equilibrium(None, t(np.ascontiguousarray(u0[:, z0:z0 + nzl])))
+    states = [lat.export_state().clone()]
+    for _ in range(K):
+        lat.slab_step()
+        slabs.exchange_faces(lat, rank, world, dist, host=True)
+        states.append(lat.export_state().clone())
+    lam, lam2 = lat.empty_lam(), lat.empty_lam()
+    gF = torch.zeros((3, nzl, ny, nx), device=dev())
+    lat.adjoint_seed(t(np.ascontiguousarray(gu[:, z0:z0 + nzl])), lam, gF, state=states[K])
+    slabs.exchange_adjoint_faces(lat, lam, rank, world, dist, host=True)
+    for k in range(K - 1, -1, -1):
+        lat.adjoint_step(states[k], lam, lam2, gF)
+        slabs.exchange_adjoint_faces(lat, lam2, rank, world, dist, host=True)
+        lam, lam2 = lam2, lam
+    torch.save((lam[:19 * nzl * ny * nx].view(19, nzl, ny, nx).cpu(), gF.cpu()), f"{out_path}.{rank}")
+    lat.check()
+    lat.close()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_processes_adjoint_matches_the_undivided_lattice(tmp_path):
+    """The slab adjoint across two rank processes on the one GPU, forward and
+    adjoint faces exchanged over gloo through host memory: lambda^0 and dL/dF
+    equal the undivided lattice's bit for bit."""
+    out = str(tmp_path / "adj")
+    mp.start_processes(_adjoint_rank_worker, args=(2, _free_port(), out), nprocs=2, start_method="spawn",
+                       join=True)
+    parts = [torch.load(f"{out}.{r}") for r in range(2)]
+    got_lam = torch.cat([p[0] for p in parts], dim=1)
+    got_gF = torch.cat([p[1] for p in parts], dim=1)
+    nx, ny, nz, K = 20, 12, 10, 5
+    shape = (nz, ny, nx)
+    u0, F = _inputs(shape, 41)
+    gu = synthetic.gaussian_force(shape, 1e-2, seed=43)
+    g = Lattice(nx, ny, nz, 0.04, walls=2, device=dev(), **RATES)
+    g.set_force_field(t(F))
+    g.init_equilibrium(None, t(u0))
+    states = [g.export_state().clone()]
+    for _ in range(K):
+        g.step(1)
+        states.append(g.export_state().clone())
+    lam, lam2 = g.empty_lam(), g.empty_lam()
+    gF = torch.zeros((3,) + shape, device=dev())
+    g.adjoint_seed(t(gu), lam, gF, state=states[K])
+    for k in range(K - 1, -1, -1):
+        g.adjoint_step(states[k], lam, lam2, gF)
+        lam, lam2 = lam2, lam
+    assert torch.equal(got_lam, lam.view(19, nz, ny, nx).cpu())
+    assert torch.equal(got_gF, gF.cpu())
+    g.close()
