@@ -46,6 +46,36 @@ def neighbours(rank: int, world: int) -> Tuple[int, int]:
     return (rank - 1) % world, (rank + 1) % world
 
 
+def _sum_over_ranks(v: torch.Tensor, dist) -> torch.Tensor:
+    """In-place sum of an FP64 tensor over the ranks of the default group (the
+    device tensor itself with NCCL, a host copy with gloo); unchanged with one
+    rank or dist None."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return v
+    if dist.get_backend() == "nccl":
+        dist.all_reduce(v)
+        return v
+    h = v.cpu()
+    dist.all_reduce(h)
+    v.copy_(h)
+    return v
+
+
+def global_moments(lat, dist=None) -> torch.Tensor:
+    """FP64 [total mass, total momentum x, y, z] (Eq. 9) of the whole lattice:
+    this slab's sums (reduce_moments, exact fixed-point totals) added over the
+    ranks by an FP64 all-reduce."""
+    return _sum_over_ranks(lat.reduce_moments(), dist)
+
+
+def global_pair(lat, a: torch.Tensor, b: torch.Tensor = None, dist=None) -> torch.Tensor:
+    """FP64 [sum (a-b)^2, sum b^2, sum a b] over the whole lattice, for fields
+    split across the slabs like the populations (L2 error norms, the dot
+    products of a finite-difference check): reduce_pair on this slab's part,
+    added over the ranks by an FP64 all-reduce."""
+    return _sum_over_ranks(lat.reduce_pair(a, b), dist)
+
+
 def exchange_planes(local: torch.Tensor, rank: int, world: int, dist) -> Tuple[torch.Tensor, torch.Tensor]:
     """Send the bottom plane down and the top plane up; return (ghost_below,
     ghost_above): the upper plane of the lower neighbour and the lower plane of

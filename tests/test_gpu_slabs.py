@@ -284,6 +284,11 @@ def _rank_worker(rank, world, port, out_path, walls, storage, periodic):
         lat.slab_step()
         slabs.exchange_faces(lat, rank, world, dist, host=True)
     torch.save(lat.populations(deviation=True).cpu(), f"{out_path}.{rank}")
+    # whole-lattice FP64 totals and an L2 error of the velocity, summed over the ranks
+    target = t(np.ascontiguousarray(synthetic.divfree_velocity(shape, seed=14, umax=0.01)[:, z0:z0 + nzl]))
+    _, u = lat.macros()
+    torch.save((slabs.global_moments(lat, dist).cpu(), slabs.global_pair(lat, u, target, dist).cpu()),
+               f"{out_path}.sums.{rank}")
     lat.check()
     lat.close()
     dist.barrier()
@@ -304,7 +309,19 @@ def test_two_rank_processes_match_the_undivided_lattice(tmp_path, case):
                        start_method="spawn", join=True)
     got = torch.cat([torch.load(f"{out}.{r}") for r in range(2)], dim=1)
     u0, F = _inputs((NZ, NY, NX), 13)
-    assert torch.equal(got, _undivided(NX, NY, NZ, walls, storage, u0, F, STEPS))
+    ref = _undivided(NX, NY, NZ, walls, storage, u0, F, STEPS)
+    assert torch.equal(got, ref)
+    g = Lattice(NX, NY, NZ, 0.04, walls=walls, storage=storage, device=dev(), **RATES)
+    g.set_force_field(t(F))
+    g.set_populations(ref.to(dev()), deviation=True)
+    _, u = g.macros()
+    target = t(synthetic.divfree_velocity((NZ, NY, NX), seed=14, umax=0.01))
+    m_ref, p_ref = g.reduce_moments().cpu(), g.reduce_pair(u, target).cpu()
+    g.close()
+    for r in range(2):
+        m, pr = torch.load(f"{out}.sums.{r}")
+        np.testing.assert_allclose(m.numpy(), m_ref.numpy(), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(pr.numpy(), p_ref.numpy(), rtol=1e-12, atol=1e-12)
 
 
 @pytest.mark.parametrize("scaling", ["weak", "strong"])

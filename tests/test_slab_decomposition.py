@@ -145,3 +145,49 @@ def test_slab_of_partitions_and_flags_faces():
     assert slabs.slab_of(10, 2, 3, periodic_z=False) == (7, 3, 1)
     assert slabs.slab_of(10, 0, 3, periodic_z=False) == (0, 4, 2)
     assert slabs.slab_of(5, 0, 1, periodic_z=False) == (0, 5, 0)
+
+
+class _FakeSums:
+    """Stands in for a slab lattice's FP64 reductions (rank-dependent values)."""
+
+    def __init__(self, rank):
+        self.rank = rank
+
+    def reduce_moments(self):
+        return torch.tensor([1.0 + self.rank, 0.5 * self.rank, -2.0 ** -40 * self.rank, 3.0], dtype=torch.float64)
+
+    def reduce_pair(self, a, b=None):
+        d = (a - b) if b is not None else a
+        return torch.stack([(d.double() ** 2).sum(), (b.double() ** 2).sum() if b is not None else
+                            torch.zeros((), dtype=torch.float64), (a.double() * b.double()).sum()
+                            if b is not None else torch.zeros((), dtype=torch.float64)])
+
+
+def _sums_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    lat = _FakeSums(rank)
+    a = torch.arange(6, dtype=torch.float32) + rank
+    b = torch.ones(6, dtype=torch.float32) * (rank - 1)
+    torch.save((slabs.global_moments(lat, dist), slabs.global_pair(lat, a, b, dist)), f"{out_path}.{rank}")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_global_sums_add_every_rank(tmp_path):
+    """The FP64 all-reduce behind the global mass/momentum and error norms of
+    a slab decomposition (gloo, 3 ranks): every rank ends with the sum of all
+    ranks' values; without a process group the slab's own values come back."""
+    world = 3
+    out = str(tmp_path / "sums")
+    mp.start_processes(_sums_worker, args=(world, _free_port(), out), nprocs=world, start_method="spawn",
+                       join=True)
+    want_m = sum(_FakeSums(r).reduce_moments() for r in range(world))
+    want_p = sum(_FakeSums(r).reduce_pair(torch.arange(6, dtype=torch.float32) + r,
+                                         torch.ones(6, dtype=torch.float32) * (r - 1)) for r in range(world))
+    for r in range(world):
+        m, pr = torch.load(f"{out}.{r}")
+        assert torch.equal(m, want_m)
+        assert torch.allclose(pr, want_p, rtol=0, atol=0)
+    assert torch.equal(slabs.global_moments(_FakeSums(2)), _FakeSums(2).reduce_moments())
