@@ -20,10 +20,10 @@ __device__ __forceinline__ void force_node(const ForceArgs &F, const Geom &g, in
     fz *= F.scale;
 }
 
-__device__ __forceinline__ bool node_of(const Geom &g, int &x, int &y, int &z) {
+__device__ __forceinline__ bool node_of(const Geom &g, int &x, int &y, int &z, int z0 = 0) {
     x = blockIdx.x * blockDim.x + threadIdx.x;
     y = blockIdx.y * blockDim.y + threadIdx.y;
-    z = blockIdx.z;
+    z = z0 + (int)blockIdx.z;
     return x < g.nx && y < g.ny;
 }
 
@@ -87,9 +87,9 @@ __global__ void k_scatter(S *dst, Geom g, int map, const float *__restrict__ f, 
 
 template <typename S, int FM, bool WALLS>
 __global__ void k_init_eq(S *dst, Geom g, int map, const float *__restrict__ rho, const float *__restrict__ u,
-                          int64_t n, ForceArgs F) {
+                          int64_t n, ForceArgs F, int z0) {
     int x, y, z;
-    if (!node_of(g, x, y, z)) return;
+    if (!node_of(g, x, y, z, z0)) return;
     const uint32_t self = ((uint32_t)z * g.ny + y) * g.nx + x;
     const float r = rho ? rho[self] : 1.0f;
     float fx, fy, fz;
@@ -115,9 +115,9 @@ __global__ void k_gather(const S *src, Geom g, int map, float *__restrict__ f, i
 
 template <typename S, int FM, bool WALLS>
 __global__ void k_macros(const S *src, Geom g, int map, ForceArgs F, float *__restrict__ rho,
-                         float *__restrict__ u, int64_t n) {
+                         float *__restrict__ u, int64_t n, int z0) {
     int x, y, z;
-    if (!node_of(g, x, y, z)) return;
+    if (!node_of(g, x, y, z, z0)) return;
     float h[kQ];
     const uint32_t self = pull_node<S, WALLS>(src, g, x, y, z, map, h);
     float fx, fy, fz, jx, jy, jz;
@@ -216,10 +216,25 @@ cudaError_t launch_scatter(int storage, const Launch &L, void *dst, const float 
     return cudaGetLastError();
 }
 
+// The planes L.z0 .. L.z0 + L.nplanes - 1 of the init and read-out kernels
+// (all planes when nplanes < 0): the launch's grid and first plane.
+static dim3 plane_grid(const Launch &L, int &z0) {
+    dim3 grid = L.grid;
+    z0 = 0;
+    if (L.nplanes >= 0) {
+        grid.z = (unsigned)L.nplanes;
+        z0 = L.z0;
+    }
+    return grid;
+}
+
 template <typename S, int FM>
 static void init_t(const Launch &L, void *dst, const float *rho, const float *u, int64_t n, const ForceArgs &F) {
-    if (L.g.walls) k_init_eq<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((S *)dst, L.g, L.map, rho, u, n, F);
-    else k_init_eq<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((S *)dst, L.g, L.map, rho, u, n, F);
+    int z0;
+    const dim3 grid = plane_grid(L, z0);
+    if (grid.z == 0) return;
+    if (L.g.walls) k_init_eq<S, FM, true><<<grid, L.block, 0, L.stream>>>((S *)dst, L.g, L.map, rho, u, n, F, z0);
+    else k_init_eq<S, FM, false><<<grid, L.block, 0, L.stream>>>((S *)dst, L.g, L.map, rho, u, n, F, z0);
 }
 
 cudaError_t launch_init_eq(int storage, const Launch &L, void *dst, const float *rho, const float *u, int64_t n,
@@ -244,8 +259,13 @@ cudaError_t launch_gather(int storage, const Launch &L, const void *src, float *
 
 template <typename S, int FM>
 static void macros_t(const Launch &L, const void *src, const ForceArgs &F, float *rho, float *u, int64_t n) {
-    if (L.g.walls) k_macros<S, FM, true><<<L.grid, L.block, 0, L.stream>>>((const S *)src, L.g, L.map, F, rho, u, n);
-    else k_macros<S, FM, false><<<L.grid, L.block, 0, L.stream>>>((const S *)src, L.g, L.map, F, rho, u, n);
+    int z0;
+    const dim3 grid = plane_grid(L, z0);
+    if (grid.z == 0) return;
+    if (L.g.walls)
+        k_macros<S, FM, true><<<grid, L.block, 0, L.stream>>>((const S *)src, L.g, L.map, F, rho, u, n, z0);
+    else
+        k_macros<S, FM, false><<<grid, L.block, 0, L.stream>>>((const S *)src, L.g, L.map, F, rho, u, n, z0);
 }
 
 cudaError_t launch_macros(int storage, const Launch &L, const void *src, const ForceArgs &F, float *rho, float *u,

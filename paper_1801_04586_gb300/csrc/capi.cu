@@ -61,6 +61,10 @@ clbm::Range::Range(const char *name) {
 
 clbm::Range::~Range() { nvtxDomainRangePop(nvtx_domain()); }
 
+// clbm_run_host moves its host input and output in this many plane chunks, so
+// that each chunk's initialisation or read-out runs beside the next copy.
+constexpr int kIoChunks = 8;
+
 struct clbm_ctx {
     clbm_params p;
     Geom g;
@@ -91,6 +95,8 @@ struct clbm_ctx {
     cudaStream_t cap_stream;   // private stream for graph capture (first use)
     cudaGraphExec_t graph;     // kGraphSteps steps from phase 0; null until built, dropped when the force changes
     bool slab_pending;         // z-slab: CLBM_SLAB_FACES done, CLBM_SLAB_INTERIOR not yet
+    cudaStream_t io_stream;    // clbm_run_host: host copies in plane chunks beside init / read-out (first use)
+    cudaEvent_t io_ev[kIoChunks];
 };
 
 namespace {
@@ -408,6 +414,11 @@ int clbm_destroy(clbm_ctx *c) {
         cudaStreamDestroy(c->copy_stream);
         cudaEventDestroy(c->ev_step);
         cudaEventDestroy(c->ev_copy);
+    }
+    if (c->io_stream) {
+        cudaStreamSynchronize(c->io_stream);
+        cudaStreamDestroy(c->io_stream);
+        for (int k = 0; k < kIoChunks; ++k) cudaEventDestroy(c->io_ev[k]);
     }
     cudaFree(c->buf[0]);
     cudaFree(c->d_flag);
@@ -765,12 +776,65 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     }
     float *d_rho = c->d_io, *d_u = c->d_io + c->n;
     const size_t nb = sizeof(float) * (size_t)c->n;
-    if (rho_h && (e = cudaMemcpyAsync(d_rho, rho_h, nb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
-        return cuda_fail(e, "clbm_run_host: copy rho");
-    if (u_h && (e = cudaMemcpyAsync(d_u, u_h, 3 * nb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
-        return cuda_fail(e, "clbm_run_host: copy u");
-    int rc = clbm_init_equilibrium(c, rho_h ? d_rho : nullptr, u_h ? d_u : nullptr);
-    if (rc != CLBM_OK) return rc;
+    // D3Q19: the host input travels in plane chunks on io_stream, and each chunk's
+    // initialisation runs on the step stream once it has landed (a node's
+    // initialisation reads only its own rho, u); the same for the read-out below.
+    const bool chunked = c->q == 19;
+    if (chunked && !c->io_stream) {
+        cudaStream_t s = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "clbm_run_host: io stream");
+        for (int k = 0; k < kIoChunks; ++k) {
+            if ((e = cudaEventCreateWithFlags(&c->io_ev[k], cudaEventDisableTiming)) != cudaSuccess) {
+                for (int j = 0; j < k; ++j) cudaEventDestroy(c->io_ev[j]);
+                cudaStreamDestroy(s);
+                return cuda_fail(e, "clbm_run_host: io events");
+            }
+        }
+        c->io_stream = s;
+    }
+    const int64_t plane = (int64_t)c->g.nx * c->g.ny;
+    const int nch = std::min(c->g.nz, kIoChunks);
+    auto chunk = [&](int k, int64_t &z0, int64_t &z1) {
+        z0 = (int64_t)c->g.nz * k / nch;
+        z1 = (int64_t)c->g.nz * (k + 1) / nch;
+    };
+    int rc = CLBM_OK;
+    if (chunked) {
+        if (c->slab_pending) return fail(CLBM_ERR_STATE, "clbm_run_host: a split slab step is pending");
+        c->steps_done = 0;  // as clbm_init_equilibrium
+        const Launch L0 = launch_of(c);
+        const ForceArgs F0 = force_at_zero(c);
+        // d_io may still be read by the step stream (an earlier job's read-out)
+        if ((e = cudaEventRecord(c->io_ev[0], c->stream)) == cudaSuccess)
+            e = cudaStreamWaitEvent(c->io_stream, c->io_ev[0], 0);
+        for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+            int64_t z0, z1;
+            chunk(k, z0, z1);
+            const int64_t off = z0 * plane;
+            const size_t bytes = sizeof(float) * (size_t)((z1 - z0) * plane);
+            if (rho_h) e = cudaMemcpyAsync(d_rho + off, rho_h + off, bytes, cudaMemcpyHostToDevice, c->io_stream);
+            for (int a = 0; a < 3 && u_h && e == cudaSuccess; ++a)
+                e = cudaMemcpyAsync(d_u + a * c->n + off, u_h + a * c->n + off, bytes, cudaMemcpyHostToDevice,
+                                    c->io_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(c->io_ev[k], c->io_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->io_ev[k], 0);
+            Launch Lk = L0;
+            Lk.z0 = (int)z0;
+            Lk.nplanes = (int)(z1 - z0);
+            if (e == cudaSuccess)
+                e = launch_init_eq(c->p.storage, Lk, c->buf[c->cur], rho_h ? d_rho : nullptr, u_h ? d_u : nullptr,
+                                   c->n, F0);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: chunked copy and initialisation");
+    } else {
+        if (rho_h && (e = cudaMemcpyAsync(d_rho, rho_h, nb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+            return cuda_fail(e, "clbm_run_host: copy rho");
+        if (u_h && (e = cudaMemcpyAsync(d_u, u_h, 3 * nb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+            return cuda_fail(e, "clbm_run_host: copy u");
+        rc = clbm_init_equilibrium(c, rho_h ? d_rho : nullptr, u_h ? d_u : nullptr);
+        if (rc != CLBM_OK) return rc;
+    }
     const bool fused = c->q == 19 && !c->aa && c->model == CLBM_MODEL_CASCADED;
     if (fused && moments_h && !c->copy_stream) {
         cudaStream_t cs = nullptr;
@@ -850,12 +914,41 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         e = cudaMemcpyAsync(moments_h + 4 * nsteps, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: moments");
     }
-    if ((rho_out || u_out) && (rc = clbm_get_macros(c, rho_out ? d_rho : nullptr, u_out ? d_u : nullptr)) != CLBM_OK)
-        return rc;
-    if (rho_out && (e = cudaMemcpyAsync(rho_out, d_rho, nb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
-        return cuda_fail(e, "clbm_run_host: copy rho back");
-    if (u_out && (e = cudaMemcpyAsync(u_out, d_u, 3 * nb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
-        return cuda_fail(e, "clbm_run_host: copy u back");
+    if (chunked && (rho_out || u_out)) {
+        // each chunk's read-out, then its copies back on io_stream beside the next chunk's read-out
+        const Launch L1 = launch_of(c);
+        const ForceArgs F1 = force_now(c);
+        for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+            int64_t z0, z1;
+            chunk(k, z0, z1);
+            const int64_t off = z0 * plane;
+            const size_t bytes = sizeof(float) * (size_t)((z1 - z0) * plane);
+            Launch Lk = L1;
+            Lk.z0 = (int)z0;
+            Lk.nplanes = (int)(z1 - z0);
+            e = launch_macros(c->p.storage, Lk, c->buf[c->cur], F1, rho_out ? d_rho : nullptr, u_out ? d_u : nullptr,
+                              c->n);
+            if (e == cudaSuccess) e = cudaEventRecord(c->io_ev[k], c->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->io_stream, c->io_ev[k], 0);
+            if (e == cudaSuccess && rho_out)
+                e = cudaMemcpyAsync(rho_out + off, d_rho + off, bytes, cudaMemcpyDeviceToHost, c->io_stream);
+            for (int a = 0; a < 3 && u_out && e == cudaSuccess; ++a)
+                e = cudaMemcpyAsync(u_out + a * c->n + off, d_u + a * c->n + off, bytes, cudaMemcpyDeviceToHost,
+                                    c->io_stream);
+        }
+        // the step stream ends after the copies (its synchronisation below covers them)
+        if (e == cudaSuccess) e = cudaEventRecord(c->io_ev[0], c->io_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->io_ev[0], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: chunked read-out and copies back");
+    } else {
+        if ((rho_out || u_out) &&
+            (rc = clbm_get_macros(c, rho_out ? d_rho : nullptr, u_out ? d_u : nullptr)) != CLBM_OK)
+            return rc;
+        if (rho_out && (e = cudaMemcpyAsync(rho_out, d_rho, nb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+            return cuda_fail(e, "clbm_run_host: copy rho back");
+        if (u_out && (e = cudaMemcpyAsync(u_out, d_u, 3 * nb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+            return cuda_fail(e, "clbm_run_host: copy u back");
+    }
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e, "clbm_run_host");
     if (moments_h)
         for (int64_t t = 0; t <= nsteps; ++t)

@@ -105,6 +105,11 @@ def test_run_host_job_matches_device_path():
     assert torch.equal(r_out, r_ref.cpu())
     assert torch.equal(u_out, u_ref.cpu())
     assert torch.equal(mom[-4:], m_ref)
+    # a second job on the same context (its host copies and read-out run in plane chunks on a second stream)
+    r_out2, u_out2 = torch.zeros(shape).pin_memory(), torch.zeros((3,) + shape).pin_memory()
+    mom_b = torch.empty_like(mom).pin_memory()
+    g2.run_host(rho_h, u_h, steps, r_out2, u_out2, mom_b)
+    assert torch.equal(r_out2, r_out) and torch.equal(u_out2, u_out) and torch.equal(mom_b, mom)
     # per-step sums formed inside the step kernels are exact fixed-point sums of
     # the same per-node values as clbm_reduce_moments: equal bit for bit
     g3, _ = make_pair(nx, ny, nz, 0.05, walls=4)
