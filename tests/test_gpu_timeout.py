@@ -16,15 +16,19 @@ from paper_1801_04586_gb300 import CLBMError, Lattice, _capi, synthetic
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("storage", ["f16", "bf16sr"])
-def test_wait_that_runs_out_reports_timeout_and_the_device_recovers(storage):
+@pytest.mark.parametrize("storage,pattern,steps", [("f16", "ab", 1), ("bf16sr", "ab", 1), ("f16", "aa", 1),
+                                                    ("f16sr", "aa", 2)])
+def test_wait_that_runs_out_reports_timeout_and_the_device_recovers(storage, pattern, steps):
+    """A/B and both in-place kinds (steps = 2: the even then the odd kind,
+    each with its first tile's copies withheld)."""
     nx, ny, nz = 64, 48, 24
     u0 = t(synthetic.divfree_velocity((nz, ny, nx), seed=17, umax=0.02))
-    lat = Lattice(nx, ny, nz, 0.05, storage=storage, device=dev(), wait_cycles=2_000_000,
+    lat = Lattice(nx, ny, nz, 0.05, storage=storage, pattern=pattern, device=dev(), wait_cycles=2_000_000,
                   inject=_capi.INJECT_DROP_COPY)
     assert lat.info()["staged"] == 1
     lat.init_equilibrium(None, u0)
-    lat.step(1)
+    for _ in range(steps):
+        lat.step(1)
     torch.cuda.synchronize()  # the kernel returned by itself
     with pytest.raises(CLBMError) as err:
         lat.check(clear=True)
