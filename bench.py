@@ -383,6 +383,8 @@ def compact(variants):
         elif name.startswith("batched"):
             out[name] = {"graph": round(v["graph_mlups"]), "per_domain": round(v["per_domain_mlups"]),
                          "frac": round(v["graph_frac"], 3)}
+            if "aa_graph_mlups" in v:
+                out[name]["aa_graph"] = round(v["aa_graph_mlups"])
         else:
             out[name] = v
     return out
@@ -497,6 +499,20 @@ def bench_batch(dev, steps, peak, ndomains=64):
     b.check()
     b.close()
     out["graph_vs_per_domain"] = out["graph_mlups"] / out["per_domain_mlups"]
+    # the same batch in place (one buffer), graph mode
+    a = Batch(doms, device=dev, pattern="aa")
+    a.init_equilibrium()
+    a.autotune(trial_steps=10)
+    a.step(32, Batch.GRAPH)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record(a.stream)
+    a.step(steps, Batch.GRAPH)
+    e1.record(a.stream)
+    torch.cuda.synchronize()
+    a.check()
+    a.close()
+    out["aa_graph_mlups"] = nodes * steps / (e0.elapsed_time(e1) * 1e-3) / 1e6
     out["graph_gbs"] = BYTES_PER_NODE * out["graph_mlups"] * 1e6 / 1e9
     out["graph_frac"] = out["graph_gbs"] / peak
     return out

@@ -478,6 +478,8 @@ typedef struct clbm_batch_info {
     int64_t total_nodes;
     int64_t state_bytes;   /* both buffers: 2 x state_bytes are allocated */
     int64_t steps_done;
+    int32_t pattern;       /* CLBM_PATTERN_AB or CLBM_PATTERN_AA */
+    int32_t buffers;       /* population buffers allocated: 2 (A/B) or 1 (in place) */
 } clbm_batch_info;
 
 /* Step modes of clbm_batch_step. */
@@ -493,6 +495,13 @@ typedef struct clbm_batch clbm_batch;
  * CLBM_ERR_OOM, CLBM_ERR_CUDA. */
 int clbm_batch_create(const clbm_domain *domains, int32_t ndomains, int32_t storage, void *stream,
                       clbm_batch **out);
+/* The same with a storage pattern: CLBM_PATTERN_AB (what clbm_batch_create
+ * makes) or CLBM_PATTERN_AA, one population buffer per domain updated in
+ * place by alternating even and odd steps (as clbm_params.pattern): half the
+ * memory, the same bits. clbm_batch_autotune then keeps a temporary copy of
+ * the state for its trials. */
+int clbm_batch_create_pattern(const clbm_domain *domains, int32_t ndomains, int32_t storage, int32_t pattern,
+                              void *stream, clbm_batch **out);
 int clbm_batch_destroy(clbm_batch *b);
 int clbm_batch_get_info(const clbm_batch *b, clbm_batch_info *info);
 /* Rebuild the work list for another block size (threads per block and

@@ -53,7 +53,8 @@ class Domain(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("ndomains", ctypes.c_int32), ("ntiles", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
-                ("total_nodes", ctypes.c_int64), ("state_bytes", ctypes.c_int64), ("steps_done", ctypes.c_int64)]
+                ("total_nodes", ctypes.c_int64), ("state_bytes", ctypes.c_int64), ("steps_done", ctypes.c_int64),
+                ("pattern", ctypes.c_int32), ("buffers", ctypes.c_int32)]
 
 
 BATCH_GRAPH, BATCH_DIRECT, BATCH_PER_DOMAIN = 0, 1, 2
@@ -103,6 +104,7 @@ SIGNATURES = {
     "clbm_slab_step": [P, I32],
     "clbm_slab_faces": [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64)],
     "clbm_batch_create": [P, I32, I32, P, ctypes.POINTER(P)],
+    "clbm_batch_create_pattern": [P, I32, I32, I32, P, ctypes.POINTER(P)],
     "clbm_batch_destroy": [P],
     "clbm_batch_get_info": [P, P],
     "clbm_batch_set_tile": [P, I32],

@@ -21,7 +21,9 @@ class Batch:
 
     GRAPH, DIRECT, PER_DOMAIN = _capi.BATCH_GRAPH, _capi.BATCH_DIRECT, _capi.BATCH_PER_DOMAIN
 
-    def __init__(self, domains: List[dict], storage: str = "f32", device=None):
+    def __init__(self, domains: List[dict], storage: str = "f32", device=None, pattern: str = "ab"):
+        """pattern "ab": two population buffers; "aa": one, updated in place by
+        alternating even and odd steps (half the memory, the same bits)."""
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required: the batch runs only in libclbm.so's kernels")
         self.lib = _capi.lib()
@@ -37,9 +39,10 @@ class Batch:
         with torch.cuda.device(self.device):
             self.stream = torch.cuda.current_stream(self.device)
             h = ctypes.c_void_p()
-            check(self.lib.clbm_batch_create(arr, len(domains), _capi.STORAGE[storage],
-                                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
-                  "clbm_batch_create")
+            check(self.lib.clbm_batch_create_pattern(arr, len(domains), _capi.STORAGE[storage],
+                                                     _capi.PATTERN[pattern],
+                                                     ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+                  "clbm_batch_create_pattern")
         self.h = h
 
     def close(self):

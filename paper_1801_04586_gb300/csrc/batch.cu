@@ -106,6 +106,66 @@ __global__ void __launch_bounds__(512) k_batch_step(const S *__restrict__ A, S *
     }
 }
 
+// The in-place (AA) pattern over the batch: every domain's one population
+// array, even and odd step kinds as k_step_aa (step_kernels.cuh): the even
+// kind reads a node's own slots and writes population i into the slot of
+// ibar; the odd kind reads (ibar, x - e_i), or (i, x) across a wall, and writes
+// population i to (i, x + e_i), or (ibar, x) across a wall. The same tiles,
+// domain table and collision as k_batch_step, so the batch stores the bits of
+// the A/B batch and of each domain stepped alone.
+template <typename S, bool SMEM, bool ODD>
+__global__ void __launch_bounds__(512) k_batch_step_aa(S *A, const DomainDesc *__restrict__ doms, int ndom,
+                                                       const int4 *__restrict__ tiles, int ntiles,
+                                                       int *__restrict__ flag) {
+    extern __shared__ DomainDesc sdom[];
+    if (SMEM) {
+        for (int i = threadIdx.x; i < ndom; i += blockDim.x) sdom[i] = doms[i];
+        __syncthreads();
+    }
+    int t = blockIdx.x;
+    if (t >= ntiles) return;
+    int4 tile = __ldg(tiles + t);
+    for (; t < ntiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        const int4 next = tn < ntiles ? __ldg(tiles + tn) : tile;
+        const DomainDesc *D = SMEM ? sdom + tile.x : doms + tile.x;
+        const Geom g = D->g;
+        const int xt = tile.y + (int)threadIdx.x;
+        const int cy = (int)(((float)xt + 0.5f) * D->inv_nx);
+        const int yt = tile.z + cy;
+        const int cz = (int)(((float)yt + 0.5f) * D->inv_ny);
+        const int x = xt - cy * g.nx, y = yt - cz * g.ny, z = tile.w + cz;
+        if (z < g.nz) {
+            S *f = A + D->offset;
+            const uint32_t self = ((uint32_t)z * g.ny + y) * g.nx + x;
+            float h[kQ];
+            if (ODD) {
+                uint32_t off[kQ];
+                int pop[kQ];
+                pull_sources<true, true>(g, x, y, z, off, pop);
+#pragma unroll
+                for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(f + CLBM_IDX(g, (size_t)pop[i] * g.stride + off[i]));
+                const float drho = collide<sizeof(S) == 2>(h, D->fx, D->fy, D->fz, D->r);
+                if (!(fabsf(drho) < 0.9f)) *flag = 1;
+                // the push targets from coordinates the compiler must treat as new (as in k_step_aa)
+                int xs = x, ys = y, zs = z;
+                asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs) : "f"(h[0]), "f"(h[kQ - 1]));
+                push_targets<true>(g, xs, ys, zs, off, pop);
+                store_each<S, kQ>(h, self, 0u,
+                                  [&](int i) { return f + CLBM_IDX(g, (size_t)pop[i] * g.stride + off[i]); });
+            } else {
+#pragma unroll
+                for (int i = 0; i < kQ; ++i) h[i] = Codec<S>::load(f + CLBM_IDX(g, (size_t)i * g.stride + self));
+                const float drho = collide<sizeof(S) == 2>(h, D->fx, D->fy, D->fz, D->r);
+                if (!(fabsf(drho) < 0.9f)) *flag = 1;
+                store_each<S, kQ>(h, self, 0u,
+                                  [&](int i) { return f + CLBM_IDX(g, (size_t)opposite(i) * g.stride + self); });
+            }
+        }
+        tile = next;
+    }
+}
+
 constexpr int kSmemDomains = 512;  // domain tables up to this size are staged in shared memory
 
 template <typename S>
@@ -117,6 +177,29 @@ static cudaError_t batch_launch_t(const void *A, void *B, const DomainDesc *doms
     else
         k_batch_step<S, false><<<grid, block, 0, s>>>((const S *)A, (S *)B, doms, ndom, tiles, ntiles, flag);
     return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t batch_launch_aa_t(void *A, const DomainDesc *doms, int ndom, const int4 *tiles, int ntiles,
+                                     int grid, dim3 block, int *flag, cudaStream_t s, bool odd) {
+    const size_t sm = ndom <= kSmemDomains ? sizeof(DomainDesc) * ndom : 0;
+    if (ndom <= kSmemDomains) {
+        if (odd) k_batch_step_aa<S, true, true><<<grid, block, sm, s>>>((S *)A, doms, ndom, tiles, ntiles, flag);
+        else k_batch_step_aa<S, true, false><<<grid, block, sm, s>>>((S *)A, doms, ndom, tiles, ntiles, flag);
+    } else {
+        if (odd) k_batch_step_aa<S, false, true><<<grid, block, 0, s>>>((S *)A, doms, ndom, tiles, ntiles, flag);
+        else k_batch_step_aa<S, false, false><<<grid, block, 0, s>>>((S *)A, doms, ndom, tiles, ntiles, flag);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t batch_launch_aa(int storage, void *A, const DomainDesc *doms, int ndom, const int4 *tiles,
+                                   int ntiles, int grid, dim3 block, int *flag, cudaStream_t s, bool odd) {
+    switch (storage) {
+        case 0: return batch_launch_aa_t<float>(A, doms, ndom, tiles, ntiles, grid, block, flag, s, odd);
+        case 1: return batch_launch_aa_t<__half>(A, doms, ndom, tiles, ntiles, grid, block, flag, s, odd);
+        default: return batch_launch_aa_t<__nv_bfloat16>(A, doms, ndom, tiles, ntiles, grid, block, flag, s, odd);
+    }
 }
 
 static cudaError_t batch_launch(int storage, const void *A, void *B, const DomainDesc *doms, int ndom,
@@ -168,6 +251,7 @@ struct clbm_batch {
     cudaGraphExec_t graph;
     int graph_steps;
     int64_t steps_done;
+    bool aa;  // in-place pattern: one buffer (buf[1] == buf[0]), step kind by the parity of steps_done
 };
 
 namespace {
@@ -188,7 +272,9 @@ Launch domain_launch(const clbm_batch *b, int d) {
     L.grid = dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
     L.stream = b->stream;
     L.packed = false;
-    L.map = 0;
+    L.staged = false;  // the per-domain schedule runs the one-node kernels
+    // state maps: A/B pull map; in place, natural slots after an even number of steps, the odd map after an odd
+    L.map = b->aa ? ((b->steps_done & 1) ? 2 : 1) : 0;
     return L;
 }
 
@@ -249,13 +335,18 @@ int build_tiles(clbm_batch *b, int T) {
     return CLBM_OK;
 }
 
+// One step of every domain: A/B from buffer `from`; in place, the odd kind when
+// `from` is 1 (the parity of the step).
 cudaError_t launch_all(clbm_batch *b, cudaStream_t s, int from) {
+    if (b->aa)
+        return batch_launch_aa(b->storage, b->buf[0], b->d_descs, b->ndom, b->d_tiles, b->ntiles, b->grid, b->block,
+                               b->d_flag, s, from == 1);
     return batch_launch(b->storage, b->buf[from], b->buf[from ^ 1], b->d_descs, b->ndom, b->d_tiles, b->ntiles,
                         b->grid, b->block, b->d_flag, s);
 }
 
-// Capture graph_steps steps starting from buffer 0 (graph_steps is even, so
-// the replay ends on buffer 0 again).
+// Capture graph_steps steps starting from buffer 0 (in place: from an even
+// step); graph_steps is even, so the replay ends there again.
 int ensure_graph(clbm_batch *b) {
     if (b->graph) return CLBM_OK;
     cudaGraph_t g = nullptr;
@@ -278,14 +369,22 @@ int ensure_graph(clbm_batch *b) {
 extern "C" {
 
 int clbm_batch_create(const clbm_domain *doms, int32_t ndomains, int32_t storage, void *stream, clbm_batch **out) {
+    return clbm_batch_create_pattern(doms, ndomains, storage, CLBM_PATTERN_AB, stream, out);
+}
+
+int clbm_batch_create_pattern(const clbm_domain *doms, int32_t ndomains, int32_t storage, int32_t pattern,
+                              void *stream, clbm_batch **out) {
     if (!doms || !out || ndomains < 1) return bfail(CLBM_ERR_ARG, "clbm_batch_create: bad argument");
     *out = nullptr;
+    if (pattern != CLBM_PATTERN_AB && pattern != CLBM_PATTERN_AA)
+        return bfail(CLBM_ERR_ARG, "clbm_batch_create: pattern must be CLBM_PATTERN_AB or CLBM_PATTERN_AA");
     if (storage < CLBM_STORAGE_F32 || storage > CLBM_STORAGE_BF16)
         return bfail(CLBM_ERR_ARG, "clbm_batch_create: storage must be f32, f16 or bf16 (round to nearest)");
     clbm_batch *b = new (std::nothrow) clbm_batch();
     if (!b) return bfail(CLBM_ERR_OOM, "clbm_batch_create: host allocation failed");
     b->ndom = ndomains;
     b->storage = storage;
+    b->aa = pattern == CLBM_PATTERN_AA;
     b->elem = storage == CLBM_STORAGE_F32 ? 4 : 2;
     b->stream = (cudaStream_t)stream;
     b->graph_steps = 16;
@@ -307,6 +406,9 @@ int clbm_batch_create(const clbm_domain *doms, int32_t ndomains, int32_t storage
         D.g.nx = p.nx; D.g.ny = p.ny; D.g.nz = p.nz;
         D.g.walls = p.walls;
         D.g.stride = (n + 63) / 64 * 64;
+#ifdef CLBM_BOUNDS_CHECK
+        D.g.bc_limit = (uint64_t)kQ * D.g.stride;  // the domain's own arrays (violations redirected, not recorded)
+#endif
         D.r.om2 = (float)(1.0 - s2);
         D.r.cb = (float)((p.s2b - s2) / 3.0);
         D.r.om3 = (float)(1.0 - p.s3);
@@ -323,13 +425,14 @@ int clbm_batch_create(const clbm_domain *doms, int32_t ndomains, int32_t storage
     }
     b->total_nodes = nodes;
     b->total_elems = off;
-    cudaError_t e = cudaMalloc(&b->buf[0], 2 * (size_t)off * b->elem);
+    const size_t nbuf = b->aa ? 1 : 2;
+    cudaError_t e = cudaMalloc(&b->buf[0], nbuf * (size_t)off * b->elem);
     if (e != cudaSuccess) {
         delete b;
         cudaGetLastError();
         return bfail(CLBM_ERR_OOM, "clbm_batch_create: cudaMalloc of the populations failed");
     }
-    b->buf[1] = (char *)b->buf[0] + (size_t)off * b->elem;
+    b->buf[1] = b->aa ? b->buf[0] : (char *)b->buf[0] + (size_t)off * b->elem;
     if ((e = cudaMalloc(&b->d_descs, sizeof(DomainDesc) * ndomains + 256)) != cudaSuccess) {
         cudaFree(b->buf[0]);
         delete b;
@@ -347,7 +450,7 @@ int clbm_batch_create(const clbm_domain *doms, int32_t ndomains, int32_t storage
     e = cudaMemcpyAsync(b->d_descs, b->descs.data(), sizeof(DomainDesc) * ndomains, cudaMemcpyHostToDevice,
                         b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flag, 0, sizeof(int), b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->buf[0], 0, 2 * (size_t)off * b->elem, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->buf[0], 0, nbuf * (size_t)off * b->elem, b->stream);
     int rc = e == cudaSuccess ? build_tiles(b, 256) : bcuda(e, "clbm_batch_create");
     if (rc != CLBM_OK) {
         clbm_batch_destroy(b);
@@ -379,6 +482,8 @@ int clbm_batch_get_info(const clbm_batch *b, clbm_batch_info *info) {
     info->threads = (int32_t)b->block.x;
     info->graph_steps = b->graph_steps;
     info->steps_done = b->steps_done;
+    info->pattern = b->aa ? CLBM_PATTERN_AA : CLBM_PATTERN_AB;
+    info->buffers = b->aa ? 1 : 2;
     return CLBM_OK;
 }
 
@@ -391,6 +496,20 @@ int clbm_batch_set_tile(clbm_batch *b, int32_t threads) {
 int clbm_batch_autotune(clbm_batch *b, int32_t trial_steps, int32_t *threads_out) {
     if (!b || trial_steps < 1) return bfail(CLBM_ERR_ARG, "clbm_batch_autotune: bad argument");
     static const int cand[] = {64, 128, 192, 256, 384, 512};
+    // in place, a trial step overwrites the state: keep a copy and put it back after the trials
+    void *saved = nullptr;
+    const size_t sbytes = (size_t)b->total_elems * b->elem;
+    if (b->aa) {
+        cudaError_t e = cudaMalloc(&saved, sbytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(CLBM_ERR_OOM, "clbm_batch_autotune: no room for the copy of an in-place state");
+        }
+        if ((e = cudaMemcpyAsync(saved, b->buf[0], sbytes, cudaMemcpyDeviceToDevice, b->stream)) != cudaSuccess) {
+            cudaFree(saved);
+            return bcuda(e, "clbm_batch_autotune: save");
+        }
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -399,10 +518,17 @@ int clbm_batch_autotune(clbm_batch *b, int32_t trial_steps, int32_t *threads_out
     int rc = CLBM_OK;
     for (int T : cand) {
         if ((rc = build_tiles(b, T)) != CLBM_OK) break;
-        // trials read the current buffer and write the other one: the state is unchanged
-        cudaError_t e = launch_all(b, b->stream, b->cur);
+        // A/B trials read the current buffer and write the other one: the state is unchanged. In place they
+        // are steps of alternating kind from the current parity on the saved state, restored afterwards.
+        int ph = b->aa ? (int)(b->steps_done & 1) : b->cur;
+        auto trial = [&]() {
+            cudaError_t r = launch_all(b, b->stream, ph);
+            if (b->aa) ph ^= 1;
+            return r;
+        };
+        cudaError_t e = trial();
         if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-        for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = launch_all(b, b->stream, b->cur);
+        for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = trial();
         if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -418,6 +544,12 @@ int clbm_batch_autotune(clbm_batch *b, int32_t trial_steps, int32_t *threads_out
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (saved) {
+        cudaError_t e = cudaMemcpyAsync(b->buf[0], saved, sbytes, cudaMemcpyDeviceToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        cudaFree(saved);
+        if (e != cudaSuccess && rc == CLBM_OK) rc = bcuda(e, "clbm_batch_autotune: restore");
+    }
     if (rc != CLBM_OK) return rc;
     if ((rc = build_tiles(b, bt)) != CLBM_OK) return rc;
     if (threads_out) *threads_out = bt;
@@ -426,6 +558,7 @@ int clbm_batch_autotune(clbm_batch *b, int32_t trial_steps, int32_t *threads_out
 
 int clbm_batch_init_equilibrium(clbm_batch *b) {
     if (!b) return bfail(CLBM_ERR_ARG, "clbm_batch_init_equilibrium: null pointer");
+    b->steps_done = 0;  // before domain_launch: the in-place pattern starts in natural order
     for (int d = 0; d < b->ndom; ++d) {
         cudaError_t e = launch_init_eq(b->storage, domain_launch(b, d), domain_ptr(b, b->cur, d), nullptr, nullptr,
                                        domain_force(b, d).n, domain_force(b, d));
@@ -440,12 +573,14 @@ int clbm_batch_step(clbm_batch *b, int64_t nsteps, int32_t mode) {
     Range range("clbm_batch_step");
     cudaError_t e = cudaSuccess;
     int64_t t = 0;
+    // the phase of the next step: the buffer (A/B) or the parity of the step (in place)
+    auto phase = [&]() { return b->aa ? (int)((b->steps_done + t) & 1) : b->cur; };
     if (mode == CLBM_BATCH_GRAPH && nsteps >= b->graph_steps) {
         int rc = ensure_graph(b);
         if (rc != CLBM_OK) return rc;
-        if (b->cur == 1) {  // the graph starts from buffer 0
+        if (phase() == 1) {  // the graph starts from phase 0
             if ((e = launch_all(b, b->stream, 1)) != cudaSuccess) return bcuda(e, "clbm_batch_step");
-            b->cur = 0;
+            if (!b->aa) b->cur = 0;
             ++t;
         }
         for (; t + b->graph_steps <= nsteps; t += b->graph_steps)
@@ -453,16 +588,21 @@ int clbm_batch_step(clbm_batch *b, int64_t nsteps, int32_t mode) {
     }
     for (; t < nsteps; ++t) {
         if (mode == CLBM_BATCH_PER_DOMAIN) {
+            const bool odd = phase() == 1;
             for (int d = 0; d < b->ndom && e == cudaSuccess; ++d) {
                 Rates r = b->descs[d].r;
-                e = launch_step(b->storage, domain_launch(b, d), domain_ptr(b, b->cur, d),
-                                domain_ptr(b, b->cur ^ 1, d), r, domain_force(b, d), b->d_flag, 0u);
+                if (b->aa)
+                    e = launch_step_aa(b->storage, domain_launch(b, d), domain_ptr(b, 0, d), r, domain_force(b, d),
+                                       b->d_flag, 0u, odd);
+                else
+                    e = launch_step(b->storage, domain_launch(b, d), domain_ptr(b, b->cur, d),
+                                    domain_ptr(b, b->cur ^ 1, d), r, domain_force(b, d), b->d_flag, 0u);
             }
         } else {
-            e = launch_all(b, b->stream, b->cur);
+            e = launch_all(b, b->stream, phase());
         }
         if (e != cudaSuccess) return bcuda(e, "clbm_batch_step");
-        b->cur ^= 1;
+        if (!b->aa) b->cur ^= 1;
     }
     b->steps_done += nsteps;
     return CLBM_OK;

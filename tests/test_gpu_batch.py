@@ -134,3 +134,54 @@ def test_batch_64_domains_full_size_sampled():
         err = np.max(np.abs(hg + W.reshape(1, 19) - fo) / np.abs(fo))
         assert err < 1e-6, (k, err)
     b.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("mode", [Batch.GRAPH, Batch.DIRECT, Batch.PER_DOMAIN])
+def test_batch_in_place_matches_ab(storage, mode):
+    """The in-place (AA) pattern over a batch: one buffer instead of two, and
+    after odd and even step counts (graph replays starting at either parity)
+    every domain's state, velocity and density equal the A/B batch's bit for
+    bit."""
+    ab = Batch(DOMAINS, storage=storage, device=dev())
+    aa = Batch(DOMAINS, storage=storage, device=dev(), pattern="aa")
+    ia, ib = aa.info(), ab.info()
+    assert (ia["pattern"], ia["buffers"], ib["pattern"], ib["buffers"]) == (1, 1, 0, 2)
+    assert ia["state_bytes"] == ib["state_bytes"]
+    for g in (ab, aa):
+        g.init_equilibrium()
+    done = 0
+    for n in (1, 1, 17, 18):  # odd and even counts; 17 and 18 steps start graph replays at both parities
+        for g in (ab, aa):
+            g.step(n, mode)
+        done += n
+        for k in range(len(DOMAINS)):
+            assert torch.equal(aa.populations(k, deviation=True), ab.populations(k, deviation=True)), (done, k)
+            ra, ua = aa.macros(k)
+            rb, ub = ab.macros(k)
+            assert torch.equal(ra, rb) and torch.equal(ua, ub)
+    aa.check()
+    ab.close()
+    aa.close()
+
+
+def test_batch_in_place_autotune_keeps_state():
+    """Autotuning an in-place batch steps a copy of its state: the state and
+    the step count are unchanged, and later steps still equal the A/B batch."""
+    ab = Batch(DOMAINS, device=dev())
+    aa = Batch(DOMAINS, device=dev(), pattern="aa")
+    for g in (ab, aa):
+        g.init_equilibrium()
+        g.step(7, Batch.DIRECT)
+    before = [aa.populations(k, deviation=True).cpu() for k in range(len(DOMAINS))]
+    threads = aa.autotune(trial_steps=3)
+    assert aa.info()["threads"] == threads and aa.info()["steps_done"] == 7
+    for k in range(len(DOMAINS)):
+        assert torch.equal(aa.populations(k, deviation=True).cpu(), before[k])
+    for g in (ab, aa):
+        g.step(30, Batch.GRAPH)
+    for k in range(len(DOMAINS)):
+        assert torch.equal(aa.populations(k, deviation=True), ab.populations(k, deviation=True))
+    aa.check()
+    ab.close()
+    aa.close()
