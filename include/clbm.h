@@ -312,9 +312,15 @@ int clbm_load_state(clbm_ctx *ctx, const void *host_buf, size_t bytes);
  * step's launch and copied back on a second stream of the context while
  * the following steps run. Otherwise they come from one
  * clbm_reduce_moments pass before each step, copied back asynchronously.
- * The last comes from one reduction after the final step. The call
- * synchronises once, at the end, then returns CLBM_ERR_UNSTABLE if any mass
- * sum is non-finite or the instability flag is set. Device scratch for the staging fields and partial sums is allocated
+ * The last comes from one reduction after the final step, beside the copies
+ * back. With D3Q19 the host copies travel in up to 8 chunks of z-planes on a
+ * second stream, each chunk initialised (and read out) as soon as it has
+ * landed (been stepped). When the fused step with sums runs, it also steps the
+ * first step chunk by chunk as the input lands, and the last step chunk by
+ * chunk, each chunk read out and copied back as soon as it and its two
+ * neighbouring chunks are stepped; the results are the same bit for bit. The call synchronises once, at the end, then returns
+ * CLBM_ERR_UNSTABLE if any mass sum is non-finite or the instability flag is
+ * set. Device scratch for the staging fields and partial sums is allocated
  * on first use and kept by the context. Host buffers should be pinned for
  * full copy speed and for the copies to overlap the steps. */
 int clbm_run_host(clbm_ctx *ctx, const float *rho_host, const float *u_host, int64_t nsteps,

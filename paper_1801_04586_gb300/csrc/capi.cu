@@ -800,42 +800,17 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         z1 = (int64_t)c->g.nz * (k + 1) / nch;
     };
     int rc = CLBM_OK;
-    if (chunked) {
-        if (c->slab_pending) return fail(CLBM_ERR_STATE, "clbm_run_host: a split slab step is pending");
-        c->steps_done = 0;  // as clbm_init_equilibrium
-        const Launch L0 = launch_of(c);
-        const ForceArgs F0 = force_at_zero(c);
-        // d_io may still be read by the step stream (an earlier job's read-out)
-        if ((e = cudaEventRecord(c->io_ev[0], c->stream)) == cudaSuccess)
-            e = cudaStreamWaitEvent(c->io_stream, c->io_ev[0], 0);
-        for (int k = 0; k < nch && e == cudaSuccess; ++k) {
-            int64_t z0, z1;
-            chunk(k, z0, z1);
-            const int64_t off = z0 * plane;
-            const size_t bytes = sizeof(float) * (size_t)((z1 - z0) * plane);
-            if (rho_h) e = cudaMemcpyAsync(d_rho + off, rho_h + off, bytes, cudaMemcpyHostToDevice, c->io_stream);
-            for (int a = 0; a < 3 && u_h && e == cudaSuccess; ++a)
-                e = cudaMemcpyAsync(d_u + a * c->n + off, u_h + a * c->n + off, bytes, cudaMemcpyHostToDevice,
-                                    c->io_stream);
-            if (e == cudaSuccess) e = cudaEventRecord(c->io_ev[k], c->io_stream);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->io_ev[k], 0);
-            Launch Lk = L0;
-            Lk.z0 = (int)z0;
-            Lk.nplanes = (int)(z1 - z0);
-            if (e == cudaSuccess)
-                e = launch_init_eq(c->p.storage, Lk, c->buf[c->cur], rho_h ? d_rho : nullptr, u_h ? d_u : nullptr,
-                                   c->n, F0);
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: chunked copy and initialisation");
-    } else {
-        if (rho_h && (e = cudaMemcpyAsync(d_rho, rho_h, nb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
-            return cuda_fail(e, "clbm_run_host: copy rho");
-        if (u_h && (e = cudaMemcpyAsync(d_u, u_h, 3 * nb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
-            return cuda_fail(e, "clbm_run_host: copy u");
-        rc = clbm_init_equilibrium(c, rho_h ? d_rho : nullptr, u_h ? d_u : nullptr);
-        if (rc != CLBM_OK) return rc;
-    }
     const bool fused = c->q == 19 && !c->aa && c->model == CLBM_MODEL_CASCADED;
+    // With per-step sums the steps are the fused kernel, which also steps a range
+    // of planes. Then the first step runs chunk by chunk as the input lands: a
+    // node's step pulls exactly the slots its own initialisation scattered to, so
+    // chunk k steps right after its initialisation. The last step runs chunk by
+    // chunk too. A node's read-out pulls from the neighbouring planes, so chunk k
+    // is read out and copied back once chunks k - 1, k and k + 1 are stepped (the
+    // two end chunks, neighbours across a periodic z, after the last).
+    const bool diag = fused && moments_h && nsteps > 0;
+    const bool first_split = chunked && diag;
+    const bool last_split = chunked && diag && nsteps > 1 && (rho_out || u_out);
     if (fused && moments_h && !c->copy_stream) {
         cudaStream_t cs = nullptr;
         cudaEvent_t e1 = nullptr, e2 = nullptr;
@@ -850,6 +825,86 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         c->ev_step = e1;
         c->ev_copy = e2;
     }
+    if (diag && (e = cudaMemsetAsync(c->d_acc, 0, sizeof(unsigned long long) * 2 * 4 * kDiagSlots, c->stream)) !=
+                    cudaSuccess)
+        return cuda_fail(e, "clbm_run_host: clear accumulators");
+    const double add0 = (double)c->n;
+    auto slot = [c](int64_t t) { return c->d_mom + 4 * (t % kMomRing); };
+    // The fused step t (or one plane range of it) from the current buffer: the
+    // exact sums of the state it pulls (state t) go to slot set t % 2. The first
+    // launch of step t > 0 first drains set (t - 1) % 2 into the totals of state t - 1.
+    auto diag_step = [&](int64_t t, const Launch &Ls, bool first) {
+        DiagSums d;
+        d.acc = c->d_acc + (t & 1) * 4 * kDiagSlots;
+        d.acc_prev = t > 0 && first ? c->d_acc + ((t - 1) & 1) * 4 * kDiagSlots : nullptr;
+        d.out_prev = t > 0 && first ? slot(t - 1) : nullptr;
+        d.add0 = add0;
+        return launch_step_diag(c->p.storage, Ls, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),
+                                c->d_flag, d, step_key(c->steps_done));
+    };
+    // chunk k's planes, with the state map of the current step count
+    auto plane_chunk = [&](int k) {
+        int64_t z0, z1;
+        chunk(k, z0, z1);
+        Launch Lk = launch_of(c);
+        Lk.z0 = (int)z0;
+        Lk.nplanes = (int)(z1 - z0);
+        return Lk;
+    };
+    // Every kMomSync steps the step stream waits for the sum copies issued
+    // kMomSync steps earlier, before their slots are reused.
+    auto mom_sync = [&]() {
+        cudaError_t r = cudaStreamWaitEvent(c->stream, c->ev_copy, 0);
+        if (r == cudaSuccess) r = cudaEventRecord(c->ev_copy, c->copy_stream);
+        return r;
+    };
+    // Chunk k's read-out of buffer b (force F), then its copies back on io_stream.
+    auto read_out = [&](int k, const void *b, const ForceArgs &F) {
+        const Launch Lk = plane_chunk(k);
+        const int64_t off = (int64_t)Lk.z0 * plane;
+        const size_t bytes = sizeof(float) * (size_t)((int64_t)Lk.nplanes * plane);
+        cudaError_t r = launch_macros(c->p.storage, Lk, b, F, rho_out ? d_rho : nullptr, u_out ? d_u : nullptr, c->n);
+        if (r == cudaSuccess) r = cudaEventRecord(c->io_ev[k], c->stream);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(c->io_stream, c->io_ev[k], 0);
+        if (r == cudaSuccess && rho_out)
+            r = cudaMemcpyAsync(rho_out + off, d_rho + off, bytes, cudaMemcpyDeviceToHost, c->io_stream);
+        for (int a = 0; a < 3 && u_out && r == cudaSuccess; ++a)
+            r = cudaMemcpyAsync(u_out + a * c->n + off, d_u + a * c->n + off, bytes, cudaMemcpyDeviceToHost,
+                                c->io_stream);
+        return r;
+    };
+    if (first_split && (e = mom_sync()) != cudaSuccess) return cuda_fail(e, "clbm_run_host: copy sync");
+    if (chunked) {
+        if (c->slab_pending) return fail(CLBM_ERR_STATE, "clbm_run_host: a split slab step is pending");
+        c->steps_done = 0;  // as clbm_init_equilibrium
+        const ForceArgs F0 = force_at_zero(c);
+        // d_io may still be read by the step stream (an earlier job's read-out)
+        if ((e = cudaEventRecord(c->io_ev[0], c->stream)) == cudaSuccess)
+            e = cudaStreamWaitEvent(c->io_stream, c->io_ev[0], 0);
+        for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+            const Launch Lk = plane_chunk(k);
+            const int64_t off = (int64_t)Lk.z0 * plane;
+            const size_t bytes = sizeof(float) * (size_t)((int64_t)Lk.nplanes * plane);
+            if (rho_h) e = cudaMemcpyAsync(d_rho + off, rho_h + off, bytes, cudaMemcpyHostToDevice, c->io_stream);
+            for (int a = 0; a < 3 && u_h && e == cudaSuccess; ++a)
+                e = cudaMemcpyAsync(d_u + a * c->n + off, u_h + a * c->n + off, bytes, cudaMemcpyHostToDevice,
+                                    c->io_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(c->io_ev[k], c->io_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->io_ev[k], 0);
+            if (e == cudaSuccess)
+                e = launch_init_eq(c->p.storage, Lk, c->buf[c->cur], rho_h ? d_rho : nullptr, u_h ? d_u : nullptr,
+                                   c->n, F0);
+            if (e == cudaSuccess && first_split) e = diag_step(0, Lk, false);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: chunked copy and initialisation");
+    } else {
+        if (rho_h && (e = cudaMemcpyAsync(d_rho, rho_h, nb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+            return cuda_fail(e, "clbm_run_host: copy rho");
+        if (u_h && (e = cudaMemcpyAsync(d_u, u_h, 3 * nb, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+            return cuda_fail(e, "clbm_run_host: copy u");
+        rc = clbm_init_equilibrium(c, rho_h ? d_rho : nullptr, u_h ? d_u : nullptr);
+        if (rc != CLBM_OK) return rc;
+    }
     for (int64_t t = 0; t < nsteps && !fused; ++t) {
         // D3Q27 and the in-place pattern: the sums of state t, then a plain step
         if (moments_h) {
@@ -859,34 +914,28 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         }
         if ((rc = clbm_step(c, 1)) != CLBM_OK) return rc;
     }
-    if (fused && moments_h && nsteps > 0 &&
-        (e = cudaMemsetAsync(c->d_acc, 0, sizeof(unsigned long long) * 2 * 4 * kDiagSlots, c->stream)) !=
-            cudaSuccess)
-        return cuda_fail(e, "clbm_run_host: clear accumulators");
     // The sums of step t - 1 land in ring slot (t - 1) % kMomRing during step t
     // and are copied back on copy_stream after it, beside the following
     // steps. (Writing them from the kernel straight into pinned host memory
     // made every step's kernel wait for that write: 9 us per step; a copy on
     // the step stream held each next step for 5 us.)
-    const double add0 = (double)c->n;
-    auto slot = [c](int64_t t) { return c->d_mom + 4 * (t % kMomRing); };
     for (int64_t t = 0; t < nsteps && fused; ++t) {
         if (moments_h) {
-            if (t % kMomSync == 0) {
-                // the copies issued up to kMomSync steps ago are done before slots are reused
-                e = cudaStreamWaitEvent(c->stream, c->ev_copy, 0);
-                if (e == cudaSuccess) e = cudaEventRecord(c->ev_copy, c->copy_stream);
-                if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: copy sync");
+            if (t % kMomSync == 0 && !(t == 0 && first_split) && (e = mom_sync()) != cudaSuccess)
+                return cuda_fail(e, "clbm_run_host: copy sync");
+            e = cudaSuccess;
+            if (t == nsteps - 1 && last_split) {
+                // chunk by chunk; chunk k - 1 is read out (state t + 1, its force) once chunk k is stepped
+                const ForceArgs F1 = force_at(c, c->steps_done + 1);
+                for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+                    e = diag_step(t, plane_chunk(k), k == 0);
+                    if (e == cudaSuccess && nch >= 3 && k >= 2) e = read_out(k - 1, c->buf[c->cur ^ 1], F1);
+                }
+                for (int k = 0; k < nch && e == cudaSuccess; ++k)
+                    if (nch < 3 || k == 0 || k == nch - 1) e = read_out(k, c->buf[c->cur ^ 1], F1);
+            } else if (t > 0 || !first_split) {  // step 0 of a split first step ran as the input landed
+                e = diag_step(t, L, true);
             }
-            // fused step: exact sums of the state it pulls (state t) into slot set t % 2; its block 0
-            // first drains set (t - 1) % 2 into the totals of state t - 1
-            DiagSums d;
-            d.acc = c->d_acc + (t & 1) * 4 * kDiagSlots;
-            d.acc_prev = t > 0 ? c->d_acc + ((t - 1) & 1) * 4 * kDiagSlots : nullptr;
-            d.out_prev = t > 0 ? slot(t - 1) : nullptr;
-            d.add0 = add0;
-            e = launch_step_diag(c->p.storage, L, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),
-                                 c->d_flag, d, step_key(c->steps_done));
             if (e == cudaSuccess && t == nsteps - 1)  // the last step's set
                 e = launch_drain4(c->d_acc + (t & 1) * 4 * kDiagSlots, slot(t), add0, c->stream);
             if (e == cudaSuccess) e = cudaEventRecord(c->ev_step, c->stream);
@@ -909,36 +958,10 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         c->cur ^= 1;
         ++c->steps_done;
     }
-    if (moments_h) {
-        if ((rc = clbm_reduce_moments(c, c->d_mom)) != CLBM_OK) return rc;
-        e = cudaMemcpyAsync(moments_h + 4 * nsteps, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: moments");
-    }
     if (chunked && (rho_out || u_out)) {
         // each chunk's read-out, then its copies back on io_stream beside the next chunk's read-out
-        const Launch L1 = launch_of(c);
         const ForceArgs F1 = force_now(c);
-        for (int k = 0; k < nch && e == cudaSuccess; ++k) {
-            int64_t z0, z1;
-            chunk(k, z0, z1);
-            const int64_t off = z0 * plane;
-            const size_t bytes = sizeof(float) * (size_t)((z1 - z0) * plane);
-            Launch Lk = L1;
-            Lk.z0 = (int)z0;
-            Lk.nplanes = (int)(z1 - z0);
-            e = launch_macros(c->p.storage, Lk, c->buf[c->cur], F1, rho_out ? d_rho : nullptr, u_out ? d_u : nullptr,
-                              c->n);
-            if (e == cudaSuccess) e = cudaEventRecord(c->io_ev[k], c->stream);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->io_stream, c->io_ev[k], 0);
-            if (e == cudaSuccess && rho_out)
-                e = cudaMemcpyAsync(rho_out + off, d_rho + off, bytes, cudaMemcpyDeviceToHost, c->io_stream);
-            for (int a = 0; a < 3 && u_out && e == cudaSuccess; ++a)
-                e = cudaMemcpyAsync(u_out + a * c->n + off, d_u + a * c->n + off, bytes, cudaMemcpyDeviceToHost,
-                                    c->io_stream);
-        }
-        // the step stream ends after the copies (its synchronisation below covers them)
-        if (e == cudaSuccess) e = cudaEventRecord(c->io_ev[0], c->io_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->io_ev[0], 0);
+        for (int k = 0; k < nch && !last_split && e == cudaSuccess; ++k) e = read_out(k, c->buf[c->cur], F1);
         if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: chunked read-out and copies back");
     } else {
         if ((rho_out || u_out) &&
@@ -948,6 +971,18 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
             return cuda_fail(e, "clbm_run_host: copy rho back");
         if (u_out && (e = cudaMemcpyAsync(u_out, d_u, 3 * nb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
             return cuda_fail(e, "clbm_run_host: copy u back");
+    }
+    // the sums of the final state, on the step stream beside the copies back
+    if (moments_h) {
+        if ((rc = clbm_reduce_moments(c, c->d_mom)) != CLBM_OK) return rc;
+        e = cudaMemcpyAsync(moments_h + 4 * nsteps, c->d_mom, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: moments");
+    }
+    if (chunked && (rho_out || u_out)) {
+        // the step stream ends after the copies (its synchronisation below covers them)
+        if ((e = cudaEventRecord(c->io_ev[0], c->io_stream)) == cudaSuccess)
+            e = cudaStreamWaitEvent(c->stream, c->io_ev[0], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: copies back");
     }
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e, "clbm_run_host");
     if (moments_h)

@@ -32,7 +32,8 @@ struct Launch {
                        // map of a z-slab with halo faces)
     long long wait_cycles = 0;  // staged step: bound of a wait for a tile's copies (0: kWaitCycles)
     bool drop_first_tile = false;  // staged step, failure injection: tile 0's copies are not issued
-    int z0 = 0, zs = 1, nplanes = -1;  // staged step: the planes z0, z0 + zs, ... (nplanes of them; -1: all)
+    int z0 = 0, zs = 1, nplanes = -1;  // staged and fused-sums steps, init, read-out: the planes z0, z0 + zs, ...
+                                       // (nplanes of them; -1: all)
 };
 
 // storage: 0 = f32, 1 = f16, 2 = bf16, 3 = f16 stochastic, 4 = bf16 stochastic
@@ -69,6 +70,8 @@ cudaError_t launch_step_aa_mrt(int storage, const Launch &L, void *f, const Rate
 // kDiagSlots x 4 accumulators acc (zero on entry). If acc_prev is not null,
 // the launch first drains that set (the previous step's) into out_prev[0..3]
 // (FP64 totals, add0 added to the first) and clears it. launch_drain4 drains a set on its own (step_diag.cu).
+// With L.nplanes >= 0 it steps the planes L.z0 .. L.z0 + L.nplanes - 1 only
+// (L.zs = 1); the launches of one step's plane ranges add into the same set.
 constexpr int kDiagSlots = 1024;
 struct DiagSums {
     unsigned long long *acc;

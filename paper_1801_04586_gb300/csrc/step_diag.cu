@@ -64,15 +64,15 @@ __global__ void __launch_bounds__(512, 2) k_step_diag(const S *__restrict__ src,
                                                       Rates r, ForceArgs F, int *__restrict__ flag,
                                                       unsigned long long *__restrict__ acc,
                                                       unsigned long long *__restrict__ acc_prev, double *out_prev,
-                                                      double add0, uint32_t key) {
+                                                      double add0, uint32_t key, int zb, int ze) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z0 = blockIdx.z * kDiagZ;
+    const int z0 = zb + blockIdx.z * kDiagZ;
     if (acc_prev && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) drain_slots(acc_prev, out_prev, add0);
     int hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};  // fixed-point parts of the sums (to_fixed_parts)
     if (x < g.nx && y < g.ny) {  // no early return: every lane joins the warp sums
 #pragma unroll 1
-        for (int z = z0; z < z0 + kDiagZ && z < g.nz; ++z) {
+        for (int z = z0; z < z0 + kDiagZ && z < ze; ++z) {
             uint32_t off[kQ];
             int pop[kQ];
             pull_sources<WALLS>(g, x, y, z, off, pop);
@@ -114,13 +114,17 @@ __global__ void __launch_bounds__(512, 2) k_step_diag(const S *__restrict__ src,
 template <typename S, int FM>
 static cudaError_t diag_walls(const Launch &L, const void *src, void *dst, const Rates &r, const ForceArgs &F,
                               int *flag, const DiagSums &d, uint32_t key) {
-    const dim3 grid(L.grid.x, L.grid.y, (L.grid.z + kDiagZ - 1) / kDiagZ);
+    // the planes z0 .. z0 + nplanes - 1 (all planes if nplanes < 0)
+    const int zb = L.nplanes < 0 ? 0 : L.z0;
+    const int np = L.nplanes < 0 ? L.g.nz : L.nplanes;
+    if (L.zs != 1 || zb < 0 || np < 1 || zb + np > L.g.nz) return cudaErrorInvalidValue;
+    const dim3 grid(L.grid.x, L.grid.y, (np + kDiagZ - 1) / kDiagZ);
     if (L.g.walls)
         k_step_diag<S, FM, true><<<grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, d.acc,
-                                                                 d.acc_prev, d.out_prev, d.add0, key);
+                                                                 d.acc_prev, d.out_prev, d.add0, key, zb, zb + np);
     else
         k_step_diag<S, FM, false><<<grid, L.block, 0, L.stream>>>((const S *)src, (S *)dst, L.g, r, F, flag, d.acc,
-                                                                  d.acc_prev, d.out_prev, d.add0, key);
+                                                                  d.acc_prev, d.out_prev, d.add0, key, zb, zb + np);
     return cudaGetLastError();
 }
 
