@@ -133,6 +133,10 @@ def test_aa_run_host_matches_ab():
         mom = torch.empty(4 * 10, dtype=torch.float64)
         g.run_host(rho, u, 9, r_out, u_out, mom)
         out[pat] = (r_out, u_out, mom)
+        # a second job starts after an odd step count: it initialises in the even state's slots again
+        r2, u2, mom2 = torch.empty_like(rho), torch.empty_like(u), torch.empty_like(mom)
+        g.run_host(rho, u, 9, r2, u2, mom2)
+        assert torch.equal(r2, r_out) and torch.equal(u2, u_out) and torch.equal(mom2, mom)
     for a, b in zip(out["ab"], out["aa"]):
         assert torch.equal(a, b)
 
