@@ -316,7 +316,7 @@ int clbm_load_state(clbm_ctx *ctx, const void *host_buf, size_t bytes);
  * back. With D3Q19 the host copies travel in up to 8 chunks of z-planes on a
  * second stream, each chunk initialised (and read out) as soon as it has
  * landed (been stepped). When the fused step with sums runs, it also steps the
- * first step chunk by chunk as the input lands, and the last step chunk by
+ * first two steps chunk by chunk as the input lands, and the last step chunk by
  * chunk, each chunk read out and copied back as soon as it and its two
  * neighbouring chunks are stepped; the results are the same bit for bit. The call synchronises once, at the end, then returns
  * CLBM_ERR_UNSTABLE if any mass sum is non-finite or the instability flag is

@@ -802,14 +802,17 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
     int rc = CLBM_OK;
     const bool fused = c->q == 19 && !c->aa && c->model == CLBM_MODEL_CASCADED;
     // With per-step sums the steps are the fused kernel, which also steps a range
-    // of planes. Then the first step runs chunk by chunk as the input lands: a
+    // of planes. Then the first two steps run chunk by chunk as the input lands: a
     // node's step pulls exactly the slots its own initialisation scattered to, so
-    // chunk k steps right after its initialisation. The last step runs chunk by
-    // chunk too. A node's read-out pulls from the neighbouring planes, so chunk k
-    // is read out and copied back once chunks k - 1, k and k + 1 are stepped (the
-    // two end chunks, neighbours across a periodic z, after the last).
+    // chunk k takes step 0 right after its initialisation. Step 1 of chunk k pulls
+    // from step 0 of chunks k - 1, k and k + 1, so it follows step 0 of chunk
+    // k + 1 (the two end chunks, neighbours across a periodic z, after the last).
+    // The last step runs chunk by chunk too. A node's read-out pulls from the
+    // neighbouring planes, so chunk k is read out and copied back once chunks
+    // k - 1, k and k + 1 are stepped (the two end chunks after the last).
     const bool diag = fused && moments_h && nsteps > 0;
     const bool first_split = chunked && diag;
+    const bool second_split = first_split && nsteps >= 3 && nch >= 3;
     const bool last_split = chunked && diag && nsteps > 1 && (rho_out || u_out);
     if (fused && moments_h && !c->copy_stream) {
         cudaStream_t cs = nullptr;
@@ -830,17 +833,21 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
         return cuda_fail(e, "clbm_run_host: clear accumulators");
     const double add0 = (double)c->n;
     auto slot = [c](int64_t t) { return c->d_mom + 4 * (t % kMomRing); };
-    // The fused step t (or one plane range of it) from the current buffer: the
-    // exact sums of the state it pulls (state t) go to slot set t % 2. The first
-    // launch of step t > 0 first drains set (t - 1) % 2 into the totals of state t - 1.
-    auto diag_step = [&](int64_t t, const Launch &Ls, bool first) {
+    // The fused step t of the job (or one plane range of it): it pulls buffer
+    // cur0 ^ (t & 1), which holds state t, and the exact sums of that state go
+    // to slot set t % 2. With drain_prev it first drains set (t - 1) % 2 into
+    // the totals of state t - 1 (the first launch of a step whose predecessor
+    // is complete).
+    const int cur0 = c->cur;
+    auto diag_step = [&](int64_t t, const Launch &Ls, bool drain_prev) {
+        const int cur = cur0 ^ (int)(t & 1);
         DiagSums d;
         d.acc = c->d_acc + (t & 1) * 4 * kDiagSlots;
-        d.acc_prev = t > 0 && first ? c->d_acc + ((t - 1) & 1) * 4 * kDiagSlots : nullptr;
-        d.out_prev = t > 0 && first ? slot(t - 1) : nullptr;
+        d.acc_prev = t > 0 && drain_prev ? c->d_acc + ((t - 1) & 1) * 4 * kDiagSlots : nullptr;
+        d.out_prev = t > 0 && drain_prev ? slot(t - 1) : nullptr;
         d.add0 = add0;
-        return launch_step_diag(c->p.storage, Ls, c->buf[c->cur], c->buf[c->cur ^ 1], c->rates, force_now(c),
-                                c->d_flag, d, step_key(c->steps_done));
+        return launch_step_diag(c->p.storage, Ls, c->buf[cur], c->buf[cur ^ 1], c->rates, force_at(c, t), c->d_flag,
+                                d, step_key(t));
     };
     // chunk k's planes, with the state map of the current step count
     auto plane_chunk = [&](int k) {
@@ -895,6 +902,13 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
                 e = launch_init_eq(c->p.storage, Lk, c->buf[c->cur], rho_h ? d_rho : nullptr, u_h ? d_u : nullptr,
                                    c->n, F0);
             if (e == cudaSuccess && first_split) e = diag_step(0, Lk, false);
+            if (e == cudaSuccess && second_split && k >= 2) e = diag_step(1, plane_chunk(k - 1), false);
+        }
+        if (e == cudaSuccess && second_split) {
+            // step 0 is complete: its totals, then step 1 of the two end chunks
+            e = launch_drain4(c->d_acc, slot(0), add0, c->stream);
+            if (e == cudaSuccess) e = diag_step(1, plane_chunk(0), false);
+            if (e == cudaSuccess) e = diag_step(1, plane_chunk(nch - 1), false);
         }
         if (e != cudaSuccess) return cuda_fail(e, "clbm_run_host: chunked copy and initialisation");
     } else {
@@ -933,7 +947,7 @@ int clbm_run_host(clbm_ctx *c, const float *rho_h, const float *u_h, int64_t nst
                 }
                 for (int k = 0; k < nch && e == cudaSuccess; ++k)
                     if (nch < 3 || k == 0 || k == nch - 1) e = read_out(k, c->buf[c->cur ^ 1], F1);
-            } else if (t > 0 || !first_split) {  // step 0 of a split first step ran as the input landed
+            } else if (!(t == 0 && first_split) && !(t == 1 && second_split)) {  // split steps ran as the input landed
                 e = diag_step(t, L, true);
             }
             if (e == cudaSuccess && t == nsteps - 1)  // the last step's set

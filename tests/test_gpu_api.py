@@ -136,11 +136,11 @@ def test_run_host_job_matches_device_path():
         assert torch.equal(m5, mom[: 4 * (n + 1)])
 
 
-@pytest.mark.parametrize("nz,walls,steps", [(1, 0, 2), (2, 0, 1), (3, 0, 2), (9, 0, 5), (40, 0, 2), (17, 4, 3),
-                                             (8, 0, 1)])
+@pytest.mark.parametrize("nz,walls,steps", [(1, 0, 2), (2, 0, 1), (3, 0, 2), (3, 0, 4), (9, 0, 5), (40, 0, 2),
+                                             (17, 4, 3), (8, 0, 1), (26, 0, 7)])
 def test_run_host_split_steps(nz, walls, steps):
-    """With per-step sums, a host job runs its first step plane chunk by plane
-    chunk as the input lands, and its last step chunk by chunk, each chunk read
+    """With per-step sums, a host job runs its first two steps plane chunk by
+    plane chunk as the input lands, and its last step chunk by chunk, each chunk read
     out as soon as it and its two neighbouring chunks are stepped. Periodic z
     makes the two end chunks neighbours; 1-3 planes give 1-3 chunks; a decaying
     z-profile force makes the read-out take the force of the final step.
